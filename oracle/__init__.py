@@ -1,0 +1,110 @@
+"""FP64 CPU oracle of Fast Local Regression (arXiv 2410.11625).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  The GPU library never imports it, and it
+never imports the GPU library.
+
+The arithmetic lives in ``flr_oracle.c`` (plain C, double precision; every function
+cites the passage of the paper it follows).  This module only marshals numpy arrays
+into it through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBPATH = os.path.join(_LIBDIR, "liboracle.so")
+_SOURCES = ["flr_oracle.c"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (OpenMP, no fast-math) and return its path."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(_LIBPATH):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(_LIBPATH) >= newest:
+            return _LIBPATH
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _LIBPATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-ffp-contract=off", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIBPATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.flr_oracle_forward.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp,
+            ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+        lib.flr_oracle_forward.restype = ctypes.c_int
+        lib.flr_oracle_threads.argtypes = []
+        lib.flr_oracle_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _fptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _as_f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use."""
+    return int(_load().flr_oracle_threads())
+
+
+def flr_forward(guide, radiance, radius, eps, coef_radius=0, map_guide=None,
+                return_coef=False):
+    """FLR forward pass in FP64 (Sec. 3.1-3.2 and the Appendix of the paper).
+
+    guide: [Q, H, W]; radiance: [3, H, W]; map_guide: [Q, H, W] or None (= guide).
+    Inputs are rounded to float32 first (the precision the GPU path reads).
+    Returns out [3, H, W] float64, and with ``return_coef`` also the per-pixel model
+    A_k before averaging as [(Q+1), 3, H, W] (row 0 is the bias).
+    """
+    rad = _as_f32(radiance)
+    if rad.ndim != 3 or rad.shape[0] != 3:
+        raise ValueError("radiance must be [3, H, W]")
+    _, H, W = rad.shape
+    g = _as_f32(guide)
+    if g is None:
+        g = np.zeros((0, H, W), np.float32)
+    q = g.shape[0]
+    if g.shape[1:] != (H, W):
+        raise ValueError("guide must be [Q, H, W] with the radiance's H, W")
+    mg = _as_f32(map_guide)
+    if mg is not None and mg.shape != g.shape:
+        raise ValueError("map_guide must match guide")
+    out = np.empty((3, H, W), np.float64)
+    coef = np.empty((q + 1, 3, H, W), np.float64) if return_coef else None
+    st = _load().flr_oracle_forward(q, H, W, _fptr(g) if q else None, _fptr(mg), _fptr(rad),
+                                    int(radius), int(coef_radius), float(eps),
+                                    _dptr(out), _dptr(coef))
+    if st != 0:
+        raise OracleError(f"flr_oracle_forward failed with status {st}")
+    return (out, coef) if return_coef else out

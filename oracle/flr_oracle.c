@@ -1,0 +1,263 @@
+/*
+ * flr_oracle.c -- plain FP64 CPU oracle of Fast Local Regression (FLR),
+ * arXiv 2410.11625 ("Fast Local Neural Regression for Low-Cost, Path Traced
+ * Lambertian Global Illumination").
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load this library.  The GPU library shares no code, header,
+ * table or helper with it, and neither side includes or links the other.
+ *
+ * Everything is double precision, written for a reader who checks it against the
+ * paper, with no blocking, fusion or reordering beyond what the paper states.
+ *
+ * Data layout: every image is planar, channel-major, row-major: plane c, row y,
+ * column x lives at [(c * H + y) * W + x].  Inputs are float32 (what the GPU path
+ * reads); all arithmetic is done after widening to double.
+ *
+ * Definition followed (Sec. 3.1, Eqs. matX/matY/argmin/closed_form; Sec. 3.2 box
+ * window; Appendix moment decomposition):
+ *   - X_k is the N x (Q+1) matrix of the guides inside the square window T_k of
+ *     radius r around pixel k, first column all ones (Eq. matX); Y_k the N x 3
+ *     radiance matrix (Eq. matY).  Windows are clipped to the image, so N = n_k
+ *     counts in-image pixels only.
+ *   - Box-filtering the per-pixel outer products x x^T and x y^T (x with its
+ *     leading 1) yields exactly X_k^T X_k and X_k^T Y_k (Sec. 3.2).
+ *   - Appendix: X^T X = [[n, u_X], [u_X^T, S]], mu_X = u_X / n,
+ *     W = S/n - mu_X^T mu_X; the top row of X^T Y is n mu_Y.
+ *   - Regulariser (the reading this build takes of "ridge eps"): the Appendix's
+ *     W-hat with its multiplicative term set to zero, i.e. M = W + eps I, and no
+ *     second additive term on the normalised matrix.  Without that second term the
+ *     Appendix's correlation normalisation cancels out, and the model is the
+ *     centred ridge  a_k = M^{-1} D,  D = X^T Y / n - mu_X^T mu_Y (guide rows),
+ *     b_k = mu_Y - a_k^T mu_X   (the bias is not penalised).
+ *   - Optional coefficient averaging over a clipped window of radius rc (rc = 0
+ *     switches it off, which is what Sec. 3.2 does), then the model is applied
+ *     to the centre pixel's guide vector z_i (Sec. 3.1, I_k = x_k A_k).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_MAX_Q 16
+
+/* Clipped window [lo, hi] of radius rad around i inside [0, n). */
+static void clip_range(int i, int rad, int n, int *lo, int *hi)
+{
+    *lo = i - rad < 0 ? 0 : i - rad;
+    *hi = i + rad > n - 1 ? n - 1 : i + rad;
+}
+
+/*
+ * Sum of one plane over the clipped square window of radius rad, done as a row
+ * pass then a column pass (the box is separable).  Every output is a direct sum of
+ * at most 2*rad+1 terms: no running sums, no prefix differences.
+ */
+static void box_sum_plane(const double *src, double *dst, double *tmp, int H, int W, int rad)
+{
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int lo, hi;
+            clip_range(x, rad, W, &lo, &hi);
+            double s = 0.0;
+            for (int xx = lo; xx <= hi; ++xx) s += src[(size_t)y * W + xx];
+            tmp[(size_t)y * W + x] = s;
+        }
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y) {
+        int lo, hi;
+        clip_range(y, rad, H, &lo, &hi);
+        for (int x = 0; x < W; ++x) {
+            double s = 0.0;
+            for (int yy = lo; yy <= hi; ++yy) s += tmp[(size_t)yy * W + x];
+            dst[(size_t)y * W + x] = s;
+        }
+    }
+}
+
+/* Number of in-image pixels of the clipped window of radius rad at (y, x). */
+static double window_count(int y, int x, int H, int W, int rad)
+{
+    int y0, y1, x0, x1;
+    clip_range(y, rad, H, &y0, &y1);
+    clip_range(x, rad, W, &x0, &x1);
+    return (double)(y1 - y0 + 1) * (double)(x1 - x0 + 1);
+}
+
+/*
+ * Cholesky factorisation M = L L^T of a q x q symmetric matrix (row-major, lower
+ * triangle read), then solve M a = d for nrhs right-hand sides stored as d[i*nrhs+c].
+ * Returns 0, or -1 if a pivot is not positive (M not positive definite).
+ */
+static int cholesky_solve(int q, const double *M, const double *d, int nrhs, double *a)
+{
+    double L[ORACLE_MAX_Q * ORACLE_MAX_Q];
+    double z[ORACLE_MAX_Q * 3];
+    for (int j = 0; j < q; ++j) {
+        double s = M[j * q + j];
+        for (int k = 0; k < j; ++k) s -= L[j * q + k] * L[j * q + k];
+        if (!(s > 0.0)) return -1;
+        L[j * q + j] = sqrt(s);
+        for (int i = j + 1; i < q; ++i) {
+            double t = M[i * q + j];
+            for (int k = 0; k < j; ++k) t -= L[i * q + k] * L[j * q + k];
+            L[i * q + j] = t / L[j * q + j];
+        }
+    }
+    for (int c = 0; c < nrhs; ++c) {
+        for (int i = 0; i < q; ++i) { /* L z = d */
+            double t = d[i * nrhs + c];
+            for (int k = 0; k < i; ++k) t -= L[i * q + k] * z[k * nrhs + c];
+            z[i * nrhs + c] = t / L[i * q + i];
+        }
+        for (int i = q - 1; i >= 0; --i) { /* L^T a = z */
+            double t = z[i * nrhs + c];
+            for (int k = i + 1; k < q; ++k) t -= L[k * q + i] * a[k * nrhs + c];
+            a[i * nrhs + c] = t / L[i * q + i];
+        }
+    }
+    return 0;
+}
+
+/* Index of the pair (i <= j) of the (q+1)x(q+1) upper triangle, row by row. */
+static int tri_index(int q1, int i, int j)
+{
+    return i * q1 - (i * (i - 1)) / 2 + (j - i);
+}
+
+/*
+ * FLR forward pass (Sec. 3.1-3.2, Appendix; see file header).
+ *
+ *   q          number of guide channels Q (0..16); the ones column is implicit
+ *   guide      [q][H][W] float32, the guides X the model is fitted on
+ *   map_guide  [q][H][W] float32 the model is applied to, or NULL for guide
+ *   radiance   [3][H][W] float32, the noisy signal Y
+ *   r          window radius (>= 0); the window is (2r+1)^2 clipped to the image
+ *   rc         coefficient-averaging radius (>= 0; 0 = none)
+ *   eps        ridge regulariser added to the centred covariance (>= 0)
+ *   out        [3][H][W] double, the result I
+ *   coef       NULL, or [(q+1)*3][H][W] double: per-pixel A_k before averaging,
+ *              plane (i*3 + c) holds row i, column c of A_k; row 0 is the bias b_k
+ *
+ * Returns 0; -1 for bad arguments; -2 for out of memory; -3 when a window's
+ * regularised covariance is not positive definite (only possible with eps = 0).
+ */
+int flr_oracle_forward(int q, int H, int W, const float *guide, const float *map_guide,
+                       const float *radiance, int r, int rc, double eps, double *out,
+                       double *coef)
+{
+    if (q < 0 || q > ORACLE_MAX_Q || H <= 0 || W <= 0 || r < 0 || rc < 0 || !(eps >= 0.0))
+        return -1;
+    if ((q > 0 && !guide) || !radiance || !out) return -1;
+    if (!map_guide) map_guide = guide;
+
+    const int q1 = q + 1;
+    const int nxx = q1 * (q1 + 1) / 2; /* upper triangle of X^T X, ones column included */
+    const int nxy = q1 * 3;            /* X^T Y */
+    const int ncoef = q1 * 3;
+    const size_t P = (size_t)H * W;
+
+    double *xx = malloc(sizeof(double) * P * nxx);
+    double *xy = malloc(sizeof(double) * P * nxy);
+    double *cf = malloc(sizeof(double) * P * ncoef);
+    double *plane = malloc(sizeof(double) * P);
+    double *tmp = malloc(sizeof(double) * P);
+    int status = 0;
+    if (!xx || !xy || !cf || !plane || !tmp) { status = -2; goto done; }
+
+    /* Step 1 (Sec. 3.2): per-pixel outer products x x^T and x y^T, x = (1, X_1..X_Q). */
+#pragma omp parallel for schedule(static)
+    for (size_t p = 0; p < P; ++p) {
+        double x[ORACLE_MAX_Q + 1], y[3];
+        x[0] = 1.0;
+        for (int i = 0; i < q; ++i) x[i + 1] = (double)guide[(size_t)i * P + p];
+        for (int c = 0; c < 3; ++c) y[c] = (double)radiance[(size_t)c * P + p];
+        for (int i = 0; i < q1; ++i)
+            for (int j = i; j < q1; ++j) xx[(size_t)tri_index(q1, i, j) * P + p] = x[i] * x[j];
+        for (int i = 0; i < q1; ++i)
+            for (int c = 0; c < 3; ++c) xy[(size_t)(i * 3 + c) * P + p] = x[i] * y[c];
+    }
+
+    /* Step 2 (Sec. 3.2): box-filter every moment plane -> X_k^T X_k and X_k^T Y_k. */
+    for (int m = 0; m < nxx; ++m) {
+        memcpy(plane, xx + (size_t)m * P, sizeof(double) * P);
+        box_sum_plane(plane, xx + (size_t)m * P, tmp, H, W, r);
+    }
+    for (int m = 0; m < nxy; ++m) {
+        memcpy(plane, xy + (size_t)m * P, sizeof(double) * P);
+        box_sum_plane(plane, xy + (size_t)m * P, tmp, H, W, r);
+    }
+
+    /* Step 3 (Appendix + closed form): per-pixel centred, regularised solve.  A pixel
+     * whose matrix is not positive definite sets `failed`; the pass then reports -3. */
+    int failed = 0;
+#pragma omp parallel for schedule(static) reduction(| : failed)
+    for (size_t p = 0; p < P; ++p) {
+        const double n = xx[(size_t)tri_index(q1, 0, 0) * P + p];
+        double mu_x[ORACLE_MAX_Q], mu_y[3];
+        double M[ORACLE_MAX_Q * ORACLE_MAX_Q], D[ORACLE_MAX_Q * 3], a[ORACLE_MAX_Q * 3];
+        for (int i = 0; i < q; ++i) mu_x[i] = xx[(size_t)tri_index(q1, 0, i + 1) * P + p] / n;
+        for (int c = 0; c < 3; ++c) mu_y[c] = xy[(size_t)(0 * 3 + c) * P + p] / n;
+        for (int i = 0; i < q; ++i)
+            for (int j = 0; j < q; ++j) {
+                int lo = i < j ? i : j, hi = i < j ? j : i;
+                double S = xx[(size_t)tri_index(q1, lo + 1, hi + 1) * P + p];
+                M[i * q + j] = S / n - mu_x[i] * mu_x[j] + (i == j ? eps : 0.0);
+            }
+        for (int i = 0; i < q; ++i)
+            for (int c = 0; c < 3; ++c)
+                D[i * 3 + c] = xy[(size_t)((i + 1) * 3 + c) * P + p] / n - mu_x[i] * mu_y[c];
+        if (q > 0 && cholesky_solve(q, M, D, 3, a) != 0) { failed = 1; continue; }
+        for (int c = 0; c < 3; ++c) {
+            double b = mu_y[c];
+            for (int i = 0; i < q; ++i) b -= a[i * 3 + c] * mu_x[i];
+            cf[(size_t)(0 * 3 + c) * P + p] = b;
+            for (int i = 0; i < q; ++i) cf[(size_t)((i + 1) * 3 + c) * P + p] = a[i * 3 + c];
+        }
+    }
+    if (failed) { status = -3; goto done; }
+    if (coef) memcpy(coef, cf, sizeof(double) * P * ncoef);
+
+    /* Step 4: mean of the coefficients over the clipped radius-rc window. */
+    if (rc > 0) {
+        for (int m = 0; m < ncoef; ++m) {
+            memcpy(plane, cf + (size_t)m * P, sizeof(double) * P);
+            box_sum_plane(plane, cf + (size_t)m * P, tmp, H, W, rc);
+#pragma omp parallel for schedule(static)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x)
+                    cf[(size_t)m * P + (size_t)y * W + x] /= window_count(y, x, H, W, rc);
+        }
+    }
+
+    /* Step 5 (Sec. 3.1): apply the model to the centre pixel, I = (1, z) A. */
+#pragma omp parallel for schedule(static)
+    for (size_t p = 0; p < P; ++p)
+        for (int c = 0; c < 3; ++c) {
+            double v = cf[(size_t)(0 * 3 + c) * P + p];
+            for (int i = 0; i < q; ++i)
+                v += cf[(size_t)((i + 1) * 3 + c) * P + p] * (double)map_guide[(size_t)i * P + p];
+            out[(size_t)c * P + p] = v;
+        }
+
+done:
+    free(xx);
+    free(xy);
+    free(cf);
+    free(plane);
+    free(tmp);
+    return status;
+}
+
+/* Number of threads the parallel loops above use (1 without OpenMP). */
+int flr_oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,103 @@
+"""Seeded synthetic inputs for FLR: procedural Lambertian rooms and random frames.
+
+This module is an input generator only and holds none of FLR's arithmetic.  Both the
+FP64 oracle (in the tests) and the GPU library (in the tests and the benchmark) consume
+what it makes, which is why it lives apart from both.
+
+``render(seed, H, W)`` gives the frame of the paper's workload shape (Sec. 4.1): eight
+noise-free guides (albedo RGB, world normal xyz, normalised depth, ambient occlusion)
+and the albedo-demodulated one-sample-per-pixel indirect radiance, traced by
+``pathtracer.c``.  ``random_frame`` gives i.i.d. uniform frames and the adversarial
+variants the parity tests use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBPATH = os.path.join(_LIBDIR, "libsynth.so")
+_SOURCES = ["pathtracer.c"]
+
+GUIDE_CHANNELS = ("albedo_r", "albedo_g", "albedo_b", "normal_x", "normal_y", "normal_z",
+                  "depth", "ao")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``libsynth.so`` with gcc (OpenMP) and return its path."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(_LIBPATH):
+        if os.path.getmtime(_LIBPATH) >= max(os.path.getmtime(s) for s in srcs):
+            return _LIBPATH
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _LIBPATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp]
+                   + srcs + ["-lm"], check=True)
+    os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIBPATH)
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.synth_render.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, fp, fp, fp,
+                                     ctypes.c_int]
+        lib.synth_render.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def render(seed: int, H: int, W: int, ref_spp: int = 0):
+    """Render the procedural room of ``seed`` at H x W.
+
+    Returns ``(guide [8,H,W], radiance [3,H,W])`` as float32, plus the ``ref_spp``-sample
+    reference [3,H,W] as a third element when ``ref_spp > 0``.
+    """
+    guide = np.empty((8, H, W), np.float32)
+    rad = np.empty((3, H, W), np.float32)
+    ref = np.empty((3, H, W), np.float32) if ref_spp > 0 else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    st = _load().synth_render(ctypes.c_uint64(seed), H, W, guide.ctypes.data_as(fp),
+                              rad.ctypes.data_as(fp),
+                              None if ref is None else ref.ctypes.data_as(fp), int(ref_spp))
+    if st != 0:
+        raise ValueError("synth_render: bad arguments")
+    return (guide, rad, ref) if ref is not None else (guide, rad)
+
+
+def random_frame(seed: int, H: int, W: int, q: int = 8, kind: str = "uniform"):
+    """Seeded random (guide [q,H,W], radiance [3,H,W]) float32 frames.
+
+    kinds:
+      uniform       i.i.d. U[0, 1] guides and radiance
+      signed        guides U[-1, 1], radiance U[0, 1]
+      const_guide   guide channel 1 constant over the frame (rank-deficient windows)
+      dup_guide     guide channel 2 duplicates channel 0 (collinear guides)
+      depth_offset  uniform guides with +100 added to the last guide channel
+      heavy_tail    uniform guides; radiance with Pareto-like fireflies
+    """
+    rng = np.random.default_rng(seed)
+    lo = -1.0 if kind == "signed" else 0.0
+    g = rng.uniform(lo, 1.0, size=(q, H, W)).astype(np.float32)
+    y = rng.uniform(0.0, 1.0, size=(3, H, W)).astype(np.float32)
+    if kind == "const_guide" and q > 1:
+        g[1] = np.float32(0.37)
+    elif kind == "dup_guide" and q > 2:
+        g[2] = g[0]
+    elif kind == "depth_offset":
+        g[q - 1] += np.float32(100.0)
+    elif kind == "heavy_tail":
+        u = rng.uniform(0.0, 1.0, size=(3, H, W))
+        y = (0.2 * (1.0 - u) ** -1.5).astype(np.float32)
+    elif kind not in ("uniform", "signed", "const_guide", "dup_guide"):
+        raise ValueError(f"unknown kind {kind!r}")
+    return g, y
