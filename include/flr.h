@@ -1,0 +1,148 @@
+/*
+ * flr.h -- C ABI of the GB300 (sm_103a) Fast Local Regression library, libflr.so.
+ *
+ * Fast Local Regression (FLR) is the denoiser of arXiv 2410.11625, "Fast Local Neural
+ * Regression for Low-Cost, Path Traced Lambertian Global Illumination".  For every pixel
+ * k it fits, over the square window T_k of radius r, an affine model from the Q guide
+ * channels (plus an implicit column of ones, Eq. matX) to the noisy RGB radiance
+ * (Eq. matY) in the least-squares sense (Eqs. argmin, closed_form), with the per-window
+ * normal equations obtained exactly by box-filtering the outer products x x^T and x y^T
+ * (Sec. 3.2).  The model is regularised as a centred ridge: the Appendix's decomposition
+ * X^T X = [[n, u_X], [u_X^T, S]], W = S/n - mu_X^T mu_X, with eps added to the diagonal
+ * of W (the Appendix's additive term; its multiplicative term is zero) and the bias left
+ * unpenalised.  Optionally the per-pixel models are averaged over a second window of
+ * radius rc before being applied to the centre pixel's guide vector (Sec. 3.1,
+ * I_k = x_k A_k).  Windows are clipped to the image.
+ *
+ * Conventions for every entry point:
+ *   - Images are planar float32, channel-major then row-major: element (c, y, x) of a
+ *     [C][H][W] image is at index (c * H + y) * W + x.  Device pointers must be 16-byte
+ *     aligned; images must not overlap the output.
+ *   - The caller owns every image.  A handle owns only its workspace (flag list,
+ *     coefficient scratch, host-path staging), allocated by flr_create/flr_reserve or
+ *     grown on first use.
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream) unless stated otherwise.  One handle must not be
+ *     used on two streams at once.
+ *   - Every function returns FLR_OK (0) or a negative flr_status; no exception or abort
+ *     crosses the ABI.  flr_status_string() names a status.
+ */
+#ifndef FLR_H
+#define FLR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum flr_status {
+    FLR_OK = 0,
+    FLR_ERR_ARG = -1,         /* a null pointer, a non-positive size, a bad parameter */
+    FLR_ERR_ALIGN = -2,       /* a device pointer is not 16-byte aligned */
+    FLR_ERR_CUDA = -3,        /* a CUDA runtime call failed (see flr_last_cuda_error) */
+    FLR_ERR_UNSUPPORTED = -4, /* q or a radius outside what this build supports */
+    FLR_ERR_NOMEM = -5        /* a workspace allocation failed */
+} flr_status;
+
+/* Largest guide count and window radii the kernels are built for. */
+#define FLR_MAX_Q 8
+#define FLR_MAX_RADIUS 16
+#define FLR_MAX_COEF_RADIUS 16
+
+/* flr_params.flags bits */
+#define FLR_FLAG_TIMING 1u /* record CUDA events around every kernel (flr_get_kernel_times) */
+
+typedef struct flr_params {
+    int q;             /* number of guide channels Q, 1..FLR_MAX_Q (bias column implicit) */
+    int radius;        /* window radius r, 0..FLR_MAX_RADIUS; window (2r+1)^2, clipped */
+    int coef_radius;   /* coefficient-averaging radius rc, 0..FLR_MAX_COEF_RADIUS; 0 = off */
+    float eps;         /* ridge term added to the centred covariance, >= 0 */
+    float pivot_ratio; /* FP64 re-solve threshold tau: a pixel whose Cholesky pivot d_j
+                          satisfies d_j <= tau * M_jj is re-solved in FP64 on the GPU.
+                          <= 0 disables the re-solve. */
+    unsigned flags;    /* FLR_FLAG_* bits; other bits must be 0 */
+} flr_params;
+
+typedef struct flr_stats {
+    unsigned long long flagged;  /* pixels of the last call whose pivot fell below tau */
+    unsigned long long resolved; /* of those, pixels re-solved in FP64 (the rest overflowed
+                                    the flag list and kept their FP32 solution) */
+} flr_stats;
+
+typedef struct flr_handle flr_handle;
+
+/*
+ * Create a handle for the given parameters (validated here).  Allocates the small
+ * device counters; image-sized workspace is allocated by flr_reserve or on first use.
+ * *out receives the handle.  Errors: FLR_ERR_ARG, FLR_ERR_UNSUPPORTED, FLR_ERR_CUDA.
+ */
+int flr_create(const flr_params *params, flr_handle **out);
+
+/* Free a handle and its workspace (synchronises the device first).  NULL is a no-op. */
+int flr_destroy(flr_handle *h);
+
+/*
+ * Allocate the workspace for frames of up to H x W pixels now, so that later calls of
+ * that size allocate nothing (needed before capturing a call in a CUDA graph).
+ * Synchronous.  Errors: FLR_ERR_ARG, FLR_ERR_NOMEM.
+ */
+int flr_reserve(flr_handle *h, int H, int W);
+
+/*
+ * FLR forward pass on device images (Sec. 3.1-3.2, Appendix; see the file header).
+ *   guide      [q][H][W]  guides X the per-pixel models are fitted on
+ *   map_guide  [q][H][W]  guides z the models are applied to, or NULL to use `guide`
+ *                         (the model/map split of Sec. 3.3)
+ *   radiance   [3][H][W]  noisy demodulated radiance Y
+ *   out        [3][H][W]  result I; must not overlap any input
+ * The result of every pixel whose Cholesky pivot ratio falls below params.pivot_ratio
+ * is replaced by an FP64 re-solve of its window on the GPU; flr_get_stats reports how
+ * many.  Grows the workspace if the frame is larger than reserved (a synchronous
+ * allocation).  Errors: FLR_ERR_ARG, FLR_ERR_ALIGN, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_denoise(flr_handle *h, const float *guide, const float *map_guide,
+                const float *radiance, float *out, int H, int W, void *stream);
+
+/*
+ * The same pass on HOST images: copies guide, map_guide (if not NULL) and radiance to
+ * handle-owned device staging, runs flr_denoise, copies the result back to `out`, and
+ * waits for the stream.  Page-locked host memory gives asynchronous copies; pageable
+ * memory works but is slower.  Errors as flr_denoise.
+ */
+int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
+                     const float *radiance, float *out, int H, int W, void *stream);
+
+/*
+ * Statistics of the last flr_denoise on this handle.  Waits for that call's stream.
+ * Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
+ */
+int flr_get_stats(flr_handle *h, flr_stats *out);
+
+/* Per-kernel launch counts and (with FLR_FLAG_TIMING) summed CUDA-event durations. */
+typedef struct flr_kernel_times {
+    double fwd_ms, fp64_ms, apply_ms;           /* summed durations; 0 without timing */
+    unsigned long long fwd_n, fp64_n, apply_n;  /* kernels launched */
+} flr_kernel_times;
+
+/*
+ * Launch counts and, when the handle was created with FLR_FLAG_TIMING, the summed
+ * durations of the forward, FP64 re-solve and apply kernels over the calls since the
+ * last reset, each measured by CUDA events recorded on the call's stream directly before
+ * and after the kernel.  Waits for the last timed call.  reset != 0 zeroes the sums
+ * afterwards.  Not a paper operation: instrumentation for roofline measurement.
+ * Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
+ */
+int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset);
+
+/* Human-readable name of a status code (static storage). */
+const char *flr_status_string(int status);
+
+/* Message of the last CUDA error seen by this library on the calling thread. */
+const char *flr_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLR_H */

@@ -1,0 +1,333 @@
+// flr_capi.cu -- the extern "C" boundary of libflr.so (declared in include/flr.h):
+// argument validation, handle and workspace management, and the launch sequence
+//   forward kernel -> FP64 re-solve of flagged pixels -> coefficient averaging + apply.
+// No exception and no abort crosses the ABI: every failure is a negative flr_status.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "flr.h"
+#include "flr_internal.cuh"
+
+namespace {
+
+thread_local char g_cuda_error[256] = "no error";
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    std::snprintf(g_cuda_error, sizeof(g_cuda_error), "%s: %s", what, cudaGetErrorString(e));
+    return FLR_ERR_CUDA;
+}
+
+#define FLR_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+struct flr_handle {
+    flr_params p;
+    int device = 0;
+    int n_sm = 0;
+    unsigned long long *d_count = nullptr;  // flagged-pixel counter
+    float *d_shift = nullptr;               // frame reference shift, Q+3 floats
+    int *d_flags = nullptr;                 // flag list
+    int flag_cap = 0;
+    float *d_coef = nullptr;  // (Q+1)*3 coefficient planes (coef_radius > 0)
+    size_t coef_px = 0;
+    float *stage = nullptr;  // host-path staging: guide, map guide, radiance, out
+    size_t stage_px = 0;
+    size_t fwd_smem = 0;
+    cudaStream_t last_stream = nullptr;
+    // instrumentation: launch counts, and event quadruples per call with FLR_FLAG_TIMING
+    unsigned long long n_fwd = 0, n_fp64 = 0, n_apply = 0;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+};
+
+namespace {
+
+int grow(flr_handle *h, int H, int W)
+{
+    const size_t px = (size_t)H * W;
+    if ((size_t)h->flag_cap < px && h->p.pivot_ratio > 0.f) {
+        if (h->d_flags) cudaFree(h->d_flags);
+        h->d_flags = nullptr;
+        h->flag_cap = 0;
+        if (px > (size_t)0x7fffffff) return FLR_ERR_ARG;
+        if (cudaMalloc(&h->d_flags, px * sizeof(int)) != cudaSuccess) return FLR_ERR_NOMEM;
+        h->flag_cap = (int)px;
+    }
+    if (h->p.coef_radius > 0 && h->coef_px < px) {
+        if (h->d_coef) cudaFree(h->d_coef);
+        h->d_coef = nullptr;
+        h->coef_px = 0;
+        if (cudaMalloc(&h->d_coef, px * (size_t)(h->p.q + 1) * 3 * sizeof(float)) != cudaSuccess)
+            return FLR_ERR_NOMEM;
+        h->coef_px = px;
+    }
+    return FLR_OK;
+}
+
+// Rows per segment of the forward kernel: minimise (waves of CTAs) x (rows walked,
+// including the 2r warm-up rows of every segment).
+int choose_segment_rows(int H, int W, int r, int n_sm)
+{
+    const int strips = (W + flr::kTW - 1) / flr::kTW;
+    int best_th = H, best_cost = -1;
+    for (int segs = 1; segs <= 256; ++segs) {
+        int th = (H + segs - 1) / segs;
+        th = (th + flr::kB - 1) / flr::kB * flr::kB;
+        const int real_segs = (H + th - 1) / th;
+        const long long waves = ((long long)strips * real_segs + n_sm - 1) / n_sm;
+        const long long cost = waves * (th + 2 * r);
+        if (best_cost < 0 || cost < best_cost) { best_cost = (int)cost; best_th = th; }
+        if (th <= flr::kB) break;
+    }
+    return best_th;
+}
+
+int validate_params(const flr_params *p)
+{
+    if (!p) return FLR_ERR_ARG;
+    if ((p->flags & ~FLR_FLAG_TIMING) != 0u || !(p->eps >= 0.f) || p->radius < 0 || p->coef_radius < 0) return FLR_ERR_ARG;
+    if (p->pivot_ratio != p->pivot_ratio) return FLR_ERR_ARG;
+    if (p->q < 1 || p->q > FLR_MAX_Q || p->radius > FLR_MAX_RADIUS ||
+        p->coef_radius > FLR_MAX_COEF_RADIUS)
+        return FLR_ERR_UNSUPPORTED;
+    return FLR_OK;
+}
+
+// With FLR_FLAG_TIMING: the next event of the handle's pool, recorded on stream s.
+cudaError_t mark(flr_handle *h, cudaStream_t s)
+{
+    if (!(h->p.flags & FLR_FLAG_TIMING)) return cudaSuccess;
+    if (h->events_used == h->events.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        h->events.push_back(ev);
+    }
+    return cudaEventRecord(h->events[h->events_used++], s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *flr_status_string(int status)
+{
+    switch (status) {
+    case FLR_OK: return "FLR_OK";
+    case FLR_ERR_ARG: return "FLR_ERR_ARG: invalid argument";
+    case FLR_ERR_ALIGN: return "FLR_ERR_ALIGN: device pointer not 16-byte aligned";
+    case FLR_ERR_CUDA: return "FLR_ERR_CUDA: CUDA runtime error";
+    case FLR_ERR_UNSUPPORTED: return "FLR_ERR_UNSUPPORTED: parameter outside the built range";
+    case FLR_ERR_NOMEM: return "FLR_ERR_NOMEM: workspace allocation failed";
+    default: return "unknown flr status";
+    }
+}
+
+const char *flr_last_cuda_error(void) { return g_cuda_error; }
+
+int flr_create(const flr_params *params, flr_handle **out)
+{
+    if (!out) return FLR_ERR_ARG;
+    *out = nullptr;
+    int st = validate_params(params);
+    if (st != FLR_OK) return st;
+    flr_handle *h = new (std::nothrow) flr_handle();
+    if (!h) return FLR_ERR_NOMEM;
+    h->p = *params;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_shift, sizeof(float) * (FLR_MAX_Q + 3));
+    if (e == cudaSuccess) e = cudaMemset(h->d_count, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        h->fwd_smem = flr::fwd_smem_bytes(h->p.q, h->p.radius);
+        e = flr::fwd_prepare(h->p.q, h->fwd_smem);
+    }
+    if (e != cudaSuccess) {
+        cuda_fail(e, "flr_create");
+        flr_destroy(h);
+        return FLR_ERR_CUDA;
+    }
+    *out = h;
+    return FLR_OK;
+}
+
+int flr_destroy(flr_handle *h)
+{
+    if (!h) return FLR_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_count);
+    cudaFree(h->d_shift);
+    cudaFree(h->d_flags);
+    cudaFree(h->d_coef);
+    cudaFree(h->stage);
+    for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+    delete h;
+    return FLR_OK;
+}
+
+int flr_reserve(flr_handle *h, int H, int W)
+{
+    if (!h || H <= 0 || W <= 0) return FLR_ERR_ARG;
+    return grow(h, H, W);
+}
+
+int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const float *radiance,
+                float *out, int H, int W, void *stream)
+{
+    if (!h || !guide || !radiance || !out || H <= 0 || W <= 0) return FLR_ERR_ARG;
+    if ((long long)H * W > 0x7fffffffLL) return FLR_ERR_ARG;
+    if (!aligned16(guide) || !aligned16(radiance) || !aligned16(out) ||
+        (map_guide && !aligned16(map_guide)))
+        return FLR_ERR_ALIGN;
+    const int q = h->p.q;
+    const size_t px = (size_t)H * W;
+    // the output must not overlap any input
+    auto overlaps = [&](const float *p, size_t n) {
+        return p && (const char *)out < (const char *)(p + n) && (const char *)p < (const char *)(out + 3 * px);
+    };
+    if (overlaps(guide, q * px) || overlaps(map_guide, q * px) || overlaps(radiance, 3 * px))
+        return FLR_ERR_ARG;
+    int st = grow(h, H, W);
+    if (st != FLR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), s), "reset counter");
+
+    flr::FwdArgs fa;
+    fa.guide = guide;
+    fa.map_guide = map_guide;
+    fa.rad = radiance;
+    fa.out = out;
+    fa.coef = h->d_coef;
+    fa.H = H;
+    fa.W = W;
+    fa.r = h->p.radius;
+    fa.rc = h->p.coef_radius;
+    fa.eps = h->p.eps;
+    fa.tau = h->p.pivot_ratio;
+    fa.TH = choose_segment_rows(H, W, h->p.radius, h->n_sm);
+    fa.flag_count = h->d_count;
+    fa.flag_list = h->d_flags;
+    fa.flag_cap = h->flag_cap;
+    fa.shift_out = h->d_shift;
+    dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
+    FLR_CUDA(mark(h, s), "timing event");
+    FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "forward kernel launch");
+    ++h->n_fwd;
+    FLR_CUDA(mark(h, s), "timing event");
+
+    if (h->p.pivot_ratio > 0.f) {
+        flr::Fp64Args da;
+        da.guide = guide;
+        da.map_guide = map_guide;
+        da.rad = radiance;
+        da.shift = h->d_shift;
+        da.out = out;
+        da.coef = h->d_coef;
+        da.H = H;
+        da.W = W;
+        da.r = h->p.radius;
+        da.rc = h->p.coef_radius;
+        da.eps = (double)h->p.eps;
+        da.flag_count = h->d_count;
+        da.flag_list = h->d_flags;
+        da.flag_cap = h->flag_cap;
+        FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "fp64 re-solve launch");
+        ++h->n_fp64;
+    }
+    FLR_CUDA(mark(h, s), "timing event");
+    if (h->p.coef_radius > 0) {
+        flr::ApplyArgs aa;
+        aa.coef = h->d_coef;
+        aa.map_guide = map_guide ? map_guide : guide;
+        aa.shift = h->d_shift;
+        aa.out = out;
+        aa.H = H;
+        aa.W = W;
+        aa.rc = h->p.coef_radius;
+        FLR_CUDA(flr::launch_apply(q, aa, s), "apply kernel launch");
+        ++h->n_apply;
+    }
+    FLR_CUDA(mark(h, s), "timing event");
+    return FLR_OK;
+}
+
+int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
+                     const float *radiance, float *out, int H, int W, void *stream)
+{
+    if (!h || !guide || !radiance || !out || H <= 0 || W <= 0) return FLR_ERR_ARG;
+    const int q = h->p.q;
+    const size_t px = (size_t)H * W;
+    if (h->stage_px < px || !h->stage) {
+        cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_px = 0;
+        if (cudaMalloc(&h->stage, px * (2 * (size_t)FLR_MAX_Q + 6) * sizeof(float)) != cudaSuccess)
+            return FLR_ERR_NOMEM;
+        h->stage_px = px;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float *dg = h->stage;
+    float *dm = dg + (size_t)q * px;
+    float *dr = dm + (size_t)q * px;
+    float *dout = dr + 3 * px;
+    FLR_CUDA(cudaMemcpyAsync(dg, guide, sizeof(float) * q * px, cudaMemcpyHostToDevice, s), "h2d guide");
+    if (map_guide)
+        FLR_CUDA(cudaMemcpyAsync(dm, map_guide, sizeof(float) * q * px, cudaMemcpyHostToDevice, s), "h2d map guide");
+    FLR_CUDA(cudaMemcpyAsync(dr, radiance, sizeof(float) * 3 * px, cudaMemcpyHostToDevice, s), "h2d radiance");
+    int st = flr_denoise(h, dg, map_guide ? dm : nullptr, dr, dout, H, W, stream);
+    if (st != FLR_OK) return st;
+    FLR_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, s), "d2h out");
+    FLR_CUDA(cudaStreamSynchronize(s), "host-path synchronise");
+    return FLR_OK;
+}
+
+int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset)
+{
+    if (!h || !out) return FLR_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->fwd_n = h->n_fwd;
+    out->fp64_n = h->n_fp64;
+    out->apply_n = h->n_apply;
+    if (h->events_used >= 4) FLR_CUDA(cudaEventSynchronize(h->events[h->events_used - 1]), "timing sync");
+    for (size_t i = 0; i + 4 <= h->events_used; i += 4) {
+        float t[3];
+        for (int k = 0; k < 3; ++k)
+            FLR_CUDA(cudaEventElapsedTime(&t[k], h->events[i + k], h->events[i + k + 1]), "timing read");
+        out->fwd_ms += t[0];
+        out->fp64_ms += t[1];
+        out->apply_ms += t[2];
+    }
+    if (reset) {
+        h->events_used = 0;
+        h->n_fwd = h->n_fp64 = h->n_apply = 0;
+    }
+    return FLR_OK;
+}
+
+int flr_get_stats(flr_handle *h, flr_stats *out)
+{
+    if (!h || !out) return FLR_ERR_ARG;
+    unsigned long long n = 0;
+    FLR_CUDA(cudaStreamSynchronize(h->last_stream), "stats synchronise");
+    FLR_CUDA(cudaMemcpy(&n, h->d_count, sizeof(n), cudaMemcpyDeviceToHost), "stats copy");
+    out->flagged = n;
+    out->resolved = h->p.pivot_ratio > 0.f ? (n < (unsigned long long)h->flag_cap ? n : (unsigned long long)h->flag_cap) : 0ull;
+    return FLR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+"""ctypes binding of libflr.so (include/flr.h): argument marshalling only.
+
+Every step of the FLR path runs in the library's CUDA kernels.  PyTorch is used for
+device memory and streams: device entry points take CUDA float32 tensors and run on
+the current torch stream.  Nothing here computes; a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+FLR_OK = 0
+STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA",
+          -4: "FLR_ERR_UNSUPPORTED", -5: "FLR_ERR_NOMEM"}
+
+# every symbol include/flr.h declares
+EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
+           "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error")
+FLAG_TIMING = 1
+
+
+class FlrParams(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("radius", ctypes.c_int), ("coef_radius", ctypes.c_int),
+                ("eps", ctypes.c_float), ("pivot_ratio", ctypes.c_float),
+                ("flags", ctypes.c_uint)]
+
+
+class FlrStats(ctypes.Structure):
+    _fields_ = [("flagged", ctypes.c_ulonglong), ("resolved", ctypes.c_ulonglong)]
+
+
+class FlrKernelTimes(ctypes.Structure):
+    _fields_ = [("fwd_ms", ctypes.c_double), ("fp64_ms", ctypes.c_double),
+                ("apply_ms", ctypes.c_double), ("fwd_n", ctypes.c_ulonglong),
+                ("fp64_n", ctypes.c_ulonglong), ("apply_n", ctypes.c_ulonglong)]
+
+
+class FlrError(RuntimeError):
+    def __init__(self, status, what):
+        lib = _lib
+        msg = STATUS.get(status, str(status))
+        if status == -3 and lib is not None:
+            msg += ": " + lib.flr_last_cuda_error().decode()
+        super().__init__(f"{what} failed: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIBPATH
+
+
+def load_library():
+    """Load libflr.so (built by ``paper_2410_11625_gb300.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIBPATH
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run paper_2410_11625_gb300.build() first")
+    lib = ctypes.CDLL(path)
+    vp, fp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
+    lib.flr_create.argtypes = [ctypes.POINTER(FlrParams), ctypes.POINTER(ctypes.c_void_p)]
+    lib.flr_destroy.argtypes = [vp]
+    lib.flr_reserve.argtypes = [vp, ip, ip]
+    lib.flr_denoise.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_denoise_host.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
+    lib.flr_get_kernel_times.argtypes = [vp, ctypes.POINTER(FlrKernelTimes), ip]
+    lib.flr_status_string.argtypes = [ip]
+    lib.flr_status_string.restype = ctypes.c_char_p
+    lib.flr_last_cuda_error.argtypes = []
+    lib.flr_last_cuda_error.restype = ctypes.c_char_p
+    for name in ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
+                 "flr_get_stats", "flr_get_kernel_times"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, what):
+    if status != FLR_OK:
+        raise FlrError(status, what)
+
+
+def _dev_ptr(t, name, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, name, shape):
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous float32 numpy array")
+    if a.shape != tuple(shape):
+        raise ValueError(f"{name} has shape {a.shape}, expected {tuple(shape)}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class FLR:
+    """A libflr handle: FLR with fixed q, radius, coef_radius, eps and pivot_ratio."""
+
+    def __init__(self, q=8, radius=8, coef_radius=None, eps=1e-3, pivot_ratio=1e-3,
+                 timing=False):
+        lib = load_library()
+        self.q, self.radius = int(q), int(radius)
+        self.coef_radius = self.radius if coef_radius is None else int(coef_radius)
+        self.eps, self.pivot_ratio = float(eps), float(pivot_ratio)
+        p = FlrParams(self.q, self.radius, self.coef_radius, self.eps, self.pivot_ratio,
+                      FLAG_TIMING if timing else 0)
+        h = ctypes.c_void_p()
+        _check(lib.flr_create(ctypes.byref(p), ctypes.byref(h)), "flr_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().flr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, H, W):
+        _check(load_library().flr_reserve(self._h, int(H), int(W)), "flr_reserve")
+
+    def denoise(self, guide, radiance, map_guide=None, out=None, stream=None):
+        """Device FLR: guide [q,H,W], radiance [3,H,W] CUDA float32 -> out [3,H,W]."""
+        import torch
+        H, W = int(radiance.shape[-2]), int(radiance.shape[-1])
+        g = _dev_ptr(guide, "guide", (self.q, H, W))
+        r = _dev_ptr(radiance, "radiance", (3, H, W))
+        m = None if map_guide is None else _dev_ptr(map_guide, "map_guide", (self.q, H, W))
+        if out is None:
+            out = torch.empty((3, H, W), dtype=torch.float32, device=radiance.device)
+        o = _dev_ptr(out, "out", (3, H, W))
+        if stream is None:
+            stream = torch.cuda.current_stream(radiance.device)
+        st = ctypes.c_void_p(stream.cuda_stream)
+        _check(load_library().flr_denoise(self._h, g, m, r, o, H, W, st), "flr_denoise")
+        return out
+
+    def denoise_host(self, guide, radiance, map_guide=None, out=None, stream=None):
+        """Host FLR: numpy float32 in and out; copies and waits inside the library."""
+        import numpy as np
+        H, W = radiance.shape[-2], radiance.shape[-1]
+        g = _host_ptr(guide, "guide", (self.q, H, W))
+        r = _host_ptr(radiance, "radiance", (3, H, W))
+        m = None if map_guide is None else _host_ptr(map_guide, "map_guide", (self.q, H, W))
+        if out is None:
+            out = np.empty((3, H, W), np.float32)
+        o = _host_ptr(out, "out", (3, H, W))
+        st = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
+        _check(load_library().flr_denoise_host(self._h, g, m, r, o, H, W, st), "flr_denoise_host")
+        return out
+
+    def kernel_times(self, reset=True):
+        """Launch counts and summed CUDA-event kernel durations (ms) since the last reset."""
+        t = FlrKernelTimes()
+        _check(load_library().flr_get_kernel_times(self._h, ctypes.byref(t), int(reset)),
+               "flr_get_kernel_times")
+        return {"fwd_ms": t.fwd_ms, "fp64_ms": t.fp64_ms, "apply_ms": t.apply_ms,
+                "fwd_n": int(t.fwd_n), "fp64_n": int(t.fp64_n), "apply_n": int(t.apply_n)}
+
+    def stats(self):
+        s = FlrStats()
+        _check(load_library().flr_get_stats(self._h, ctypes.byref(s)), "flr_get_stats")
+        return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+
+
+def denoise(guide, radiance, radius=8, eps=1e-3, coef_radius=None, map_guide=None,
+            pivot_ratio=1e-3):
+    """One-shot FLR on CUDA tensors (creates and frees a handle)."""
+    f = FLR(int(guide.shape[0]), radius, coef_radius, eps, pivot_ratio)
+    try:
+        return f.denoise(guide, radiance, map_guide=map_guide)
+    finally:
+        import torch
+        torch.cuda.current_stream(radiance.device).synchronize()
+        f.close()

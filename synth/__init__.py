@@ -83,7 +83,8 @@ def random_frame(seed: int, H: int, W: int, q: int = 8, kind: str = "uniform"):
       const_guide   guide channel 1 constant over the frame (rank-deficient windows)
       dup_guide     guide channel 2 duplicates channel 0 (collinear guides)
       depth_offset  uniform guides with +100 added to the last guide channel
-      heavy_tail    uniform guides; radiance with Pareto-like fireflies
+      heavy_tail    uniform guides; Pareto(alpha = 1.5) radiance: fireflies up to ~10^3
+                    times the median at 10^5 pixels
     """
     rng = np.random.default_rng(seed)
     lo = -1.0 if kind == "signed" else 0.0
@@ -97,7 +98,7 @@ def random_frame(seed: int, H: int, W: int, q: int = 8, kind: str = "uniform"):
         g[q - 1] += np.float32(100.0)
     elif kind == "heavy_tail":
         u = rng.uniform(0.0, 1.0, size=(3, H, W))
-        y = (0.2 * (1.0 - u) ** -1.5).astype(np.float32)
+        y = (0.2 * (1.0 - u) ** (-1.0 / 1.5)).astype(np.float32)
     elif kind not in ("uniform", "signed", "const_guide", "dup_guide"):
         raise ValueError(f"unknown kind {kind!r}")
     return g, y

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/flr.h declares, and
+rejects bad parameters with a status code (CPU only: no call here reaches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2410_11625_gb300 import flr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return flr.load_library()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert {"flr_create", "flr_denoise", "flr_destroy"} <= names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(flr.EXPORTS) == names
+
+
+def test_status_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert lib.flr_status_string(code)
+    assert lib.flr_status_string(0) == b"FLR_OK"
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(q=0), -4), (dict(q=9), -4), (dict(radius=17), -4), (dict(coef_radius=17), -4),
+    (dict(radius=-1), -1), (dict(coef_radius=-1), -1), (dict(eps=-1.0), -1),
+    (dict(eps=float("nan")), -1), (dict(flags=2), -1), (dict(pivot_ratio=float("nan")), -1),
+])
+def test_create_rejects_bad_params(lib, kw, status):
+    p = dict(q=8, radius=8, coef_radius=8, eps=1e-3, pivot_ratio=1e-3, flags=0)
+    p.update(kw)
+    params = flr.FlrParams(p["q"], p["radius"], p["coef_radius"], p["eps"], p["pivot_ratio"], p["flags"])
+    h = ctypes.c_void_p()
+    assert lib.flr_create(ctypes.byref(params), ctypes.byref(h)) == status
+    assert not h.value
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.flr_create(None, None) == -1
+    assert lib.flr_destroy(None) == 0
+    assert lib.flr_denoise(None, None, None, None, None, 8, 8, None) == -1
+    assert lib.flr_denoise_host(None, None, None, None, None, 8, 8, None) == -1
+    assert lib.flr_reserve(None, 8, 8) == -1
+    assert lib.flr_get_stats(None, None) == -1
+    assert lib.flr_get_kernel_times(None, None, 0) == -1

@@ -1,0 +1,197 @@
+"""Parity of the CUDA FLR path (through the C ABI) with the FP64 oracle, element by element.
+
+Sizes span several 96-column strips and row segments with ragged tails; edge cases cover
+images narrower or shorter than the window, single rows and columns, degenerate guides
+(constant, duplicated, offset by +100), heavy-tailed radiance, every supported Q, a
+separate map guide, and a small eps that forces the FP64 re-solve.  The bar is
+max relative error <= 1e-4 (helpers.rel_err).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import TOL, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def flr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2410_11625_gb300 import flr as mod
+    return mod
+
+
+def run_gpu(flr, g, y, r, rc, eps, map_guide=None, pivot_ratio=1e-3, stats=False):
+    import torch
+    f = flr.FLR(q=g.shape[0], radius=r, coef_radius=rc, eps=eps, pivot_ratio=pivot_ratio)
+    out = f.denoise(to_dev(g), to_dev(y), map_guide=None if map_guide is None else to_dev(map_guide))
+    torch.cuda.synchronize()
+    res = out.cpu().numpy()
+    st = f.stats()
+    f.close()
+    return (res, st) if stats else res
+
+
+def check(flr, g, y, r, rc, eps=1e-3, map_guide=None, tol=TOL):
+    ref = oracle.flr_forward(g, y, r, eps, coef_radius=rc, map_guide=map_guide)
+    got = run_gpu(flr, g, y, r, rc, eps, map_guide=map_guide)
+    assert np.all(np.isfinite(got))
+    err = rel_err(got, ref)
+    assert err <= tol, f"max rel err {err:.3e}"
+    return err
+
+
+@pytest.mark.parametrize("rc", [5, 0])
+def test_rendered_256_radius5(flr, rc):
+    g, y = synth.render(0, 256, 256)
+    check(flr, g, y, 5, rc)
+
+
+@pytest.mark.parametrize("H,W,r,rc", [
+    (200, 237, 8, 8), (131, 301, 3, 2), (97, 193, 16, 16), (64, 96, 1, 1),
+    (150, 130, 8, 0), (77, 250, 16, 0), (40, 40, 0, 3), (45, 61, 0, 0),
+])
+def test_random_uniform_frames(flr, H, W, r, rc):
+    g, y = synth.random_frame(100 + H + W, H, W, 8)
+    check(flr, g, y, r, rc)
+
+
+@pytest.mark.parametrize("kind", ["signed", "const_guide", "dup_guide", "depth_offset", "heavy_tail"])
+def test_adversarial_frames(flr, kind):
+    g, y = synth.random_frame(7, 120, 210, 8, kind=kind)
+    check(flr, g, y, 6, 6)
+
+
+@pytest.mark.parametrize("H,W,r,rc", [
+    (5, 40, 8, 8), (40, 5, 8, 8), (1, 300, 4, 2), (300, 1, 4, 2), (1, 1, 3, 3), (2, 3, 16, 16),
+    (17, 17, 8, 8),
+])
+def test_small_and_thin_images(flr, H, W, r, rc):
+    g, y = synth.random_frame(H * 1000 + W, H, W, 8)
+    check(flr, g, y, r, rc)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5, 6, 7])
+def test_every_guide_count(flr, q):
+    g, y = synth.random_frame(50 + q, 90, 170, q)
+    check(flr, g, y, 4, 3)
+
+
+def test_separate_map_guide(flr):
+    """A map guide z different from the model guide x (Sec. 3.3): random full-rank guides."""
+    g, y = synth.random_frame(61, 128, 160, 8)
+    z, _ = synth.random_frame(62, 128, 160, 8)
+    check(flr, g, y, 6, 6, map_guide=z)
+    check(flr, g, y, 6, 0, map_guide=z)
+
+
+@pytest.mark.parametrize("rc", [6, 0])
+def test_separate_map_guide_rendered(flr, rc):
+    """Rendered guides (piecewise-constant albedo, so windows with flat directions) and a
+    perturbed map guide.  Along a flat direction the FP32 rounding of the centred moments
+    (about u * S_jj / n) is amplified by 1 / eps in the model; with z = x it meets
+    (z - mu) . v = 0 and vanishes, with z != x it reaches the output as an absolute error.
+    Bar: max |got - ref| <= 1e-4 * RMS(ref), i.e. the parity metric's floor alone."""
+    g, y = synth.render(3, 128, 160)
+    z = (g + synth.random_frame(9, 128, 160, 8)[0] * 0.05).astype(np.float32)
+    ref = oracle.flr_forward(g, y, 6, 1e-3, coef_radius=rc, map_guide=z)
+    got = run_gpu(flr, g, y, 6, rc, 1e-3, map_guide=z)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.sqrt(np.mean(ref ** 2))
+
+
+def test_fp64_resolve_of_every_pixel(flr):
+    """pivot_ratio = 1 flags every pixel (a pivot never exceeds its diagonal), so with
+    rc = 0 the whole result comes from the FP64 re-solve kernel: it must match the FP64
+    oracle to float32 output rounding, even at eps = 1e-6 where FP32 alone cannot."""
+    g, y = synth.render(5, 96, 200)
+    eps = 1e-6
+    ref = oracle.flr_forward(g, y, 4, eps, coef_radius=0)
+    got, st = run_gpu(flr, g, y, 4, 0, eps, pivot_ratio=1.0, stats=True)
+    assert st["flagged"] == 96 * 200 and st["resolved"] == st["flagged"]
+    assert rel_err(got, ref) <= 2e-6
+
+
+def test_fp64_coefficients_feed_the_average(flr):
+    """Every pixel re-solved in FP64 with rc > 0: the FP64 models are written to the
+    coefficient planes that the FP32 averaging kernel reads."""
+    g, y = synth.render(6, 96, 200)
+    ref = oracle.flr_forward(g, y, 4, 1e-3, coef_radius=4)
+    got, st = run_gpu(flr, g, y, 4, 4, 1e-3, pivot_ratio=1.0, stats=True)
+    assert st["flagged"] == 96 * 200
+    assert rel_err(got, ref) <= TOL
+
+
+def test_small_eps_reports_and_reduces_error(flr):
+    """eps = 1e-5 on rendered guides: pivots fall below tau, are counted and re-solved in
+    FP64, and the re-solve lowers the RMS error against the oracle (the worst pixel may be
+    an unflagged one, whose FP32 error the pivot test does not see)."""
+    g, y = synth.render(5, 96, 200)
+    eps = 1e-5
+    ref = oracle.flr_forward(g, y, 4, eps, coef_radius=0)
+    got0, st0 = run_gpu(flr, g, y, 4, 0, eps, pivot_ratio=0.0, stats=True)
+    got1, st1 = run_gpu(flr, g, y, 4, 0, eps, pivot_ratio=1e-3, stats=True)
+    assert st0["flagged"] == 0 and st1["flagged"] > 0 and st1["resolved"] == st1["flagged"]
+    rms = lambda a: float(np.sqrt(np.mean((a - ref) ** 2)))
+    assert rms(got1) < rms(got0)
+
+
+def test_rendered_full_hd_sampled_blocks(flr):
+    """1920x1080, r = rc = 8 (the benchmark's launch): 16 blocks, including corners and
+    edges, checked against the oracle run on the block plus its radius-(r + rc) halo,
+    which contains every input the block's outputs depend on."""
+    import torch
+    H, W, r, rc = 1080, 1920, 8, 8
+    g, y = synth.render(1, H, W)
+    f = flr.FLR(q=8, radius=r, coef_radius=rc, eps=1e-3)
+    out = f.denoise(to_dev(g), to_dev(y))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    f.close()
+    assert np.all(np.isfinite(got))
+    rng = np.random.default_rng(0)
+    R = r + rc
+    B = 32
+    corners = [(0, 0), (0, W - B), (H - B, 0), (H - B, W - B)]
+    edges = [(0, 900), (H - B, 500), (400, 0), (700, W - B)]
+    inner = [(int(rng.integers(0, H - B)), int(rng.integers(0, W - B))) for _ in range(8)]
+    worst = 0.0
+    for by, bx in corners + edges + inner:
+        y0, y1 = max(0, by - R), min(H, by + B + R)
+        x0, x1 = max(0, bx - R), min(W, bx + B + R)
+        ref = oracle.flr_forward(g[:, y0:y1, x0:x1], y[:, y0:y1, x0:x1], r, 1e-3, coef_radius=rc)
+        ref = ref[:, by - y0:by - y0 + B, bx - x0:bx - x0 + B]
+        worst = max(worst, rel_err(got[:, by:by + B, bx:bx + B], ref))
+    assert worst <= TOL, f"max rel err {worst:.3e}"
+
+
+def test_deterministic_and_host_path_matches(flr):
+    import torch
+    g, y = synth.render(2, 150, 260)
+    f = flr.FLR(q=8, radius=8, coef_radius=8, eps=1e-3)
+    a = f.denoise(to_dev(g), to_dev(y)).cpu().numpy()
+    b = f.denoise(to_dev(g), to_dev(y)).cpu().numpy()
+    c = f.denoise_host(g, y)
+    torch.cuda.synchronize()
+    f.close()
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
+
+
+def test_misaligned_pointer_is_rejected(flr):
+    import torch
+    g, y = synth.random_frame(1, 16, 16, 8)
+    G = torch.zeros(8 * 256 + 1, device="cuda")
+    f = flr.FLR(q=8, radius=2, coef_radius=0)
+    lib = flr.load_library()
+    import ctypes
+    st = lib.flr_denoise(f._h, ctypes.c_void_p(G.data_ptr() + 4), None,
+                         ctypes.c_void_p(to_dev(y).data_ptr()),
+                         ctypes.c_void_p(torch.empty(3 * 256, device="cuda").data_ptr()), 16, 16, None)
+    assert st == -2
+    f.close()
