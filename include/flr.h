@@ -135,6 +135,27 @@ typedef struct flr_kernel_times {
  */
 int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset);
 
+/*
+ * FLR pass without any device allocation, for callers that cannot call cudaMalloc: code
+ * running inside a custom device allocator or a memory-pool callback, a host application
+ * that forbids allocations after start-up, or a plugin that only receives the buffers its
+ * host hands it.  The paper has no counterpart: this is an integration variant of
+ * flr_denoise, with the same arguments except that the parameters replace the handle.
+ *
+ * The workspace (coefficient planes, flag list, flag counter, reference shift) is one
+ * file-scope __device__ array sized for FLR_NOALLOC_MAX_PIXELS pixels; every GPU that loads
+ * the library holds it until the process exits.  Frames larger than that are rejected with
+ * FLR_ERR_UNSUPPORTED.  The first call on a device looks up the array's device address and
+ * configures the kernels (no allocation); make that first call before capturing any stream.
+ * All calls on a device share the array and leave the last call's contents in it: calls
+ * that overlap on the GPU race, so the caller must serialise them.  No statistics are kept
+ * (flr_get_stats needs a handle).
+ * Errors: FLR_ERR_ARG, FLR_ERR_ALIGN, FLR_ERR_UNSUPPORTED, FLR_ERR_CUDA.
+ */
+#define FLR_NOALLOC_MAX_PIXELS (256 * 256)
+int flr_denoise_noalloc(const flr_params *params, const float *guide, const float *map_guide,
+                        const float *radiance, float *out, int H, int W, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *flr_status_string(int status);
 

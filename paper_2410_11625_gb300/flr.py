@@ -17,7 +17,8 @@ STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA
 
 # every symbol include/flr.h declares
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
-           "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error")
+           "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
+           "flr_denoise_noalloc")
 FLAG_TIMING = 1
 
 
@@ -71,6 +72,8 @@ def load_library():
     lib.flr_denoise_host.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
     lib.flr_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
     lib.flr_get_kernel_times.argtypes = [vp, ctypes.POINTER(FlrKernelTimes), ip]
+    lib.flr_denoise_noalloc.argtypes = [ctypes.POINTER(FlrParams), fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_denoise_noalloc.restype = ctypes.c_int
     lib.flr_status_string.argtypes = [ip]
     lib.flr_status_string.restype = ctypes.c_char_p
     lib.flr_last_cuda_error.argtypes = []
