@@ -27,43 +27,75 @@ static_assert(kAW * (kAH / kARun) == kAThreads, "one thread per (column, 8-row r
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
-                 "r"(valid ? 4 : 0));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0));
 }
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0));
+}
+
+// Tile geometry: the tile covers rows ty0 - rc .. ty0 + kAH + rc and columns starting at
+// tx0 - RCA (RCA = rc rounded up to a multiple of 4, so rows start 16-byte aligned).
+struct ApplyGeom {
+    int RCA, TWa, THh, TS, HS;
+    __host__ __device__ ApplyGeom(int rc)
+    {
+        RCA = (rc + 3) & ~3;
+        TWa = kAW + 2 * RCA;
+        THh = kAH + 2 * rc;
+        TS = TWa + 4;   // 16-byte aligned rows
+        HS = kAW + 1;   // odd: the column walks of the vertical pass are conflict-free
+    }
+    __host__ __device__ size_t floats() const { return (size_t)2 * THh * TS + (size_t)THh * HS; }
+};
 
 // Copy the tile + halo of one coefficient plane into shared memory (zero outside the
 // image), asynchronously: each warp copies whole rows, lanes along the row.
-__device__ __forceinline__ void load_tile(float *T, int TS, const float *src, int H, int W, int ty0,
-                                          int tx0, int rc, int THh, int TWh, int warp, int lane)
+__device__ __forceinline__ void load_tile(float *T, const ApplyGeom &g, const float *src, int H, int W,
+                                          int ty0, int tx0, int rc, int warp, int lane)
 {
-    for (int row = warp; row < THh; row += kAThreads / 32) {
+    const int xs0 = tx0 - g.RCA;
+    const bool vec = (W & 3) == 0;
+    for (int row = warp; row < g.THh; row += kAThreads / 32) {
         const int sy = ty0 - rc + row;
         const bool row_ok = sy >= 0 && sy < H;
         const float *srow = src + (size_t)(row_ok ? sy : 0) * W;
-        for (int col = lane; col < TWh; col += 32) {
-            const int sx = tx0 - rc + col;
-            const bool ok = row_ok && sx >= 0 && sx < W;
-            cp_async4(T + row * TS + col, ok ? srow + sx : src, ok);
+        float *trow = T + row * g.TS;
+        if (vec) {
+            for (int c = lane; c < (g.TWa >> 2); c += 32) {
+                const int sx = xs0 + 4 * c;
+                const bool ok = row_ok && sx >= 0 && sx < W;
+                cp_async16(trow + 4 * c, ok ? srow + sx : src, ok);
+            }
+        } else {
+            for (int col = lane; col < g.TWa; col += 32) {
+                const int sx = xs0 + col;
+                const bool ok = row_ok && sx >= 0 && sx < W;
+                cp_async4(trow + col, ok ? srow + sx : src, ok);
+            }
         }
     }
     asm volatile("cp.async.commit_group;\n" ::);
 }
 
-template <int Q>
-__global__ void __launch_bounds__(kAThreads) flr_apply_kernel(const ApplyArgs a)
+template <int Q, int RT>
+__global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const ApplyArgs a)
 {
-    extern __shared__ float sm[];
-    const int H = a.H, W = a.W, rc = a.rc;
-    const int TWh = kAW + 2 * rc, THh = kAH + 2 * rc;
-    const int TS = TWh + 1, HS = kAW + 1;
-    float *T0 = sm;             // [THh][TS]   coefficient plane tile + halo, double-buffered
-    float *T1 = T0 + THh * TS;
-    float *Hb = T1 + THh * TS;  // [THh][HS]   horizontal sums
+    extern __shared__ __align__(16) float sm[];
+    const int H = a.H, W = a.W;
+    const int rc = RT >= 0 ? RT : a.rc;
+    const ApplyGeom g(rc);
+    float *T0 = sm;                 // [THh][TS]   coefficient plane tile + halo, double-buffered
+    float *T1 = T0 + g.THh * g.TS;
+    float *Hb = T1 + g.THh * g.TS;  // [THh][HS]   horizontal sums
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx0 = blockIdx.x * kAW, ty0 = blockIdx.y * kAH;
     const int x = tid % kAW, run = tid / kAW;
     const int gx = tx0 + x;
     const size_t plane = (size_t)H * W;
+    const int xoff = g.RCA - rc;  // tile column of output column 0's window start
     constexpr int NP = 3 * (Q + 1);
 
     float acc[3][kARun];
@@ -72,7 +104,7 @@ __global__ void __launch_bounds__(kAThreads) flr_apply_kernel(const ApplyArgs a)
 #pragma unroll
         for (int t = 0; t < kARun; ++t) acc[c][t] = 0.f;
 
-    load_tile(T0, TS, a.coef, H, W, ty0, tx0, rc, THh, TWh, warp, lane);
+    load_tile(T0, g, a.coef, H, W, ty0, tx0, rc, warp, lane);
     for (int i = 0; i <= Q; ++i) {
         float zf[kARun];
 #pragma unroll
@@ -90,36 +122,70 @@ __global__ void __launch_bounds__(kAThreads) flr_apply_kernel(const ApplyArgs a)
             const int p = 3 * i + c;
             float *Tc = (p & 1) ? T1 : T0;
             if (p + 1 < NP) {
-                load_tile((p & 1) ? T0 : T1, TS, a.coef + (size_t)(p + 1) * plane, H, W, ty0, tx0, rc,
-                          THh, TWh, warp, lane);
+                load_tile((p & 1) ? T0 : T1, g, a.coef + (size_t)(p + 1) * plane, H, W, ty0, tx0, rc, warp, lane);
                 asm volatile("cp.async.wait_group 1;\n" ::);
             } else {
                 asm volatile("cp.async.wait_group 0;\n" ::);
             }
             __syncthreads();  // plane p is in Tc for every thread
-            for (int item = tid; item < THh * 4; item += kAThreads) {
+            // horizontal sums: 16 outputs per item, operands held in registers
+            for (int item = tid; item < g.THh * 4; item += kAThreads) {
                 const int row = item >> 2, xr = (item & 3) * 16;
-                const float *q = Tc + row * TS + xr;
-                float *h = Hb + row * HS + xr;
-                float s = 0.f;
-                for (int k = 0; k <= 2 * rc; ++k) s += q[k];
-                h[0] = s;
+                const float *q = Tc + row * g.TS + xr + xoff;
+                float *h = Hb + row * g.HS + xr;
+                if constexpr (RT >= 0) {
+                    constexpr int N = 16 + 2 * RT;
+                    float v[N];
 #pragma unroll
-                for (int t = 1; t < 16; ++t) {
-                    s += q[t + 2 * rc] - q[t - 1];
-                    h[t] = s;
+                    for (int k = 0; k < N; ++k) v[k] = q[k];
+                    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k <= 2 * RT; ++k) s4[k & 3] += v[k];
+                    float s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                    h[0] = s;
+#pragma unroll
+                    for (int t = 1; t < 16; ++t) {
+                        s += v[t + 2 * RT] - v[t - 1];
+                        h[t] = s;
+                    }
+                } else {
+                    float s = 0.f;
+                    for (int k = 0; k <= 2 * rc; ++k) s += q[k];
+                    h[0] = s;
+#pragma unroll
+                    for (int t = 1; t < 16; ++t) {
+                        s += q[t + 2 * rc] - q[t - 1];
+                        h[t] = s;
+                    }
                 }
             }
             __syncthreads();  // Hb complete; Tc may be refilled from here on
             {
-                const float *q = Hb + (run * kARun) * HS + x;
-                float s = 0.f;
-                for (int k = 0; k <= 2 * rc; ++k) s += q[k * HS];
-                acc[c][0] = fmaf(s, zf[0], acc[c][0]);
+                const float *q = Hb + (run * kARun) * g.HS + x;
+                if constexpr (RT >= 0) {
+                    constexpr int N = kARun + 2 * RT;
+                    float v[N];
 #pragma unroll
-                for (int t = 1; t < kARun; ++t) {
-                    s += q[(t + 2 * rc) * HS] - q[(t - 1) * HS];
-                    acc[c][t] = fmaf(s, zf[t], acc[c][t]);
+                    for (int k = 0; k < N; ++k) v[k] = q[k * g.HS];
+                    float s2[2] = {0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k <= 2 * RT; ++k) s2[k & 1] += v[k];
+                    float s = s2[0] + s2[1];
+                    acc[c][0] = fmaf(s, zf[0], acc[c][0]);
+#pragma unroll
+                    for (int t = 1; t < kARun; ++t) {
+                        s += v[t + 2 * RT] - v[t - 1];
+                        acc[c][t] = fmaf(s, zf[t], acc[c][t]);
+                    }
+                } else {
+                    float s = 0.f;
+                    for (int k = 0; k <= 2 * rc; ++k) s += q[k * g.HS];
+                    acc[c][0] = fmaf(s, zf[0], acc[c][0]);
+#pragma unroll
+                    for (int t = 1; t < kARun; ++t) {
+                        s += q[(t + 2 * rc) * g.HS] - q[(t - 1) * g.HS];
+                        acc[c][t] = fmaf(s, zf[t], acc[c][t]);
+                    }
                 }
             }
         }
@@ -140,17 +206,27 @@ __global__ void __launch_bounds__(kAThreads) flr_apply_kernel(const ApplyArgs a)
     }
 }
 
-template <int Q>
-cudaError_t launch_apply_q(const ApplyArgs &a, cudaStream_t st)
+template <int Q, int RT>
+cudaError_t launch_apply_qr(const ApplyArgs &a, cudaStream_t st)
 {
-    const int TWh = kAW + 2 * a.rc, THh = kAH + 2 * a.rc;
-    const size_t smem = sizeof(float) * ((size_t)2 * THh * (TWh + 1) + (size_t)THh * (kAW + 1));
-    cudaError_t e = cudaFuncSetAttribute(flr_apply_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const ApplyGeom g(a.rc);
+    const size_t smem = sizeof(float) * g.floats();
+    cudaError_t e = cudaFuncSetAttribute(flr_apply_kernel<Q, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + kAW - 1) / kAW, (a.H + kAH - 1) / kAH);
-    flr_apply_kernel<Q><<<grid, kAThreads, smem, st>>>(a);
+    flr_apply_kernel<Q, RT><<<grid, kAThreads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t launch_apply_q(const ApplyArgs &a, cudaStream_t st)
+{
+    if constexpr (Q == 8) {
+        if (a.rc == 8) return launch_apply_qr<8, 8>(a, st);
+        if (a.rc == 5) return launch_apply_qr<8, 5>(a, st);
+    }
+    return launch_apply_qr<Q, -1>(a, st);
 }
 
 }  // namespace

@@ -154,7 +154,7 @@ int flr_create(const flr_params *params, flr_handle **out)
     if (e == cudaSuccess) e = cudaMemset(h->d_count, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) {
         h->fwd_smem = flr::fwd_smem_bytes(h->p.q, h->p.radius);
-        e = flr::fwd_prepare(h->p.q, h->fwd_smem);
+        e = flr::fwd_prepare(h->p.q, h->p.radius, h->fwd_smem);
     }
     if (e != cudaSuccess) {
         cuda_fail(e, "flr_create");

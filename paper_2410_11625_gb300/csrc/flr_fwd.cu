@@ -214,66 +214,169 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
     return low;
 }
 
-// Asynchronous 4-byte global->shared copy; src_size 0 writes a zero (no global read).
+// Asynchronous global->shared copies; a src_size of 0 writes zeros without reading.
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
-                 "r"(valid ? 4 : 0));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// Stage the input rows a batch of kB walker steps needs: for step b, row yv + b + r
-// enters the window and row yv + b - r - 1 leaves it.  Layout [2][kB][Q+3][WS] (0 =
-// entering, 1 = leaving); rows outside the image or not yet summed are zero-filled.
+// Shared-memory geometry of one CTA for radius r.
+struct FwdGeom {
+    int Wi;   // walker (input) columns: kTW + 2r
+    int RA;   // r rounded up to a multiple of 4: staged rows start at column x0 - RA
+    int WSt;  // staged row length: kTW + 2 RA (a multiple of 4)
+    int VS;   // row stride of the window-sum buffer
+    __host__ __device__ FwdGeom(int r, bool vec_hpass)
+    {
+        Wi = kTW + 2 * r;
+        RA = (r + 3) & ~3;
+        WSt = kTW + 2 * RA;
+        // vectorised H-pass: 16-byte aligned rows with stride = 4 (mod 8) floats, so the
+        // eight lanes of each 128-bit access phase hit distinct banks; scalar H-pass: an
+        // odd stride, so 32 lanes on 32 rows hit distinct banks
+        VS = vec_hpass ? (((Wi + 3) & ~7) + 4) : (Wi | 1);
+    }
+};
+
+// Stage the input rows of kB walker steps: for step b, row yv + b + r enters the window
+// and row yv + b - r - 1 leaves it.  Layout [2][kB][Q+3][WSt] (0 = entering, 1 = leaving);
+// staged column j is global column x0 - RA + j; anything outside the image is zero.
 template <int Q>
-__device__ __forceinline__ void stage_batch(float *stage, int WS, const FwdArgs &a, int yv,
-                                            int first_row, int xg0, int Wi, int warp, int lane)
+__device__ __forceinline__ void stage_batch(float *stage, const FwdGeom &gm, const FwdArgs &a,
+                                            int r, int yv, int x0, int warp, int lane)
 {
     constexpr int NS = Q + 3;
     const size_t plane = (size_t)a.H * a.W;
+    const int xs0 = x0 - gm.RA;
+    const bool vec = (a.W & 3) == 0;  // 16-byte rows: every 4-column chunk is all in or all out
     for (int row = warp; row < 2 * kB * NS; row += kThreads / 32) {
-        const int el = row / (kB * NS), rem = row % (kB * NS);
-        const int b = rem / NS, k = rem % NS;
-        const int y = el == 0 ? yv + b + a.r : yv + b - a.r - 1;
-        const bool row_ok = y >= 0 && y < a.H && (el == 0 || y >= first_row);
+        const int el = row / (kB * NS), rem = row - el * (kB * NS);
+        const int b = rem / NS, k = rem - b * NS;
+        const int y = el == 0 ? yv + b + r : yv + b - r - 1;
+        const bool row_ok = y >= 0 && y < a.H;
         const float *base = k < Q ? a.guide + (size_t)k * plane : a.rad + (size_t)(k - Q) * plane;
         const float *src_row = base + (size_t)(row_ok ? y : 0) * a.W;
-        float *dst = stage + (size_t)row * WS;
-        for (int wx = lane; wx < Wi; wx += 32) {
-            const int gx = xg0 + wx;
-            const bool ok = row_ok && gx >= 0 && gx < a.W;
-            cp_async4(dst + wx, ok ? src_row + gx : a.rad, ok);
+        float *dst = stage + (size_t)row * gm.WSt;
+        if (vec) {
+            for (int c = lane; c < (gm.WSt >> 2); c += 32) {
+                const int gx = xs0 + 4 * c;
+                const bool ok = row_ok && gx >= 0 && gx < a.W;
+                cp_async16(dst + 4 * c, ok ? src_row + gx : a.rad, ok);
+            }
+        } else {
+            for (int j = lane; j < gm.WSt; j += 32) {
+                const int gx = xs0 + j;
+                const bool ok = row_ok && gx >= 0 && gx < a.W;
+                cp_async4(dst + j, ok ? src_row + gx : a.rad, ok);
+            }
         }
     }
     cp_async_commit();
 }
 
-template <int Q>
+// Horizontal radius-r sums of one shared-memory row, in place: slot xo <- sum of
+// p[xo .. xo + 2r] for xo in [0, kTW).  Chunks of 8 outputs load every operand before
+// writing, so no slot is overwritten while still needed.  RT >= 0: radius known at
+// compile time and 16/8-byte vector accesses; RT < 0: runtime radius, scalar accesses.
+template <int RT>
+__device__ __forceinline__ void hsum_row(float *p, int r)
+{
+    float s;
+    if constexpr (RT >= 0) {
+        constexpr int N = 2 * RT + 1;
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < N; ++k) t[k & 3] += p[k];
+        s = (t[0] + t[1]) + (t[2] + t[3]);
+    } else {
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+        int k = 0;
+        for (; k + 4 <= 2 * r + 1; k += 4) {
+            t0 += p[k];
+            t1 += p[k + 1];
+            t2 += p[k + 2];
+            t3 += p[k + 3];
+        }
+        for (; k <= 2 * r; ++k) t0 += p[k];
+        s = (t0 + t1) + (t2 + t3);
+    }
+    float vprev = 0.f;
+#pragma unroll 2
+    for (int xo = 0; xo < kTW; xo += 8) {
+        float add[8], old[8];
+        if constexpr (RT >= 0) {
+            const float4 o0 = *reinterpret_cast<const float4 *>(p + xo);
+            const float4 o1 = *reinterpret_cast<const float4 *>(p + xo + 4);
+            old[0] = o0.x; old[1] = o0.y; old[2] = o0.z; old[3] = o0.w;
+            old[4] = o1.x; old[5] = o1.y; old[6] = o1.z; old[7] = o1.w;
+            if constexpr ((2 * RT) % 4 == 0) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(p + xo + 2 * RT);
+                const float4 a1 = *reinterpret_cast<const float4 *>(p + xo + 2 * RT + 4);
+                add[0] = a0.x; add[1] = a0.y; add[2] = a0.z; add[3] = a0.w;
+                add[4] = a1.x; add[5] = a1.y; add[6] = a1.z; add[7] = a1.w;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) {
+                    const float2 v = *reinterpret_cast<const float2 *>(p + xo + 2 * RT + t);
+                    add[t] = v.x;
+                    add[t + 1] = v.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                add[t] = p[xo + t + 2 * r];
+                old[t] = p[xo + t];
+            }
+        }
+        float out[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (xo + t > 0) s += add[t] - vprev;
+            vprev = old[t];
+            out[t] = s;
+        }
+        if constexpr (RT >= 0) {
+            *reinterpret_cast<float4 *>(p + xo) = make_float4(out[0], out[1], out[2], out[3]);
+            *reinterpret_cast<float4 *>(p + xo + 4) = make_float4(out[4], out[5], out[6], out[7]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) p[xo + t] = out[t];
+        }
+    }
+}
+
+template <int Q, int RT>
 __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
 {
     using C = Chan<Q>;
     constexpr int NS = Q + 3;
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     __shared__ float s_cta[NS], s_ref[NS];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int H = a.H, W = a.W, r = a.r;
+    const int H = a.H, W = a.W;
+    const int r = RT >= 0 ? RT : a.r;
+    const FwdGeom gm(r, RT >= 0);
     const int x0 = blockIdx.x * kTW;
     const int y0 = blockIdx.y * a.TH;
     const int y1 = min(y0 + a.TH, H);
-    const int Wi = kTW + 2 * r;
-    const int Wi_pad = (Wi + 31) & ~31;
-    const int VS = Wi + 1;  // odd row stride: conflict-free for every access pattern below
-    const int nColWarps = Wi_pad >> 5;
-    float *Vbuf = smem;                                // [kB][NCH][VS]  window sums
-    float *stage = smem + (size_t)kB * C::NCH * VS;    // [2][kB][NS][Wi_pad] input rows
+    const int nColWarps = (gm.Wi + 31) >> 5;
+    float *Vbuf = smem;                                   // [kB][NCH][VS]  window sums
+    float *stage = smem + (size_t)kB * C::NCH * gm.VS;    // [2][kB][NS][WSt] input rows
 
     const int first_row = y0 - r;  // first input row summed by this segment
-    const int xg0 = x0 - r;        // global column of walker column 0
-    int yv = y0 - 2 * r;           // first virtual row: the walkers start with an empty window
-    stage_batch<Q>(stage, Wi_pad, a, yv, first_row, xg0, Wi, warp, lane);
+    int yv = y0 - 2 * r;           // first virtual row: the walkers start from an empty window
+    stage_batch<Q>(stage, gm, a, r, yv, x0, warp, lane);
 
     // reference shifts (overlaps the first copies)
     if (warp == 0) {
@@ -285,14 +388,18 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
     __syncthreads();
     if (blockIdx.x == 0 && blockIdx.y == 0 && tid < NS) a.shift_out[tid] = s_ref[tid];
 
-    // walker identity: warp -> (channel group, 32-column block)
+    // walker identity: warp -> (channel group, 32-column block); walker column wx is
+    // global column x0 - r + wx and staged column wx + (RA - r)
     const int group = warp / nColWarps;
     const int wx = (warp % nColWarps) * 32 + lane;
-    const bool walker = group < 3 && wx < Wi;
-    const bool col_in = walker && xg0 + wx >= 0 && xg0 + wx < W;
-    float sh[NS];
+    const bool walker = group < 3 && wx < gm.Wi;
+    const int gxw = x0 - r + wx;
+    // outside the image the staged values are zero, so a zero shift keeps them zero
+    const bool col_in = gxw >= 0 && gxw < W;
+    float shl[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) sh[k] = s_cta[k];
+    for (int k = 0; k < NS; ++k) shl[k] = col_in ? s_cta[k] : 0.f;
+    const int scol = wx + (gm.RA - r);
 
     float V[C::GMAX];
 #pragma unroll
@@ -311,57 +418,36 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
                 if (yc < y1) {
                     const bool ein_ok = yc + r >= 0 && yc + r < H;
                     const bool lout_ok = yc - r - 1 >= first_row && yc - r - 1 >= 0;
-                    const float *se = stage + (size_t)(b * NS) * Wi_pad + wx;
-                    const float *sl = stage + (size_t)((kB + b) * NS) * Wi_pad + wx;
+                    const float *se = stage + (size_t)(b * NS) * gm.WSt + scol;
+                    const float *sl = stage + (size_t)((kB + b) * NS) * gm.WSt + scol;
                     float e[NS], l[NS];
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        e[k] = (col_in && ein_ok) ? se[k * Wi_pad] - sh[k] : 0.f;
-                        l[k] = (col_in && lout_ok) ? sl[k * Wi_pad] - sh[k] : 0.f;
+                        e[k] = 0.f;
+                        l[k] = 0.f;
+                    }
+                    if (ein_ok) {
+#pragma unroll
+                        for (int k = 0; k < NS; ++k) e[k] = se[k * gm.WSt] - shl[k];
+                    }
+                    if (lout_ok) {
+#pragma unroll
+                        for (int k = 0; k < NS; ++k) l[k] = sl[k * gm.WSt] - shl[k];
                     }
                     if (group == 0) walker_update<Q, 0, true>(V, e, l);
                     else if (group == 1) walker_update<Q, 1, true>(V, e, l);
                     else walker_update<Q, 2, true>(V, e, l);
                 }
-                walker_store_dispatch<Q>(group, V, Vbuf + (size_t)b * C::NCH * VS + wx, VS);
+                walker_store_dispatch<Q>(group, V, Vbuf + (size_t)b * C::NCH * gm.VS + wx, gm.VS);
             }
         }
         __syncthreads();
         // prefetch the next batch's rows while this one is summed and solved
-        if (yv + kB < y1) stage_batch<Q>(stage, Wi_pad, a, yv + kB, first_row, xg0, Wi, warp, lane);
+        if (yv + kB < y1) stage_batch<Q>(stage, gm, a, r, yv + kB, x0, warp, lane);
         if (yv + kB - 1 < y0) continue;  // warm-up batch: nothing to solve yet
 
-        // 2. H-pass, one thread per (row, channel), in place: slot xo <- sum V[xo..xo+2r].
-        //    Chunks of 8 outputs load all their operands before writing any slot.
-        for (int row = tid; row < kB * C::NCH; row += kThreads) {
-            float *p = Vbuf + (size_t)row * VS;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int k = 0;
-            for (; k + 4 <= 2 * r + 1; k += 4) {
-                s0 += p[k];
-                s1 += p[k + 1];
-                s2 += p[k + 2];
-                s3 += p[k + 3];
-            }
-            for (; k <= 2 * r; ++k) s0 += p[k];
-            float s = (s0 + s1) + (s2 + s3);
-            float vprev = 0.f;
-#pragma unroll 1
-            for (int xo = 0; xo < kTW; xo += 8) {
-                float add[8], old[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    add[t] = p[xo + t + 2 * r];
-                    old[t] = p[xo + t];
-                }
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    if (xo + t > 0) s += add[t] - vprev;
-                    vprev = old[t];
-                    p[xo + t] = s;
-                }
-            }
-        }
+        // 2. H-pass, one thread per (row, channel)
+        for (int row = tid; row < kB * C::NCH; row += kThreads) hsum_row<RT>(Vbuf + (size_t)row * gm.VS, r);
         __syncthreads();
         // 3. solve, one thread per pixel of the batch
         {
@@ -371,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
                 const float ny = (float)(min(yc + r, H - 1) - max(yc - r, 0) + 1);
                 const float nx = (float)(min(xc + r, W - 1) - max(xc - r, 0) + 1);
                 float A[Q][3], bv[3], mu[Q];
-                const bool low = solve_pixel<Q>(Vbuf + (size_t)b * C::NCH * VS + xo, VS, ny * nx,
+                const bool low = solve_pixel<Q>(Vbuf + (size_t)b * C::NCH * gm.VS + xo, gm.VS, ny * nx,
                                                 eps, tau, A, bv, mu);
                 // re-express the bias relative to the frame reference shift
 #pragma unroll
@@ -414,26 +500,49 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
     cp_async_wait_all();
 }
 
-template <int Q>
-cudaError_t launch_fwd_q(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
+// Radii with a compile-time specialisation (the radii of the 256x256 and 1080p workloads);
+// every other radius runs the generic kernel.
+__host__ __device__ constexpr bool specialised(int q, int r) { return q == 8 && (r == 5 || r == 8); }
+
+template <int Q, int RT>
+cudaError_t launch_fwd_qr(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
-    flr_fwd_kernel<Q><<<grid, kThreads, smem, st>>>(a);
+    flr_fwd_kernel<Q, RT><<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int Q>
-cudaError_t prepare_q(size_t smem)
+template <int Q, int RT>
+cudaError_t prepare_qr(size_t smem)
 {
-    return cudaFuncSetAttribute(flr_fwd_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(flr_fwd_kernel<Q, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
+}
+
+template <int Q>
+cudaError_t launch_fwd_q(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
+{
+    if constexpr (Q == 8) {
+        if (a.r == 8) return launch_fwd_qr<8, 8>(a, grid, smem, st);
+        if (a.r == 5) return launch_fwd_qr<8, 5>(a, grid, smem, st);
+    }
+    return launch_fwd_qr<Q, -1>(a, grid, smem, st);
+}
+
+template <int Q>
+cudaError_t prepare_q(int r, size_t smem)
+{
+    if constexpr (Q == 8) {
+        if (r == 8) return prepare_qr<8, 8>(smem);
+        if (r == 5) return prepare_qr<8, 5>(smem);
+    }
+    return prepare_qr<Q, -1>(smem);
 }
 
 template <int Q>
 size_t smem_q(int r)
 {
-    const int Wi = kTW + 2 * r;
-    const int Wi_pad = (Wi + 31) & ~31;
-    return sizeof(float) * ((size_t)kB * Chan<Q>::NCH * (Wi + 1) + (size_t)2 * kB * (Q + 3) * Wi_pad);
+    const FwdGeom gm(r, specialised(Q, r));
+    return sizeof(float) * ((size_t)kB * Chan<Q>::NCH * gm.VS + (size_t)2 * kB * (Q + 3) * gm.WSt);
 }
 
 }  // namespace
@@ -463,9 +572,9 @@ size_t fwd_smem_bytes(int q, int r)
     return 0;
 }
 
-cudaError_t fwd_prepare(int q, size_t smem)
+cudaError_t fwd_prepare(int q, int r, size_t smem)
 {
-    FLR_Q_DISPATCH(q, return prepare_q<QQ>(smem));
+    FLR_Q_DISPATCH(q, return prepare_q<QQ>(r, smem));
     return cudaErrorInvalidValue;
 }
 

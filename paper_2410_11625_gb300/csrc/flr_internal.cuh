@@ -129,7 +129,7 @@ struct Fp64Args {
 // Host-side launchers (defined in the .cu files; q is dispatched to a template).
 cudaError_t launch_fwd(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st);
 size_t fwd_smem_bytes(int q, int r);
-cudaError_t fwd_prepare(int q, size_t smem);
+cudaError_t fwd_prepare(int q, int r, size_t smem);
 cudaError_t launch_apply(int q, const ApplyArgs &a, cudaStream_t st);
 cudaError_t launch_fp64(int q, const Fp64Args &a, int n_sm, cudaStream_t st);
 

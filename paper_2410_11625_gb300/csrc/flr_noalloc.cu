@@ -41,6 +41,7 @@ std::mutex g_setup_mutex;
 unsigned char *g_scratch_ptr[kMaxDevices];  // device address of the array, per device
 int g_n_sm[kMaxDevices];
 size_t g_smem_ready[kMaxDevices][FLR_MAX_Q + 1];  // forward-kernel shared memory configured
+int g_smem_radius[kMaxDevices][FLR_MAX_Q + 1];     // ... for the kernel of this radius
 
 // Once per device, with that device current: the device address of the array (the host
 // symbol is only a stand-in and must never reach a kernel) and the SM count.
@@ -104,9 +105,10 @@ extern "C" int flr_denoise_noalloc(const flr_params *p, const float *guide, cons
     const size_t smem = flr::fwd_smem_bytes(q, p->radius);
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (g_smem_ready[dev][q] < smem) {
-            if (flr::fwd_prepare(q, smem) != cudaSuccess) return FLR_ERR_CUDA;
+        if (g_smem_ready[dev][q] < smem || g_smem_radius[dev][q] != p->radius) {
+            if (flr::fwd_prepare(q, p->radius, smem) != cudaSuccess) return FLR_ERR_CUDA;
             g_smem_ready[dev][q] = smem;
+            g_smem_radius[dev][q] = p->radius;
         }
     }
     unsigned char *base = g_scratch_ptr[dev];
