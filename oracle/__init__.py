@@ -51,6 +51,10 @@ def _load():
             ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp,
             ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
         lib.flr_oracle_forward.restype = ctypes.c_int
+        lib.flr_oracle_backward.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_int,
+            ctypes.c_double, dp, dp, dp, dp, dp]
+        lib.flr_oracle_backward.restype = ctypes.c_int
         lib.flr_oracle_threads.argtypes = []
         lib.flr_oracle_threads.restype = ctypes.c_int
         _lib = lib
@@ -108,3 +112,32 @@ def flr_forward(guide, radiance, radius, eps, coef_radius=0, map_guide=None,
     if st != 0:
         raise OracleError(f"flr_oracle_forward failed with status {st}")
     return (out, coef) if return_coef else out
+
+
+def flr_backward(guide, radiance, grad_out, radius, eps, coef_radius=0, map_guide=None):
+    """FP64 gradient of <grad_out, FLR(guide, radiance)> (reverse-mode through Sec. 3.1-3.2).
+
+    Returns a dict with ``guide`` [Q,H,W], ``radiance`` [3,H,W], ``eps`` (float) and, when a
+    separate ``map_guide`` is given, ``map_guide`` [Q,H,W].  Without a map guide the guide
+    gradient includes the path through the applied guide.
+    """
+    rad = _as_f32(radiance)
+    g = _as_f32(guide)
+    q, H, W = g.shape
+    mg = _as_f32(map_guide)
+    go = np.ascontiguousarray(grad_out, dtype=np.float64)
+    if go.shape != (3, H, W):
+        raise ValueError("grad_out must be [3, H, W]")
+    gg = np.empty((q, H, W), np.float64)
+    gm = np.empty((q, H, W), np.float64) if mg is not None else None
+    gr = np.empty((3, H, W), np.float64)
+    ge = np.zeros(1, np.float64)
+    st = _load().flr_oracle_backward(q, H, W, _fptr(g), _fptr(mg), _fptr(rad), int(radius),
+                                     int(coef_radius), float(eps), _dptr(go), _dptr(gg),
+                                     _dptr(gm), _dptr(gr), _dptr(ge))
+    if st != 0:
+        raise OracleError(f"flr_oracle_backward failed with status {st}")
+    res = {"guide": gg, "radiance": gr, "eps": float(ge[0])}
+    if gm is not None:
+        res["map_guide"] = gm
+    return res

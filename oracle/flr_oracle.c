@@ -261,3 +261,210 @@ int flr_oracle_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * FLR backward pass in FP64: the gradient of L = <grad_out, I> with respect to the guides,
+ * the map guides, the radiance and eps, for the forward pass above.
+ *
+ * The paper trains through FLR by backpropagation (Sec. 3.2: the window's sigma and the
+ * regularisers are learned; Sec. 3.3: FLNR "builds on a differentiable implementation of
+ * FLR") but prints no adjoint.  This is the reverse-mode derivative of the forward's steps
+ * in reverse order, with g = grad_out:
+ *   apply      I_i = Abar_i^T (1, z_i):      G(Abar_i) = (1, z_i) g_i^T,  dz_i = abar_i g_i
+ *   average    Abar_i = mean_{k in T'_i} A_k: G(A_k) = sum_{i: k in T'_i} G(Abar_i) / m_i
+ *   bias       b = nu - a^T mu:              G(nu) = Gb,  Ga' = Ga - mu Gb^T,  G(mu) = -a Gb
+ *   solve      a = M^{-1} D:                 GD = M^{-1} Ga',  GM = -(GD a^T + a GD^T)/2
+ *   regulariser M = W + eps I:               G(eps) = trace(GM)
+ *   centring   W = S/n - mu mu^T, D = XY/n - mu nu^T:
+ *                  GS = GM/n, GXY = GD/n, G(mu) += -2 GM mu - GD nu, G(nu) += -GD^T mu
+ *   means      mu = Sx/n, nu = Sy/n:         GSx = G(mu)/n, GSy = G(nu)/n
+ *   window sums (S = sum x x^T, XY = sum x y^T over T_k; j in T_k <=> k in T_j):
+ *      dx_j = sum_{k in T_j} GSx_k + 2 GS_k x_j + GXY_k y_j
+ *      dy_j = sum_{k in T_j} GSy_k + GXY_k^T x_j
+ *
+ *   grad_out     [3][H][W] double
+ *   grad_guide   [q][H][W] double (model-guide gradient; when map_guide is NULL the map
+ *                guide is the guide and its gradient is added here as well)
+ *   grad_map     [q][H][W] double or NULL (only with a separate map_guide)
+ *   grad_rad     [3][H][W] double
+ *   grad_eps     double* or NULL
+ * Returns 0, or the forward's error codes.
+ */
+int flr_oracle_backward(int q, int H, int W, const float *guide, const float *map_guide,
+                        const float *radiance, int r, int rc, double eps, const double *grad_out,
+                        double *grad_guide, double *grad_map, double *grad_rad, double *grad_eps)
+{
+    if (q < 1 || q > ORACLE_MAX_Q || H <= 0 || W <= 0 || r < 0 || rc < 0 || !(eps >= 0.0))
+        return -1;
+    if (!guide || !radiance || !grad_out || !grad_guide || !grad_rad) return -1;
+    const float *zg = map_guide ? map_guide : guide;
+    const int q1 = q + 1;
+    const size_t P = (size_t)H * W;
+    const int ncoef = q1 * 3;
+
+    /* forward quantities: per-pixel models A_k (before averaging), via the forward pass */
+    double *A = malloc(sizeof(double) * P * ncoef);
+    double *outf = malloc(sizeof(double) * P * 3);
+    double *xx = malloc(sizeof(double) * P * (q1 * (q1 + 1) / 2));
+    double *plane = malloc(sizeof(double) * P);
+    double *tmp = malloc(sizeof(double) * P);
+    double *GA = malloc(sizeof(double) * P * ncoef);      /* G(A_k) after the average */
+    double *GS = malloc(sizeof(double) * P * (q * q + 3 * q + q + 3)); /* per-k gradients */
+    int status = 0;
+    if (!A || !outf || !xx || !plane || !tmp || !GA || !GS) { status = -2; goto done; }
+    status = flr_oracle_forward(q, H, W, guide, map_guide, radiance, r, rc, eps, outf, A);
+    if (status) goto done;
+
+    /* window sums again (the forward recomputed, Sec. 3.2), for n, mu, nu and M */
+    const int nxx = q1 * (q1 + 1) / 2;
+    double *xy = malloc(sizeof(double) * P * q1 * 3);
+    if (!xy) { status = -2; goto done; }
+    for (size_t p = 0; p < P; ++p) {
+        double x[ORACLE_MAX_Q + 1], y[3];
+        x[0] = 1.0;
+        for (int i = 0; i < q; ++i) x[i + 1] = (double)guide[(size_t)i * P + p];
+        for (int c = 0; c < 3; ++c) y[c] = (double)radiance[(size_t)c * P + p];
+        for (int i = 0; i < q1; ++i)
+            for (int j = i; j < q1; ++j) xx[(size_t)tri_index(q1, i, j) * P + p] = x[i] * x[j];
+        for (int i = 0; i < q1; ++i)
+            for (int c = 0; c < 3; ++c) xy[(size_t)(i * 3 + c) * P + p] = x[i] * y[c];
+    }
+    for (int m = 0; m < nxx; ++m) {
+        memcpy(plane, xx + (size_t)m * P, sizeof(double) * P);
+        box_sum_plane(plane, xx + (size_t)m * P, tmp, H, W, r);
+    }
+    for (int m = 0; m < q1 * 3; ++m) {
+        memcpy(plane, xy + (size_t)m * P, sizeof(double) * P);
+        box_sum_plane(plane, xy + (size_t)m * P, tmp, H, W, r);
+    }
+
+    /* apply: G(Abar_i) = (1, z_i) g_i^T / m_i (divided by m_i ready for the average's
+     * adjoint), and the map-guide gradient abar_i g_i */
+    double *abar = malloc(sizeof(double) * P * ncoef);
+    if (!abar) { free(xy); status = -2; goto done; }
+    memcpy(abar, A, sizeof(double) * P * ncoef);
+    if (rc > 0) {
+        for (int m = 0; m < ncoef; ++m) {
+            memcpy(plane, abar + (size_t)m * P, sizeof(double) * P);
+            box_sum_plane(plane, abar + (size_t)m * P, tmp, H, W, rc);
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x)
+                    abar[(size_t)m * P + (size_t)y * W + x] /= window_count(y, x, H, W, rc);
+        }
+    }
+    double *gz = map_guide ? grad_map : grad_guide; /* may be NULL with a separate map guide */
+    memset(grad_guide, 0, sizeof(double) * P * q);
+    if (map_guide && grad_map) memset(grad_map, 0, sizeof(double) * P * q);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const double m_i = rc > 0 ? window_count(y, x, H, W, rc) : 1.0;
+            for (int c = 0; c < 3; ++c) {
+                const double g = grad_out[(size_t)c * P + p];
+                GA[(size_t)(0 * 3 + c) * P + p] = g / m_i;
+                for (int i = 0; i < q; ++i) {
+                    GA[(size_t)((i + 1) * 3 + c) * P + p] = (double)zg[(size_t)i * P + p] * g / m_i;
+                    if (gz) gz[(size_t)i * P + p] += abar[(size_t)((i + 1) * 3 + c) * P + p] * g;
+                }
+            }
+        }
+    free(abar);
+    /* average: G(A_k) = sum over i with k in T'_i of G(Abar_i) / m_i */
+    if (rc > 0) {
+        for (int m = 0; m < ncoef; ++m) {
+            memcpy(plane, GA + (size_t)m * P, sizeof(double) * P);
+            box_sum_plane(plane, GA + (size_t)m * P, tmp, H, W, rc);
+        }
+    }
+
+    /* per-pixel adjoint of bias, solve, regulariser, centring and means.
+     * GS layout per pixel: [q*q] GS (full symmetric), [3q] GXY, [q] GSx, [3] GSy */
+    const int ng = q * q + 3 * q + q + 3;
+    double geps = 0.0;
+    for (size_t p = 0; p < P; ++p) {
+        const double n = xx[(size_t)tri_index(q1, 0, 0) * P + p];
+        double mu[ORACLE_MAX_Q], nu[3], M[ORACLE_MAX_Q * ORACLE_MAX_Q], a[ORACLE_MAX_Q * 3];
+        double Gb[3], Gap[ORACLE_MAX_Q * 3], GD[ORACLE_MAX_Q * 3], GM[ORACLE_MAX_Q * ORACLE_MAX_Q];
+        double Gmu[ORACLE_MAX_Q], Gnu[3];
+        for (int i = 0; i < q; ++i) mu[i] = xx[(size_t)tri_index(q1, 0, i + 1) * P + p] / n;
+        for (int c = 0; c < 3; ++c) nu[c] = xy[(size_t)c * P + p] / n;
+        for (int i = 0; i < q; ++i)
+            for (int j = 0; j < q; ++j) {
+                int lo = i < j ? i : j, hi = i < j ? j : i;
+                M[i * q + j] = xx[(size_t)tri_index(q1, lo + 1, hi + 1) * P + p] / n - mu[i] * mu[j] +
+                               (i == j ? eps : 0.0);
+            }
+        for (int i = 0; i < q; ++i)
+            for (int c = 0; c < 3; ++c) a[i * 3 + c] = A[(size_t)((i + 1) * 3 + c) * P + p];
+        for (int c = 0; c < 3; ++c) Gb[c] = GA[(size_t)c * P + p];
+        /* bias b = nu - a^T mu */
+        for (int c = 0; c < 3; ++c) Gnu[c] = Gb[c];
+        for (int i = 0; i < q; ++i) {
+            Gmu[i] = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                Gap[i * 3 + c] = GA[(size_t)((i + 1) * 3 + c) * P + p] - mu[i] * Gb[c];
+                Gmu[i] -= a[i * 3 + c] * Gb[c];
+            }
+        }
+        /* solve a = M^{-1} D: GD = M^{-1} Ga', GM = -(GD a^T + a GD^T) / 2 */
+        if (cholesky_solve(q, M, Gap, 3, GD) != 0) { status = -3; break; }
+        for (int i = 0; i < q; ++i)
+            for (int j = 0; j < q; ++j) {
+                double s = 0.0;
+                for (int c = 0; c < 3; ++c) s += GD[i * 3 + c] * a[j * 3 + c] + a[i * 3 + c] * GD[j * 3 + c];
+                GM[i * q + j] = -0.5 * s;
+            }
+        for (int i = 0; i < q; ++i) geps += GM[i * q + i];
+        /* centring W = S/n - mu mu^T, D = XY/n - mu nu^T */
+        for (int i = 0; i < q; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < q; ++j) s += GM[i * q + j] * mu[j];
+            Gmu[i] -= 2.0 * s;
+            for (int c = 0; c < 3; ++c) Gmu[i] -= GD[i * 3 + c] * nu[c];
+        }
+        for (int c = 0; c < 3; ++c)
+            for (int i = 0; i < q; ++i) Gnu[c] -= GD[i * 3 + c] * mu[i];
+        double *gs = GS + (size_t)p * ng;
+        for (int i = 0; i < q * q; ++i) gs[i] = GM[i] / n;
+        for (int i = 0; i < 3 * q; ++i) gs[q * q + i] = GD[i] / n;
+        for (int i = 0; i < q; ++i) gs[q * q + 3 * q + i] = Gmu[i] / n;
+        for (int c = 0; c < 3; ++c) gs[q * q + 4 * q + c] = Gnu[c] / n;
+    }
+    free(xy);
+    if (status) goto done;
+    if (grad_eps) *grad_eps = geps;
+
+    /* window sums of the per-k gradients, contracted with the inputs at j */
+    for (int m = 0; m < ng; ++m) {
+        for (size_t p = 0; p < P; ++p) plane[p] = GS[p * ng + m];
+        box_sum_plane(plane, plane, tmp, H, W, r);
+        for (size_t p = 0; p < P; ++p) GS[p * ng + m] = plane[p];
+    }
+    for (size_t p = 0; p < P; ++p) {
+        const double *gs = GS + p * ng;
+        double x[ORACLE_MAX_Q], y[3];
+        for (int i = 0; i < q; ++i) x[i] = (double)guide[(size_t)i * P + p];
+        for (int c = 0; c < 3; ++c) y[c] = (double)radiance[(size_t)c * P + p];
+        for (int i = 0; i < q; ++i) {
+            double d = gs[q * q + 3 * q + i];
+            for (int j = 0; j < q; ++j) d += 2.0 * gs[i * q + j] * x[j];
+            for (int c = 0; c < 3; ++c) d += gs[q * q + i * 3 + c] * y[c];
+            grad_guide[(size_t)i * P + p] += d;
+        }
+        for (int c = 0; c < 3; ++c) {
+            double d = gs[q * q + 4 * q + c];
+            for (int i = 0; i < q; ++i) d += gs[q * q + i * 3 + c] * x[i];
+            grad_rad[(size_t)c * P + p] = d;
+        }
+    }
+
+done:
+    free(A);
+    free(outf);
+    free(xx);
+    free(plane);
+    free(tmp);
+    free(GA);
+    free(GS);
+    return status;
+}
