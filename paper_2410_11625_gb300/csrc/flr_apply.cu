@@ -128,33 +128,43 @@ __global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const ApplyArgs
                 asm volatile("cp.async.wait_group 0;\n" ::);
             }
             __syncthreads();  // plane p is in Tc for every thread
-            // horizontal sums: 16 outputs per item, operands held in registers
+            // horizontal sums: 16 outputs per item, operands held in registers; consecutive
+            // lanes take consecutive rows (16-byte loads, row stride = 4 mod 8 floats: the
+            // eight lanes of each 128-bit phase hit distinct banks)
             for (int item = tid; item < g.THh * 4; item += kAThreads) {
-                const int row = item >> 2, xr = (item & 3) * 16;
-                const float *q = Tc + row * g.TS + xr + xoff;
+                const int xr = (item / g.THh) * 16, row = item % g.THh;
+                const float *q = Tc + row * g.TS + xr;  // 16-byte aligned
                 float *h = Hb + row * g.HS + xr;
                 if constexpr (RT >= 0) {
-                    constexpr int N = 16 + 2 * RT;
+                    constexpr int RCA = (RT + 3) & ~3, XO = RCA - RT;
+                    constexpr int N = 16 + 2 * RCA;
                     float v[N];
 #pragma unroll
-                    for (int k = 0; k < N; ++k) v[k] = q[k];
+                    for (int k = 0; k < N; k += 4) {
+                        const float4 f = *reinterpret_cast<const float4 *>(q + k);
+                        v[k] = f.x;
+                        v[k + 1] = f.y;
+                        v[k + 2] = f.z;
+                        v[k + 3] = f.w;
+                    }
                     float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int k = 0; k <= 2 * RT; ++k) s4[k & 3] += v[k];
+                    for (int k = 0; k <= 2 * RT; ++k) s4[k & 3] += v[XO + k];
                     float s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
                     h[0] = s;
 #pragma unroll
                     for (int t = 1; t < 16; ++t) {
-                        s += v[t + 2 * RT] - v[t - 1];
+                        s += v[XO + t + 2 * RT] - v[XO + t - 1];
                         h[t] = s;
                     }
                 } else {
+                    const float *qq = q + xoff;
                     float s = 0.f;
-                    for (int k = 0; k <= 2 * rc; ++k) s += q[k];
+                    for (int k = 0; k <= 2 * rc; ++k) s += qq[k];
                     h[0] = s;
 #pragma unroll
                     for (int t = 1; t < 16; ++t) {
-                        s += q[t + 2 * rc] - q[t - 1];
+                        s += qq[t + 2 * rc] - qq[t - 1];
                         h[t] = s;
                     }
                 }

@@ -130,23 +130,25 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
                                             float (&mu)[Q])
 {
     using C = Chan<Q>;
+    // A one-pixel window (n = 1) has centred moments exactly zero.  Dividing the guide
+    // moments by infinity there (inv_nx = 0) makes mu = 0, M = eps I and D = 0 exactly,
+    // so a = 0 and b = mu_y, instead of leaving x x - x x to a rounding that 1/eps would
+    // amplify.
     const float inv_n = 1.0f / n;
+    const float inv_nx = n > 1.5f ? inv_n : 0.f;
     float muy[3];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) mu[i] = Sp[(C::X0 + i) * VS] * inv_n;
+    for (int i = 0; i < Q; ++i) mu[i] = Sp[(C::X0 + i) * VS] * inv_nx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) muy[c] = Sp[(C::Y0 + c) * VS] * inv_n;
-    // M = S/n - mu mu^T + eps I (lower triangle), D = XY/n - mu muy^T.  A one-pixel
-    // window (n = 1) has centred moments exactly zero; they are set so rather than left to
-    // the rounding of x x - x x, which 1/eps would amplify.
-    const float live = n > 1.5f ? 1.f : 0.f;
+    // M = S/n - mu mu^T + eps I (lower triangle), D = XY/n - mu muy^T
     float L[Q * (Q + 1) / 2];
 #pragma unroll
     for (int i = 0; i < Q; ++i)
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             if (j <= i) {
-                float m = live * fmaf(-mu[i], mu[j], Sp[C::xx(j, i) * VS] * inv_n);
+                float m = fmaf(-mu[i], mu[j], Sp[C::xx(j, i) * VS] * inv_nx);
                 if (i == j) m += eps;
                 L[tri(i, j)] = m;
             }
@@ -155,8 +157,7 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
 #pragma unroll
     for (int i = 0; i < Q; ++i)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            D[i][c] = live * fmaf(-mu[i], muy[c], Sp[C::xy(i, c) * VS] * inv_n);
+        for (int c = 0; c < 3; ++c) D[i][c] = fmaf(-mu[i], muy[c], Sp[C::xy(i, c) * VS] * inv_nx);
 
     // left-looking Cholesky M = L L^T, keeping 1 / L_jj.  Inner loops run to Q with a
     // predicate so that every loop unrolls completely and L stays in registers.
