@@ -105,6 +105,27 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide,
                 const float *radiance, float *out, int H, int W, void *stream);
 
 /*
+ * Gradient of L = <grad_out, I> through the FLR pass with the same inputs: the adjoint of
+ * every step of flr_denoise (the paper trains through FLR by backpropagation, Sec. 3.2,
+ * and builds FLNR on a differentiable FLR, Sec. 3.3).  The window moments and per-pixel
+ * solves are recomputed from the inputs, not stored by the forward call.
+ *   grad_out        [3][H][W]  dL/dI
+ *   grad_guide      [q][H][W]  dL/d guide; with map_guide == NULL it includes the path
+ *                              through the applied guide
+ *   grad_map_guide  [q][H][W]  dL/d map_guide, or NULL (ignored when map_guide is NULL)
+ *   grad_radiance   [3][H][W]  dL/d radiance
+ *   grad_eps        device pointer to one double receiving dL/d eps, or NULL
+ * All pointers are device pointers; outputs must not overlap inputs.  Pixels flagged by the
+ * pivot test get FP64 models, as in flr_denoise; the adjoint solve itself is FP32.  The
+ * first call at a frame size allocates the handle's backward workspace: 9 (Q+1) + 2 NCH
+ * floats per pixel for Q = FLR_MAX_Q, NCH = Q + 3 + Q(Q+1)/2 + 3Q (223 floats, 892 B).
+ * Errors: FLR_ERR_ARG, FLR_ERR_ALIGN, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_backward(flr_handle *h, const float *guide, const float *map_guide, const float *radiance,
+                 const float *grad_out, float *grad_guide, float *grad_map_guide, float *grad_radiance,
+                 double *grad_eps, int H, int W, void *stream);
+
+/*
  * The same pass on HOST images: copies guide, map_guide (if not NULL) and radiance to
  * handle-owned device staging, runs flr_denoise, copies the result back to `out`, and
  * waits for the stream.  Page-locked host memory gives asynchronous copies; pageable

@@ -45,6 +45,9 @@ struct flr_handle {
     size_t coef_px = 0;
     float *stage = nullptr;  // host-path staging: guide, map guide, radiance, out
     size_t stage_px = 0;
+    float *bwd = nullptr;  // backward workspace: models, fields/averaged models, G(A), GS, BS
+    size_t bwd_px = 0;
+    size_t adj_smem = 0;
     size_t fwd_smem = 0;
     cudaStream_t last_stream = nullptr;
     // instrumentation: launch counts, and event quadruples per call with FLR_FLAG_TIMING
@@ -156,6 +159,10 @@ int flr_create(const flr_params *params, flr_handle **out)
         h->fwd_smem = flr::fwd_smem_bytes(h->p.q, h->p.radius);
         e = flr::fwd_prepare(h->p.q, h->p.radius, h->fwd_smem);
     }
+    if (e == cudaSuccess) {
+        h->adj_smem = flr::adj_smem_bytes(h->p.q, h->p.radius);
+        e = flr::adj_prepare(h->p.q, h->p.radius, h->adj_smem);
+    }
     if (e != cudaSuccess) {
         cuda_fail(e, "flr_create");
         flr_destroy(h);
@@ -174,6 +181,7 @@ int flr_destroy(flr_handle *h)
     cudaFree(h->d_flags);
     cudaFree(h->d_coef);
     cudaFree(h->stage);
+    cudaFree(h->bwd);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     delete h;
     return FLR_OK;
@@ -224,6 +232,10 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
     fa.flag_list = h->d_flags;
     fa.flag_cap = h->flag_cap;
     fa.shift_out = h->d_shift;
+    fa.force_coef = 0;
+    fa.gA = nullptr;
+    fa.gS = nullptr;
+    fa.geps = nullptr;
     dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
     FLR_CUDA(mark(h, s), "timing event");
     FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "forward kernel launch");
@@ -246,6 +258,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
         da.flag_count = h->d_count;
         da.flag_list = h->d_flags;
         da.flag_cap = h->flag_cap;
+        da.force_coef = 0;
         FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "fp64 re-solve launch");
         ++h->n_fp64;
     }
@@ -263,6 +276,128 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
         ++h->n_apply;
     }
     FLR_CUDA(mark(h, s), "timing event");
+    return FLR_OK;
+}
+
+int flr_backward(flr_handle *h, const float *guide, const float *map_guide, const float *radiance,
+                 const float *grad_out, float *grad_guide, float *grad_map_guide, float *grad_radiance,
+                 double *grad_eps, int H, int W, void *stream)
+{
+    if (!h || !guide || !radiance || !grad_out || !grad_guide || !grad_radiance || H <= 0 || W <= 0)
+        return FLR_ERR_ARG;
+    if ((long long)H * W > 0x7fffffffLL) return FLR_ERR_ARG;
+    if (!aligned16(guide) || !aligned16(radiance) || !aligned16(grad_out) || !aligned16(grad_guide) ||
+        !aligned16(grad_radiance) || (map_guide && !aligned16(map_guide)) ||
+        (grad_map_guide && !aligned16(grad_map_guide)))
+        return FLR_ERR_ALIGN;
+    const int q = h->p.q;
+    const int nch = q + 3 + q * (q + 1) / 2 + 3 * q;
+    const int ncf = 3 * (q + 1);
+    const size_t px = (size_t)H * W;
+    int st = grow(h, H, W);
+    if (st != FLR_OK) return st;
+    if (h->bwd_px < px || !h->bwd) {
+        cudaFree(h->bwd);
+        h->bwd = nullptr;
+        h->bwd_px = 0;
+        const size_t planes = 3 * (size_t)(3 * (FLR_MAX_Q + 1)) + 2 * (size_t)(FLR_MAX_Q + 3 + FLR_MAX_Q * (FLR_MAX_Q + 1) / 2 + 3 * FLR_MAX_Q);
+        if (cudaMalloc(&h->bwd, px * planes * sizeof(float)) != cudaSuccess) return FLR_ERR_NOMEM;
+        h->bwd_px = px;
+    }
+    float *Acoef = h->bwd;                 // per-pixel models A_k
+    float *F = Acoef + (size_t)ncf * px;   // fields, later the box-averaged models
+    float *GA = F + (size_t)ncf * px;      // G(A_k)
+    float *GS = GA + (size_t)ncf * px;     // per-pixel moment gradients
+    float *BS = GS + (size_t)nch * px;     // their window sums
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const int r = h->p.radius, rc = h->p.coef_radius;
+
+    // 1. models A_k (forward kernel, coefficient output forced), FP64 re-solve of flagged pixels
+    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), s), "reset counter");
+    flr::FwdArgs fa;
+    fa.guide = guide;
+    fa.map_guide = map_guide;
+    fa.rad = radiance;
+    fa.out = nullptr;
+    fa.coef = Acoef;
+    fa.H = H;
+    fa.W = W;
+    fa.r = r;
+    fa.rc = rc;
+    fa.eps = h->p.eps;
+    fa.tau = h->p.pivot_ratio;
+    fa.TH = choose_segment_rows(H, W, r, h->n_sm);
+    fa.flag_count = h->d_count;
+    fa.flag_list = h->d_flags;
+    fa.flag_cap = h->flag_cap;
+    fa.shift_out = h->d_shift;
+    fa.force_coef = 1;
+    fa.gA = nullptr;
+    fa.gS = nullptr;
+    fa.geps = nullptr;
+    dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
+    FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "backward: model kernel launch");
+    if (h->p.pivot_ratio > 0.f) {
+        flr::Fp64Args da;
+        da.guide = guide;
+        da.map_guide = map_guide;
+        da.rad = radiance;
+        da.shift = h->d_shift;
+        da.out = nullptr;
+        da.coef = Acoef;
+        da.H = H;
+        da.W = W;
+        da.r = r;
+        da.rc = rc;
+        da.eps = (double)h->p.eps;
+        da.flag_count = h->d_count;
+        da.flag_list = h->d_flags;
+        da.flag_cap = h->flag_cap;
+        da.force_coef = 1;
+        FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "backward: fp64 re-solve launch");
+    }
+    // 2. adjoint of the apply and of the average: G(A_k)
+    const float *z = map_guide ? map_guide : guide;
+    FLR_CUDA(flr::launch_bwd_fields(q, grad_out, z, h->d_shift, F, H, W, rc, s), "backward: fields launch");
+    const float *gA = F;
+    if (rc > 0) {
+        FLR_CUDA(flr::launch_box_sum(F, GA, ncf, H, W, rc, s), "backward: average adjoint launch");
+        gA = GA;
+    }
+    // 3. per-pixel adjoint solve (moments recomputed) -> GS, d/d eps
+    if (grad_eps) FLR_CUDA(cudaMemsetAsync(grad_eps, 0, sizeof(double), s), "backward: reset eps gradient");
+    double *geps = grad_eps;
+    if (!geps) {
+        geps = (double *)(BS + (size_t)nch * px);  // unused slot at the end of the workspace
+    }
+    fa.gA = gA;
+    fa.gS = GS;
+    fa.geps = geps;
+    fa.force_coef = 0;
+    FLR_CUDA(flr::launch_adj(q, fa, grid, h->adj_smem, s), "backward: adjoint kernel launch");
+    // 4. adjoint of the window sums, the averaged models for the applied guide, contraction
+    FLR_CUDA(flr::launch_box_sum(GS, BS, nch, H, W, r, s), "backward: window-sum adjoint launch");
+    const float *BA = Acoef;
+    if (rc > 0) {
+        FLR_CUDA(flr::launch_box_sum(Acoef, F, ncf, H, W, rc, s), "backward: model average launch");
+        BA = F;
+    }
+    flr::BwdArgs ba;
+    ba.guide = guide;
+    ba.rad = radiance;
+    ba.shift = h->d_shift;
+    ba.g = grad_out;
+    ba.BS = BS;
+    ba.BA = BA;
+    ba.grad_guide = grad_guide;
+    ba.grad_map = grad_map_guide;
+    ba.grad_rad = grad_radiance;
+    ba.H = H;
+    ba.W = W;
+    ba.rc = rc;
+    ba.separate_map = map_guide != nullptr;
+    FLR_CUDA(flr::launch_bwd_contract(q, ba, s), "backward: contraction launch");
     return FLR_OK;
 }
 

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kDThreads) flr_fp64_kernel(const Fp64Args a)
             for (int i = 0; i < Q; ++i) b -= A[i][c] * (mu[i] + (cen[i] - (double)s[i]));
             bv[c] = b;
         }
-        if (a.rc == 0) {
+        if (a.rc == 0 && !a.force_coef) {
             const float *zg = a.map_guide ? a.map_guide : a.guide;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {

@@ -122,12 +122,133 @@ __device__ __forceinline__ void walker_store_dispatch(int group, const float (&V
 
 __device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
+// X = M^{-1} B for the factor M = L L^T (packed lower triangle, 1/L_jj in inv_d), 3 RHS.
+template <int Q>
+__device__ __forceinline__ void chol_solve3(const float (&L)[Q * (Q + 1) / 2], const float (&inv_d)[Q],
+                                            const float (&B)[Q][3], float (&X)[Q][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float z[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float t = B[i][c];
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (k < i) t = fmaf(-L[tri(i, k)], z[k], t);
+            z[i] = t * inv_d[i];
+        }
+#pragma unroll
+        for (int ii = 0; ii < Q; ++ii) {
+            const int i = Q - 1 - ii;
+            float t = z[i];
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (k > i) t = fmaf(-L[tri(k, i)], X[k][c], t);
+            X[i][c] = t * inv_d[i];
+        }
+    }
+}
+
+// Adjoint of one pixel's model (the reverse of bias, solve, regulariser, centring and
+// means), given G(b), G(a) relative to the frame reference shift.  Writes the per-pixel
+// gradients of the window sums, in moment-channel order, re-expressed so that the
+// contraction with (x - s_ref, y - s_ref) gives the input gradients; returns d/d eps.
+template <int Q>
+__device__ __forceinline__ float adjoint_pixel(const float (&A)[Q][3], const float (&mu)[Q],
+                                               const float (&muy)[3], const float (&L)[Q * (Q + 1) / 2],
+                                               const float (&inv_d)[Q], float n, const float *gA,
+                                               float *gS, size_t plane, size_t off, const float *s_cta,
+                                               const float *s_ref)
+{
+    using C = Chan<Q>;
+    float Gb[3], Gap[Q][3], Gmu[Q], Gnu[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Gb[c] = __ldg(gA + c * plane + off);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float dl = s_cta[i] - s_ref[i];
+        Gmu[i] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // b_ref = b + (s_cta_y - s_ref_y) - a^T (s_cta - s_ref), then b = muy - a^T mu
+            const float ga = __ldg(gA + (3 * (i + 1) + c) * plane + off) - dl * Gb[c];
+            Gap[i][c] = fmaf(-mu[i], Gb[c], ga);
+            Gmu[i] = fmaf(-A[i][c], Gb[c], Gmu[i]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Gnu[c] = Gb[c];
+    float GD[Q][3];
+    chol_solve3<Q>(L, inv_d, Gap, GD);
+    const float inv_n = 1.0f / n;
+    const float live = n > 1.5f ? inv_n : 0.f;  // one-pixel window: the model path is constant
+    float geps = 0.f;
+    float Gxx[Q * (Q + 1) / 2];
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            if (j <= i) {
+                float t = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) t = fmaf(GD[i][c], A[j][c], fmaf(A[i][c], GD[j][c], t));
+                const float gm = -0.5f * t;
+                if (i == j) geps += gm;
+                Gxx[tri(i, j)] = gm;
+                Gmu[i] = fmaf(-2.f * gm, mu[j], Gmu[i]);
+                if (j != i) Gmu[j] = fmaf(-2.f * gm, mu[i], Gmu[j]);
+            }
+        }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Gmu[i] = fmaf(-GD[i][c], muy[c], Gmu[i]);
+            Gnu[c] = fmaf(-GD[i][c], mu[i], Gnu[c]);
+        }
+    // scale by 1/n and move the linear terms from the CTA shift to the frame shift
+    float dl[Q], dly[3];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dl[i] = s_cta[i] - s_ref[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dly[c] = s_cta[Q + c] - s_ref[Q + c];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float gx = Gmu[i];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) gx = fmaf(-2.f * Gxx[i >= j ? tri(i, j) : tri(j, i)], dl[j], gx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gx = fmaf(-GD[i][c], dly[c], gx);
+        gS[(C::X0 + i) * plane + off] = gx * live;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float gy = Gnu[c];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gy = fmaf(-GD[i][c], dl[i], gy);
+        // with n = 1 only the mean of y survives: G(nu) = G(b) exactly
+        gS[(C::Y0 + c) * plane + off] = (n > 1.5f ? gy : Gb[c]) * inv_n;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            if (j >= i) gS[C::xx(i, j) * plane + off] = Gxx[tri(j, i)] * live;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gS[C::xy(i, c) * plane + off] = GD[i][c] * live;
+    return geps;
+}
+
 // Centred ridge solve of one pixel from its window sums S(ch) = Sp[ch * VS].
 // Returns the model (a, b) in the CTA-shifted coordinates and whether a pivot fell low.
 template <int Q>
 __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, float eps,
                                             float tau, float (&A)[Q][3], float (&bv)[3],
-                                            float (&mu)[Q])
+                                            float (&mu)[Q], float (&muy)[3],
+                                            float (&L)[Q * (Q + 1) / 2], float (&inv_d)[Q])
 {
     using C = Chan<Q>;
     // A one-pixel window (n = 1) has centred moments exactly zero.  Dividing the guide
@@ -136,13 +257,11 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
     // amplify.
     const float inv_n = 1.0f / n;
     const float inv_nx = n > 1.5f ? inv_n : 0.f;
-    float muy[3];
 #pragma unroll
     for (int i = 0; i < Q; ++i) mu[i] = Sp[(C::X0 + i) * VS] * inv_nx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) muy[c] = Sp[(C::Y0 + c) * VS] * inv_n;
     // M = S/n - mu mu^T + eps I (lower triangle), D = XY/n - mu muy^T
-    float L[Q * (Q + 1) / 2];
 #pragma unroll
     for (int i = 0; i < Q; ++i)
 #pragma unroll
@@ -162,7 +281,6 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
     // left-looking Cholesky M = L L^T, keeping 1 / L_jj.  Inner loops run to Q with a
     // predicate so that every loop unrolls completely and L stays in registers.
     bool low = false;
-    float inv_d[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const float mjj = L[tri(j, j)];
@@ -356,7 +474,7 @@ __device__ __forceinline__ void hsum_row(float *p, int r)
     }
 }
 
-template <int Q, int RT>
+template <int Q, int RT, bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
 {
     using C = Chan<Q>;
@@ -408,6 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
 
     const float tau = a.tau;
     const float eps = a.eps;
+    float geps_acc = 0.f;  // adjoint mode: this thread's share of d L / d eps
     for (; yv < y1; yv += kB) {
         // 1. V-pass over the staged rows
         cp_async_wait_all();
@@ -457,40 +576,45 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
             if (yc >= y0 && yc < y1 && xc < W) {
                 const float ny = (float)(min(yc + r, H - 1) - max(yc - r, 0) + 1);
                 const float nx = (float)(min(xc + r, W - 1) - max(xc - r, 0) + 1);
-                float A[Q][3], bv[3], mu[Q];
+                float A[Q][3], bv[3], mu[Q], muy[3], L[Q * (Q + 1) / 2], inv_d[Q];
                 const bool low = solve_pixel<Q>(Vbuf + (size_t)b * C::NCH * gm.VS + xo, gm.VS, ny * nx,
-                                                eps, tau, A, bv, mu);
-                // re-express the bias relative to the frame reference shift
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float bb = bv[c] + (s_cta[Q + c] - s_ref[Q + c]);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) bb = fmaf(-A[i][c], s_cta[i] - s_ref[i], bb);
-                    bv[c] = bb;
-                }
+                                                eps, tau, A, bv, mu, muy, L, inv_d);
                 const size_t plane = (size_t)H * W;
                 const size_t off = (size_t)yc * W + xc;
-                if (a.rc == 0) {
-                    const float *zg = a.map_guide ? a.map_guide : a.guide;
-                    float z[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) z[i] = __ldg(zg + i * plane + off) - s_ref[i];
+                if constexpr (ADJ) {
+                    geps_acc += adjoint_pixel<Q>(A, mu, muy, L, inv_d, ny * nx, a.gA, a.gS, plane, off,
+                                                 s_cta, s_ref);
+                } else {
+                    // re-express the bias relative to the frame reference shift
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        float o = bv[c];
+                        float bb = bv[c] + (s_cta[Q + c] - s_ref[Q + c]);
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) o = fmaf(A[i][c], z[i], o);
-                        a.out[c * plane + off] = o + s_ref[Q + c];
+                        for (int i = 0; i < Q; ++i) bb = fmaf(-A[i][c], s_cta[i] - s_ref[i], bb);
+                        bv[c] = bb;
                     }
-                } else {
+                    if (a.rc == 0 && !a.force_coef) {
+                        const float *zg = a.map_guide ? a.map_guide : a.guide;
+                        float z[Q];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) a.coef[c * plane + off] = bv[c];
+                        for (int i = 0; i < Q; ++i) z[i] = __ldg(zg + i * plane + off) - s_ref[i];
 #pragma unroll
-                    for (int i = 0; i < Q; ++i)
+                        for (int c = 0; c < 3; ++c) {
+                            float o = bv[c];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) a.coef[(3 * (i + 1) + c) * plane + off] = A[i][c];
+                            for (int i = 0; i < Q; ++i) o = fmaf(A[i][c], z[i], o);
+                            a.out[c * plane + off] = o + s_ref[Q + c];
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) a.coef[c * plane + off] = bv[c];
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.coef[(3 * (i + 1) + c) * plane + off] = A[i][c];
+                    }
                 }
-                if (low && tau > 0.f) {
+                if (!ADJ && low && tau > 0.f) {
                     const unsigned long long slot = atomicAdd(a.flag_count, 1ull);
                     if (slot < (unsigned long long)a.flag_cap) a.flag_list[slot] = (int)off;
                 }
@@ -499,83 +623,107 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
         __syncthreads();
     }
     cp_async_wait_all();
+    if constexpr (ADJ) {
+        double g = (double)geps_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        if (lane == 0 && g != 0.0) atomicAdd(a.geps, g);
+    }
 }
 
 // Radii with a compile-time specialisation (the radii of the 256x256 and 1080p workloads);
 // every other radius runs the generic kernel.
 __host__ __device__ constexpr bool specialised(int q, int r) { return q == 8 && (r == 5 || r == 8); }
 
-template <int Q, int RT>
+template <int Q, int RT, bool ADJ>
 cudaError_t launch_fwd_qr(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
-    flr_fwd_kernel<Q, RT><<<grid, kThreads, smem, st>>>(a);
+    flr_fwd_kernel<Q, RT, ADJ><<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int Q, int RT>
+template <int Q, int RT, bool ADJ>
 cudaError_t prepare_qr(size_t smem)
 {
-    return cudaFuncSetAttribute(flr_fwd_kernel<Q, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(flr_fwd_kernel<Q, RT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }
 
-template <int Q>
+template <int Q, bool ADJ>
 cudaError_t launch_fwd_q(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
-    if constexpr (Q == 8) {
-        if (a.r == 8) return launch_fwd_qr<8, 8>(a, grid, smem, st);
-        if (a.r == 5) return launch_fwd_qr<8, 5>(a, grid, smem, st);
+    if constexpr (Q == 8 && !ADJ) {
+        if (a.r == 8) return launch_fwd_qr<8, 8, false>(a, grid, smem, st);
+        if (a.r == 5) return launch_fwd_qr<8, 5, false>(a, grid, smem, st);
     }
-    return launch_fwd_qr<Q, -1>(a, grid, smem, st);
+    return launch_fwd_qr<Q, -1, ADJ>(a, grid, smem, st);
 }
 
-template <int Q>
+template <int Q, bool ADJ>
 cudaError_t prepare_q(int r, size_t smem)
 {
-    if constexpr (Q == 8) {
-        if (r == 8) return prepare_qr<8, 8>(smem);
-        if (r == 5) return prepare_qr<8, 5>(smem);
+    if constexpr (Q == 8 && !ADJ) {
+        if (r == 8) return prepare_qr<8, 8, false>(smem);
+        if (r == 5) return prepare_qr<8, 5, false>(smem);
     }
-    return prepare_qr<Q, -1>(smem);
+    return prepare_qr<Q, -1, ADJ>(smem);
 }
 
 template <int Q>
-size_t smem_q(int r)
+size_t smem_q(int r, bool adj)
 {
-    const FwdGeom gm(r, specialised(Q, r));
+    const FwdGeom gm(r, !adj && specialised(Q, r));
     return sizeof(float) * ((size_t)kB * Chan<Q>::NCH * gm.VS + (size_t)2 * kB * (Q + 3) * gm.WSt);
 }
 
 }  // namespace
 
-#define FLR_Q_DISPATCH(q, CALL)  \
+#define FLR_Q_DISPATCH(q, ...)  \
     switch (q) {                 \
-    case 1: { constexpr int QQ = 1; CALL; } \
-    case 2: { constexpr int QQ = 2; CALL; } \
-    case 3: { constexpr int QQ = 3; CALL; } \
-    case 4: { constexpr int QQ = 4; CALL; } \
-    case 5: { constexpr int QQ = 5; CALL; } \
-    case 6: { constexpr int QQ = 6; CALL; } \
-    case 7: { constexpr int QQ = 7; CALL; } \
-    case 8: { constexpr int QQ = 8; CALL; } \
+    case 1: { constexpr int QQ = 1; __VA_ARGS__; } \
+    case 2: { constexpr int QQ = 2; __VA_ARGS__; } \
+    case 3: { constexpr int QQ = 3; __VA_ARGS__; } \
+    case 4: { constexpr int QQ = 4; __VA_ARGS__; } \
+    case 5: { constexpr int QQ = 5; __VA_ARGS__; } \
+    case 6: { constexpr int QQ = 6; __VA_ARGS__; } \
+    case 7: { constexpr int QQ = 7; __VA_ARGS__; } \
+    case 8: { constexpr int QQ = 8; __VA_ARGS__; } \
     default: break;              \
     }
 
 cudaError_t launch_fwd(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
-    FLR_Q_DISPATCH(q, return launch_fwd_q<QQ>(a, grid, smem, st));
+    FLR_Q_DISPATCH(q, return launch_fwd_q<QQ, false>(a, grid, smem, st));
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adj(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
+{
+    FLR_Q_DISPATCH(q, return launch_fwd_q<QQ, true>(a, grid, smem, st));
     return cudaErrorInvalidValue;
 }
 
 size_t fwd_smem_bytes(int q, int r)
 {
-    FLR_Q_DISPATCH(q, return smem_q<QQ>(r));
+    FLR_Q_DISPATCH(q, return smem_q<QQ>(r, false));
+    return 0;
+}
+
+size_t adj_smem_bytes(int q, int r)
+{
+    FLR_Q_DISPATCH(q, return smem_q<QQ>(r, true));
     return 0;
 }
 
 cudaError_t fwd_prepare(int q, int r, size_t smem)
 {
-    FLR_Q_DISPATCH(q, return prepare_q<QQ>(r, smem));
+    FLR_Q_DISPATCH(q, return prepare_q<QQ, false>(r, smem));
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t adj_prepare(int q, int r, size_t smem)
+{
+    FLR_Q_DISPATCH(q, return prepare_q<QQ, true>(r, smem));
     return cudaErrorInvalidValue;
 }
 

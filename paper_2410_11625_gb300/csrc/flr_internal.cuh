@@ -108,6 +108,11 @@ struct FwdArgs {
     int *flag_list;                  // flagged pixel indices y * W + x
     int flag_cap;
     float *shift_out;  // frame reference shift (Q+3 floats), written by block (0, 0)
+    int force_coef;    // write the coefficient planes even when rc == 0 (backward pass)
+    // adjoint mode only: G(A_k) planes in, per-pixel moment gradients out, d/d eps
+    const float *gA;   // [(Q+1)*3][H][W]: row 0 = G(b_k), rows 1..Q = G(a_k)
+    float *gS;         // [NCH][H][W] in moment-channel order (see Chan)
+    double *geps;      // accumulated d L / d eps
 };
 
 struct ApplyArgs {
@@ -120,17 +125,34 @@ struct Fp64Args {
     const float *guide, *map_guide, *rad, *shift;
     float *out, *coef;
     int H, W, r, rc;
+    int force_coef;  // write the model to the coefficient planes even when rc == 0
     double eps;
     const unsigned long long *flag_count;
     const int *flag_list;
     int flag_cap;
 };
 
+struct BwdArgs {
+    const float *guide, *rad, *shift, *g;  // inputs, frame reference shift, dL/dI
+    const float *BS;                       // [NCH] box-summed moment gradients
+    const float *BA;                       // [(Q+1)*3] box-summed (rc > 0) or raw models
+    float *grad_guide, *grad_map, *grad_rad;
+    int H, W, rc;
+    int separate_map;                      // the map guide is not the model guide
+};
+
 // Host-side launchers (defined in the .cu files; q is dispatched to a template).
 cudaError_t launch_fwd(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t launch_adj(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t adj_prepare(int q, int r, size_t smem);
 size_t fwd_smem_bytes(int q, int r);
+size_t adj_smem_bytes(int q, int r);
 cudaError_t fwd_prepare(int q, int r, size_t smem);
 cudaError_t launch_apply(int q, const ApplyArgs &a, cudaStream_t st);
 cudaError_t launch_fp64(int q, const Fp64Args &a, int n_sm, cudaStream_t st);
+cudaError_t launch_bwd_fields(int q, const float *g, const float *z, const float *shift, float *F, int H, int W,
+                              int rc, cudaStream_t st);
+cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st);
+cudaError_t launch_bwd_contract(int q, const BwdArgs &a, cudaStream_t st);
 
 }  // namespace flr

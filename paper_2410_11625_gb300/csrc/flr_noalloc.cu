@@ -136,6 +136,10 @@ extern "C" int flr_denoise_noalloc(const flr_params *p, const float *guide, cons
     fa.flag_list = flags;
     fa.flag_cap = (int)kMaxPx;
     fa.shift_out = shift;
+    fa.force_coef = 0;
+    fa.gA = nullptr;
+    fa.gS = nullptr;
+    fa.geps = nullptr;
     dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
     if (flr::launch_fwd(q, fa, grid, smem, s) != cudaSuccess) return FLR_ERR_CUDA;
     if (p->pivot_ratio > 0.f) {
@@ -154,6 +158,7 @@ extern "C" int flr_denoise_noalloc(const flr_params *p, const float *guide, cons
         da.flag_count = count;
         da.flag_list = flags;
         da.flag_cap = (int)kMaxPx;
+        da.force_coef = 0;
         if (flr::launch_fp64(q, da, g_n_sm[dev], s) != cudaSuccess) return FLR_ERR_CUDA;
     }
     if (p->coef_radius > 0) {

@@ -18,7 +18,7 @@ STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA
 # every symbol include/flr.h declares
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
            "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
-           "flr_denoise_noalloc")
+           "flr_denoise_noalloc", "flr_backward")
 FLAG_TIMING = 1
 
 
@@ -72,6 +72,8 @@ def load_library():
     lib.flr_denoise_host.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
     lib.flr_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
     lib.flr_get_kernel_times.argtypes = [vp, ctypes.POINTER(FlrKernelTimes), ip]
+    lib.flr_backward.argtypes = [vp, fp, fp, fp, fp, fp, fp, fp, vp, ip, ip, vp]
+    lib.flr_backward.restype = ctypes.c_int
     lib.flr_denoise_noalloc.argtypes = [ctypes.POINTER(FlrParams), fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_noalloc.restype = ctypes.c_int
     lib.flr_status_string.argtypes = [ip]
@@ -155,6 +157,34 @@ class FLR:
         _check(load_library().flr_denoise(self._h, g, m, r, o, H, W, st), "flr_denoise")
         return out
 
+    def backward(self, guide, radiance, grad_out, map_guide=None, need_eps=False, stream=None):
+        """Device FLR adjoint: gradients of <grad_out, I> for guide, radiance, map guide
+        (when given) and eps.  Returns a dict of CUDA tensors (eps as a 1-element float64)."""
+        import torch
+        H, W = int(radiance.shape[-2]), int(radiance.shape[-1])
+        dev = radiance.device
+        g = _dev_ptr(guide, "guide", (self.q, H, W))
+        r = _dev_ptr(radiance, "radiance", (3, H, W))
+        go = _dev_ptr(grad_out, "grad_out", (3, H, W))
+        m = None if map_guide is None else _dev_ptr(map_guide, "map_guide", (self.q, H, W))
+        gg = torch.empty((self.q, H, W), dtype=torch.float32, device=dev)
+        gr = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+        gm = torch.empty((self.q, H, W), dtype=torch.float32, device=dev) if map_guide is not None else None
+        ge = torch.zeros(1, dtype=torch.float64, device=dev) if need_eps else None
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        st = load_library().flr_backward(
+            self._h, g, m, r, go, ctypes.c_void_p(gg.data_ptr()),
+            None if gm is None else ctypes.c_void_p(gm.data_ptr()), ctypes.c_void_p(gr.data_ptr()),
+            None if ge is None else ctypes.c_void_p(ge.data_ptr()), H, W, ctypes.c_void_p(stream.cuda_stream))
+        _check(st, "flr_backward")
+        res = {"guide": gg, "radiance": gr}
+        if gm is not None:
+            res["map_guide"] = gm
+        if ge is not None:
+            res["eps"] = ge
+        return res
+
     def denoise_host(self, guide, radiance, map_guide=None, out=None, stream=None):
         """Host FLR: numpy float32 in and out; copies and waits inside the library."""
         import numpy as np
@@ -193,3 +223,48 @@ def denoise(guide, radiance, radius=8, eps=1e-3, coef_radius=None, map_guide=Non
         import torch
         torch.cuda.current_stream(radiance.device).synchronize()
         f.close()
+
+
+def _autograd_function():
+    import torch
+
+    class FLRFunction(torch.autograd.Function):
+        """torch.autograd.Function around flr_denoise / flr_backward (CUDA tensors).
+
+        apply(handle, guide, radiance, map_guide=None) -> I; the backward pass recomputes
+        the window moments instead of keeping them from the forward.
+        """
+
+        @staticmethod
+        def forward(ctx, handle, guide, radiance, map_guide=None):
+            guide = guide.contiguous()
+            radiance = radiance.contiguous()
+            map_guide = None if map_guide is None else map_guide.contiguous()
+            ctx.handle = handle
+            ctx.has_map = map_guide is not None
+            if ctx.has_map:
+                ctx.save_for_backward(guide, radiance, map_guide)
+            else:
+                ctx.save_for_backward(guide, radiance)
+            return handle.denoise(guide, radiance, map_guide=map_guide)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            saved = ctx.saved_tensors
+            guide, radiance = saved[0], saved[1]
+            map_guide = saved[2] if ctx.has_map else None
+            res = ctx.handle.backward(guide, radiance, grad_out.contiguous(), map_guide=map_guide)
+            return None, res["guide"], res["radiance"], res.get("map_guide")
+
+    return FLRFunction
+
+
+_FLRFunction = None
+
+
+def flr_autograd(handle, guide, radiance, map_guide=None):
+    """Differentiable FLR: I = FLR(guide, radiance[, map_guide]) with CUDA-kernel backward."""
+    global _FLRFunction
+    if _FLRFunction is None:
+        _FLRFunction = _autograd_function()
+    return _FLRFunction.apply(handle, guide, radiance, map_guide)
