@@ -55,6 +55,10 @@ def _load():
             ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_int,
             ctypes.c_double, dp, dp, dp, dp, dp]
         lib.flr_oracle_backward.restype = ctypes.c_int
+        lib.flr_oracle_fast.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_int,
+            ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
+        lib.flr_oracle_fast.restype = ctypes.c_int
         lib.flr_oracle_threads.argtypes = []
         lib.flr_oracle_threads.restype = ctypes.c_int
         _lib = lib
@@ -141,3 +145,30 @@ def flr_backward(guide, radiance, grad_out, radius, eps, coef_radius=0, map_guid
     if gm is not None:
         res["map_guide"] = gm
     return res
+
+
+def flr_fast(guide, radiance, factor=8, sigma_blocks=1.25, taps=3, eps=1e-3, map_guide=None,
+             scale=1, return_coef=False):
+    """Fast FLR in FP64 (Sec. 3.2, and Sec. 3.2.1 when ``scale`` > 1).
+
+    guide [Q,Hi,Wi] and radiance [3,Hi,Wi] at the input resolution; map_guide [Q,Hi*scale,
+    Wi*scale] (None: the guide, scale 1).  Moments are summed over factor x factor blocks,
+    blurred by a Gaussian of ``sigma_blocks`` block units truncated at ``taps`` blocks,
+    solved per block and bilinearly interpolated.  Returns out [3,Ho,Wo] (float64) and
+    with ``return_coef`` the block models [(Q+1),3,Hb,Wb].
+    """
+    g = _as_f32(guide)
+    rad = _as_f32(radiance)
+    q, Hi, Wi = g.shape
+    mg = _as_f32(map_guide)
+    Ho, Wo = Hi * scale, Wi * scale
+    if mg is not None and mg.shape != (q, Ho, Wo):
+        raise ValueError("map_guide must be [Q, Hi*scale, Wi*scale]")
+    Hb, Wb = -(-Hi // factor), -(-Wi // factor)
+    out = np.empty((3, Ho, Wo), np.float64)
+    coef = np.empty((q + 1, 3, Hb, Wb), np.float64) if return_coef else None
+    st = _load().flr_oracle_fast(q, Hi, Wi, _fptr(g), _fptr(rad), _fptr(mg), int(factor), int(scale),
+                                 float(sigma_blocks), int(taps), float(eps), _dptr(out), _dptr(coef))
+    if st != 0:
+        raise OracleError(f"flr_oracle_fast failed with status {st}")
+    return (out, coef) if return_coef else out

@@ -468,3 +468,140 @@ done:
     free(GS);
     return status;
 }
+
+/*
+ * Fast FLR in FP64 (Sec. 3.2 "Fast Local Regression", and Sec. 3.2.1 for the joint
+ * denoising and upsampling): the paper's implementation choice for speed.
+ *   1. outer products x x^T, x y^T at every input pixel (x with its leading 1);
+ *   2. downsample: sum them over F x F blocks (the strided box filter of the first of the
+ *      paper's four kernels), clipped at the image border;
+ *   3. blur the block moments with a separable Gaussian of standard deviation sigma_b
+ *      block units (sigma / F for a full-resolution sigma), truncated at `taps` blocks and
+ *      clipped at the grid border (second kernel); this is the weighted least squares of
+ *      Sec. 3.2 with each pixel weighted by the Gaussian weight of its block;
+ *   4. per block the centred ridge model, as in flr_oracle_forward (third kernel);
+ *   5. bilinear interpolation of the block models to every output pixel and application
+ *      to the map guide there (fourth kernel).
+ * The output grid is s times finer than the input grid (s = 1: plain fast FLR; s > 1:
+ * joint denoising and upsampling, with model guides and radiance given at the input
+ * resolution and the map guide at the output resolution).  Block (i, j) has its centre at
+ * output coordinate ((i + 1/2) F s - 1/2, (j + 1/2) F s - 1/2); coordinates outside the
+ * outermost centres take the edge block's model.
+ *
+ *   guide      [q][Hi][Wi]  model guides;  radiance [3][Hi][Wi]
+ *   map_guide  [q][Ho][Wo] with Ho = Hi s, Wo = Wi s (NULL: the guide itself, s = 1 only)
+ *   out        [3][Ho][Wo] double;  coef: NULL or [(q+1)*3][Hb][Wb] block models
+ * Returns 0, -1 for bad arguments, -2 out of memory, -3 not positive definite.
+ */
+int flr_oracle_fast(int q, int Hi, int Wi, const float *guide, const float *radiance,
+                    const float *map_guide, int F, int s, double sigma_b, int taps, double eps,
+                    double *out, double *coef)
+{
+    if (q < 1 || q > ORACLE_MAX_Q || Hi <= 0 || Wi <= 0 || F < 1 || s < 1 || taps < 0 ||
+        !(sigma_b > 0.0) || !(eps >= 0.0) || !guide || !radiance || !out)
+        return -1;
+    if (!map_guide && s != 1) return -1;
+    if (!map_guide) map_guide = guide;
+    const int Ho = Hi * s, Wo = Wi * s;
+    const int Hb = (Hi + F - 1) / F, Wb = (Wi + F - 1) / F;
+    const int q1 = q + 1, nxx = q1 * (q1 + 1) / 2, nm = nxx + 3 * q1;
+    const size_t Pi = (size_t)Hi * Wi, Pb = (size_t)Hb * Wb, Po = (size_t)Ho * Wo;
+    double *blk = calloc(Pb * nm, sizeof(double));
+    double *tmpb = malloc(sizeof(double) * Pb * nm);
+    double *cf = malloc(sizeof(double) * Pb * q1 * 3);
+    double *w = malloc(sizeof(double) * (2 * taps + 1));
+    int status = 0;
+    if (!blk || !tmpb || !cf || !w) { status = -2; goto done; }
+
+    /* steps 1-2: block sums of the outer products */
+    for (int y = 0; y < Hi; ++y)
+        for (int x = 0; x < Wi; ++x) {
+            const size_t p = (size_t)y * Wi + x;
+            double v[ORACLE_MAX_Q + 1], yv[3];
+            v[0] = 1.0;
+            for (int i = 0; i < q; ++i) v[i + 1] = (double)guide[(size_t)i * Pi + p];
+            for (int c = 0; c < 3; ++c) yv[c] = (double)radiance[(size_t)c * Pi + p];
+            double *b = blk + ((size_t)(y / F) * Wb + x / F) * nm;
+            for (int i = 0; i < q1; ++i)
+                for (int j = i; j < q1; ++j) b[tri_index(q1, i, j)] += v[i] * v[j];
+            for (int i = 0; i < q1; ++i)
+                for (int c = 0; c < 3; ++c) b[nxx + i * 3 + c] += v[i] * yv[c];
+        }
+    /* step 3: separable Gaussian over the block grid, clipped */
+    for (int d = -taps; d <= taps; ++d) w[d + taps] = exp(-(double)d * d / (2.0 * sigma_b * sigma_b));
+    for (int by = 0; by < Hb; ++by)
+        for (int bx = 0; bx < Wb; ++bx)
+            for (int m = 0; m < nm; ++m) {
+                double acc = 0.0;
+                for (int d = -taps; d <= taps; ++d) {
+                    const int xx2 = bx + d;
+                    if (xx2 >= 0 && xx2 < Wb) acc += w[d + taps] * blk[((size_t)by * Wb + xx2) * nm + m];
+                }
+                tmpb[((size_t)by * Wb + bx) * nm + m] = acc;
+            }
+    for (int by = 0; by < Hb; ++by)
+        for (int bx = 0; bx < Wb; ++bx)
+            for (int m = 0; m < nm; ++m) {
+                double acc = 0.0;
+                for (int d = -taps; d <= taps; ++d) {
+                    const int yy = by + d;
+                    if (yy >= 0 && yy < Hb) acc += w[d + taps] * tmpb[((size_t)yy * Wb + bx) * nm + m];
+                }
+                blk[((size_t)by * Wb + bx) * nm + m] = acc;
+            }
+    /* step 4: per-block centred ridge (Appendix), as in flr_oracle_forward */
+    for (size_t k = 0; k < Pb && status == 0; ++k) {
+        const double *b = blk + k * nm;
+        const double n = b[tri_index(q1, 0, 0)];
+        double mu[ORACLE_MAX_Q], mu_y[3], M[ORACLE_MAX_Q * ORACLE_MAX_Q], D[ORACLE_MAX_Q * 3], a[ORACLE_MAX_Q * 3];
+        for (int i = 0; i < q; ++i) mu[i] = b[tri_index(q1, 0, i + 1)] / n;
+        for (int c = 0; c < 3; ++c) mu_y[c] = b[nxx + c] / n;
+        for (int i = 0; i < q; ++i)
+            for (int j = 0; j < q; ++j) {
+                int lo = i < j ? i : j, hi = i < j ? j : i;
+                M[i * q + j] = b[tri_index(q1, lo + 1, hi + 1)] / n - mu[i] * mu[j] + (i == j ? eps : 0.0);
+            }
+        for (int i = 0; i < q; ++i)
+            for (int c = 0; c < 3; ++c) D[i * 3 + c] = b[nxx + (i + 1) * 3 + c] / n - mu[i] * mu_y[c];
+        if (cholesky_solve(q, M, D, 3, a) != 0) { status = -3; break; }
+        for (int c = 0; c < 3; ++c) {
+            double bb = mu_y[c];
+            for (int i = 0; i < q; ++i) bb -= a[i * 3 + c] * mu[i];
+            cf[(size_t)(0 * 3 + c) * Pb + k] = bb;
+            for (int i = 0; i < q; ++i) cf[(size_t)((i + 1) * 3 + c) * Pb + k] = a[i * 3 + c];
+        }
+    }
+    if (status) goto done;
+    if (coef) memcpy(coef, cf, sizeof(double) * Pb * q1 * 3);
+    /* step 5: bilinear interpolation of the block models, applied to the map guide */
+    for (int yo = 0; yo < Ho; ++yo)
+        for (int xo = 0; xo < Wo; ++xo) {
+            double u = (yo + 0.5) / ((double)F * s) - 0.5, v = (xo + 0.5) / ((double)F * s) - 0.5;
+            if (u < 0) u = 0;
+            if (u > Hb - 1) u = Hb - 1;
+            if (v < 0) v = 0;
+            if (v > Wb - 1) v = Wb - 1;
+            int i0 = (int)floor(u), j0 = (int)floor(v);
+            if (i0 > Hb - 2) i0 = Hb > 1 ? Hb - 2 : 0;
+            if (j0 > Wb - 2) j0 = Wb > 1 ? Wb - 2 : 0;
+            const int i1 = Hb > 1 ? i0 + 1 : 0, j1 = Wb > 1 ? j0 + 1 : 0;
+            const double fy = u - i0, fx = v - j0;
+            const size_t po = (size_t)yo * Wo + xo;
+            for (int c = 0; c < 3; ++c) {
+                double o = 0.0;
+                for (int i = 0; i <= q; ++i) {
+                    const double *pl = cf + (size_t)(i * 3 + c) * Pb;
+                    const double val = (1 - fy) * ((1 - fx) * pl[(size_t)i0 * Wb + j0] + fx * pl[(size_t)i0 * Wb + j1]) +
+                                       fy * ((1 - fx) * pl[(size_t)i1 * Wb + j0] + fx * pl[(size_t)i1 * Wb + j1]);
+                    o += val * (i == 0 ? 1.0 : (double)map_guide[(size_t)(i - 1) * Po + po]);
+                }
+                out[(size_t)c * Po + po] = o;
+            }
+        }
+done:
+    free(blk);
+    free(tmpb);
+    free(cf);
+    free(w);
+    return status;
+}
