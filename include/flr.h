@@ -177,6 +177,53 @@ int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset);
 int flr_denoise_noalloc(const flr_params *params, const float *guide, const float *map_guide,
                         const float *radiance, float *out, int H, int W, void *stream);
 
+/*
+ * Fast FLR: the paper's own implementation of the method (Sec. 3.2, "Fast Local
+ * Regression"), and its joint denoising and upsampling (Sec. 3.2.1).  The outer products
+ * are summed over factor x factor blocks of the input grid (a strided box filter), blurred
+ * over the block grid by a separable Gaussian, the centred ridge model of flr_denoise is
+ * solved once per block, and the block models are bilinearly interpolated to every output
+ * pixel and applied to the map guide there.  Equivalent to weighted least squares with
+ * each pixel weighted by the Gaussian weight of its block (Sec. 3.2's WLS equation).
+ */
+typedef struct flr_fast_params {
+    int q;             /* guide channels, 1..FLR_MAX_Q */
+    int factor;        /* input pixels per block side: 2, 4 or 8 (the paper: 8) */
+    int scale;         /* output pixels per input pixel side, 1..8: 1 = fast FLR; 2, 4 =
+                          joint denoising and upsampling (model guide and radiance at the
+                          input resolution, map guide and output at scale x it) */
+    float sigma;       /* Gaussian standard deviation in blocks (the paper: sigma / 8, i.e.
+                          1.25 for Fig. 3's sigma = 10 pixels) */
+    int taps;          /* Gaussian half-width in blocks, 0..8 */
+    float eps;         /* ridge term, >= 0 */
+    float pivot_ratio; /* FP64 re-solve threshold per block (as flr_params); <= 0: off */
+    unsigned flags;    /* must be 0 */
+} flr_fast_params;
+
+typedef struct flr_fast_handle flr_fast_handle;
+
+/* Create / destroy a fast-FLR handle.  Errors: FLR_ERR_ARG, FLR_ERR_UNSUPPORTED, FLR_ERR_NOMEM. */
+int flr_fast_create(const flr_fast_params *params, flr_fast_handle **out);
+int flr_fast_destroy(flr_fast_handle *h);
+
+/*
+ * Fast FLR on device images.
+ *   guide      [q][Hi][Wi]            model guides (input resolution)
+ *   radiance   [3][Hi][Wi]            noisy radiance (input resolution)
+ *   map_guide  [q][Hi*s][Wi*s]        guides the models are applied to; NULL = guide (s = 1)
+ *   out        [3][Hi*s][Wi*s]        result
+ * Block (i, j) covers input rows [i F, i F + F) and columns [j F, j F + F) (clipped) and has
+ * its centre at output coordinate ((i + 1/2) F s - 1/2, (j + 1/2) F s - 1/2); outputs
+ * beyond the outermost centres use the edge models.  The per-block workspace
+ * (2 NCH + 3 (q+1) floats per block) is allocated on first use.
+ * Errors: FLR_ERR_ARG, FLR_ERR_ALIGN, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_fast_denoise(flr_fast_handle *h, const float *guide, const float *map_guide,
+                     const float *radiance, float *out, int Hi, int Wi, void *stream);
+
+/* Blocks of the last call whose pivot fell below the threshold (re-solved in FP64). */
+int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out);
+
 /* Human-readable name of a status code (static storage). */
 const char *flr_status_string(int status);
 

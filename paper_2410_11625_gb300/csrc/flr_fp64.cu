@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kDThreads) flr_fp64_kernel(const Fp64Args a)
             double d = L[j][j];
 #pragma unroll
             for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-            d = sqrt(d > 0.0 ? d : 1e-300);
+            d = sqrt(d > a.eps ? d : (a.eps > 0.0 ? a.eps : 1e-300));  // every exact pivot is >= eps
             L[j][j] = d;
 #pragma unroll
             for (int i = j + 1; i < Q; ++i) {

@@ -18,7 +18,8 @@ STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA
 # every symbol include/flr.h declares
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
            "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
-           "flr_denoise_noalloc", "flr_backward")
+           "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
+           "flr_fast_denoise", "flr_fast_get_stats")
 FLAG_TIMING = 1
 
 
@@ -26,6 +27,12 @@ class FlrParams(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("radius", ctypes.c_int), ("coef_radius", ctypes.c_int),
                 ("eps", ctypes.c_float), ("pivot_ratio", ctypes.c_float),
                 ("flags", ctypes.c_uint)]
+
+
+class FlrFastParams(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("factor", ctypes.c_int), ("scale", ctypes.c_int),
+                ("sigma", ctypes.c_float), ("taps", ctypes.c_int), ("eps", ctypes.c_float),
+                ("pivot_ratio", ctypes.c_float), ("flags", ctypes.c_uint)]
 
 
 class FlrStats(ctypes.Structure):
@@ -74,6 +81,12 @@ def load_library():
     lib.flr_get_kernel_times.argtypes = [vp, ctypes.POINTER(FlrKernelTimes), ip]
     lib.flr_backward.argtypes = [vp, fp, fp, fp, fp, fp, fp, fp, vp, ip, ip, vp]
     lib.flr_backward.restype = ctypes.c_int
+    lib.flr_fast_create.argtypes = [ctypes.POINTER(FlrFastParams), ctypes.POINTER(ctypes.c_void_p)]
+    lib.flr_fast_destroy.argtypes = [vp]
+    lib.flr_fast_denoise.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_fast_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
+    for name in ("flr_fast_create", "flr_fast_destroy", "flr_fast_denoise", "flr_fast_get_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.flr_denoise_noalloc.argtypes = [ctypes.POINTER(FlrParams), fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_noalloc.restype = ctypes.c_int
     lib.flr_status_string.argtypes = [ip]
@@ -210,6 +223,52 @@ class FLR:
     def stats(self):
         s = FlrStats()
         _check(load_library().flr_get_stats(self._h, ctypes.byref(s)), "flr_get_stats")
+        return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+
+
+class FastFLR:
+    """A fast-FLR handle (Sec. 3.2 block-downsampled moments; Sec. 3.2.1 with scale > 1)."""
+
+    def __init__(self, q=8, factor=8, scale=1, sigma=1.25, taps=3, eps=1e-3, pivot_ratio=1e-3):
+        lib = load_library()
+        self.q, self.factor, self.scale = int(q), int(factor), int(scale)
+        p = FlrFastParams(self.q, self.factor, self.scale, float(sigma), int(taps), float(eps),
+                          float(pivot_ratio), 0)
+        h = ctypes.c_void_p()
+        _check(lib.flr_fast_create(ctypes.byref(p), ctypes.byref(h)), "flr_fast_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().flr_fast_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def denoise(self, guide, radiance, map_guide=None, out=None, stream=None):
+        """guide [q,Hi,Wi], radiance [3,Hi,Wi] (CUDA float32); map_guide [q,Hi*s,Wi*s]."""
+        import torch
+        Hi, Wi = int(radiance.shape[-2]), int(radiance.shape[-1])
+        Ho, Wo = Hi * self.scale, Wi * self.scale
+        g = _dev_ptr(guide, "guide", (self.q, Hi, Wi))
+        r = _dev_ptr(radiance, "radiance", (3, Hi, Wi))
+        m = None if map_guide is None else _dev_ptr(map_guide, "map_guide", (self.q, Ho, Wo))
+        if out is None:
+            out = torch.empty((3, Ho, Wo), dtype=torch.float32, device=radiance.device)
+        o = _dev_ptr(out, "out", (3, Ho, Wo))
+        if stream is None:
+            stream = torch.cuda.current_stream(radiance.device)
+        _check(load_library().flr_fast_denoise(self._h, g, m, r, o, Hi, Wi,
+                                               ctypes.c_void_p(stream.cuda_stream)), "flr_fast_denoise")
+        return out
+
+    def stats(self):
+        s = FlrStats()
+        _check(load_library().flr_fast_get_stats(self._h, ctypes.byref(s)), "flr_fast_get_stats")
         return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
 
 
