@@ -42,7 +42,8 @@ typedef enum flr_status {
     FLR_ERR_ALIGN = -2,       /* a device pointer is not 16-byte aligned */
     FLR_ERR_CUDA = -3,        /* a CUDA runtime call failed (see flr_last_cuda_error) */
     FLR_ERR_UNSUPPORTED = -4, /* q or a radius outside what this build supports */
-    FLR_ERR_NOMEM = -5        /* a workspace allocation failed */
+    FLR_ERR_NOMEM = -5,       /* a workspace allocation failed */
+    FLR_ERR_TIMEOUT = -6      /* a device-side wait ran out of time (flr_fast_batch_status) */
 } flr_status;
 
 /* Largest guide count and window radii the kernels are built for. */
@@ -223,6 +224,49 @@ int flr_fast_denoise(flr_fast_handle *h, const float *guide, const float *map_gu
 
 /* Blocks of the last call whose pivot fell below the threshold (re-solved in FP64). */
 int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out);
+
+/* One frame of a batch: device pointers as in flr_denoise / flr_fast_denoise. */
+typedef struct flr_frame {
+    const float *guide;     /* [q][H][W] (fast path: input resolution) */
+    const float *map_guide; /* [q][H*s][W*s], or NULL to use the guide (s = 1) */
+    const float *radiance;  /* [3][H][W] */
+    float *out;             /* [3][H*s][W*s] */
+    int H, W;               /* input size */
+} flr_frame;
+
+#define FLR_MAX_BATCH 16
+#define FLR_BATCH_TIMEOUT 1 /* device status word value after a barrier wait ran out */
+
+/*
+ * The per-pixel FLR pass (flr_denoise) over n frames of any sizes, in order, on one stream.
+ * Errors as flr_denoise, for the first frame that fails.
+ */
+int flr_denoise_batch(flr_handle *h, int n, const flr_frame *frames, void *stream);
+
+/*
+ * Batched fast FLR / joint denoising and upsampling (Sec. 3.2, 3.2.1) of n <= FLR_MAX_BATCH
+ * frames of mixed sizes in ONE persistent cooperative kernel launch: every stage of every
+ * frame is a work item of the same kernel, with a grid barrier between the four stages.
+ * The frame table is passed by value in the kernel parameters, so the call can be captured
+ * in a CUDA graph once flr_fast_reserve_batch has allocated the workspace for these sizes
+ * (after that the call allocates nothing).  Supported for q in {1, 4, 8} and every factor.
+ * Each barrier wait is bounded (2 s): if it runs out, the kernel records FLR_BATCH_TIMEOUT
+ * and finishes without hanging; flr_fast_batch_status reports it.
+ * Errors: FLR_ERR_ARG, FLR_ERR_ALIGN, FLR_ERR_UNSUPPORTED, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_fast_reserve_batch(flr_fast_handle *h, int n, const flr_frame *frames);
+int flr_fast_denoise_batch(flr_fast_handle *h, int n, const flr_frame *frames, void *stream);
+
+/* Waits for the last batch and returns FLR_OK, or FLR_ERR_TIMEOUT if a barrier ran out. */
+int flr_fast_batch_status(flr_fast_handle *h);
+
+/*
+ * Self-test of the bounded device wait: launches `ctas` CTAs on a grid barrier that expects
+ * one more CTA than exists, so every wait runs out after timeout_ns; *status receives the
+ * device status word (FLR_BATCH_TIMEOUT on success of the test).  No fault is involved.
+ * Not a paper operation.  Errors: FLR_ERR_ARG, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_barrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
 
 /* Human-readable name of a status code (static storage). */
 const char *flr_status_string(int status);

@@ -135,6 +135,7 @@ const char *flr_status_string(int status)
     case FLR_ERR_CUDA: return "FLR_ERR_CUDA: CUDA runtime error";
     case FLR_ERR_UNSUPPORTED: return "FLR_ERR_UNSUPPORTED: parameter outside the built range";
     case FLR_ERR_NOMEM: return "FLR_ERR_NOMEM: workspace allocation failed";
+    case FLR_ERR_TIMEOUT: return "FLR_ERR_TIMEOUT: a device-side wait ran out of time";
     default: return "unknown flr status";
     }
 }
@@ -398,6 +399,17 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     ba.rc = rc;
     ba.separate_map = map_guide != nullptr;
     FLR_CUDA(flr::launch_bwd_contract(q, ba, s), "backward: contraction launch");
+    return FLR_OK;
+}
+
+int flr_denoise_batch(flr_handle *h, int n, const flr_frame *frames, void *stream)
+{
+    if (!h || n <= 0 || !frames) return FLR_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const flr_frame &f = frames[i];
+        int st = flr_denoise(h, f.guide, f.map_guide, f.radiance, f.out, f.H, f.W, stream);
+        if (st != FLR_OK) return st;
+    }
     return FLR_OK;
 }
 

@@ -154,5 +154,12 @@ cudaError_t launch_bwd_fields(int q, const float *g, const float *z, const float
                               int rc, cudaStream_t st);
 cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st);
 cudaError_t launch_bwd_contract(int q, const BwdArgs &a, cudaStream_t st);
+namespace fast { struct FastArgs; }
+bool batch_supported(int q, int F);
+cudaError_t launch_batch(int q, int F, const void *args, cudaStream_t st);
+size_t batch_args_size();
+void fill_batch_args(void *args, int n, const fast::FastArgs *frames, unsigned *count, unsigned *gen, int *status);
+cudaError_t launch_barrier_selftest(unsigned *count, unsigned *gen, unsigned expected, int *status,
+                                    unsigned long long timeout_ns, int grid, cudaStream_t st);
 
 }  // namespace flr

@@ -19,7 +19,9 @@ STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
            "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
            "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
-           "flr_fast_denoise", "flr_fast_get_stats")
+           "flr_fast_denoise", "flr_fast_get_stats", "flr_denoise_batch", "flr_fast_reserve_batch",
+           "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest")
+BATCH_TIMEOUT = 1
 FLAG_TIMING = 1
 
 
@@ -33,6 +35,11 @@ class FlrFastParams(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("factor", ctypes.c_int), ("scale", ctypes.c_int),
                 ("sigma", ctypes.c_float), ("taps", ctypes.c_int), ("eps", ctypes.c_float),
                 ("pivot_ratio", ctypes.c_float), ("flags", ctypes.c_uint)]
+
+
+class FlrFrame(ctypes.Structure):
+    _fields_ = [("guide", ctypes.c_void_p), ("map_guide", ctypes.c_void_p), ("radiance", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int)]
 
 
 class FlrStats(ctypes.Structure):
@@ -86,6 +93,14 @@ def load_library():
     lib.flr_fast_denoise.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
     lib.flr_fast_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
     for name in ("flr_fast_create", "flr_fast_destroy", "flr_fast_denoise", "flr_fast_get_stats"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.flr_denoise_batch.argtypes = [vp, ip, ctypes.POINTER(FlrFrame), vp]
+    lib.flr_fast_reserve_batch.argtypes = [vp, ip, ctypes.POINTER(FlrFrame)]
+    lib.flr_fast_denoise_batch.argtypes = [vp, ip, ctypes.POINTER(FlrFrame), vp]
+    lib.flr_fast_batch_status.argtypes = [vp]
+    lib.flr_barrier_selftest.argtypes = [ip, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_int)]
+    for name in ("flr_denoise_batch", "flr_fast_reserve_batch", "flr_fast_denoise_batch",
+                 "flr_fast_batch_status", "flr_barrier_selftest"):
         getattr(lib, name).restype = ctypes.c_int
     lib.flr_denoise_noalloc.argtypes = [ctypes.POINTER(FlrParams), fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_noalloc.restype = ctypes.c_int
@@ -212,6 +227,20 @@ class FLR:
         _check(load_library().flr_denoise_host(self._h, g, m, r, o, H, W, st), "flr_denoise_host")
         return out
 
+    def denoise_batch(self, frames, stream=None):
+        """Per-pixel FLR over frames in order: list of (guide, radiance, map_guide, out)."""
+        import torch
+        arr = (FlrFrame * len(frames))()
+        for i, (g, y, z, o) in enumerate(frames):
+            H, W = int(y.shape[-2]), int(y.shape[-1])
+            arr[i] = FlrFrame(_dev_ptr(g, "guide", (self.q, H, W)).value,
+                              None if z is None else _dev_ptr(z, "map_guide", (self.q, H, W)).value,
+                              _dev_ptr(y, "radiance", (3, H, W)).value, _dev_ptr(o, "out", (3, H, W)).value, H, W)
+        if stream is None:
+            stream = torch.cuda.current_stream(frames[0][1].device)
+        _check(load_library().flr_denoise_batch(self._h, len(frames), arr, ctypes.c_void_p(stream.cuda_stream)),
+               "flr_denoise_batch")
+
     def kernel_times(self, reset=True):
         """Launch counts and summed CUDA-event kernel durations (ms) since the last reset."""
         t = FlrKernelTimes()
@@ -266,10 +295,48 @@ class FastFLR:
                                                ctypes.c_void_p(stream.cuda_stream)), "flr_fast_denoise")
         return out
 
+    def _frames(self, frames):
+        arr = (FlrFrame * len(frames))()
+        for i, (g, y, z, o) in enumerate(frames):
+            Hi, Wi = int(y.shape[-2]), int(y.shape[-1])
+            Ho, Wo = Hi * self.scale, Wi * self.scale
+            arr[i] = FlrFrame(_dev_ptr(g, "guide", (self.q, Hi, Wi)).value,
+                              None if z is None else _dev_ptr(z, "map_guide", (self.q, Ho, Wo)).value,
+                              _dev_ptr(y, "radiance", (3, Hi, Wi)).value,
+                              _dev_ptr(o, "out", (3, Ho, Wo)).value, Hi, Wi)
+        return arr
+
+    def reserve_batch(self, frames):
+        """frames: list of (guide, radiance, map_guide or None, out) CUDA tensors."""
+        arr = self._frames(frames)
+        _check(load_library().flr_fast_reserve_batch(self._h, len(frames), arr), "flr_fast_reserve_batch")
+
+    def denoise_batch(self, frames, stream=None):
+        """One persistent launch over every frame: list of (guide, radiance, map_guide, out)."""
+        import torch
+        arr = self._frames(frames)
+        if stream is None:
+            stream = torch.cuda.current_stream(frames[0][1].device)
+        _check(load_library().flr_fast_denoise_batch(self._h, len(frames), arr,
+                                                     ctypes.c_void_p(stream.cuda_stream)), "flr_fast_denoise_batch")
+
+    def batch_status(self):
+        """FLR_OK (0) or FLR_ERR_TIMEOUT (-6) for the last batch (waits for it)."""
+        return int(load_library().flr_fast_batch_status(self._h))
+
     def stats(self):
         s = FlrStats()
         _check(load_library().flr_fast_get_stats(self._h, ctypes.byref(s)), "flr_fast_get_stats")
         return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+
+
+def barrier_selftest(ctas=4, timeout_ns=50_000_000):
+    """Run a grid barrier that can never complete; returns the device status word, which
+    must be BATCH_TIMEOUT (the bounded wait ran out and the kernel returned)."""
+    st = ctypes.c_int(0)
+    _check(load_library().flr_barrier_selftest(int(ctas), ctypes.c_ulonglong(timeout_ns), ctypes.byref(st)),
+           "flr_barrier_selftest")
+    return int(st.value)
 
 
 def denoise(guide, radiance, radius=8, eps=1e-3, coef_radius=None, map_guide=None,
