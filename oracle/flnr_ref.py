@@ -1,0 +1,90 @@
+"""FP64 CPU oracle of the FLNR guide network (Sec. 3.3), in plain PyTorch CPU float64 ops.
+
+TEST INFRASTRUCTURE: only tests, the smoke check and the benchmark's CPU leg use it.
+
+The network maps the 11 input channels (Q = 8 guides and the noisy RGB radiance,
+concatenated channel-wise, Sec. 3.3) to 8 enhanced guide channels through a 3-level U-Net
+(Sec. 3.3's blocks; widths 16 / 32 / 64, ReLU as the activation):
+  input projection   conv3x3 11->16, ReLU;  conv1x1 16->16, ReLU              -> f0 (H)
+  encoder level 1    avgpool 2x2;  conv3x3 16->32, ReLU;  conv3x3 32->32, ReLU -> f1 (H/2)
+  encoder level 2    avgpool 2x2;  conv3x3 32->64, ReLU;  conv3x3 64->64, ReLU -> f2 (H/4)
+  decoder level 1    nearest 2x up(f2) ++ f1;  conv3x3 96->32, ReLU;  conv3x3 32->32, ReLU -> d1
+  decoder level 0    nearest 2x up(d1) ++ f0;  conv3x3 48->16, ReLU;  conv3x3 16->16, ReLU -> d0
+  output             conv3x3 16->16, ReLU;  conv1x1 16->8;  sigmoid          -> X'
+All 3x3 convolutions have stride 1 and zero padding 1.  H and W must be multiples of 4.
+Weights are [Cout][Cin][kh][kw] with a bias per output channel.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+# (name, kind, cin, cout, kernel) in execution order; kind: conv with ReLU ("cr"),
+# conv without activation ("c")
+LAYERS = [
+    ("in0", "cr", 11, 16, 3), ("in1", "cr", 16, 16, 1),
+    ("e1a", "cr", 16, 32, 3), ("e1b", "cr", 32, 32, 3),
+    ("e2a", "cr", 32, 64, 3), ("e2b", "cr", 64, 64, 3),
+    ("d1a", "cr", 96, 32, 3), ("d1b", "cr", 32, 32, 3),
+    ("d0a", "cr", 48, 16, 3), ("d0b", "cr", 16, 16, 3),
+    ("o0", "cr", 16, 16, 3), ("o1", "c", 16, 8, 1),
+]
+
+
+def init_weights(seed=0):
+    """He-uniform weights and zero biases, float32 (the dtype the GPU master copy keeps)."""
+    rng = np.random.default_rng(seed)
+    params = {}
+    for name, _, cin, cout, k in LAYERS:
+        bound = np.sqrt(6.0 / (cin * k * k))
+        params[name + ".w"] = rng.uniform(-bound, bound, size=(cout, cin, k, k)).astype(np.float32)
+        params[name + ".b"] = np.zeros(cout, np.float32)
+    return params
+
+
+def forward(x, params):
+    """x: [N, 11, H, W] float64 tensor; params: dict of float64 tensors. Returns [N, 8, H, W]."""
+    def conv(t, name, relu):
+        w, b = params[name + ".w"], params[name + ".b"]
+        y = F.conv2d(t, w, b, padding=w.shape[-1] // 2)
+        return F.relu(y) if relu else y
+
+    f0 = conv(conv(x, "in0", True), "in1", True)
+    f1 = conv(conv(F.avg_pool2d(f0, 2), "e1a", True), "e1b", True)
+    f2 = conv(conv(F.avg_pool2d(f1, 2), "e2a", True), "e2b", True)
+    d1 = torch.cat([F.interpolate(f2, scale_factor=2, mode="nearest"), f1], dim=1)
+    d1 = conv(conv(d1, "d1a", True), "d1b", True)
+    d0 = torch.cat([F.interpolate(d1, scale_factor=2, mode="nearest"), f0], dim=1)
+    d0 = conv(conv(d0, "d0a", True), "d0b", True)
+    return torch.sigmoid(conv(conv(d0, "o0", True), "o1", False))
+
+
+def forward_backward(x, params, grad_out):
+    """FP64 forward and reverse-mode gradients (torch autograd on CPU).
+
+    x [N,11,H,W], params (numpy float32/float64 dict), grad_out [N,8,H,W] (dL/dX').
+    Returns (out, grads) with grads[name] for every parameter and grads["input"].
+    """
+    xt = torch.tensor(np.asarray(x, np.float64), requires_grad=True)
+    pt = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in params.items()}
+    out = forward(xt, pt)
+    out.backward(torch.tensor(np.asarray(grad_out, np.float64)))
+    grads = {k: v.grad.numpy() for k, v in pt.items()}
+    grads["input"] = xt.grad.numpy()
+    return out.detach().numpy(), grads
+
+
+def conv2d_direct(x, w, b):
+    """Reference 2-D convolution by explicit summation (stride 1, zero padding k//2):
+    y[n, o, i, j] = b[o] + sum_{c, u, v} w[o, c, u, v] x[n, c, i + u - k//2, j + v - k//2]."""
+    N, C, H, W = x.shape
+    O, _, k, _ = w.shape
+    p = k // 2
+    xp = np.zeros((N, C, H + 2 * p, W + 2 * p))
+    xp[:, :, p:p + H, p:p + W] = x
+    y = np.zeros((N, O, H, W)) + b[None, :, None, None]
+    for u in range(k):
+        for v in range(k):
+            y += np.einsum("oc,nchw->nohw", w[:, :, u, v], xp[:, :, u:u + H, v:v + W])
+    return y
