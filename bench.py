@@ -1,6 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark of the FLR hot path: ms per 1920x1080 frame on GB300.
 
+Besides the headline, `rows` reports the other parts of the path: the FLR adjoint, the
+paper's fast FLR, joint 2x upsampling, batched serving, and FLNR (training on rendered
+crops, PSNR against high-spp references on held-out rooms, 1080p inference time).
+
 One step = one full FLR pass (windowed moments, per-pixel Cholesky solve, FP64 re-solve
 of flagged pixels, coefficient averaging and apply) over one frame whose inputs are
 already in HBM.  Four rendered frames rotate, so every step reads inputs larger than L2.
@@ -227,6 +231,72 @@ def serving_batch(flr, torch, np, dev, stream, n_iter=100):
             "what": "flr_fast_denoise_batch: one persistent cooperative kernel, 4 stages x 8 frames"}
 
 
+# FLNR network (Sec. 3.3): multiply-accumulates per full-resolution pixel, layer by layer
+# (Cin x Cout x k^2, divided by 4 at half and 16 at quarter resolution)
+FLNR_MACS_PER_PIXEL = (11 * 16 * 9 + 16 * 16 + (16 * 32 * 9 + 32 * 32 * 9) / 4 + (32 * 64 * 9 + 64 * 64 * 9) / 16
+                       + (96 * 32 * 9 + 32 * 32 * 9) / 4 + 48 * 16 * 9 + 16 * 16 * 9 + 16 * 16 * 9 + 16 * 8)
+
+
+def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
+    """FLNR rows: training on rendered crops, PSNR against 1024 spp references on held-out
+    rooms, 1080p inference time (network + FLR on its guides), training-step time."""
+    from paper_2410_11625_gb300 import flnr, flnr_train, flr
+    rows = {}
+    t0 = time.perf_counter()
+    scenes = flnr_train.render_scenes(range(1, 33), 192, 192, ref_spp=1024, noise=8)
+    held_out = flnr_train.render_scenes(range(flnr_train.EVAL_SEED0, flnr_train.EVAL_SEED0 + 6), 256, 256,
+                                        ref_spp=1024)
+    t_render = time.perf_counter() - t0
+    tr = flnr_train.Trainer(flnr.init_weights(0), batch=16, crop=128, lr=2e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr.train(scenes, train_steps, seed=0, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    p_flr, p_net = flnr_train.evaluate(tr.net, tr.flr, held_out)
+    rows["flnr_psnr"] = {
+        "psnr_flr_db": round(float(np.mean(p_flr)), 3), "psnr_flnr_db": round(float(np.mean(p_net)), 3),
+        "gain_db": round(float(np.mean(p_net) - np.mean(p_flr)), 3),
+        "per_scene_gain_db": [round(a - b, 2) for a, b in zip(p_net, p_flr)],
+        "what": (f"held-out rooms (seeds 1000000..1000005, 256x256) vs 1024 spp references, albedo-modulated, "
+                 f"clamped to [0,1]; network trained here for {train_steps} steps (batch 16 x 128^2 crops of 32 "
+                 f"rooms, 8 noise realisations each, L1, Adam lr 2e-3 cosine to 1e-4) in {t_train:.1f} s; "
+                 f"rendering {t_render:.1f} s on the host"),
+    }
+    xs, rs = flnr_train.sample_batch(np.random.default_rng(1), scenes, 16, 128)
+    t_step = timed(lambda i: tr.step(xs, rs), 50)
+    rows["flnr_train_step"] = {"ms_per_step": round(t_step, 4),
+                               "what": "batch 16 x 128x128: FLNR fwd, 16 x FLR, L1, 16 x FLR adjoint, FLNR bwd, Adam; "
+                                       "includes the pinned H2D copy of the batch"}
+    # 1080p inference with the trained weights
+    weights = tr.net.get_weights()
+    tr.net.close()
+    net = flnr.FLNR(H * W, weights)
+    f = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
+    f.reserve(H, W)
+    xin = [torch.cat([g, y]).unsqueeze(0).contiguous() for g, y in dev_frames]
+    guides = torch.empty((1, 8, H, W), dtype=torch.float32, device=dev)
+    out = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    t_net = timed(lambda i: net.forward(xin[i % len(xin)], out=guides), 50)
+    net.forward(xin[0], out=guides)
+    t_flr = timed(lambda i: f.denoise(guides[0], dev_frames[0][1], out=out), 50)
+
+    def both(i):
+        net.forward(xin[i % len(xin)], out=guides)
+        f.denoise(guides[0], dev_frames[i % len(xin)][1], out=out)
+    t_both = timed(both, 50)
+    tflops = 2 * FLNR_MACS_PER_PIXEL * H * W / (t_net * 1e-3) / 1e12
+    peak = float(load_peaks()[0]["bf16_tflops"])
+    rows["flnr_1080p"] = {"ms_per_frame": round(t_both, 4), "net_ms": round(t_net, 4), "flr_on_net_guides_ms": round(t_flr, 4),
+                          "net_tflops": round(tflops, 2), "net_tensor_frac": round(tflops / peak, 4),
+                          "net_macs_per_pixel": FLNR_MACS_PER_PIXEL,
+                          "what": "FLNR guide network (BF16 mma.sync implicit-GEMM convs, FP32 accumulation) + FP32 FLR "
+                                  "r=8 on its guides, 1920x1080; tensor fraction of measured dense bf16 peak"}
+    f.close()
+    net.close()
+    return rows
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -314,6 +384,8 @@ def run_ours(args):
     rows["joint_upsample_2x_1080p"] = {"ms_per_frame": round(t_joint, 5),
                                        "what": "Sec. 3.2.1: 960x540 radiance and model guides, 1920x1080 map guide and output"}
     rows["batch_serving"] = serving_batch(flr, torch, np, dev, stream)
+    if rank == 0 and args.flnr_steps > 0:
+        rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps))
 
     if rank != 0:
         return
@@ -411,6 +483,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--flnr-steps", type=int, default=2000,
+                    help="FLNR training steps before its PSNR and 1080p rows (0 skips the FLNR rows)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -268,6 +268,80 @@ int flr_fast_batch_status(flr_fast_handle *h);
  */
 int flr_barrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
 
+/*
+ * FLNR (Sec. 3.3, "Fast Local Neural Regression"): a U-Net maps the guides and the noisy
+ * radiance, concatenated channel-wise (11 channels: Q = 8 guides, then RGB), to 8 enhanced
+ * guide channels that FLR then uses (Fig. 2).  Layers, in order (3x3 convolutions stride 1,
+ * zero padding 1; ReLU unless stated):
+ *   in0 3x3 11->16, in1 1x1 16->16 | avgpool, e1a 3x3 16->32, e1b 3x3 32->32 |
+ *   avgpool, e2a 3x3 32->64, e2b 3x3 64->64 | up2 ++ e1b: d1a 3x3 96->32, d1b 3x3 32->32 |
+ *   up2 ++ in1: d0a 3x3 48->16, d0b 3x3 16->16 | o0 3x3 16->16, o1 1x1 16->8 + sigmoid.
+ * The network reads the radiance channels as log(1 + max(Y, 0)) (fireflies stay bounded).
+ * BF16 convolutions on the tensor cores with FP32 accumulation; FP32 master weights.
+ * Parameters are one flat float array: per layer its weights [Cout][Cin][k][k] then its
+ * biases [Cout], layers in the order above (flnr_param_count() floats).
+ */
+typedef struct flnr_net flnr_net;
+
+/* Number of parameters (floats). */
+size_t flnr_param_count(void);
+
+/* Create a network whose activation buffers hold up to max_pixels = N*H*W input pixels. */
+int flnr_create(int max_pixels, flnr_net **out);
+int flnr_destroy(flnr_net *net);
+
+/* Copy the master weights from / to host memory (count = flnr_param_count()); synchronous.
+ * flnr_set_weights also clears the Adam moments (a new model starts a new optimisation). */
+int flnr_set_weights(flnr_net *net, const float *host, size_t count);
+int flnr_get_weights(flnr_net *net, float *host, size_t count);
+
+/*
+ * Forward pass on N images: in [N][11][H][W] planar float32 (device), guide_out
+ * [N][8][H][W] planar float32 (device; NULL keeps the result only inside the network).
+ * H and W multiples of 4.  Keeps the activations for flnr_guide_backward.
+ * Errors: FLR_ERR_ARG, FLR_ERR_UNSUPPORTED (more than max_pixels), FLR_ERR_CUDA.
+ */
+int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, int H, int W, void *stream);
+
+/*
+ * One layer of the network by itself, with the network's current weights: the same
+ * kernels flnr_guide_forward and flnr_guide_backward launch for that layer (Sec. 3.3), so
+ * that each can be checked on its own.  layer = 0..11 in the order above.  Tensors are
+ * device NHWC bfloat16 (raw 16-bit patterns) with channel counts padded to multiples of
+ * 16: CinP = 16 * ceil(Cin / 16), CoutP likewise; the padding channels of the outputs are
+ * written (as zero where the padded weights are zero).
+ *   FLNR_OP_FORWARD  a = x [N][H][W][CinP]; out = y [N][H][W][CoutP] = bf16(ReLU(conv(x) + b)),
+ *                    or, for layer 11, float32 planar [N][8][H][W] = sigmoid(conv(x) + b)
+ *   FLNR_OP_DGRAD    a = dz [N][H][W][CoutP] (gradient w.r.t. the layer's pre-activation);
+ *                    mask = [N][H][W][CinP] or NULL; out = dx [N][H][W][CinP] =
+ *                    bf16((mask > 0) * transposed convolution of dz)
+ *   FLNR_OP_WGRAD    a = x, b = dz; adds dL/dW and dL/db of the layer into the gradient
+ *                    buffer (flnr_get_grads / flnr_zero_grads)
+ * Runs on `stream` without waiting.  Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
+ */
+#define FLNR_OP_FORWARD 0
+#define FLNR_OP_DGRAD 1
+#define FLNR_OP_WGRAD 2
+int flnr_layer(flnr_net *net, int layer, int op, const void *a, const void *b, const void *mask, void *out,
+               int N, int H, int W, void *stream);
+
+/*
+ * Backward pass of the last forward: grad_out [N][8][H][W] = dL/d(enhanced guides);
+ * ACCUMULATES the parameter gradients (flnr_zero_grads clears them).
+ */
+int flnr_guide_backward(flnr_net *net, const float *grad_out, void *stream);
+int flnr_zero_grads(flnr_net *net, void *stream);
+int flnr_get_grads(flnr_net *net, float *host, size_t count);
+
+/* One Adam step on the FP32 master weights (step >= 1), then the BF16 copies are refreshed. */
+int flnr_adam_step(flnr_net *net, float lr, float beta1, float beta2, float eps, int step, void *stream);
+
+/*
+ * Mean absolute error of pred against ref (count floats, device): *loss (device float)
+ * receives it and grad (device) its gradient sign(pred - ref) / count.
+ */
+int flnr_l1_loss(const float *pred, const float *ref, float *grad, float *loss, size_t count, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *flr_status_string(int status);
 

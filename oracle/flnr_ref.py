@@ -5,6 +5,7 @@ TEST INFRASTRUCTURE: only tests, the smoke check and the benchmark's CPU leg use
 The network maps the 11 input channels (Q = 8 guides and the noisy RGB radiance,
 concatenated channel-wise, Sec. 3.3) to 8 enhanced guide channels through a 3-level U-Net
 (Sec. 3.3's blocks; widths 16 / 32 / 64, ReLU as the activation):
+  input              guides X unchanged, radiance Y as log(1 + max(Y, 0))
   input projection   conv3x3 11->16, ReLU;  conv1x1 16->16, ReLU              -> f0 (H)
   encoder level 1    avgpool 2x2;  conv3x3 16->32, ReLU;  conv3x3 32->32, ReLU -> f1 (H/2)
   encoder level 2    avgpool 2x2;  conv3x3 32->64, ReLU;  conv3x3 64->64, ReLU -> f2 (H/4)
@@ -13,6 +14,14 @@ concatenated channel-wise, Sec. 3.3) to 8 enhanced guide channels through a 3-le
   output             conv3x3 16->16, ReLU;  conv1x1 16->8;  sigmoid          -> X'
 All 3x3 convolutions have stride 1 and zero padding 1.  H and W must be multiples of 4.
 Weights are [Cout][Cin][kh][kw] with a bias per output channel.
+
+`bf16_storage=True` takes the network's rounding decisions in the precision a BF16
+implementation stores (every product and sum still in float64): the input, the weights,
+each ReLU output and each pooled map are rounded to bfloat16 (round to nearest even) on
+the forward pass; on the reverse pass the gradient with respect to each pre-activation,
+each pooled map and each concatenation is rounded to bfloat16.  The ReLU masks are then
+the same on both sides, which the comparison of gradients needs: a mask decided
+differently at one pixel changes that pixel's whole contribution to a weight gradient.
 """
 from __future__ import annotations
 
@@ -33,34 +42,72 @@ LAYERS = [
 
 
 def init_weights(seed=0):
-    """He-uniform weights and zero biases, float32 (the dtype the GPU master copy keeps)."""
+    """He-uniform weights and zero biases, float32 (the dtype the GPU master copy keeps);
+    the output projection o1 at a tenth of its He bound."""
     rng = np.random.default_rng(seed)
     params = {}
     for name, _, cin, cout, k in LAYERS:
-        bound = np.sqrt(6.0 / (cin * k * k))
+        bound = np.sqrt(6.0 / (cin * k * k)) * (0.1 if name == "o1" else 1.0)
         params[name + ".w"] = rng.uniform(-bound, bound, size=(cout, cin, k, k)).astype(np.float32)
         params[name + ".b"] = np.zeros(cout, np.float32)
     return params
 
 
-def forward(x, params):
-    """x: [N, 11, H, W] float64 tensor; params: dict of float64 tensors. Returns [N, 8, H, W]."""
-    def conv(t, name, relu):
-        w, b = params[name + ".w"], params[name + ".b"]
-        y = F.conv2d(t, w, b, padding=w.shape[-1] // 2)
-        return F.relu(y) if relu else y
+def round_bf16(t):
+    """Round float64 values to bfloat16 (nearest even) through float32, returned as float64."""
+    return t.to(torch.float32).to(torch.bfloat16).to(torch.float64)
 
-    f0 = conv(conv(x, "in0", True), "in1", True)
-    f1 = conv(conv(F.avg_pool2d(f0, 2), "e1a", True), "e1b", True)
-    f2 = conv(conv(F.avg_pool2d(f1, 2), "e2a", True), "e2b", True)
-    d1 = torch.cat([F.interpolate(f2, scale_factor=2, mode="nearest"), f1], dim=1)
-    d1 = conv(conv(d1, "d1a", True), "d1b", True)
-    d0 = torch.cat([F.interpolate(d1, scale_factor=2, mode="nearest"), f0], dim=1)
-    d0 = conv(conv(d0, "d0a", True), "d0b", True)
+
+class _RoundValue(torch.autograd.Function):
+    """Forward: round to bfloat16.  Backward: the gradient passes unchanged."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return round_bf16(t)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+class _RoundGrad(torch.autograd.Function):
+    """Forward: identity.  Backward: the incoming gradient is rounded to bfloat16."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return round_bf16(g)
+
+
+def forward(x, params, bf16_storage=False):
+    """x: [N, 11, H, W] float64 tensor; params: dict of float64 tensors. Returns [N, 8, H, W]."""
+    R = _RoundValue.apply if bf16_storage else (lambda t: t)
+    G = _RoundGrad.apply if bf16_storage else (lambda t: t)
+
+    def conv(t, name, relu):
+        w, b = R(params[name + ".w"]), params[name + ".b"]
+        z = G(F.conv2d(t, w, b, padding=w.shape[-1] // 2))
+        return R(F.relu(z)) if relu else z
+
+    def pool(t):
+        return G(R(F.avg_pool2d(t, 2)))
+
+    def upcat(lo, skip):
+        return G(torch.cat([F.interpolate(lo, scale_factor=2, mode="nearest"), skip], dim=1))
+
+    x = torch.cat([x[:, :8], torch.log1p(torch.clamp(x[:, 8:], min=0.0))], dim=1)
+    f0 = conv(conv(R(x), "in0", True), "in1", True)
+    f1 = conv(conv(pool(f0), "e1a", True), "e1b", True)
+    f2 = conv(conv(pool(f1), "e2a", True), "e2b", True)
+    d1 = conv(conv(upcat(f2, f1), "d1a", True), "d1b", True)
+    d0 = conv(conv(upcat(d1, f0), "d0a", True), "d0b", True)
     return torch.sigmoid(conv(conv(d0, "o0", True), "o1", False))
 
 
-def forward_backward(x, params, grad_out):
+def forward_backward(x, params, grad_out, bf16_storage=False):
     """FP64 forward and reverse-mode gradients (torch autograd on CPU).
 
     x [N,11,H,W], params (numpy float32/float64 dict), grad_out [N,8,H,W] (dL/dX').
@@ -68,7 +115,7 @@ def forward_backward(x, params, grad_out):
     """
     xt = torch.tensor(np.asarray(x, np.float64), requires_grad=True)
     pt = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in params.items()}
-    out = forward(xt, pt)
+    out = forward(xt, pt, bf16_storage)
     out.backward(torch.tensor(np.asarray(grad_out, np.float64)))
     grads = {k: v.grad.numpy() for k, v in pt.items()}
     grads["input"] = xt.grad.numpy()

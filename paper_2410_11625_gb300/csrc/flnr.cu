@@ -1,0 +1,784 @@
+// flnr.cu -- the FLNR guide network (Sec. 3.3) on sm_103a: BF16 implicit-GEMM convolutions
+// on the tensor cores (mma.sync m16n8k16, FP32 accumulation), its backward pass (dgrad as a
+// convolution with rotated, transposed weights; wgrad as a per-tap GEMM over pixels),
+// Adam on FP32 master weights, and the flnr_* entry points of include/flr.h.
+//
+// Network (weights and order as oracle/flnr_ref.py): 11 inputs (8 guides + noisy RGB)
+//   in0 3x3 11->16 ReLU, in1 1x1 16->16 ReLU                                   f0 (H)
+//   avgpool, e1a 3x3 16->32 ReLU, e1b 3x3 32->32 ReLU                          f1 (H/2)
+//   avgpool, e2a 3x3 32->64 ReLU, e2b 3x3 64->64 ReLU                          f2 (H/4)
+//   up(f2) ++ f1, d1a 3x3 96->32 ReLU, d1b 3x3 32->32 ReLU                     d1 (H/2)
+//   up(d1) ++ f0, d0a 3x3 48->16 ReLU, d0b 3x3 16->16 ReLU                     d0 (H)
+//   o0 3x3 16->16 ReLU, o1 1x1 16->8, sigmoid                                  X' (8 ch)
+// Activations are NHWC BF16 (channels innermost; the 11 inputs padded to 16, the 8 outputs
+// of o1 computed as 16 with zero weights); the enhanced guides leave as planar FP32 for FLR.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "flr.h"
+
+namespace flnr {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kNL = 12;
+struct LayerDef {
+    int cin, cout, k, relu;  // true sizes (o1's cout is 8)
+};
+constexpr LayerDef kLayers[kNL] = {
+    {11, 16, 3, 1}, {16, 16, 1, 1}, {16, 32, 3, 1}, {32, 32, 3, 1}, {32, 64, 3, 1}, {64, 64, 3, 1},
+    {96, 32, 3, 1}, {32, 32, 3, 1}, {48, 16, 3, 1}, {16, 16, 3, 1}, {16, 16, 3, 1}, {16, 8, 1, 0}};
+__host__ __device__ constexpr int pad16(int c) { return (c + 15) / 16 * 16; }
+
+// ---------------------------------------------------------------------------------------
+// Tensor-core primitive: D = A (16x16, row) * B (16x8, col) + C, BF16 inputs, FP32 accum.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// ---------------------------------------------------------------------------------------
+// Convolution, implicit GEMM.  M = 128 output pixels (an 8 x 16 tile), N = COUT, K = taps x CIN.
+// x [N][H][W][CIN] bf16, w [taps][COUT][CIN] bf16, bias [COUT] fp32.
+// Output: OUTM 0 -> y [N][H][W][ystride] bf16 at channel offset 0 (ACT 1 = ReLU);
+//         OUTM 1 -> yf planar fp32 [N][8][H][W], sigmoid of channels 0..7.
+// MASK: multiply the result by (mask > 0), mask [N][H][W][COUT] bf16 (the ReLU of the layer
+// that produced this gradient's target).
+struct ConvArgs {
+    const bf16 *x, *w, *mask;
+    const float *bias;
+    bf16 *y;
+    float *yf;
+    int N, H, W, ystride;
+    int nbias;  // valid bias entries (the true output channels); 0 without bias
+};
+
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK>
+__global__ void __launch_bounds__(128) conv_kernel(const ConvArgs a)
+{
+    constexpr int TH = 8, TW = 16, P = KS / 2;
+    constexpr int SH = TH + 2 * P, SW = TW + 2 * P;
+    constexpr int CS = CIN + 8;  // padded pixel stride: conflict-free fragment loads
+    constexpr int NT = COUT / 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16 *sx = reinterpret_cast<bf16 *>(smem_raw);  // [SH][SW][CS]
+    bf16 *sw = sx + SH * SW * CS;                    // [KS*KS][COUT][CS]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = blockIdx.z, ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    const size_t img = (size_t)n * a.H * a.W;
+    for (int i = tid; i < SH * SW * (CIN / 8); i += 128) {
+        const int pix = i / (CIN / 8), c8 = i % (CIN / 8);
+        const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+            v = *reinterpret_cast<const uint4 *>(a.x + (img + (size_t)yy * a.W + xx) * CIN + c8 * 8);
+        *reinterpret_cast<uint4 *>(sx + pix * CS + c8 * 8) = v;
+    }
+    for (int i = tid; i < KS * KS * COUT * (CIN / 8); i += 128) {
+        const int row = i / (CIN / 8), c8 = i % (CIN / 8);
+        *reinterpret_cast<uint4 *>(sw + row * CS + c8 * 8) = *reinterpret_cast<const uint4 *>(a.w + row * CIN + c8 * 8);
+    }
+    __syncthreads();
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+#pragma unroll
+    for (int ky = 0; ky < KS; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < KS; ++kx) {
+            const int tap = ky * KS + kx;
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                uint32_t af[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const bf16 *r0 = sx + ((2 * warp + mt + ky) * SW + g + kx) * CS + kc * 16 + 2 * t;
+                    const bf16 *r8 = r0 + 8 * CS;
+                    af[mt][0] = ld32(r0);
+                    af[mt][1] = ld32(r8);
+                    af[mt][2] = ld32(r0 + 8);
+                    af[mt][3] = ld32(r8 + 8);
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const bf16 *wb = sw + (tap * COUT + nt * 8 + g) * CS + kc * 16 + 2 * t;
+                    const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
+                    mma_bf16(acc[0][nt], af[0], b0, b1);
+                    mma_bf16(acc[1][nt], af[1], b0, b1);
+                }
+            }
+        }
+    // epilogue
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int yy = ty0 + 2 * warp + mt;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int xx = tx0 + g + 8 * half;
+            if (yy >= a.H || xx >= a.W) continue;
+            const size_t pix = img + (size_t)yy * a.W + xx;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int c = nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * half] + (c < a.nbias ? a.bias[c] : 0.f);
+                float v1 = acc[mt][nt][2 * half + 1] + (c + 1 < a.nbias ? a.bias[c + 1] : 0.f);
+                if (ACT == 1) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if (MASK) {
+                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + c);
+                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                }
+                if (OUTM == 0) {
+                    *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ystride + c) = __floats2bfloat162_rn(v0, v1);
+                } else if (c < 8) {
+                    const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
+                    a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v0));
+                    a.yf[((size_t)n * 8 + c + 1) * hw + off] = 1.f / (1.f + expf(-v1));
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Weight gradient of one convolution tap: dW[o][i][tap] += sum_p dz[p][o] x[p + off(tap)][i]
+// as a GEMM with M = COUT, N = CIN, K = pixels (128 per staged tile).  Grid (taps, chunks);
+// each CTA walks its chunk of pixel tiles with the accumulators in registers, then adds
+// them to the FP32 master-layout gradient [Cout][Cin][k][k] with atomics (pads skipped).
+struct WgradArgs {
+    const bf16 *x, *dz;
+    float *gw;  // master layout
+    int N, H, W, cin_true, cout_true, tiles_per_cta;
+};
+
+template <int CIN, int COUT, int KS>
+__global__ void __launch_bounds__(256) wgrad_kernel(const WgradArgs a)
+{
+    constexpr int TP = 128, PS = TP + 8;  // pixels per tile, padded row stride
+    constexpr int MT = COUT / 16, NTL = CIN / 8, TILES = MT * NTL;
+    constexpr int PER = (TILES + 7) / 8;
+    __shared__ __align__(16) bf16 dzT[COUT * PS];
+    __shared__ __align__(16) bf16 xT[CIN * PS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tap = blockIdx.x, dy = tap / KS - KS / 2, dx = tap % KS - KS / 2;
+    const long long P = (long long)a.N * a.H * a.W;
+    const long long ntiles = (P + TP - 1) / TP;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[PER][4];
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+    for (long long tile = (long long)blockIdx.y * a.tiles_per_cta;
+         tile < ntiles && tile < (long long)(blockIdx.y + 1) * a.tiles_per_cta; ++tile) {
+        const long long p0 = tile * TP;
+        for (int i = tid; i < TP * COUT; i += 256) {
+            const int p = i / COUT, c = i % COUT;
+            dzT[c * PS + p] = (p0 + p < P) ? a.dz[(p0 + p) * COUT + c] : __float2bfloat16(0.f);
+        }
+        for (int i = tid; i < TP * CIN; i += 256) {
+            const int p = i / CIN, c = i % CIN;
+            bf16 v = __float2bfloat16(0.f);
+            const long long q = p0 + p;
+            if (q < P) {
+                const long long hw = (long long)a.H * a.W;
+                const int n = (int)(q / hw), rem = (int)(q % hw), y = rem / a.W + dy, x = rem % a.W + dx;
+                if (y >= 0 && y < a.H && x >= 0 && x < a.W) v = a.x[((long long)n * hw + (long long)y * a.W + x) * CIN + c];
+            }
+            xT[c * PS + p] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int tl = warp + 8 * j;
+            if (tl < TILES) {
+                const int mt = tl / NTL, nt = tl % NTL;
+#pragma unroll
+                for (int k = 0; k < TP / 16; ++k) {
+                    uint32_t af[4];
+                    const bf16 *r0 = dzT + (mt * 16 + g) * PS + k * 16 + 2 * t;
+                    af[0] = ld32(r0);
+                    af[1] = ld32(r0 + 8 * PS);
+                    af[2] = ld32(r0 + 8);
+                    af[3] = ld32(r0 + 8 * PS + 8);
+                    const bf16 *b = xT + (nt * 8 + g) * PS + k * 16 + 2 * t;
+                    mma_bf16(acc[j], af, ld32(b), ld32(b + 8));
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int tl = warp + 8 * j;
+        if (tl >= TILES) continue;
+        const int mt = tl / NTL, nt = tl % NTL;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int o = mt * 16 + g + (e >= 2 ? 8 : 0), i = nt * 8 + 2 * t + (e & 1);
+            if (o < a.cout_true && i < a.cin_true)
+                atomicAdd(a.gw + ((size_t)o * a.cin_true + i) * KS * KS + tap, acc[j][e]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Elementwise and layout kernels
+// planar fp32 [N][11][H][W] -> NHWC bf16 with 16 channels (11 used); the radiance channels
+// enter the network as log(1 + max(Y, 0)), which keeps fireflies from dominating the features
+__global__ void pack_input_kernel(const float *in, bf16 *x, int N, int H, int W)
+{
+    const size_t hw = (size_t)H * W, total = (size_t)N * hw;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = p / hw, o = p % hw;
+        alignas(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float u = 0.f;
+            if (c < 8) u = in[(n * 11 + c) * hw + o];
+            else if (c < 11) u = log1pf(fmaxf(in[(n * 11 + c) * hw + o], 0.f));  // radiance: log(1 + max(Y, 0))
+            v[c] = __float2bfloat16(u);
+        }
+        *reinterpret_cast<uint4 *>(x + p * 16) = *reinterpret_cast<uint4 *>(v);
+        *reinterpret_cast<uint4 *>(x + p * 16 + 8) = *reinterpret_cast<uint4 *>(v + 8);
+    }
+}
+
+// 2x2 average pool: x [N][H][W][C] -> y [N][H/2][W/2][C]
+__global__ void pool_kernel(const bf16 *x, bf16 *y, int N, int H, int W, int C)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const size_t total = (size_t)N * Ho * Wo * C;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const size_t q = e / C;
+        const int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho), n = (int)(q / ((size_t)Wo * Ho));
+        const size_t b = (((size_t)n * H + 2 * yo) * W + 2 * xo) * C + c;
+        const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (size_t)W * C]) +
+                        __bfloat162float(x[b + (size_t)W * C + C]);
+        y[e] = __float2bfloat16(0.25f * s);
+    }
+}
+
+// y [N][H][W][Ca+Cb] = nearest-2x-up(a [N][H/2][W/2][Ca]) ++ b [N][H][W][Cb]
+__global__ void upcat_kernel(const bf16 *lo, const bf16 *skip, bf16 *y, int N, int H, int W, int Ca, int Cb)
+{
+    const int C = Ca + Cb;
+    const size_t total = (size_t)N * H * W * C;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const size_t p = e / C;
+        const int x = (int)(p % W), yy = (int)((p / W) % H), n = (int)(p / ((size_t)W * H));
+        y[e] = c < Ca ? lo[(((size_t)n * (H / 2) + yy / 2) * (W / 2) + x / 2) * Ca + c] : skip[p * Cb + (c - Ca)];
+    }
+}
+
+// gradient of the sigmoid output head: dz[p][c] = g * s (1 - s) for c < 8, 0 for the pads
+__global__ void sigmoid_bwd_kernel(const float *g, const float *s, bf16 *dz, int N, int H, int W)
+{
+    const size_t hw = (size_t)H * W, total = (size_t)N * hw;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = p / hw, o = p % hw;
+        alignas(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float d = 0.f;
+            if (c < 8) {
+                const float sv = s[(n * 8 + c) * hw + o];
+                d = g[(n * 8 + c) * hw + o] * sv * (1.f - sv);
+            }
+            v[c] = __float2bfloat16(d);
+        }
+        *reinterpret_cast<uint4 *>(dz + p * 16) = *reinterpret_cast<uint4 *>(v);
+        *reinterpret_cast<uint4 *>(dz + p * 16 + 8) = *reinterpret_cast<uint4 *>(v + 8);
+    }
+}
+
+// backward of up ++ skip: g_lo[q][c] = mask(lo) * sum_{2x2} gy[p][c] (c < Ca);
+// g_skip[p][c] = gy[p][Ca + c] (unmasked, the caller masks where the skip is consumed)
+__global__ void upcat_bwd_kernel(const bf16 *gy, const bf16 *lo, bf16 *g_lo, float *g_skip, int N, int H, int W,
+                                 int Ca, int Cb)
+{
+    const int C = Ca + Cb, Hl = H / 2, Wl = W / 2;
+    const size_t tl = (size_t)N * Hl * Wl * Ca, ts = (size_t)N * H * W * Cb;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tl + ts; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < tl) {
+            const int c = (int)(e % Ca);
+            const size_t q = e / Ca;
+            const int xl = (int)(q % Wl), yl = (int)((q / Wl) % Hl), n = (int)(q / ((size_t)Wl * Hl));
+            const size_t b = (((size_t)n * H + 2 * yl) * W + 2 * xl) * C + c;
+            const float s = __bfloat162float(gy[b]) + __bfloat162float(gy[b + C]) + __bfloat162float(gy[b + (size_t)W * C]) +
+                            __bfloat162float(gy[b + (size_t)W * C + C]);
+            g_lo[e] = __float2bfloat16(__bfloat162float(lo[e]) > 0.f ? s : 0.f);
+        } else {
+            const size_t f = e - tl;
+            const int c = (int)(f % Cb);
+            g_skip[f] = __bfloat162float(gy[(f / Cb) * C + Ca + c]);
+        }
+    }
+}
+
+// gradient of a ReLU feature used by a pool and a skip: g = mask(f) * (g_skip + up(g_pool) / 4)
+__global__ void pool_bwd_kernel(const float *g_skip, const bf16 *g_pool, const bf16 *f, bf16 *g, int N, int H, int W, int C)
+{
+    const size_t total = (size_t)N * H * W * C;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const size_t p = e / C;
+        const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((size_t)W * H));
+        const float gp = __bfloat162float(g_pool[(((size_t)n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c]);
+        const float v = g_skip[e] + 0.25f * gp;
+        g[e] = __float2bfloat16(__bfloat162float(f[e]) > 0.f ? v : 0.f);
+    }
+}
+
+// bias gradient: gb[c] += sum_p dz[p][c], c < ctrue (one CTA per channel block)
+__global__ void bias_grad_kernel(const bf16 *dz, float *gb, long long P, int C, int ctrue)
+{
+    __shared__ float part[256];
+    for (int c = 0; c < ctrue; ++c) {
+        float s = 0.f;
+        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
+            s += __bfloat162float(dz[p * C + c]);
+        part[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) atomicAdd(gb + c, part[0]);
+        __syncthreads();
+    }
+}
+
+// master fp32 [Cout][Cin][k][k] -> forward bf16 [tap][CoutP][CinP] and dgrad bf16
+// [tap'][CinP][CoutP] with tap' = taps - 1 - tap (rotated by 180 degrees), zero pads
+__global__ void weights_kernel(const float *w, bf16 *wf, bf16 *wd, int cin, int cout, int cinp, int coutp, int k)
+{
+    const int taps = k * k;
+    const int total = taps * coutp * cinp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int i = e % cinp, o = (e / cinp) % coutp, tap = e / (cinp * coutp);
+        const float v = (i < cin && o < cout) ? w[((size_t)o * cin + i) * taps + tap] : 0.f;
+        wf[e] = __float2bfloat16(v);
+        wd[((size_t)(taps - 1 - tap) * cinp + i) * coutp + o] = __float2bfloat16(v);
+    }
+}
+
+__global__ void adam_kernel(float *w, const float *g, float *m, float *v, size_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const float gr = g[e];
+        const float mm = b1 * m[e] + (1.f - b1) * gr;
+        const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
+        m[e] = mm;
+        v[e] = vv;
+        w[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    }
+}
+
+// L1 loss between prediction and reference (planar fp32, n values): writes d/dpred = sign / n
+// and accumulates the mean absolute error into *loss
+__global__ void l1_kernel(const float *pred, const float *ref, float *grad, float *loss, size_t n)
+{
+    __shared__ float part[256];
+    float s = 0.f;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const float d = pred[e] - ref[e];
+        grad[e] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (float)n;
+        s += fabsf(d);
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, part[0] / (float)n);
+}
+
+int egrid(size_t n) { return (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192); }
+
+// ---------------------------------------------------------------------------------------
+// Launch helpers for the template instantiations the network uses.
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK>
+cudaError_t conv_launch(const ConvArgs &a, cudaStream_t st)
+{
+    constexpr int P = KS / 2;
+    const size_t smem = sizeof(bf16) * ((size_t)(8 + 2 * P) * (16 + 2 * P) * (CIN + 8) + (size_t)KS * KS * COUT * (CIN + 8));
+    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, KS, ACT, OUTM, MASK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + 15) / 16, (a.H + 7) / 8, a.N);
+    conv_kernel<CIN, COUT, KS, ACT, OUTM, MASK><<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int KS>
+cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H, int W, int cin_true, int cout_true,
+                         int n_sm, cudaStream_t st)
+{
+    WgradArgs a{x, dz, gw, N, H, W, cin_true, cout_true, 0};
+    const long long ntiles = ((long long)N * H * W + 127) / 128;
+    const int chunks = (int)(ntiles < 2LL * n_sm ? ntiles : 2LL * n_sm);
+    a.tiles_per_cta = (int)((ntiles + chunks - 1) / chunks);
+    dim3 grid(KS * KS, chunks);
+    wgrad_kernel<CIN, COUT, KS><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace flnr
+
+// =========================================================================================
+// The network object behind flnr_*.
+
+struct flnr_net {
+    int max_pix = 0;  // N * H * W the activation buffers hold
+    int n_sm = 0;
+    size_t nparam = 0;
+    size_t poff[flnr::kNL][2];  // offsets of each layer's weights and bias in the flat arrays
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // master fp32, grads, Adam moments
+    __nv_bfloat16 *wf[flnr::kNL] = {}, *wd[flnr::kNL] = {};          // bf16 forward / dgrad weights
+    std::vector<void *> bufs;
+    // activations (bf16 NHWC) and gradients
+    __nv_bfloat16 *x0, *a0, *f0, *p0, *a1, *f1, *p1, *a2, *f2, *c1, *a3, *d1, *c0, *a4, *d0, *a5;
+    __nv_bfloat16 *gA, *gB, *gC, *gLo;  // gradient scratch (largest: 48 channels at full res)
+    float *gskip0, *gskip1;             // skip gradients (fp32)
+    float *out = nullptr;               // last forward output, planar fp32 [N][8][H][W]
+    int N = 0, H = 0, W = 0;            // shape of the last forward
+    bool weights_fresh = false;
+};
+
+namespace {
+
+template <typename T>
+int nalloc(flnr_net *n, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return FLR_ERR_NOMEM;
+    n->bufs.push_back(q);
+    *p = (T *)q;
+    return FLR_OK;
+}
+
+cudaError_t refresh_weights(flnr_net *n, cudaStream_t st)
+{
+    for (int l = 0; l < flnr::kNL; ++l) {
+        const auto &d = flnr::kLayers[l];
+        const int cinp = flnr::pad16(d.cin), coutp = flnr::pad16(d.cout);
+        const int total = d.k * d.k * cinp * coutp;
+        flnr::weights_kernel<<<(total + 255) / 256, 256, 0, st>>>(n->w + n->poff[l][0], n->wf[l], n->wd[l], d.cin,
+                                                                   d.cout, cinp, coutp, d.k);
+    }
+    n->weights_fresh = true;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t flnr_param_count(void)
+{
+    size_t s = 0;
+    for (int l = 0; l < flnr::kNL; ++l) {
+        const auto &d = flnr::kLayers[l];
+        s += (size_t)d.cout * d.cin * d.k * d.k + d.cout;
+    }
+    return s;
+}
+
+int flnr_create(int max_pixels, flnr_net **out)
+{
+    if (!out || max_pixels <= 0) return FLR_ERR_ARG;
+    *out = nullptr;
+    flnr_net *n = new (std::nothrow) flnr_net();
+    if (!n) return FLR_ERR_NOMEM;
+    n->max_pix = max_pixels;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    size_t off = 0;
+    for (int l = 0; l < flnr::kNL; ++l) {
+        const auto &d = flnr::kLayers[l];
+        n->poff[l][0] = off;
+        off += (size_t)d.cout * d.cin * d.k * d.k;
+        n->poff[l][1] = off;
+        off += d.cout;
+    }
+    n->nparam = off;
+    const size_t P = (size_t)max_pixels, P2 = P / 4 + 1, P4 = P / 16 + 1;
+    int st = FLR_OK;
+    st |= nalloc(n, &n->w, off) | nalloc(n, &n->g, off) | nalloc(n, &n->m, off) | nalloc(n, &n->v, off);
+    for (int l = 0; l < flnr::kNL && st == FLR_OK; ++l) {
+        const auto &d = flnr::kLayers[l];
+        const size_t e = (size_t)d.k * d.k * flnr::pad16(d.cin) * flnr::pad16(d.cout);
+        st |= nalloc(n, &n->wf[l], e) | nalloc(n, &n->wd[l], e);
+    }
+    st |= nalloc(n, &n->x0, P * 16) | nalloc(n, &n->a0, P * 16) | nalloc(n, &n->f0, P * 16) | nalloc(n, &n->p0, P2 * 16);
+    st |= nalloc(n, &n->a1, P2 * 32) | nalloc(n, &n->f1, P2 * 32) | nalloc(n, &n->p1, P4 * 32);
+    st |= nalloc(n, &n->a2, P4 * 64) | nalloc(n, &n->f2, P4 * 64) | nalloc(n, &n->c1, P2 * 96);
+    st |= nalloc(n, &n->a3, P2 * 32) | nalloc(n, &n->d1, P2 * 32) | nalloc(n, &n->c0, P * 48);
+    st |= nalloc(n, &n->a4, P * 16) | nalloc(n, &n->d0, P * 16) | nalloc(n, &n->a5, P * 16);
+    st |= nalloc(n, &n->gA, P * 48) | nalloc(n, &n->gB, P * 48) | nalloc(n, &n->gC, P * 48) | nalloc(n, &n->gLo, P * 16);
+    st |= nalloc(n, &n->gskip0, P * 16) | nalloc(n, &n->gskip1, P2 * 32) | nalloc(n, &n->out, P * 8);
+    if (st != FLR_OK) {
+        flnr_destroy(n);
+        return FLR_ERR_NOMEM;
+    }
+    cudaMemset(n->g, 0, off * sizeof(float));
+    cudaMemset(n->m, 0, off * sizeof(float));
+    cudaMemset(n->v, 0, off * sizeof(float));
+    *out = n;
+    return FLR_OK;
+}
+
+int flnr_destroy(flnr_net *n)
+{
+    if (!n) return FLR_OK;
+    cudaDeviceSynchronize();
+    for (void *p : n->bufs) cudaFree(p);
+    delete n;
+    return FLR_OK;
+}
+
+int flnr_set_weights(flnr_net *n, const float *host, size_t count)
+{
+    if (!n || !host || count != n->nparam) return FLR_ERR_ARG;
+    if (cudaMemcpy(n->w, host, count * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return FLR_ERR_CUDA;
+    if (cudaMemset(n->m, 0, count * sizeof(float)) != cudaSuccess || cudaMemset(n->v, 0, count * sizeof(float)) != cudaSuccess)
+        return FLR_ERR_CUDA;
+    if (refresh_weights(n, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FLR_ERR_CUDA;
+    return FLR_OK;
+}
+
+int flnr_get_weights(flnr_net *n, float *host, size_t count)
+{
+    if (!n || !host || count != n->nparam) return FLR_ERR_ARG;
+    return cudaMemcpy(host, n->w, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+int flnr_get_grads(flnr_net *n, float *host, size_t count)
+{
+    if (!n || !host || count != n->nparam) return FLR_ERR_ARG;
+    return cudaMemcpy(host, n->g, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+int flnr_zero_grads(flnr_net *n, void *stream)
+{
+    if (!n) return FLR_ERR_ARG;
+    return cudaMemsetAsync(n->g, 0, n->nparam * sizeof(float), (cudaStream_t)stream) == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+#define FLNR_TRY(x)                                 \
+    do {                                            \
+        if ((x) != cudaSuccess) return FLR_ERR_CUDA; \
+    } while (0)
+
+int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, int H, int W, void *stream)
+{
+    using namespace flnr;
+    if (!n || !in || N <= 0 || H <= 0 || W <= 0 || (H % 4) || (W % 4)) return FLR_ERR_ARG;
+    if ((long long)N * H * W > n->max_pix) return FLR_ERR_UNSUPPORTED;
+    if (!n->weights_fresh) return FLR_ERR_ARG;  // flnr_set_weights first
+    cudaStream_t st = (cudaStream_t)stream;
+    n->N = N;
+    n->H = H;
+    n->W = W;
+    const size_t P = (size_t)N * H * W;
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    auto bias = [&](int l) { return n->w + n->poff[l][1]; };
+    pack_input_kernel<<<egrid(P), 256, 0, st>>>(in, n->x0, N, H, W);
+    FLNR_TRY(cudaGetLastError());
+    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>({n->x0, n->wf[0], nullptr, bias(0), n->a0, nullptr, N, H, W, 16, kLayers[0].cout}, st)));
+    FLNR_TRY((conv_launch<16, 16, 1, 1, 0, false>({n->a0, n->wf[1], nullptr, bias(1), n->f0, nullptr, N, H, W, 16, kLayers[1].cout}, st)));
+    pool_kernel<<<egrid(P / 4 * 16), 256, 0, st>>>(n->f0, n->p0, N, H, W, 16);
+    FLNR_TRY((conv_launch<16, 32, 3, 1, 0, false>({n->p0, n->wf[2], nullptr, bias(2), n->a1, nullptr, N, H2, W2, 32, kLayers[2].cout}, st)));
+    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false>({n->a1, n->wf[3], nullptr, bias(3), n->f1, nullptr, N, H2, W2, 32, kLayers[3].cout}, st)));
+    pool_kernel<<<egrid(P / 16 * 32), 256, 0, st>>>(n->f1, n->p1, N, H2, W2, 32);
+    FLNR_TRY((conv_launch<32, 64, 3, 1, 0, false>({n->p1, n->wf[4], nullptr, bias(4), n->a2, nullptr, N, H4, W4, 64, kLayers[4].cout}, st)));
+    FLNR_TRY((conv_launch<64, 64, 3, 1, 0, false>({n->a2, n->wf[5], nullptr, bias(5), n->f2, nullptr, N, H4, W4, 64, kLayers[5].cout}, st)));
+    upcat_kernel<<<egrid(P / 4 * 96), 256, 0, st>>>(n->f2, n->f1, n->c1, N, H2, W2, 64, 32);
+    FLNR_TRY((conv_launch<96, 32, 3, 1, 0, false>({n->c1, n->wf[6], nullptr, bias(6), n->a3, nullptr, N, H2, W2, 32, kLayers[6].cout}, st)));
+    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false>({n->a3, n->wf[7], nullptr, bias(7), n->d1, nullptr, N, H2, W2, 32, kLayers[7].cout}, st)));
+    upcat_kernel<<<egrid(P * 48), 256, 0, st>>>(n->d1, n->f0, n->c0, N, H, W, 32, 16);
+    FLNR_TRY((conv_launch<48, 16, 3, 1, 0, false>({n->c0, n->wf[8], nullptr, bias(8), n->a4, nullptr, N, H, W, 16, kLayers[8].cout}, st)));
+    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>({n->a4, n->wf[9], nullptr, bias(9), n->d0, nullptr, N, H, W, 16, kLayers[9].cout}, st)));
+    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>({n->d0, n->wf[10], nullptr, bias(10), n->a5, nullptr, N, H, W, 16, kLayers[10].cout}, st)));
+    float *yf = guide_out ? guide_out : n->out;
+    FLNR_TRY((conv_launch<16, 16, 1, 2, 1, false>({n->a5, n->wf[11], nullptr, bias(11), nullptr, yf, N, H, W, 16, kLayers[11].cout}, st)));
+    if (guide_out)
+        FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return FLR_OK;
+}
+
+int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
+{
+    using namespace flnr;
+    if (!n || !grad_out || n->N <= 0) return FLR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = n->N, H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const size_t P = (size_t)N * H * W;
+    const int ns = n->n_sm;
+    auto gw = [&](int l) { return n->g + n->poff[l][0]; };
+    auto gb = [&](int l) { return n->g + n->poff[l][1]; };
+    auto bgrad = [&](const __nv_bfloat16 *dz, long long pix, int C, int ctrue, int l) {
+        bias_grad_kernel<<<64, 256, 0, st>>>(dz, gb(l), pix, C, ctrue);
+    };
+    // output head: sigmoid, o1 (1x1, 16 -> 8 padded to 16), o0
+    sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W);
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, 8, ns, st)));
+    bgrad(n->gA, (long long)P, 16, 8, 11);
+    FLNR_TRY((conv_launch<16, 16, 1, 0, 0, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, ns, st)));
+    bgrad(n->gB, (long long)P, 16, 16, 10);
+    FLNR_TRY((conv_launch<16, 16, 3, 0, 0, true>({n->gB, n->wd[10], n->d0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
+    // decoder level 0
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, ns, st)));
+    bgrad(n->gA, (long long)P, 16, 16, 9);
+    FLNR_TRY((conv_launch<16, 16, 3, 0, 0, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, ns, st)));
+    bgrad(n->gB, (long long)P, 16, 16, 8);
+    FLNR_TRY((conv_launch<16, 48, 3, 0, 0, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, st)));
+    upcat_bwd_kernel<<<egrid(P * 48), 256, 0, st>>>(n->gC, n->d1, n->gLo, n->gskip0, N, H, W, 32, 16);  // gLo = dz(d1b)
+    // decoder level 1 (H/2)
+    const size_t P2 = P / 4;
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, ns, st)));
+    bgrad(n->gLo, (long long)P2, 32, 32, 7);
+    FLNR_TRY((conv_launch<32, 32, 3, 0, 0, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
+    FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, ns, st)));
+    bgrad(n->gA, (long long)P2, 32, 32, 6);
+    FLNR_TRY((conv_launch<32, 96, 3, 0, 0, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, st)));
+    upcat_bwd_kernel<<<egrid(P2 * 96), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
+    // encoder level 2 (H/4)
+    const size_t P4 = P / 16;
+    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gLo, gw(5), N, H4, W4, 64, 64, ns, st)));
+    bgrad(n->gLo, (long long)P4, 64, 64, 5);
+    FLNR_TRY((conv_launch<64, 64, 3, 0, 0, true>({n->gLo, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H4, W4, 64}, st)));
+    FLNR_TRY((wgrad_launch<32, 64, 3>(n->p1, n->gA, gw(4), N, H4, W4, 32, 64, ns, st)));
+    bgrad(n->gA, (long long)P4, 64, 64, 4);
+    FLNR_TRY((conv_launch<64, 32, 3, 0, 0, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H4, W4, 32}, st)));
+    pool_bwd_kernel<<<egrid(P2 * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gLo, N, H2, W2, 32);  // dz(e1b)
+    // encoder level 1 (H/2)
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gLo, gw(3), N, H2, W2, 32, 32, ns, st)));
+    bgrad(n->gLo, (long long)P2, 32, 32, 3);
+    FLNR_TRY((conv_launch<32, 32, 3, 0, 0, true>({n->gLo, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
+    FLNR_TRY((wgrad_launch<16, 32, 3>(n->p0, n->gA, gw(2), N, H2, W2, 16, 32, ns, st)));
+    bgrad(n->gA, (long long)P2, 32, 32, 2);
+    FLNR_TRY((conv_launch<32, 16, 3, 0, 0, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 16}, st)));
+    pool_bwd_kernel<<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
+    // input projection (H)
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, ns, st)));
+    bgrad(n->gLo, (long long)P, 16, 16, 1);
+    FLNR_TRY((conv_launch<16, 16, 1, 0, 0, true>({n->gLo, n->wd[1], n->a0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->x0, n->gA, gw(0), N, H, W, 11, 16, ns, st)));
+    bgrad(n->gA, (long long)P, 16, 16, 0);
+    return cudaGetLastError() == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One layer's kernels by themselves (flnr_layer): CI / CO are the padded channel counts.
+template <int CI, int CO, int KS>
+int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const void *mask, void *out, int N, int H,
+              int W, cudaStream_t st)
+{
+    using namespace flnr;
+    using bf = __nv_bfloat16;
+    const auto &d = kLayers[l];
+    const long long P = (long long)N * H * W;
+    if (op == FLNR_OP_FORWARD) {
+        const float *bias = n->w + n->poff[l][1];
+        if (l == kNL - 1)
+            FLNR_TRY((conv_launch<CI, CO, KS, 2, 1, false>({(const bf *)a, n->wf[l], nullptr, bias, nullptr, (float *)out, N, H, W, CO, d.cout}, st)));
+        else
+            FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false>({(const bf *)a, n->wf[l], nullptr, bias, (bf *)out, nullptr, N, H, W, CO, d.cout}, st)));
+    } else if (op == FLNR_OP_DGRAD) {
+        if (mask)
+            FLNR_TRY((conv_launch<CO, CI, KS, 0, 0, true>({(const bf *)a, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+        else
+            FLNR_TRY((conv_launch<CO, CI, KS, 0, 0, false>({(const bf *)a, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+    } else {
+        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, (const bf *)b, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->n_sm, st)));
+        bias_grad_kernel<<<64, 256, 0, st>>>((const bf *)b, n->g + n->poff[l][1], P, CO, d.cout);
+        FLNR_TRY(cudaGetLastError());
+    }
+    return FLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, const void *mask, void *out, int N, int H,
+               int W, void *stream)
+{
+    if (!n || layer < 0 || layer >= flnr::kNL || op < FLNR_OP_FORWARD || op > FLNR_OP_WGRAD || !a || N <= 0 ||
+        H <= 0 || W <= 0)
+        return FLR_ERR_ARG;
+    if ((op == FLNR_OP_WGRAD && !b) || (op != FLNR_OP_WGRAD && !out)) return FLR_ERR_ARG;
+    if ((long long)N * H * W > 0x7fffffffLL) return FLR_ERR_ARG;
+    if (!n->weights_fresh) return FLR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (layer) {
+    case 0: return layer_ops<16, 16, 3>(n, 0, op, a, b, mask, out, N, H, W, st);
+    case 1: return layer_ops<16, 16, 1>(n, 1, op, a, b, mask, out, N, H, W, st);
+    case 2: return layer_ops<16, 32, 3>(n, 2, op, a, b, mask, out, N, H, W, st);
+    case 3: return layer_ops<32, 32, 3>(n, 3, op, a, b, mask, out, N, H, W, st);
+    case 4: return layer_ops<32, 64, 3>(n, 4, op, a, b, mask, out, N, H, W, st);
+    case 5: return layer_ops<64, 64, 3>(n, 5, op, a, b, mask, out, N, H, W, st);
+    case 6: return layer_ops<96, 32, 3>(n, 6, op, a, b, mask, out, N, H, W, st);
+    case 7: return layer_ops<32, 32, 3>(n, 7, op, a, b, mask, out, N, H, W, st);
+    case 8: return layer_ops<48, 16, 3>(n, 8, op, a, b, mask, out, N, H, W, st);
+    case 9: return layer_ops<16, 16, 3>(n, 9, op, a, b, mask, out, N, H, W, st);
+    case 10: return layer_ops<16, 16, 3>(n, 10, op, a, b, mask, out, N, H, W, st);
+    default: return layer_ops<16, 16, 1>(n, 11, op, a, b, mask, out, N, H, W, st);
+    }
+}
+
+int flnr_adam_step(flnr_net *n, float lr, float beta1, float beta2, float eps, int step, void *stream)
+{
+    if (!n || step < 1 || !(lr >= 0.f)) return FLR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    flnr::adam_kernel<<<flnr::egrid(n->nparam), 256, 0, st>>>(n->w, n->g, n->m, n->v, n->nparam, lr, beta1, beta2, eps, c1, c2);
+    FLNR_TRY(cudaGetLastError());
+    FLNR_TRY(refresh_weights(n, st));
+    return FLR_OK;
+}
+
+int flnr_l1_loss(const float *pred, const float *ref, float *grad, float *loss, size_t count, void *stream)
+{
+    if (!pred || !ref || !grad || !loss || count == 0) return FLR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    FLNR_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    flnr::l1_kernel<<<flnr::egrid(count) < 1024 ? flnr::egrid(count) : 1024, 256, 0, st>>>(pred, ref, grad, loss, count);
+    return cudaGetLastError() == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+}  // extern "C"

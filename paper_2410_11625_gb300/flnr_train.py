@@ -1,0 +1,135 @@
+"""FLNR training and evaluation (Sec. 3.3): the guide network is trained end to end
+through FLR, on crops of the project's own rendered scenes.
+
+One training step (batch B of c x c crops):
+  X' = FLNR(X || Y)                      flnr_guide_forward
+  I_b = FLR(X'_b, Y_b), per crop         flr_denoise (X' is both model and map guide)
+  L = mean |I - I_ref|, dL/dI             flnr_l1_loss
+  dL/dX'_b = FLR adjoint, per crop       flr_backward
+  parameter gradients                     flnr_guide_backward
+  Adam on the FP32 master weights         flnr_adam_step (BF16 copies refreshed)
+Every step runs in the library's kernels; this module samples crops on the host and
+moves them to the device.  Data: `synth.render` scenes with 1 spp inputs and high-spp
+references; held-out evaluation scenes use seeds >= 1,000,000.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import flnr as _flnr
+from . import flr as _flr
+
+EVAL_SEED0 = 1_000_000
+
+
+def render_scenes(seeds, H, W, ref_spp=1024, noise=1):
+    """Per seed: (x [11,H,W], ref [3,H,W], albedo [3,H,W], extra [noise-1,3,H,W]) float32,
+    x = guides ++ 1 spp radiance; `extra` holds further independent 1 spp renders of the
+    same scene (cheap next to the reference), which training draws from as well."""
+    import synth
+    out = []
+    for s in seeds:
+        g, y, ref = synth.render(int(s), H, W, ref_spp=ref_spp)
+        extra = synth.render_noise(int(s), H, W, noise - 1) if noise > 1 else np.empty((0, 3, H, W), np.float32)
+        out.append((np.ascontiguousarray(np.concatenate([g, y])), ref, g[:3].copy(), extra))
+    return out
+
+
+def sample_batch(rng, scenes, batch, crop):
+    """Random crops (random scene, noise realisation, position, horizontal / vertical flips):
+    x [B,11,c,c], ref [B,3,c,c]."""
+    xs = np.empty((batch, 11, crop, crop), np.float32)
+    rs = np.empty((batch, 3, crop, crop), np.float32)
+    for b in range(batch):
+        x, ref, _, extra = scenes[rng.integers(len(scenes))]
+        H, W = x.shape[1:]
+        i, j = rng.integers(0, H - crop + 1), rng.integers(0, W - crop + 1)
+        k = rng.integers(len(extra) + 1)
+        cx = x[:, i:i + crop, j:j + crop]
+        if k > 0:
+            cx = np.concatenate([cx[:8], extra[k - 1][:, i:i + crop, j:j + crop]])
+        cr = ref[:, i:i + crop, j:j + crop]
+        if rng.random() < 0.5:
+            cx, cr = cx[:, :, ::-1], cr[:, :, ::-1]
+        if rng.random() < 0.5:
+            cx, cr = cx[:, ::-1], cr[:, ::-1]
+        xs[b], rs[b] = cx, cr
+    return xs, rs
+
+
+class Trainer:
+    """Holds the network, the FLR handle and the device buffers of one batch shape."""
+
+    def __init__(self, weights, batch=16, crop=128, radius=8, eps=1e-3, lr=1e-3, device="cuda"):
+        import torch
+        self.B, self.c, self.lr = batch, crop, lr
+        self.net = _flnr.FLNR(batch * crop * crop, weights)
+        self.flr = _flr.FLR(q=8, radius=radius, eps=eps)
+        self.flr.reserve(crop, crop)
+        opt = dict(dtype=torch.float32, device=device)
+        self.x_host = torch.empty((batch, 11, crop, crop), dtype=torch.float32).pin_memory()
+        self.r_host = torch.empty((batch, 3, crop, crop), dtype=torch.float32).pin_memory()
+        self.x = torch.empty((batch, 11, crop, crop), **opt)
+        self.ref = torch.empty((batch, 3, crop, crop), **opt)
+        self.guides = torch.empty((batch, 8, crop, crop), **opt)
+        self.out = torch.empty((batch, 3, crop, crop), **opt)
+        self.g_guides = torch.empty((batch, 8, crop, crop), **opt)
+        self.g_rad = torch.empty((3, crop, crop), **opt)
+        self.steps = 0
+
+    def step(self, xs, rs):
+        """One optimisation step on host crops; returns the loss as a device tensor."""
+        self.x_host.numpy()[...] = xs
+        self.r_host.numpy()[...] = rs
+        self.x.copy_(self.x_host, non_blocking=True)
+        self.ref.copy_(self.r_host, non_blocking=True)
+        self.net.forward(self.x, out=self.guides)
+        for b in range(self.B):
+            self.flr.denoise(self.guides[b], self.x[b, 8:11], out=self.out[b])
+        loss, g_out = _flnr.l1_loss(self.out, self.ref)
+        for b in range(self.B):
+            self.flr.backward(self.guides[b], self.x[b, 8:11], g_out[b], grad_guide=self.g_guides[b],
+                              grad_radiance=self.g_rad)
+        self.net.zero_grads(self.x)
+        self.net.backward(self.g_guides)
+        self.steps += 1
+        self.net.adam_step(self.steps, lr=self.lr, stream_of=self.x)
+        return loss
+
+    def train(self, scenes, steps, seed=0, lr_final=None, log_every=0):
+        """`steps` Adam steps on random crops of `scenes`; cosine decay to lr_final."""
+        rng = np.random.default_rng(seed)
+        lr0, lr1 = self.lr, (self.lr if lr_final is None else lr_final)
+        losses = []
+        for t in range(steps):
+            self.lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * t / max(steps, 1)))
+            loss = self.step(*sample_batch(rng, scenes, self.B, self.c))
+            if log_every and (t % log_every == 0 or t == steps - 1):
+                losses.append((t, float(loss.item())))
+        self.lr = lr0
+        return losses
+
+
+def psnr(img, ref):
+    """PSNR in dB of the albedo-modulated images clamped to [0, 1] (peak 1)."""
+    a = np.clip(np.asarray(img, np.float64), 0.0, 1.0)
+    b = np.clip(np.asarray(ref, np.float64), 0.0, 1.0)
+    return float(10.0 * np.log10(1.0 / max(np.mean((a - b) ** 2), 1e-20)))
+
+
+def evaluate(net, flr, scenes):
+    """PSNR of plain FLR (rendered guides) and of FLNR (network guides) against each
+    scene's reference, after albedo modulation.  Returns two lists."""
+    import torch
+    p_flr, p_flnr = [], []
+    for x, ref, alb, _ in scenes:
+        xd = torch.from_numpy(x[None]).cuda()
+        y = xd[0, 8:11]
+        plain = flr.denoise(xd[0, :8], y).cpu().numpy()
+        guides = net.forward(xd)
+        learned = flr.denoise(guides[0], y).cpu().numpy()
+        p_flr.append(psnr(plain * alb, ref * alb))
+        p_flnr.append(psnr(learned * alb, ref * alb))
+    return p_flr, p_flnr

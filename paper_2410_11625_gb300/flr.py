@@ -20,7 +20,10 @@ EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoi
            "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
            "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
            "flr_fast_denoise", "flr_fast_get_stats", "flr_denoise_batch", "flr_fast_reserve_batch",
-           "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest")
+           "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest",
+           "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
+           "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_get_grads",
+           "flnr_adam_step", "flnr_l1_loss", "flnr_layer")
 BATCH_TIMEOUT = 1
 FLAG_TIMING = 1
 
@@ -185,9 +188,11 @@ class FLR:
         _check(load_library().flr_denoise(self._h, g, m, r, o, H, W, st), "flr_denoise")
         return out
 
-    def backward(self, guide, radiance, grad_out, map_guide=None, need_eps=False, stream=None):
+    def backward(self, guide, radiance, grad_out, map_guide=None, need_eps=False, stream=None,
+                 grad_guide=None, grad_radiance=None):
         """Device FLR adjoint: gradients of <grad_out, I> for guide, radiance, map guide
-        (when given) and eps.  Returns a dict of CUDA tensors (eps as a 1-element float64)."""
+        (when given) and eps.  Returns a dict of CUDA tensors (eps as a 1-element float64);
+        grad_guide / grad_radiance may be given as preallocated outputs."""
         import torch
         H, W = int(radiance.shape[-2]), int(radiance.shape[-1])
         dev = radiance.device
@@ -195,8 +200,10 @@ class FLR:
         r = _dev_ptr(radiance, "radiance", (3, H, W))
         go = _dev_ptr(grad_out, "grad_out", (3, H, W))
         m = None if map_guide is None else _dev_ptr(map_guide, "map_guide", (self.q, H, W))
-        gg = torch.empty((self.q, H, W), dtype=torch.float32, device=dev)
-        gr = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+        gg = torch.empty((self.q, H, W), dtype=torch.float32, device=dev) if grad_guide is None else grad_guide
+        gr = torch.empty((3, H, W), dtype=torch.float32, device=dev) if grad_radiance is None else grad_radiance
+        _dev_ptr(gg, "grad_guide", (self.q, H, W))
+        _dev_ptr(gr, "grad_radiance", (3, H, W))
         gm = torch.empty((self.q, H, W), dtype=torch.float32, device=dev) if map_guide is not None else None
         ge = torch.zeros(1, dtype=torch.float64, device=dev) if need_eps else None
         if stream is None:

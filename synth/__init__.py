@@ -52,6 +52,9 @@ def _load():
         lib.synth_render.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, fp, fp, fp,
                                      ctypes.c_int]
         lib.synth_render.restype = ctypes.c_int
+        lib.synth_render_noise.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.c_int, fp]
+        lib.synth_render_noise.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -72,6 +75,17 @@ def render(seed: int, H: int, W: int, ref_spp: int = 0):
     if st != 0:
         raise ValueError("synth_render: bad arguments")
     return (guide, rad, ref) if ref is not None else (guide, rad)
+
+
+def render_noise(seed: int, H: int, W: int, count: int, first: int = 0):
+    """``count`` further independent 1 spp radiance renders [count,3,H,W] of the scene of
+    ``seed`` (same guides and reference as ``render``), realisations first..first+count-1."""
+    rad = np.empty((count, 3, H, W), np.float32)
+    st = _load().synth_render_noise(ctypes.c_uint64(seed), H, W, ctypes.c_uint64(first), int(count),
+                                    rad.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if st != 0:
+        raise ValueError("synth_render_noise: bad arguments")
+    return rad
 
 
 def random_frame(seed: int, H: int, W: int, q: int = 8, kind: str = "uniform"):

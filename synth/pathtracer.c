@@ -328,6 +328,23 @@ static void indirect_sample(const scene_t *s, uint64_t seed, uint64_t pixel, uin
  *   reference [3][H][W]  or NULL: mean of `ref_spp` further samples (indices 1..ref_spp)
  * Returns 0, or -1 for bad arguments.
  */
+/* Primary hit of pixel (x, y): direction d, hit h, hit point hp, normal n facing the camera. */
+static void primary(const scene_t *s, int x, int y, int H, int W, vec3 *d, hit_t *h, vec3 *hp, vec3 *n)
+{
+    float sx = (2.0f * (x + 0.5f) / W - 1.0f) * s->tan_half_fov * ((float)W / H);
+    float sy = (1.0f - 2.0f * (y + 0.5f) / H) * s->tan_half_fov;
+    *d = vnorm(vadd(s->cam_fwd, vadd(vmul(s->cam_right, sx), vmul(s->cam_up, sy))));
+    if (!intersect(s, s->cam_pos, *d, INFINITY, h)) {
+        /* cannot happen in a closed room; keep the frame well defined */
+        h->t = 1.0f;
+        h->n = v3(0, 1, 0);
+        h->albedo = s->wall_albedo[2];
+    }
+    *hp = vadd(s->cam_pos, vmul(*d, h->t));
+    *n = h->n;
+    if (vdot(*n, *d) > 0) *n = vmul(*n, -1.0f);
+}
+
 int synth_render(uint64_t seed, int H, int W, float *guide, float *radiance, float *reference,
                  int ref_spp)
 {
@@ -341,19 +358,9 @@ int synth_render(uint64_t seed, int H, int W, float *guide, float *radiance, flo
         for (int x = 0; x < W; ++x) {
             const size_t p = (size_t)y * W + x;
             const uint64_t pix = (uint64_t)p;
-            float sx = (2.0f * (x + 0.5f) / W - 1.0f) * s.tan_half_fov * ((float)W / H);
-            float sy = (1.0f - 2.0f * (y + 0.5f) / H) * s.tan_half_fov;
-            vec3 d = vnorm(vadd(s.cam_fwd, vadd(vmul(s.cam_right, sx), vmul(s.cam_up, sy))));
+            vec3 d, hp, n;
             hit_t h;
-            if (!intersect(&s, s.cam_pos, d, INFINITY, &h)) {
-                /* cannot happen in a closed room; keep the frame well defined */
-                h.t = 1.0f;
-                h.n = v3(0, 1, 0);
-                h.albedo = s.wall_albedo[2];
-            }
-            vec3 hp = vadd(s.cam_pos, vmul(d, h.t));
-            vec3 n = h.n;
-            if (vdot(n, d) > 0) n = vmul(n, -1.0f);
+            primary(&s, x, y, H, W, &d, &h, &hp, &n);
             for (int c = 0; c < 3; ++c) guide[(size_t)c * P + p] = h.albedo[c];
             guide[3 * P + p] = n.x;
             guide[4 * P + p] = n.y;
@@ -377,6 +384,37 @@ int synth_render(uint64_t seed, int H, int W, float *guide, float *radiance, flo
                     for (int c = 0; c < 3; ++c) acc[c] += v[c];
                 }
                 for (int c = 0; c < 3; ++c) reference[(size_t)c * P + p] = (float)(acc[c] / ref_spp);
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Further independent one-sample-per-pixel renders of the radiance of the scene of `seed`
+ * (the same guides as synth_render): realisation j in [0, count) uses sample index
+ * NOISE_SAMPLE0 + first + j, apart from the indices of the frame, its reference and AO.
+ *   radiance [count][3][H][W]
+ * Returns 0, or -1 for bad arguments.
+ */
+#define NOISE_SAMPLE0 (1ULL << 40)
+int synth_render_noise(uint64_t seed, int H, int W, uint64_t first, int count, float *radiance)
+{
+    if (H <= 0 || W <= 0 || count <= 0 || !radiance) return -1;
+    scene_t s;
+    build_scene(seed, &s);
+    const size_t P = (size_t)H * W;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            vec3 d, hp, n;
+            hit_t h;
+            primary(&s, x, y, H, W, &d, &h, &hp, &n);
+            for (int j = 0; j < count; ++j) {
+                float v[3];
+                indirect_sample(&s, seed, (uint64_t)p, NOISE_SAMPLE0 + first + (uint64_t)j, hp, n, v);
+                for (int c = 0; c < 3; ++c) radiance[((size_t)j * 3 + c) * P + p] = v[c];
             }
         }
     }

@@ -59,3 +59,75 @@ def test_gradients_match_finite_differences():
             return loss(params, xx)
         fd = rich(fx, 1e-6)
         assert abs(fd - grads["input"][idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def bf16_bits(a):
+    """Round-to-nearest-even of float32 values to bfloat16, by integer arithmetic on the
+    IEEE-754 bit patterns (finite inputs): keep the top 16 bits, adding 0x7FFF plus the
+    lowest kept bit before truncating."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_rounding_is_nearest_even():
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.normal(size=4000) * 10.0 ** rng.integers(-6, 6, 4000),
+                        # exact ties between two bfloat16 neighbours, both parities
+                        np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 2 ** -8 + 2 ** -16, 0.0])])
+    got = flnr_ref.round_bf16(torch.tensor(v)).numpy()
+    assert np.array_equal(got, bf16_bits(v.astype(np.float32)))
+    assert got[-5] == 1.0 and got[-4] == 1 + 4 * 2 ** -8 and got[-3] == -1.0
+
+
+def test_bf16_storage_forward_matches_explicit_rounding():
+    """The emulated forward equals a numpy restatement: log(1 + max(Y, 0)) radiance input,
+    explicit-sum convolutions in float64 with bit-level bfloat16 rounding of the input,
+    weights, ReLU outputs and pooled maps (Sec. 3.3's network)."""
+    rng = np.random.default_rng(7)
+    params = flnr_ref.init_weights(4)
+    for k in params:
+        if k.endswith(".b"):
+            params[k] = rng.normal(scale=0.05, size=params[k].shape).astype(np.float32)
+    x = rng.uniform(size=(1, 11, 8, 12))
+    x[:, 8:] = rng.normal(size=(1, 3, 8, 12)) * 3.0  # negative and firefly-like radiance
+    pt = {k: torch.tensor(v.astype(np.float64)) for k, v in params.items()}
+    got = flnr_ref.forward(torch.tensor(x), pt, bf16_storage=True).numpy()
+
+    def conv(t, n, relu=True):
+        z = flnr_ref.conv2d_direct(t, bf16_bits(params[n + ".w"]), params[n + ".b"].astype(np.float64))
+        return bf16_bits(np.maximum(z, 0.0)) if relu else z
+
+    def pool(t):
+        N, C, H, W = t.shape
+        return bf16_bits(t.reshape(N, C, H // 2, 2, W // 2, 2).mean(axis=(3, 5)))
+
+    def up(t):
+        return t.repeat(2, axis=2).repeat(2, axis=3)
+
+    xin = np.concatenate([x[:, :8], np.log1p(np.maximum(x[:, 8:], 0.0))], axis=1)
+    f0 = conv(conv(bf16_bits(xin), "in0"), "in1")
+    f1 = conv(conv(pool(f0), "e1a"), "e1b")
+    f2 = conv(conv(pool(f1), "e2a"), "e2b")
+    d1 = conv(conv(np.concatenate([up(f2), f1], 1), "d1a"), "d1b")
+    d0 = conv(conv(np.concatenate([up(d1), f0], 1), "d0a"), "d0b")
+    ref = 1.0 / (1.0 + np.exp(-conv(conv(d0, "o0"), "o1", relu=False)))
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_bf16_storage_gradients_of_the_head():
+    """Under BF16 storage the output bias gradient is the pixel sum of the bfloat16-rounded
+    sigmoid gradient g s (1 - s), and the emulated gradients stay close to the float64 ones
+    (a few bfloat16 rounding units of the gradient's scale)."""
+    rng = np.random.default_rng(8)
+    params = flnr_ref.init_weights(6)
+    x = rng.uniform(size=(1, 11, 12, 16))
+    G = rng.normal(size=(1, 8, 12, 16))
+    out, g16 = flnr_ref.forward_backward(x, params, G, bf16_storage=True)
+    ref_b = bf16_bits((G * out * (1.0 - out)).astype(np.float32)).sum(axis=(0, 2, 3))
+    assert np.max(np.abs(g16["o1.b"] - ref_b)) < 1e-9
+    out64, g64 = flnr_ref.forward_backward(x, params, G)
+    assert np.max(np.abs(out - out64)) < 3e-2
+    for name in ("o1.w", "o0.w", "d0b.w"):
+        a, b = g16[name], g64[name]
+        assert np.sum(a * b) / np.linalg.norm(a) / np.linalg.norm(b) > 0.95, name
