@@ -231,6 +231,8 @@ def serving_batch(flr, torch, np, dev, stream, n_iter=100):
             "what": "flr_fast_denoise_batch: one persistent cooperative kernel, 4 stages x 8 frames"}
 
 
+ROW_NAMES = ("backward", "fast", "joint", "serving", "flnr")
+
 # FLNR network (Sec. 3.3): multiply-accumulates per full-resolution pixel, layer by layer
 # (Cin x Cout x k^2, divided by 4 at half and 16 at quarter resolution)
 FLNR_MACS_PER_PIXEL = (11 * 16 * 9 + 16 * 16 + (16 * 32 * 9 + 32 * 32 * 9) / 4 + (32 * 64 * 9 + 64 * 64 * 9) / 16
@@ -242,6 +244,8 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
     rooms, 1080p inference time (network + FLR on its guides), training-step time."""
     from paper_2410_11625_gb300 import flnr, flnr_train, flr
     rows = {}
+    if train_steps <= 0:  # timing only, with the initial weights
+        return flnr_inference_row(flnr.init_weights(0), dev_frames, torch, dev, timed, rows)
     t0 = time.perf_counter()
     scenes = flnr_train.render_scenes(range(1, 33), 192, 192, ref_spp=1024, noise=8)
     held_out = flnr_train.render_scenes(range(flnr_train.EVAL_SEED0, flnr_train.EVAL_SEED0 + 6), 256, 256,
@@ -268,9 +272,14 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
     rows["flnr_train_step"] = {"ms_per_step": round(t_step, 4),
                                "what": "batch 16 x 128x128: FLNR fwd, 16 x FLR, L1, 16 x FLR adjoint, FLNR bwd, Adam; "
                                        "includes the pinned H2D copy of the batch"}
-    # 1080p inference with the trained weights
     weights = tr.net.get_weights()
     tr.net.close()
+    return flnr_inference_row(weights, dev_frames, torch, dev, timed, rows)
+
+
+def flnr_inference_row(weights, dev_frames, torch, dev, timed, rows):
+    """1080p inference: the network, FLR on its guides, and both in sequence."""
+    from paper_2410_11625_gb300 import flnr, flr
     net = flnr.FLNR(H * W, weights)
     f = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
     f.reserve(H, W)
@@ -365,26 +374,31 @@ def run_ours(args):
         return e0.elapsed_time(e1) / n
 
     rows = {}
-    fb = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
-    gout = torch.randn((3, H, W), dtype=torch.float32, device=dev)
-    rows["backward_1080p"] = {"ms_per_frame": round(timed(lambda i: fb.backward(*dev_frames[i % N_FRAMES], gout), 20), 4),
-                              "what": "flr_backward: guide, radiance gradients, r=rc=8"}
-    fb.close()
-    ff = flr.FastFLR(q=Q, factor=8, scale=1, sigma=1.25, taps=3, eps=EPS, pivot_ratio=TAU)
-    t_fast = timed(lambda i: ff.denoise(*dev_frames[i % N_FRAMES], out=out), 200)
-    ff.close()
-    rows["fast_flr_1080p"] = {"ms_per_frame": round(t_fast, 5),
-                              "hbm_frac": round(frame_bytes(Q) / (t_fast * 1e-3) / 1e9 / float(load_peaks()[0]["hbm_gbs"]), 4),
-                              "what": "Sec. 3.2 fast FLR: 8x8 block moments, Gaussian sigma 1.25 blocks, 3 taps"}
-    lo = [(torch.from_numpy(np.ascontiguousarray(g[:, ::2, ::2])).to(dev),
-           torch.from_numpy(np.ascontiguousarray(y[:, ::2, ::2])).to(dev)) for g, y in frames[:2]]
-    fj = flr.FastFLR(q=Q, factor=4, scale=2, sigma=1.25, taps=3, eps=EPS, pivot_ratio=TAU)
-    t_joint = timed(lambda i: fj.denoise(*lo[i % 2], map_guide=dev_frames[i % 2][0], out=out), 200)
-    fj.close()
-    rows["joint_upsample_2x_1080p"] = {"ms_per_frame": round(t_joint, 5),
-                                       "what": "Sec. 3.2.1: 960x540 radiance and model guides, 1920x1080 map guide and output"}
-    rows["batch_serving"] = serving_batch(flr, torch, np, dev, stream)
-    if rank == 0 and args.flnr_steps > 0:
+    want = set(ROW_NAMES) if args.rows == "all" else set(args.rows.split(",")) - {"none"}
+    if "backward" in want:
+        fb = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
+        gout = torch.randn((3, H, W), dtype=torch.float32, device=dev)
+        rows["backward_1080p"] = {"ms_per_frame": round(timed(lambda i: fb.backward(*dev_frames[i % N_FRAMES], gout), 20), 4),
+                                  "what": "flr_backward: guide, radiance gradients, r=rc=8"}
+        fb.close()
+    if "fast" in want:
+        ff = flr.FastFLR(q=Q, factor=8, scale=1, sigma=1.25, taps=3, eps=EPS, pivot_ratio=TAU)
+        t_fast = timed(lambda i: ff.denoise(*dev_frames[i % N_FRAMES], out=out), 200)
+        ff.close()
+        rows["fast_flr_1080p"] = {"ms_per_frame": round(t_fast, 5),
+                                  "hbm_frac": round(frame_bytes(Q) / (t_fast * 1e-3) / 1e9 / float(load_peaks()[0]["hbm_gbs"]), 4),
+                                  "what": "Sec. 3.2 fast FLR: 8x8 block moments, Gaussian sigma 1.25 blocks, 3 taps"}
+    if "joint" in want:
+        lo = [(torch.from_numpy(np.ascontiguousarray(g[:, ::2, ::2])).to(dev),
+               torch.from_numpy(np.ascontiguousarray(y[:, ::2, ::2])).to(dev)) for g, y in frames[:2]]
+        fj = flr.FastFLR(q=Q, factor=4, scale=2, sigma=1.25, taps=3, eps=EPS, pivot_ratio=TAU)
+        t_joint = timed(lambda i: fj.denoise(*lo[i % 2], map_guide=dev_frames[i % 2][0], out=out), 200)
+        fj.close()
+        rows["joint_upsample_2x_1080p"] = {"ms_per_frame": round(t_joint, 5),
+                                           "what": "Sec. 3.2.1: 960x540 radiance and model guides, 1920x1080 map guide and output"}
+    if "serving" in want:
+        rows["batch_serving"] = serving_batch(flr, torch, np, dev, stream)
+    if rank == 0 and "flnr" in want:
         rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps))
 
     if rank != 0:
@@ -483,8 +497,10 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rows", default="all",
+                    help="comma list of extra rows to run: " + ",".join(ROW_NAMES) + " (or all, none)")
     ap.add_argument("--flnr-steps", type=int, default=2000,
-                    help="FLNR training steps before its PSNR and 1080p rows (0 skips the FLNR rows)")
+                    help="FLNR training steps before its PSNR and 1080p rows (0: 1080p timing only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

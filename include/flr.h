@@ -311,7 +311,14 @@ int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, 
  * 16: CinP = 16 * ceil(Cin / 16), CoutP likewise; the padding channels of the outputs are
  * written (as zero where the padded weights are zero).
  *   FLNR_OP_FORWARD  a = x [N][H][W][CinP]; out = y [N][H][W][CoutP] = bf16(ReLU(conv(x) + b)),
- *                    or, for layer 11, float32 planar [N][8][H][W] = sigmoid(conv(x) + b)
+ *                    or, for layer 11, float32 planar [N][8][H][W] = sigmoid(conv(x) + b).
+ *                    Layers 6 and 8 with b != NULL: a = the half-resolution decoder input
+ *                    [N][H/2][W/2][64 or 32] and b = the skip [N][H][W][32 or 16]; the
+ *                    kernel forms their concatenation (nearest 2x upsampling of a, then b)
+ *                    while loading, as the network does.  Layers 1 and 3 with out2 != NULL:
+ *                    out2 [N][H/2][W/2][CoutP] also receives the 2x2 average of the stored
+ *                    bf16 outputs, rounded to bf16, as the network's encoder reads it.
+ *                    Both fused forms need H and W even.
  *   FLNR_OP_DGRAD    a = dz [N][H][W][CoutP] (gradient w.r.t. the layer's pre-activation);
  *                    mask = [N][H][W][CinP] or NULL; out = dx [N][H][W][CinP] =
  *                    bf16((mask > 0) * transposed convolution of dz)
@@ -323,7 +330,7 @@ int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, 
 #define FLNR_OP_DGRAD 1
 #define FLNR_OP_WGRAD 2
 int flnr_layer(flnr_net *net, int layer, int op, const void *a, const void *b, const void *mask, void *out,
-               int N, int H, int W, void *stream);
+               void *out2, int N, int H, int W, void *stream);
 
 /*
  * Backward pass of the last forward: grad_out [N][8][H][W] = dL/d(enhanced guides);

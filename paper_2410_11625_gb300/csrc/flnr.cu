@@ -51,12 +51,25 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
 // ---------------------------------------------------------------------------------------
-// Convolution, implicit GEMM.  M = 128 output pixels (an 8 x 16 tile), N = COUT, K = taps x CIN.
+// Asynchronous 16-byte global -> shared copies (zero fill when !valid).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Convolution (stride 1, zero padding KS/2) as an implicit GEMM on the tensor cores.
 // x [N][H][W][CIN] bf16, w [taps][COUT][CIN] bf16, bias [COUT] fp32.
 // Output: OUTM 0 -> y [N][H][W][ystride] bf16 at channel offset 0 (ACT 1 = ReLU);
 //         OUTM 1 -> yf planar fp32 [N][8][H][W], sigmoid of channels 0..7.
 // MASK: multiply the result by (mask > 0), mask [N][H][W][COUT] bf16 (the ReLU of the layer
-// that produced this gradient's target).
+// input, for input gradients).
+// CA > 0: the input is the concatenation of the nearest 2x upsampling of x [N][H/2][W/2][CA]
+// (channels 0..CA-1) and x2 [N][H][W][CIN-CA] (the rest), formed while staging.
+// POOL: also writes yp [N][H/2][W/2][COUT], the 2x2 average of the bf16 outputs (H, W even).
 struct ConvArgs {
     const bf16 *x, *w, *mask;
     const float *bias;
@@ -64,101 +77,148 @@ struct ConvArgs {
     float *yf;
     int N, H, W, ystride;
     int nbias;  // valid bias entries (the true output channels); 0 without bias
+    const bf16 *x2;
+    bf16 *yp;
 };
 
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK>
-__global__ void __launch_bounds__(128) conv_kernel(const ConvArgs a)
+// Persistent CTAs: the weights are staged in shared memory once per CTA; the CTA then walks
+// tiles of TH = 2 * WARPS rows by 16 pixels, the next tile's input (with halo) loading by
+// cp.async while the current one is computed.  Warp w owns rows 2w, 2w+1 of the tile: two
+// m16 fragments (16 pixels of a row each) times COUT/8 n8 fragments.
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA, bool POOL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
 {
-    constexpr int TH = 8, TW = 16, P = KS / 2;
+    constexpr int NTH = WARPS * 32, TH = 2 * WARPS, TW = 16, P = KS / 2;
     constexpr int SH = TH + 2 * P, SW = TW + 2 * P;
     constexpr int CS = CIN + 8;  // padded pixel stride: conflict-free fragment loads
-    constexpr int NT = COUT / 8;
+    constexpr int NT = COUT / 8, C8 = CIN / 8;
+    constexpr int XT = SH * SW * CS, WT = KS * KS * COUT * CS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *sx = reinterpret_cast<bf16 *>(smem_raw);  // [SH][SW][CS]
-    bf16 *sw = sx + SH * SW * CS;                    // [KS*KS][COUT][CS]
+    bf16 *sw = reinterpret_cast<bf16 *>(smem_raw);  // [KS*KS][COUT][CS]
+    bf16 *sxb = sw + WT;                             // 2 x [SH][SW][CS]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = blockIdx.z, ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-    const size_t img = (size_t)n * a.H * a.W;
-    for (int i = tid; i < SH * SW * (CIN / 8); i += 128) {
-        const int pix = i / (CIN / 8), c8 = i % (CIN / 8);
-        const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-            v = *reinterpret_cast<const uint4 *>(a.x + (img + (size_t)yy * a.W + xx) * CIN + c8 * 8);
-        *reinterpret_cast<uint4 *>(sx + pix * CS + c8 * 8) = v;
+    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
+    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
+    for (int i = tid; i < KS * KS * COUT * C8; i += NTH) {
+        const int row = i / C8, c8 = i % C8;
+        cp_async16(sw + row * CS + c8 * 8, a.w + row * CIN + c8 * 8, true);
     }
-    for (int i = tid; i < KS * KS * COUT * (CIN / 8); i += 128) {
-        const int row = i / (CIN / 8), c8 = i % (CIN / 8);
-        *reinterpret_cast<uint4 *>(sw + row * CS + c8 * 8) = *reinterpret_cast<const uint4 *>(a.w + row * CIN + c8 * 8);
-    }
-    __syncthreads();
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][NT][4];
+    auto stage = [&](int t, bf16 *sx) {
+        const int n = t / per_img, r = t % per_img;
+        const int ty0 = (r / tiles_x) * TH, tx0 = (r % tiles_x) * TW;
+        for (int i = tid; i < SH * SW * C8; i += NTH) {
+            const int pix = i / C8, c8 = i % C8;
+            const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
+            const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = a.x;
+            if (in) {
+                if (CA > 0 && c8 < CA / 8)
+                    src = a.x + (((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2) * CA + c8 * 8;
+                else if (CA > 0)
+                    src = a.x2 + (((size_t)n * a.H + yy) * a.W + xx) * (CIN - CA) + (c8 - CA / 8) * 8;
+                else
+                    src = a.x + (((size_t)n * a.H + yy) * a.W + xx) * CIN + c8 * 8;
+            }
+            cp_async16(sx + pix * CS + c8 * 8, src, in);
+        }
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) stage(t, sxb);
+    cp_async_commit();
+    const int g = lane >> 2, q = lane & 3;
+    for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+        const bf16 *sx = sxb + (it & 1) * XT;
+        if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x, sxb + ((it + 1) & 1) * XT);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        float acc[2][NT][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
 #pragma unroll
-    for (int ky = 0; ky < KS; ++ky)
+        for (int ky = 0; ky < KS; ++ky)
 #pragma unroll
-        for (int kx = 0; kx < KS; ++kx) {
-            const int tap = ky * KS + kx;
+            for (int kx = 0; kx < KS; ++kx) {
+                const int tap = ky * KS + kx;
 #pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                uint32_t af[2][4];
+                for (int kc = 0; kc < CIN / 16; ++kc) {
+                    uint32_t af[2][4];
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const bf16 *r0 = sx + ((2 * warp + mt + ky) * SW + g + kx) * CS + kc * 16 + 2 * t;
-                    const bf16 *r8 = r0 + 8 * CS;
-                    af[mt][0] = ld32(r0);
-                    af[mt][1] = ld32(r8);
-                    af[mt][2] = ld32(r0 + 8);
-                    af[mt][3] = ld32(r8 + 8);
-                }
+                    for (int mt = 0; mt < 2; ++mt) {
+                        const bf16 *r0 = sx + ((2 * warp + mt + ky) * SW + g + kx) * CS + kc * 16 + 2 * q;
+                        const bf16 *r8 = r0 + 8 * CS;
+                        af[mt][0] = ld32(r0);
+                        af[mt][1] = ld32(r8);
+                        af[mt][2] = ld32(r0 + 8);
+                        af[mt][3] = ld32(r8 + 8);
+                    }
 #pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    const bf16 *wb = sw + (tap * COUT + nt * 8 + g) * CS + kc * 16 + 2 * t;
-                    const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
-                    mma_bf16(acc[0][nt], af[0], b0, b1);
-                    mma_bf16(acc[1][nt], af[1], b0, b1);
+                    for (int nt = 0; nt < NT; ++nt) {
+                        const bf16 *wb = sw + (tap * COUT + nt * 8 + g) * CS + kc * 16 + 2 * q;
+                        const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
+                        mma_bf16(acc[0][nt], af[0], b0, b1);
+                        mma_bf16(acc[1][nt], af[1], b0, b1);
+                    }
                 }
             }
-        }
-    // epilogue
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int yy = ty0 + 2 * warp + mt;
+        // epilogue: lane holds pixels g and g + 8 of rows 2w, 2w + 1, channels 2q, 2q + 1 of
+        // each n8 fragment
+        const int n = t / per_img, r = t % per_img;
+        const int ty0 = (r / tiles_x) * TH, tx0 = (r % tiles_x) * TW;
+        const size_t img = (size_t)n * a.H * a.W;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int xx = tx0 + g + 8 * half;
-            if (yy >= a.H || xx >= a.W) continue;
-            const size_t pix = img + (size_t)yy * a.W + xx;
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-                const int c = nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * half] + (c < a.nbias ? a.bias[c] : 0.f);
-                float v1 = acc[mt][nt][2 * half + 1] + (c + 1 < a.nbias ? a.bias[c + 1] : 0.f);
-                if (ACT == 1) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
+                const int c = nt * 8 + 2 * q;
+                float ps0 = 0.f, ps1 = 0.f;  // pooled sums (POOL)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int yy = ty0 + 2 * warp + mt;
+                    const bool in = yy < a.H && xx < a.W;
+                    const size_t pix = img + (size_t)yy * a.W + xx;
+                    float v0 = acc[mt][nt][2 * half] + (c < a.nbias ? a.bias[c] : 0.f);
+                    float v1 = acc[mt][nt][2 * half + 1] + (c + 1 < a.nbias ? a.bias[c + 1] : 0.f);
+                    if (ACT == 1) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                    if (MASK && in) {
+                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + c);
+                        if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                    }
+                    if (OUTM == 0) {
+                        const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+                        if (in) *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ystride + c) = o;
+                        ps0 += __bfloat162float(o.x);
+                        ps1 += __bfloat162float(o.y);
+                    } else if (c < 8 && in) {
+                        const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
+                        a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v0));
+                        a.yf[((size_t)n * 8 + c + 1) * hw + off] = 1.f / (1.f + expf(-v1));
+                    }
                 }
-                if (MASK) {
-                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + c);
-                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
-                }
-                if (OUTM == 0) {
-                    *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ystride + c) = __floats2bfloat162_rn(v0, v1);
-                } else if (c < 8) {
-                    const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
-                    a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v0));
-                    a.yf[((size_t)n * 8 + c + 1) * hw + off] = 1.f / (1.f + expf(-v1));
+                if (POOL) {
+                    // pixel pairs (g, g + 1) sit in lanes 4 apart
+                    ps0 += __shfl_xor_sync(0xffffffffu, ps0, 4);
+                    ps1 += __shfl_xor_sync(0xffffffffu, ps1, 4);
+                    const int yy = ty0 + 2 * warp;
+                    if ((g & 1) == 0 && yy < a.H && xx < a.W) {
+                        const size_t pp = ((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2;
+                        *reinterpret_cast<__nv_bfloat162 *>(a.yp + pp * COUT + c) = __floats2bfloat162_rn(0.25f * ps0, 0.25f * ps1);
+                    }
                 }
             }
         }
+        __syncthreads();  // the next iteration stages into this buffer
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -265,32 +325,27 @@ __global__ void pack_input_kernel(const float *in, bf16 *x, int N, int H, int W)
     }
 }
 
-// 2x2 average pool: x [N][H][W][C] -> y [N][H/2][W/2][C]
-__global__ void pool_kernel(const bf16 *x, bf16 *y, int N, int H, int W, int C)
-{
-    const int Ho = H / 2, Wo = W / 2;
-    const size_t total = (size_t)N * Ho * Wo * C;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const size_t q = e / C;
-        const int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho), n = (int)(q / ((size_t)Wo * Ho));
-        const size_t b = (((size_t)n * H + 2 * yo) * W + 2 * xo) * C + c;
-        const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (size_t)W * C]) +
-                        __bfloat162float(x[b + (size_t)W * C + C]);
-        y[e] = __float2bfloat16(0.25f * s);
-    }
-}
-
-// y [N][H][W][Ca+Cb] = nearest-2x-up(a [N][H/2][W/2][Ca]) ++ b [N][H][W][Cb]
+// nearest 2x upsampling of lo [N][H/2][W/2][Ca] concatenated with skip [N][H][W][Cb] (the
+// input of a decoder level, materialised for its weight gradient)
 __global__ void upcat_kernel(const bf16 *lo, const bf16 *skip, bf16 *y, int N, int H, int W, int Ca, int Cb)
 {
-    const int C = Ca + Cb;
-    const size_t total = (size_t)N * H * W * C;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const size_t p = e / C;
-        const int x = (int)(p % W), yy = (int)((p / W) % H), n = (int)(p / ((size_t)W * H));
-        y[e] = c < Ca ? lo[(((size_t)n * (H / 2) + yy / 2) * (W / 2) + x / 2) * Ca + c] : skip[p * Cb + (c - Ca)];
+    // one thread per (pixel, 8-channel group) of y [N][H][W][Ca + Cb]: 16-byte copies
+    const int C8 = (Ca + Cb) / 8, A8 = Ca / 8;
+    const long long total = (long long)N * H * W * C8;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(e % C8);
+        const long long p = e / C8;
+        const uint4 *src;
+        if (c8 < A8) {
+            const int x = (int)(p % W);
+            const long long rowp = p / W;  // n * H + y
+            const int yy = (int)(rowp % H);
+            const long long n = rowp / H;
+            src = reinterpret_cast<const uint4 *>(lo + ((n * (H / 2) + yy / 2) * (W / 2) + x / 2) * Ca + c8 * 8);
+        } else {
+            src = reinterpret_cast<const uint4 *>(skip + p * Cb + (c8 - A8) * 8);
+        }
+        reinterpret_cast<uint4 *>(y)[e] = *src;
     }
 }
 
@@ -423,16 +478,27 @@ int egrid(size_t n) { return (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 81
 
 // ---------------------------------------------------------------------------------------
 // Launch helpers for the template instantiations the network uses.
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK>
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA = 0, bool POOL = false, int WARPS = 8>
 cudaError_t conv_launch(const ConvArgs &a, cudaStream_t st)
 {
-    constexpr int P = KS / 2;
-    const size_t smem = sizeof(bf16) * ((size_t)(8 + 2 * P) * (16 + 2 * P) * (CIN + 8) + (size_t)KS * KS * COUT * (CIN + 8));
-    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, KS, ACT, OUTM, MASK>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.W + 15) / 16, (a.H + 7) / 8, a.N);
-    conv_kernel<CIN, COUT, KS, ACT, OUTM, MASK><<<grid, 128, smem, st>>>(a);
+    constexpr int P = KS / 2, TH = 2 * WARPS, TW = 16;
+    constexpr size_t smem = sizeof(bf16) * ((size_t)KS * KS * COUT * (CIN + 8) + 2 * (size_t)(TH + 2 * P) * (TW + 2 * P) * (CIN + 8));
+    static_assert(smem <= 227 * 1024, "conv tile does not fit in shared memory");
+    auto kern = conv_kernel<CIN, COUT, KS, ACT, OUTM, MASK, CA, POOL, WARPS>;
+    static int per_sm = 0, n_sm = 0;  // occupancy of this instantiation, computed once
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem)) != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const long long ntiles = (long long)a.N * ((a.H + TH - 1) / TH) * ((a.W + TW - 1) / TW);
+    if (ntiles <= 0) return cudaSuccess;
+    const long long cap = (long long)per_sm * n_sm;
+    kern<<<(int)(ntiles < cap ? ntiles : cap), WARPS * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -613,23 +679,37 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     auto bias = [&](int l) { return n->w + n->poff[l][1]; };
     pack_input_kernel<<<egrid(P), 256, 0, st>>>(in, n->x0, N, H, W);
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>({n->x0, n->wf[0], nullptr, bias(0), n->a0, nullptr, N, H, W, 16, kLayers[0].cout}, st)));
-    FLNR_TRY((conv_launch<16, 16, 1, 1, 0, false>({n->a0, n->wf[1], nullptr, bias(1), n->f0, nullptr, N, H, W, 16, kLayers[1].cout}, st)));
-    pool_kernel<<<egrid(P / 4 * 16), 256, 0, st>>>(n->f0, n->p0, N, H, W, 16);
-    FLNR_TRY((conv_launch<16, 32, 3, 1, 0, false>({n->p0, n->wf[2], nullptr, bias(2), n->a1, nullptr, N, H2, W2, 32, kLayers[2].cout}, st)));
-    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false>({n->a1, n->wf[3], nullptr, bias(3), n->f1, nullptr, N, H2, W2, 32, kLayers[3].cout}, st)));
-    pool_kernel<<<egrid(P / 16 * 32), 256, 0, st>>>(n->f1, n->p1, N, H2, W2, 32);
-    FLNR_TRY((conv_launch<32, 64, 3, 1, 0, false>({n->p1, n->wf[4], nullptr, bias(4), n->a2, nullptr, N, H4, W4, 64, kLayers[4].cout}, st)));
-    FLNR_TRY((conv_launch<64, 64, 3, 1, 0, false>({n->a2, n->wf[5], nullptr, bias(5), n->f2, nullptr, N, H4, W4, 64, kLayers[5].cout}, st)));
-    upcat_kernel<<<egrid(P / 4 * 96), 256, 0, st>>>(n->f2, n->f1, n->c1, N, H2, W2, 64, 32);
-    FLNR_TRY((conv_launch<96, 32, 3, 1, 0, false>({n->c1, n->wf[6], nullptr, bias(6), n->a3, nullptr, N, H2, W2, 32, kLayers[6].cout}, st)));
-    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false>({n->a3, n->wf[7], nullptr, bias(7), n->d1, nullptr, N, H2, W2, 32, kLayers[7].cout}, st)));
-    upcat_kernel<<<egrid(P * 48), 256, 0, st>>>(n->d1, n->f0, n->c0, N, H, W, 32, 16);
-    FLNR_TRY((conv_launch<48, 16, 3, 1, 0, false>({n->c0, n->wf[8], nullptr, bias(8), n->a4, nullptr, N, H, W, 16, kLayers[8].cout}, st)));
-    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>({n->a4, n->wf[9], nullptr, bias(9), n->d0, nullptr, N, H, W, 16, kLayers[9].cout}, st)));
-    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>({n->d0, n->wf[10], nullptr, bias(10), n->a5, nullptr, N, H, W, 16, kLayers[10].cout}, st)));
+    const ConvArgs z{};
+    auto conv = [&](const __nv_bfloat16 *x, int l, __nv_bfloat16 *y, int h, int w) {
+        ConvArgs c = z;
+        c.x = x; c.w = n->wf[l]; c.bias = bias(l); c.y = y; c.N = N; c.H = h; c.W = w;
+        c.ystride = pad16(kLayers[l].cout); c.nbias = kLayers[l].cout;
+        return c;
+    };
+    ConvArgs c;
+    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>(conv(n->x0, 0, n->a0, H, W), st)));
+    c = conv(n->a0, 1, n->f0, H, W);
+    c.yp = n->p0;  // 2x2 average pool of f0 for the encoder
+    FLNR_TRY((conv_launch<16, 16, 1, 1, 0, false, 0, true>(c, st)));
+    FLNR_TRY((conv_launch<16, 32, 3, 1, 0, false>(conv(n->p0, 2, n->a1, H2, W2), st)));
+    c = conv(n->a1, 3, n->f1, H2, W2);
+    c.yp = n->p1;
+    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false, 0, true>(c, st)));
+    FLNR_TRY((conv_launch<32, 64, 3, 1, 0, false>(conv(n->p1, 4, n->a2, H4, W4), st)));
+    FLNR_TRY((conv_launch<64, 64, 3, 1, 0, false>(conv(n->a2, 5, n->f2, H4, W4), st)));
+    c = conv(n->f2, 6, n->a3, H2, W2);  // input up(f2) ++ f1, formed while staging
+    c.x2 = n->f1;
+    FLNR_TRY((conv_launch<96, 32, 3, 1, 0, false, 64>(c, st)));
+    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false>(conv(n->a3, 7, n->d1, H2, W2), st)));
+    c = conv(n->d1, 8, n->a4, H, W);  // input up(d1) ++ f0
+    c.x2 = n->f0;
+    FLNR_TRY((conv_launch<48, 16, 3, 1, 0, false, 32>(c, st)));
+    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>(conv(n->a4, 9, n->d0, H, W), st)));
+    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>(conv(n->d0, 10, n->a5, H, W), st)));
     float *yf = guide_out ? guide_out : n->out;
-    FLNR_TRY((conv_launch<16, 16, 1, 2, 1, false>({n->a5, n->wf[11], nullptr, bias(11), nullptr, yf, N, H, W, 16, kLayers[11].cout}, st)));
+    c = conv(n->a5, 11, nullptr, H, W);
+    c.yf = yf;
+    FLNR_TRY((conv_launch<16, 16, 1, 2, 1, false>(c, st)));
     if (guide_out)
         FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return FLR_OK;
@@ -660,6 +740,8 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
     FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, ns, st)));
     bgrad(n->gA, (long long)P, 16, 16, 9);
     FLNR_TRY((conv_launch<16, 16, 3, 0, 0, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    upcat_kernel<<<egrid(P * 6), 256, 0, st>>>(n->d1, n->f0, n->c0, N, H, W, 32, 16);  // d0a's input
+    FLNR_TRY(cudaGetLastError());
     FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, ns, st)));
     bgrad(n->gB, (long long)P, 16, 16, 8);
     FLNR_TRY((conv_launch<16, 48, 3, 0, 0, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, st)));
@@ -669,6 +751,8 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
     FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, ns, st)));
     bgrad(n->gLo, (long long)P2, 32, 32, 7);
     FLNR_TRY((conv_launch<32, 32, 3, 0, 0, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
+    upcat_kernel<<<egrid(P2 * 12), 256, 0, st>>>(n->f2, n->f1, n->c1, N, H2, W2, 64, 32);  // d1a's input
+    FLNR_TRY(cudaGetLastError());
     FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, ns, st)));
     bgrad(n->gA, (long long)P2, 32, 32, 6);
     FLNR_TRY((conv_launch<32, 96, 3, 0, 0, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, st)));
@@ -703,21 +787,49 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
 
 namespace {
 
-// One layer's kernels by themselves (flnr_layer): CI / CO are the padded channel counts.
-template <int CI, int CO, int KS>
-int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const void *mask, void *out, int N, int H,
-              int W, cudaStream_t st)
+// One layer's kernels by themselves (flnr_layer): CI / CO are the padded channel counts, CA
+// the upsampled part of a decoder input, POOL whether the layer's output feeds a pool.
+template <int CI, int CO, int KS, int CA, bool POOL, bool HEAD = false>
+int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const void *mask, void *out, void *out2,
+              int N, int H, int W, cudaStream_t st)
 {
     using namespace flnr;
     using bf = __nv_bfloat16;
     const auto &d = kLayers[l];
     const long long P = (long long)N * H * W;
     if (op == FLNR_OP_FORWARD) {
-        const float *bias = n->w + n->poff[l][1];
-        if (l == kNL - 1)
-            FLNR_TRY((conv_launch<CI, CO, KS, 2, 1, false>({(const bf *)a, n->wf[l], nullptr, bias, nullptr, (float *)out, N, H, W, CO, d.cout}, st)));
-        else
-            FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false>({(const bf *)a, n->wf[l], nullptr, bias, (bf *)out, nullptr, N, H, W, CO, d.cout}, st)));
+        ConvArgs c{};
+        c.x = (const bf *)a;
+        c.w = n->wf[l];
+        c.bias = n->w + n->poff[l][1];
+        c.N = N;
+        c.H = H;
+        c.W = W;
+        c.ystride = CO;
+        c.nbias = d.cout;
+        if constexpr (HEAD) {
+            c.yf = (float *)out;
+            FLNR_TRY((conv_launch<CI, CO, KS, 2, 1, false>(c, st)));
+        } else {
+            c.y = (bf *)out;
+            if constexpr (CA > 0) {
+                if (b) {
+                    if ((H | W) & 1) return FLR_ERR_ARG;
+                    c.x2 = (const bf *)b;
+                    FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false, CA>(c, st)));
+                    return FLR_OK;
+                }
+            }
+            if constexpr (POOL) {
+                if (out2) {
+                    if ((H | W) & 1) return FLR_ERR_ARG;
+                    c.yp = (bf *)out2;
+                    FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false, 0, true>(c, st)));
+                    return FLR_OK;
+                }
+            }
+            FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false>(c, st)));
+        }
     } else if (op == FLNR_OP_DGRAD) {
         if (mask)
             FLNR_TRY((conv_launch<CO, CI, KS, 0, 0, true>({(const bf *)a, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
@@ -735,8 +847,8 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
 
 extern "C" {
 
-int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, const void *mask, void *out, int N, int H,
-               int W, void *stream)
+int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, const void *mask, void *out, void *out2,
+               int N, int H, int W, void *stream)
 {
     if (!n || layer < 0 || layer >= flnr::kNL || op < FLNR_OP_FORWARD || op > FLNR_OP_WGRAD || !a || N <= 0 ||
         H <= 0 || W <= 0)
@@ -746,18 +858,18 @@ int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, con
     if (!n->weights_fresh) return FLR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     switch (layer) {
-    case 0: return layer_ops<16, 16, 3>(n, 0, op, a, b, mask, out, N, H, W, st);
-    case 1: return layer_ops<16, 16, 1>(n, 1, op, a, b, mask, out, N, H, W, st);
-    case 2: return layer_ops<16, 32, 3>(n, 2, op, a, b, mask, out, N, H, W, st);
-    case 3: return layer_ops<32, 32, 3>(n, 3, op, a, b, mask, out, N, H, W, st);
-    case 4: return layer_ops<32, 64, 3>(n, 4, op, a, b, mask, out, N, H, W, st);
-    case 5: return layer_ops<64, 64, 3>(n, 5, op, a, b, mask, out, N, H, W, st);
-    case 6: return layer_ops<96, 32, 3>(n, 6, op, a, b, mask, out, N, H, W, st);
-    case 7: return layer_ops<32, 32, 3>(n, 7, op, a, b, mask, out, N, H, W, st);
-    case 8: return layer_ops<48, 16, 3>(n, 8, op, a, b, mask, out, N, H, W, st);
-    case 9: return layer_ops<16, 16, 3>(n, 9, op, a, b, mask, out, N, H, W, st);
-    case 10: return layer_ops<16, 16, 3>(n, 10, op, a, b, mask, out, N, H, W, st);
-    default: return layer_ops<16, 16, 1>(n, 11, op, a, b, mask, out, N, H, W, st);
+    case 0: return layer_ops<16, 16, 3, 0, false>(n, 0, op, a, b, mask, out, out2, N, H, W, st);
+    case 1: return layer_ops<16, 16, 1, 0, true>(n, 1, op, a, b, mask, out, out2, N, H, W, st);
+    case 2: return layer_ops<16, 32, 3, 0, false>(n, 2, op, a, b, mask, out, out2, N, H, W, st);
+    case 3: return layer_ops<32, 32, 3, 0, true>(n, 3, op, a, b, mask, out, out2, N, H, W, st);
+    case 4: return layer_ops<32, 64, 3, 0, false>(n, 4, op, a, b, mask, out, out2, N, H, W, st);
+    case 5: return layer_ops<64, 64, 3, 0, false>(n, 5, op, a, b, mask, out, out2, N, H, W, st);
+    case 6: return layer_ops<96, 32, 3, 64, false>(n, 6, op, a, b, mask, out, out2, N, H, W, st);
+    case 7: return layer_ops<32, 32, 3, 0, false>(n, 7, op, a, b, mask, out, out2, N, H, W, st);
+    case 8: return layer_ops<48, 16, 3, 32, false>(n, 8, op, a, b, mask, out, out2, N, H, W, st);
+    case 9: return layer_ops<16, 16, 3, 0, false>(n, 9, op, a, b, mask, out, out2, N, H, W, st);
+    case 10: return layer_ops<16, 16, 3, 0, false>(n, 10, op, a, b, mask, out, out2, N, H, W, st);
+    default: return layer_ops<16, 16, 1, 0, false, true>(n, 11, op, a, b, mask, out, out2, N, H, W, st);
     }
 }
 

@@ -97,6 +97,54 @@ def test_layer_forward(net, l, N, H, W):
     assert np.mean(got != exact) <= 0.01
 
 
+@pytest.mark.parametrize("l,ca", [(6, 64), (8, 32)])
+@pytest.mark.parametrize("N,H,W", SIZES)
+def test_decoder_layer_forms_the_concatenation_on_load(net, l, ca, N, H, W):
+    """Layers 6 and 8 read up2(lo) ++ skip directly (the network's fused form)."""
+    name, cin, cout, k = flnr.LAYERS[l]
+    rng = np.random.default_rng(4000 * l + H)
+    p = params_with_bias(11)
+    net.set_weights(p)
+    w = flnr_ref.round_bf16(torch.tensor(p[name + ".w"].astype(np.float64))).numpy()
+    b = p[name + ".b"].astype(np.float64)
+    lo, lov = bf16_tensor(np.abs(rng.normal(size=(N, H // 2, W // 2, ca))))
+    sk, skv = bf16_tensor(np.abs(rng.normal(size=(N, H, W, cin - ca))))
+    xv = np.concatenate([lov.repeat(2, axis=1).repeat(2, axis=2), skv], axis=3)
+    out = torch.empty((N, H, W, pad16(cout)), dtype=torch.bfloat16, device="cuda")
+    net.layer(l, net.OP_FORWARD, lo, b=sk, out=out, size=(N, H, W))
+    got = out.float().cpu().numpy().astype(np.float64)[..., :cout].transpose(0, 3, 1, 2)
+    z = F.conv2d(nchw(xv), torch.tensor(w), torch.tensor(b), padding=1).numpy()
+    S = F.conv2d(nchw(np.abs(xv)), torch.tensor(np.abs(w)), torch.tensor(np.abs(b)), padding=1).numpy()
+    check_bound(got, np.maximum(z, 0.0), S, cin * 9 + 1, f"{name} fused concatenation")
+
+
+@pytest.mark.parametrize("l", [1, 3])
+@pytest.mark.parametrize("N,H,W", SIZES)
+def test_encoder_layer_writes_the_pooled_output(net, l, N, H, W):
+    """Layers 1 and 3 also write the 2x2 average of their bf16 outputs (the next level's
+    input): within the pooled bound of the four outputs plus one more bf16 rounding."""
+    name, cin, cout, k = flnr.LAYERS[l]
+    rng = np.random.default_rng(5000 * l + H)
+    p = params_with_bias(11)
+    net.set_weights(p)
+    w = flnr_ref.round_bf16(torch.tensor(p[name + ".w"].astype(np.float64))).numpy()
+    b = p[name + ".b"].astype(np.float64)
+    x, xv = bf16_tensor(np.abs(rng.normal(size=(N, H, W, pad16(cin)))))
+    out = torch.empty((N, H, W, pad16(cout)), dtype=torch.bfloat16, device="cuda")
+    pooled = torch.empty((N, H // 2, W // 2, pad16(cout)), dtype=torch.bfloat16, device="cuda")
+    net.layer(l, net.OP_FORWARD, x, out=out, out2=pooled)
+    z = F.conv2d(nchw(xv[..., :cin]), torch.tensor(w), torch.tensor(b), padding=k // 2).numpy()
+    S = F.conv2d(nchw(np.abs(xv[..., :cin])), torch.tensor(np.abs(w)), torch.tensor(np.abs(b)), padding=k // 2).numpy()
+    ref = np.maximum(z, 0.0)
+    bound = 2.0 ** -8 * ref + (1 + 2.0 ** -8) * (cin * k * k + 1) * 2.0 ** -23 * S
+    got = out.float().cpu().numpy().astype(np.float64)[..., :cout].transpose(0, 3, 1, 2)
+    assert np.all(np.abs(got - ref) <= bound)
+    pool = lambda a: F.avg_pool2d(torch.tensor(a), 2).numpy()
+    gp = pooled.float().cpu().numpy().astype(np.float64)[..., :cout].transpose(0, 3, 1, 2)
+    ref_p = pool(ref)
+    assert np.all(np.abs(gp - ref_p) <= 2.0 ** -8 * ref_p + (1 + 2.0 ** -8) * pool(bound))
+
+
 @pytest.mark.parametrize("l", range(12))
 @pytest.mark.parametrize("masked", [False, True])
 @pytest.mark.parametrize("N,H,W", SIZES[:2])
