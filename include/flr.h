@@ -277,7 +277,8 @@ int flr_barrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
  *   avgpool, e2a 3x3 32->64, e2b 3x3 64->64 | up2 ++ e1b: d1a 3x3 96->32, d1b 3x3 32->32 |
  *   up2 ++ in1: d0a 3x3 48->16, d0b 3x3 16->16 | o0 3x3 16->16, o1 1x1 16->8 + sigmoid.
  * The network reads the radiance channels as log(1 + max(Y, 0)) (fireflies stay bounded).
- * BF16 convolutions on the tensor cores with FP32 accumulation; FP32 master weights.
+ * BF16 convolutions on the tensor cores with FP32 accumulation (forward: tcgen05 UMMA with
+ * accumulators in tensor memory; backward: warp-level MMA); FP32 master weights.
  * Parameters are one flat float array: per layer its weights [Cout][Cin][k][k] then its
  * biases [Cout], layers in the order above (flnr_param_count() floats).
  */
@@ -326,6 +327,14 @@ int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, 
  *                    buffer (flnr_get_grads / flnr_zero_grads)
  * Runs on `stream` without waiting.  Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
  */
+/*
+ * Waits for the device and reports whether a tensor-core kernel of this network ran out of
+ * time waiting for its own MMAs (each wait is bounded at 1 s; the kernel then stops and frees
+ * its tensor memory instead of hanging).  Returns FLR_OK or FLR_ERR_TIMEOUT (and clears the
+ * flag); FLR_ERR_ARG, FLR_ERR_CUDA.
+ */
+int flnr_status(flnr_net *net);
+
 #define FLNR_OP_FORWARD 0
 #define FLNR_OP_DGRAD 1
 #define FLNR_OP_WGRAD 2

@@ -12,8 +12,10 @@
 //   o0 3x3 16->16 ReLU, o1 1x1 16->8, sigmoid                                  X' (8 ch)
 // Activations are NHWC BF16 (channels innermost; the 11 inputs padded to 16, the 8 outputs
 // of o1 computed as 16 with zero weights); the enhanced guides leave as planar FP32 for FLR.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdint>
@@ -79,6 +81,7 @@ struct ConvArgs {
     int nbias;  // valid bias entries (the true output channels); 0 without bias
     const bf16 *x2;
     bf16 *yp;
+    int *status;  // tensor-core path: set to FLNR_STATUS_TIMEOUT if a completion wait ran out
 };
 
 // Persistent CTAs: the weights are staged in shared memory once per CTA; the CTA then walks
@@ -219,6 +222,359 @@ __global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
         __syncthreads();  // the next iteration stages into this buffer
     }
     cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------------
+// The same convolution on the fifth-generation tensor cores (tcgen05): BF16 operands in shared
+// memory, FP32 accumulators in tensor memory (TMEM).
+//
+// A tile is 16 rows x 8 pixels = the M = 128 rows of one UMMA.  The input tile (with halo) is
+// staged as [channel chunk c8][row][col][8 channels], so 8 consecutive pixels of one row and
+// one 8-channel chunk form a contiguous 128-byte core matrix.  For tap (ky, kx) the operand A
+// (128 output pixels x 16 channels) is then the no-swizzle K-major layout starting at pixel
+// (ky, kx) of chunk 2kk: 8-row groups (output rows) SW * 16 bytes apart, the two K halves
+// (chunks 2kk, 2kk + 1) SH * SW * 16 bytes apart.  No im2col copy is made.  The weights are
+// staged once per CTA as [tap][c8][COUT][8]: operand B (COUT x 16, K-major) has 8-row groups
+// 128 bytes apart and K halves COUT * 16 bytes apart.  Thread 0 issues the taps x CIN/16 MMAs
+// of a tile and commits them to an mbarrier; the four warps then read the accumulator rows of
+// their TMEM lane quarter (one output pixel per thread) and run the epilogue, while the next
+// tile's input is already loading.  Every wait is bounded by the global timer.
+#define FLNR_STATUS_TIMEOUT 1
+constexpr unsigned long long kTcTimeoutNs = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major; LBO = distance between the two K
+// halves of a core-matrix pair, SBO = distance between 8-row groups
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// bounded wait for the mbarrier phase with the given parity, polled by lane 0 of the warp
+// (try_wait suspends the thread for up to 20 us per call); false if it ran out
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+            uint32_t done;
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(mbar), "r"(parity)
+                : "memory");
+            if (done) break;
+            if (global_ns() - t0 > kTcTimeoutNs) {
+                ok = 0;
+                break;
+            }
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <int N>
+constexpr int tmem_cols()
+{
+    return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+}
+
+template <int CIN, int COUT, int KS, int CA>
+struct TcGeom {
+    static constexpr int TH = 16, TW = 8, P = KS / 2, SH = TH + 2 * P, SW = TW + 2 * P, C8 = CIN / 8;
+    static constexpr int NBUF = 3;                                // input ring: tiles i, i + 1, i + 2
+    static constexpr int PS = (SH * SW * 16 + 127) / 128 * 128;   // one channel-chunk plane [SH][SW][8]
+    static constexpr int XBYTES = C8 * PS;                        // one input buffer
+    static constexpr int WBYTES = (KS * KS * C8 * COUT * 16 + 127) / 128 * 128;
+    static constexpr int TMA_C8 = (CIN - CA) / 8;                 // chunks loaded by TMA (the rest: upsampled)
+    static constexpr int TMA_BYTES = TMA_C8 * SH * SW * 16;
+    static constexpr int SMEM = 128 + WBYTES + NBUF * XBYTES + 64;  // alignment slack, mbarriers, TMEM slot
+    static constexpr int COLS = tmem_cols<2 * COUT>();            // two accumulators of COUT columns
+};
+
+// Kernel parameters: the tensor map (4-D: channels, W, H, N) of the operand that TMA stages
+// (x, or the skip x2 of a decoder layer) and the convolution arguments.
+struct alignas(128) TcArgs {
+    CUtensorMap tm;
+    ConvArgs c;
+};
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+// single-thread bounded wait on an mbarrier phase (the TMA issuer)
+__device__ __forceinline__ bool mbar_wait_thread(uint32_t mbar, uint32_t parity)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kTcTimeoutNs) return false;
+    }
+}
+
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA, bool POOL>
+__global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ TcArgs args)
+{
+    using G = TcGeom<CIN, COUT, KS, CA>;
+    constexpr int TH = G::TH, TW = G::TW, P = G::P, SH = G::SH, SW = G::SW, C8 = G::C8, NBUF = G::NBUF, PS = G::PS;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && 2 * COUT <= 256, "UMMA shape");
+    const ConvArgs &a = args.c;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    unsigned char *sw = base;                        // weights [tap][c8][COUT][8]
+    unsigned char *sx0 = base + G::WBYTES;           // NBUF input buffers of C8 planes [SH][SW][8]
+    uint64_t *full = reinterpret_cast<uint64_t *>(sx0 + NBUF * G::XBYTES);  // [NBUF] TMA arrivals
+    uint64_t *mmab = full + NBUF;                                           // [2] MMA completion
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mmab + 2);
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
+    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
+    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // tiles of this CTA
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(G::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NBUF + 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.tm)) : "memory");
+        s_abort = 0;
+    }
+    // weights: global [tap][COUT][CIN] -> shared [tap][c8][COUT][8]
+    for (int i = tid; i < KS * KS * COUT * C8; i += 128) {
+        const int c8 = i % C8, row = i / C8, tap = row / COUT, co = row % COUT;
+        cp_async16(sw + ((tap * C8 + c8) * COUT + co) * 16, a.w + (size_t)row * CIN + c8 * 8, true);
+    }
+    auto tile_origin = [&](int j, int &n, int &ty0, int &tx0) {
+        const int t = blockIdx.x + j * gridDim.x;
+        n = t / per_img;
+        const int r = t % per_img;
+        ty0 = (r / tiles_x) * TH;
+        tx0 = (r % tiles_x) * TW;
+    };
+    // TMA part of tile j (thread 0): one 4-D box (8 channels, SW, SH, 1) per channel chunk;
+    // the halo outside the image is zero-filled by the copy engine
+    auto stage_tma = [&](int j) {
+        if (j >= mine) return;
+        int n, ty0, tx0;
+        tile_origin(j, n, ty0, tx0);
+        const uint32_t bar = smem_u32(full + j % NBUF);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(G::TMA_BYTES) : "memory");
+        const uint32_t dst = smem_u32(sx0 + (j % NBUF) * G::XBYTES);
+#pragma unroll
+        for (int k = 0; k < G::TMA_C8; ++k)
+            tma_load_4d(dst + (CA / 8 + k) * PS, &args.tm, k * 8, tx0 - P, ty0 - P, n, bar);
+    };
+    // upsampled part of a decoder input (CA > 0, all threads): nearest 2x of x [N][H/2][W/2][CA]
+    auto stage_up = [&](int j) {
+        if (CA == 0 || j >= mine) return;
+        int n, ty0, tx0;
+        tile_origin(j, n, ty0, tx0);
+        constexpr int CA8 = CA > 0 ? CA / 8 : 1;
+        unsigned char *sx = sx0 + (j % NBUF) * G::XBYTES;
+        for (int i = tid; i < SH * SW * CA8; i += 128) {
+            const int pix = i / CA8, c8 = i % CA8;
+            const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
+            const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = in ? a.x + (((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2) * CA + c8 * 8 : a.x;
+            cp_async16(sx + c8 * PS + pix * 16, src, in);
+        }
+    };
+    __syncthreads();  // barriers initialised before the first TMA arrives on them
+    if (tid == 0) {
+        stage_tma(0);
+        stage_tma(1);
+    }
+    stage_up(0);
+    cp_async_commit();  // group: weights + upsampled part of tile 0
+    stage_up(1);
+    cp_async_commit();
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = *tslot;
+    const uint32_t mmab_a = smem_u32(mmab);
+    constexpr uint32_t idesc = umma_idesc(COUT);
+    const uint64_t adesc0 = umma_sdesc(smem_u32(sx0), PS, SW * 16);
+    const uint64_t bdesc0 = umma_sdesc(smem_u32(sw), COUT * 16, 128);
+    float bias[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bias[c] = c < a.nbias ? a.bias[c] : 0.f;
+
+    // epilogue of this CTA's j-th tile from accumulator j & 1: thread (warp w, lane l) owns
+    // accumulator row 32w + l = pixel (4w + l / 8, l % 8) of the tile
+    auto epilogue = [&](int j) {
+        int n, ty0, tx0;
+        tile_origin(j, n, ty0, tx0);
+        const int yy = ty0 + 4 * warp + (lane >> 3), xx = tx0 + (lane & 7);
+        const bool in = yy < a.H && xx < a.W;
+        const size_t pix = ((size_t)n * a.H + yy) * a.W + xx;
+        float v[COUT];
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float q[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((j & 1) * COUT + c0), q);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[c0 + i] = q[i];
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) {
+            v[c] += bias[c];
+            if (ACT == 1) v[c] = fmaxf(v[c], 0.f);
+        }
+        if (MASK && in) {
+#pragma unroll
+            for (int c8 = 0; c8 < COUT / 8; ++c8) {
+                const uint4 m = *reinterpret_cast<const uint4 *>(a.mask + pix * COUT + c8 * 8);
+                const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&m);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (!(__bfloat162float(mh[i].x) > 0.f)) v[c8 * 8 + 2 * i] = 0.f;
+                    if (!(__bfloat162float(mh[i].y) > 0.f)) v[c8 * 8 + 2 * i + 1] = 0.f;
+                }
+            }
+        }
+        if (OUTM == 0) {
+#pragma unroll
+            for (int c8 = 0; c8 < COUT / 8; ++c8) {
+                uint4 o;
+                __nv_bfloat162 *oh = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) oh[i] = __floats2bfloat162_rn(v[c8 * 8 + 2 * i], v[c8 * 8 + 2 * i + 1]);
+                if (in) *reinterpret_cast<uint4 *>(a.y + pix * a.ystride + c8 * 8) = o;
+                if (POOL) {
+                    // 2x2 average of the stored values: column pairs are lanes l, l ^ 1, row
+                    // pairs lanes l, l ^ 8
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float s0 = __bfloat162float(oh[i].x), s1 = __bfloat162float(oh[i].y);
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, 8);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, 8);
+                        oh[i] = __floats2bfloat162_rn(0.25f * s0, 0.25f * s1);
+                    }
+                    if (in && (lane & 9) == 0) {
+                        const size_t pp = ((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2;
+                        *reinterpret_cast<uint4 *>(a.yp + pp * COUT + c8 * 8) = o;
+                    }
+                }
+            }
+        } else if (in) {
+            const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v[c]));
+        }
+    };
+    auto fail = [&]() {
+        atomicExch(&s_abort, 1);
+        if (a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
+    };
+    auto wait_mma = [&](int j) {  // MMAs of tile j complete (bounded)
+        if (!mbar_wait_warp(mmab_a + 8 * (j & 1), (uint32_t)((j >> 1) & 1)) && lane == 0) fail();
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+    };
+
+    // software pipeline: the MMAs of tile j run while tile j - 1's epilogue runs and tiles
+    // j + 1 and j + 2 load
+    int consumed = 0;  // tiles whose TMA arrival thread 0 has waited for
+    for (int j = 0; j < mine; ++j) {
+        cp_async_wait<1>();  // all groups but the newest: weights and tile j's upsampled part
+        asm volatile("fence.proxy.async.shared::cta;\n");  // thread-written bytes visible to the tensor core
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0) {
+            if (!mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1))) fail();
+            consumed = j + 1;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint64_t ab = adesc0 + (uint64_t)(((j % NBUF) * G::XBYTES) >> 4);
+            const uint32_t d = tmem + (uint32_t)((j & 1) * COUT);
+#pragma unroll
+            for (int tap = 0; tap < KS * KS; ++tap) {
+#pragma unroll
+                for (int kk = 0; kk < C8 / 2; ++kk) {
+                    const uint32_t aoff = (uint32_t)((2 * kk * PS + ((tap / KS) * SW + tap % KS) * 16) >> 4);
+                    const uint32_t boff = (uint32_t)(((tap * C8 + 2 * kk) * COUT * 16) >> 4);
+                    umma_bf16(d, ab + aoff, bdesc0 + boff, idesc, (tap | kk) ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                mmab_a + 8 * (j & 1)));
+        }
+        if (j >= 1) wait_mma(j - 1);  // frees tile j - 1's input buffer and accumulator
+        if (tid == 0) stage_tma(j + 2);  // into the buffer tile j - 1 used
+        stage_up(j + 2);
+        cp_async_commit();
+        if (j >= 1) epilogue(j - 1);
+    }
+    if (mine > 0 && !s_abort) {
+        wait_mma(mine - 1);
+        epilogue(mine - 1);
+    }
+    cp_async_wait<0>();
+    if (tid == 0) {  // after an abort: let the TMA loads still in flight land before the CTA exits
+        const int issued = mine < consumed + 2 ? mine : consumed + 2;
+        for (int j = consumed; j < issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::COLS));
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -502,6 +858,87 @@ cudaError_t conv_launch(const ConvArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Launch of the tensor-core convolution.  The occupancy API reports one CTA per SM for
+// kernels that allocate tensor memory, so the resident count is computed here from the
+// kernel's registers, shared memory and threads, and capped at 512 / (TMEM columns per CTA);
+// where threads alone would allow more CTAs than TMEM can hold, the shared-memory request is
+// raised so that no more can be resident (an allocation never has to wait for another CTA).
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 4-D map of an NHWC bf16 tensor [N][H][W][C]: box (8 channels, bw, bh, 1), zero fill outside
+cudaError_t make_tmap(CUtensorMap *m, const void *base, int C, int W, int H, int N, int bw, int bh)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Launch of the tensor-core convolution.  The occupancy API reports one CTA per SM for
+// kernels that allocate tensor memory, so the resident count is computed here from the
+// kernel's registers, shared memory and threads, and capped at 512 / (TMEM columns per CTA);
+// where threads alone would allow more CTAs than TMEM can hold, the shared-memory request is
+// raised so that no more can be resident (an allocation never has to wait for another CTA).
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA = 0, bool POOL = false>
+cudaError_t conv_tc_launch(const ConvArgs &a, cudaStream_t st)
+{
+    using G = TcGeom<CIN, COUT, KS, CA>;
+    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreadsPerSm = 2048;
+    constexpr int tmem_cap = 512 / G::COLS;
+    constexpr int min_smem = tmem_cap < kThreadsPerSm / 128 ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
+    constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
+    static_assert(smem <= 227 * 1024, "tensor-core conv tile does not fit in shared memory");
+    auto kern = conv_tc_kernel<CIN, COUT, KS, ACT, OUTM, MASK, CA, POOL>;
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = 65536 / (regs_per_warp * 4);
+        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
+        int r = kThreadsPerSm / 128;
+        r = r < by_regs ? r : by_regs;
+        r = r < by_smem ? r : by_smem;
+        r = r < tmem_cap ? r : tmem_cap;
+        if (r < 1) return cudaErrorInvalidConfiguration;
+        per_sm = r;
+    }
+    const long long ntiles = (long long)a.N * ((a.H + G::TH - 1) / G::TH) * ((a.W + G::TW - 1) / G::TW);
+    if (ntiles <= 0) return cudaSuccess;
+    TcArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.c = a;
+    cudaError_t e = CA > 0 ? make_tmap(&ta.tm, a.x2, CIN - CA, a.W, a.H, a.N, G::SW, G::SH)
+                           : make_tmap(&ta.tm, a.x, CIN, a.W, a.H, a.N, G::SW, G::SH);
+    if (e != cudaSuccess) return e;
+    const long long cap = (long long)per_sm * n_sm;
+    kern<<<(int)(ntiles < cap ? ntiles : cap), 128, smem, st>>>(ta);
+    return cudaGetLastError();
+}
+
 template <int CIN, int COUT, int KS>
 cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H, int W, int cin_true, int cout_true,
                          int n_sm, cudaStream_t st)
@@ -534,6 +971,7 @@ struct flnr_net {
     __nv_bfloat16 *gA, *gB, *gC, *gLo;  // gradient scratch (largest: 48 channels at full res)
     float *gskip0, *gskip1;             // skip gradients (fp32)
     float *out = nullptr;               // last forward output, planar fp32 [N][8][H][W]
+    int *status = nullptr;              // device status word of the tensor-core kernels
     int N = 0, H = 0, W = 0;            // shape of the last forward
     bool weights_fresh = false;
 };
@@ -611,10 +1049,12 @@ int flnr_create(int max_pixels, flnr_net **out)
     st |= nalloc(n, &n->a4, P * 16) | nalloc(n, &n->d0, P * 16) | nalloc(n, &n->a5, P * 16);
     st |= nalloc(n, &n->gA, P * 48) | nalloc(n, &n->gB, P * 48) | nalloc(n, &n->gC, P * 48) | nalloc(n, &n->gLo, P * 16);
     st |= nalloc(n, &n->gskip0, P * 16) | nalloc(n, &n->gskip1, P2 * 32) | nalloc(n, &n->out, P * 8);
+    st |= nalloc(n, &n->status, 1);
     if (st != FLR_OK) {
         flnr_destroy(n);
         return FLR_ERR_NOMEM;
     }
+    cudaMemset(n->status, 0, sizeof(int));
     cudaMemset(n->g, 0, off * sizeof(float));
     cudaMemset(n->m, 0, off * sizeof(float));
     cudaMemset(n->v, 0, off * sizeof(float));
@@ -683,33 +1123,33 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     auto conv = [&](const __nv_bfloat16 *x, int l, __nv_bfloat16 *y, int h, int w) {
         ConvArgs c = z;
         c.x = x; c.w = n->wf[l]; c.bias = bias(l); c.y = y; c.N = N; c.H = h; c.W = w;
-        c.ystride = pad16(kLayers[l].cout); c.nbias = kLayers[l].cout;
+        c.ystride = pad16(kLayers[l].cout); c.nbias = kLayers[l].cout; c.status = n->status;
         return c;
     };
     ConvArgs c;
-    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>(conv(n->x0, 0, n->a0, H, W), st)));
+    FLNR_TRY((conv_tc_launch<16, 16, 3, 1, 0, false>(conv(n->x0, 0, n->a0, H, W), st)));
     c = conv(n->a0, 1, n->f0, H, W);
     c.yp = n->p0;  // 2x2 average pool of f0 for the encoder
-    FLNR_TRY((conv_launch<16, 16, 1, 1, 0, false, 0, true>(c, st)));
-    FLNR_TRY((conv_launch<16, 32, 3, 1, 0, false>(conv(n->p0, 2, n->a1, H2, W2), st)));
+    FLNR_TRY((conv_tc_launch<16, 16, 1, 1, 0, false, 0, true>(c, st)));
+    FLNR_TRY((conv_tc_launch<16, 32, 3, 1, 0, false>(conv(n->p0, 2, n->a1, H2, W2), st)));
     c = conv(n->a1, 3, n->f1, H2, W2);
     c.yp = n->p1;
-    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false, 0, true>(c, st)));
-    FLNR_TRY((conv_launch<32, 64, 3, 1, 0, false>(conv(n->p1, 4, n->a2, H4, W4), st)));
-    FLNR_TRY((conv_launch<64, 64, 3, 1, 0, false>(conv(n->a2, 5, n->f2, H4, W4), st)));
+    FLNR_TRY((conv_tc_launch<32, 32, 3, 1, 0, false, 0, true>(c, st)));
+    FLNR_TRY((conv_tc_launch<32, 64, 3, 1, 0, false>(conv(n->p1, 4, n->a2, H4, W4), st)));
+    FLNR_TRY((conv_tc_launch<64, 64, 3, 1, 0, false>(conv(n->a2, 5, n->f2, H4, W4), st)));
     c = conv(n->f2, 6, n->a3, H2, W2);  // input up(f2) ++ f1, formed while staging
     c.x2 = n->f1;
-    FLNR_TRY((conv_launch<96, 32, 3, 1, 0, false, 64>(c, st)));
-    FLNR_TRY((conv_launch<32, 32, 3, 1, 0, false>(conv(n->a3, 7, n->d1, H2, W2), st)));
+    FLNR_TRY((conv_tc_launch<96, 32, 3, 1, 0, false, 64>(c, st)));
+    FLNR_TRY((conv_tc_launch<32, 32, 3, 1, 0, false>(conv(n->a3, 7, n->d1, H2, W2), st)));
     c = conv(n->d1, 8, n->a4, H, W);  // input up(d1) ++ f0
     c.x2 = n->f0;
-    FLNR_TRY((conv_launch<48, 16, 3, 1, 0, false, 32>(c, st)));
-    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>(conv(n->a4, 9, n->d0, H, W), st)));
-    FLNR_TRY((conv_launch<16, 16, 3, 1, 0, false>(conv(n->d0, 10, n->a5, H, W), st)));
+    FLNR_TRY((conv_tc_launch<48, 16, 3, 1, 0, false, 32>(c, st)));
+    FLNR_TRY((conv_tc_launch<16, 16, 3, 1, 0, false>(conv(n->a4, 9, n->d0, H, W), st)));
+    FLNR_TRY((conv_tc_launch<16, 16, 3, 1, 0, false>(conv(n->d0, 10, n->a5, H, W), st)));
     float *yf = guide_out ? guide_out : n->out;
     c = conv(n->a5, 11, nullptr, H, W);
     c.yf = yf;
-    FLNR_TRY((conv_launch<16, 16, 1, 2, 1, false>(c, st)));
+    FLNR_TRY((conv_tc_launch<16, 16, 1, 2, 1, false>(c, st)));
     if (guide_out)
         FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return FLR_OK;
@@ -807,16 +1247,17 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
         c.W = W;
         c.ystride = CO;
         c.nbias = d.cout;
+        c.status = n->status;
         if constexpr (HEAD) {
             c.yf = (float *)out;
-            FLNR_TRY((conv_launch<CI, CO, KS, 2, 1, false>(c, st)));
+            FLNR_TRY((conv_tc_launch<CI, CO, KS, 2, 1, false>(c, st)));
         } else {
             c.y = (bf *)out;
             if constexpr (CA > 0) {
                 if (b) {
                     if ((H | W) & 1) return FLR_ERR_ARG;
                     c.x2 = (const bf *)b;
-                    FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false, CA>(c, st)));
+                    FLNR_TRY((conv_tc_launch<CI, CO, KS, 1, 0, false, CA>(c, st)));
                     return FLR_OK;
                 }
             }
@@ -824,11 +1265,11 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
                 if (out2) {
                     if ((H | W) & 1) return FLR_ERR_ARG;
                     c.yp = (bf *)out2;
-                    FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false, 0, true>(c, st)));
+                    FLNR_TRY((conv_tc_launch<CI, CO, KS, 1, 0, false, 0, true>(c, st)));
                     return FLR_OK;
                 }
             }
-            FLNR_TRY((conv_launch<CI, CO, KS, 1, 0, false>(c, st)));
+            FLNR_TRY((conv_tc_launch<CI, CO, KS, 1, 0, false>(c, st)));
         }
     } else if (op == FLNR_OP_DGRAD) {
         if (mask)
@@ -871,6 +1312,16 @@ int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, con
     case 10: return layer_ops<16, 16, 3, 0, false>(n, 10, op, a, b, mask, out, out2, N, H, W, st);
     default: return layer_ops<16, 16, 1, 0, false, true>(n, 11, op, a, b, mask, out, out2, N, H, W, st);
     }
+}
+
+int flnr_status(flnr_net *n)
+{
+    if (!n) return FLR_ERR_ARG;
+    int h = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FLR_ERR_CUDA;
+    if (cudaMemcpy(&h, n->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FLR_ERR_CUDA;
+    if (h != 0 && cudaMemset(n->status, 0, sizeof(int)) != cudaSuccess) return FLR_ERR_CUDA;
+    return h ? FLR_ERR_TIMEOUT : FLR_OK;
 }
 
 int flnr_adam_step(flnr_net *n, float lr, float beta1, float beta2, float eps, int step, void *stream)

@@ -37,9 +37,10 @@ def _lib():
         lib.flnr_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ip, vp]
         lib.flnr_l1_loss.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.flnr_layer.argtypes = [vp, ip, ip, vp, vp, vp, vp, vp, ip, ip, ip, vp]
+        lib.flnr_status.argtypes = [vp]
         for name in ("flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights", "flnr_get_grads",
                      "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_adam_step",
-                     "flnr_l1_loss", "flnr_layer"):
+                     "flnr_l1_loss", "flnr_layer", "flnr_status"):
             getattr(lib, name).restype = ctypes.c_int
         _bound = True
     return lib
@@ -136,6 +137,10 @@ class FLNR:
                     "flnr_guide_backward")
 
     OP_FORWARD, OP_DGRAD, OP_WGRAD = 0, 1, 2
+
+    def status(self):
+        """Waits for the device; raises if a tensor-core kernel's bounded wait ran out."""
+        _flr._check(_lib().flnr_status(self._h), "flnr_status")
 
     def layer(self, layer, op, a, b=None, mask=None, out=None, out2=None, size=None):
         """One layer's kernels by themselves (flnr_layer): a, b, mask, out, out2 are CUDA

@@ -13,7 +13,7 @@ from . import _build
 
 FLR_OK = 0
 STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA",
-          -4: "FLR_ERR_UNSUPPORTED", -5: "FLR_ERR_NOMEM"}
+          -4: "FLR_ERR_UNSUPPORTED", -5: "FLR_ERR_NOMEM", -6: "FLR_ERR_TIMEOUT"}
 
 # every symbol include/flr.h declares
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
@@ -23,7 +23,7 @@ EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoi
            "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest",
            "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
            "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_get_grads",
-           "flnr_adam_step", "flnr_l1_loss", "flnr_layer")
+           "flnr_adam_step", "flnr_l1_loss", "flnr_layer", "flnr_status")
 BATCH_TIMEOUT = 1
 FLAG_TIMING = 1
 
