@@ -137,7 +137,9 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
 
 /*
  * Statistics of the last flr_denoise on this handle.  Waits for that call's stream.
- * Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
+ * Returns FLR_ERR_TIMEOUT (after filling *out) if a kernel of an earlier call on this
+ * handle stopped because one of its bounded device waits (1 s) ran out; the flag is then
+ * cleared.  Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
  */
 int flr_get_stats(flr_handle *h, flr_stats *out);
 

@@ -11,12 +11,18 @@
 // This kernel is bound by HBM: it reads (Q+1)*3 coefficient planes plus the Q map-guide
 // planes and writes 3 planes, and does ~6 flops per value read.  A CTA owns a 64 x 32
 // output tile; for each coefficient plane it stages the tile plus a radius-rc halo in
-// shared memory with asynchronous copies, double-buffered so plane p+1 is in flight while
-// plane p is summed (zero outside the image, which is what clipping the window means for
-// a sum), slides a horizontal then a vertical radius-rc sum, and accumulates
-// sum_k A_k[i][c] * (z_i - s_i) in registers.  Division by the window size happens once
-// at the end, so the 27 averaged coefficients are never materialised.
+// shared memory, double-buffered so plane p+1 is in flight while plane p is summed (zero
+// outside the image, which is what clipping the window means for a sum), slides a
+// horizontal then a vertical radius-rc sum, and accumulates sum_k A_k[i][c] * (z_i - s_i)
+// in registers.  Division by the window size happens once at the end, so the 27 averaged
+// coefficients are never materialised.  When rows are 16-byte aligned (W % 4 == 0) one
+// thread stages each plane tile with a single TMA box copy (the copy engine zero-fills
+// the halo outside the image) completing on an mbarrier; otherwise every thread issues
+// 4-byte asynchronous copies.
+#include <cstring>
+
 #include "flr_internal.cuh"
+#include "tma.cuh"
 
 namespace flr {
 namespace {
@@ -45,10 +51,24 @@ struct ApplyGeom {
         RCA = (rc + 3) & ~3;
         TWa = kAW + 2 * RCA;
         THh = kAH + 2 * rc;
-        TS = TWa + 4;   // 16-byte aligned rows
+        TS = TWa + 4;   // 16-byte aligned rows (also the TMA box width)
         HS = kAW + 1;   // odd: the column walks of the vertical pass are conflict-free
     }
-    __host__ __device__ size_t floats() const { return (size_t)2 * THh * TS + (size_t)THh * HS; }
+    __host__ __device__ int tile_floats() const { return (THh * TS + 31) / 32 * 32; }  // 128-byte multiple
+    __host__ __device__ size_t floats() const
+    {
+        return 32 + (size_t)2 * tile_floats() + (size_t)THh * HS + 8;  // alignment slack, tiles, Hb, mbarriers
+    }
+};
+
+constexpr unsigned long long kApplyTimeoutNs = 1000000000ull;  // 1 s per wait
+
+// Kernel parameters: the TMA map of the coefficient planes (valid when use_tma) and the
+// apply arguments.
+struct alignas(128) ApplyKArgs {
+    CUtensorMap tm;
+    ApplyArgs a;
+    int use_tma;
 };
 
 // Copy the tile + halo of one coefficient plane into shared memory (zero outside the
@@ -81,15 +101,20 @@ __device__ __forceinline__ void load_tile(float *T, const ApplyGeom &g, const fl
 }
 
 template <int Q, int RT>
-__global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const ApplyArgs a)
+__global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const __grid_constant__ ApplyKArgs ka)
 {
     extern __shared__ __align__(16) float sm[];
+    const ApplyArgs &a = ka.a;
+    const bool use_tma = ka.use_tma != 0;
     const int H = a.H, W = a.W;
     const int rc = RT >= 0 ? RT : a.rc;
     const ApplyGeom g(rc);
-    float *T0 = sm;                 // [THh][TS]   coefficient plane tile + halo, double-buffered
-    float *T1 = T0 + g.THh * g.TS;
-    float *Hb = T1 + g.THh * g.TS;  // [THh][HS]   horizontal sums
+    float *base = sm + (((128 - (tma::smem_addr(sm) & 127)) & 127) >> 2);  // 128-byte aligned
+    float *T0 = base;               // [THh][TS]   coefficient plane tile + halo, double-buffered
+    float *T1 = T0 + g.tile_floats();
+    float *Hb = T1 + g.tile_floats();  // [THh][HS]   horizontal sums
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Hb + ((g.THh * g.HS + 1) & ~1));  // [2] TMA arrivals
+    __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx0 = blockIdx.x * kAW, ty0 = blockIdx.y * kAH;
     const int x = tid % kAW, run = tid / kAW;
@@ -104,7 +129,28 @@ __global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const ApplyArgs
 #pragma unroll
         for (int t = 0; t < kARun; ++t) acc[c][t] = 0.f;
 
-    load_tile(T0, g, a.coef, H, W, ty0, tx0, rc, warp, lane);
+    // stage plane p of the tile into T: one TMA box copy, or asynchronous copies
+    auto stage = [&](float *T, int p) {
+        if (use_tma) {
+            if (tid == 0) {
+                uint64_t *b = bar + (p & 1);
+                tma::mbar_expect_tx(b, (unsigned)(g.THh * g.TS * 4));
+                tma::load_3d(T, &ka.tm, tx0 - g.RCA, ty0 - rc, p, b);
+            }
+        } else {
+            load_tile(T, g, a.coef + (size_t)p * plane, H, W, ty0, tx0, rc, warp, lane);
+        }
+    };
+    if (tid == 0) {
+        s_abort = 0;
+        if (use_tma) {
+            tma::mbar_init(bar, 1);
+            tma::mbar_init(bar + 1, 1);
+            tma::mbar_init_fence();
+        }
+    }
+    __syncthreads();
+    stage(T0, 0);
     for (int i = 0; i <= Q; ++i) {
         float zf[kARun];
 #pragma unroll
@@ -121,13 +167,23 @@ __global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const ApplyArgs
         for (int c = 0; c < 3; ++c) {
             const int p = 3 * i + c;
             float *Tc = (p & 1) ? T1 : T0;
-            if (p + 1 < NP) {
-                load_tile((p & 1) ? T0 : T1, g, a.coef + (size_t)(p + 1) * plane, H, W, ty0, tx0, rc, warp, lane);
+            if (p + 1 < NP) stage((p & 1) ? T0 : T1, p + 1);
+            if (use_tma) {
+                if (!tma::wait_warp(bar + (p & 1), (uint32_t)((p >> 1) & 1), kApplyTimeoutNs) && lane == 0) {
+                    s_abort = 1;
+                    if (a.status) atomicExch(a.status, 1);
+                }
+            } else if (p + 1 < NP) {
                 asm volatile("cp.async.wait_group 1;\n" ::);
             } else {
                 asm volatile("cp.async.wait_group 0;\n" ::);
             }
             __syncthreads();  // plane p is in Tc for every thread
+            if (s_abort) {  // let a copy still in flight land before the CTA exits, then stop
+                if (use_tma && p + 1 < NP && warp == 0)
+                    tma::wait_warp(bar + ((p + 1) & 1), (uint32_t)(((p + 1) >> 1) & 1), kApplyTimeoutNs);
+                return;
+            }
             // horizontal sums: 16 outputs per item, operands held in registers; consecutive
             // lanes take consecutive rows (16-byte loads, row stride = 4 mod 8 floats: the
             // eight lanes of each 128-bit phase hit distinct banks)
@@ -170,6 +226,7 @@ __global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const ApplyArgs
                 }
             }
             __syncthreads();  // Hb complete; Tc may be refilled from here on
+            if (use_tma && tid == 0) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             {
                 const float *q = Hb + (run * kARun) * g.HS + x;
                 if constexpr (RT >= 0) {
@@ -225,7 +282,14 @@ cudaError_t launch_apply_qr(const ApplyArgs &a, cudaStream_t st)
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + kAW - 1) / kAW, (a.H + kAH - 1) / kAH);
-    flr_apply_kernel<Q, RT><<<grid, kAThreads, smem, st>>>(a);
+    ApplyKArgs ka;
+    std::memset(&ka, 0, sizeof(ka));
+    ka.a = a;
+    ka.use_tma = ((a.W & 3) == 0 && ((uintptr_t)a.coef & 15) == 0 &&
+                  tma::encode_planes_f32(&ka.tm, a.coef, a.W, a.H, 3 * (Q + 1), g.TS, g.THh) == cudaSuccess)
+                     ? 1
+                     : 0;
+    flr_apply_kernel<Q, RT><<<grid, kAThreads, smem, st>>>(ka);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ struct flr_handle {
     int device = 0;
     int n_sm = 0;
     unsigned long long *d_count = nullptr;  // flagged-pixel counter
+    int *d_status = nullptr;                // set by a kernel whose bounded wait ran out
     float *d_shift = nullptr;               // frame reference shift, Q+3 floats
     int *d_flags = nullptr;                 // flag list
     int flag_cap = 0;
@@ -156,6 +157,8 @@ int flr_create(const flr_params *params, flr_handle **out)
     if (e == cudaSuccess) e = cudaMalloc(&h->d_count, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_shift, sizeof(float) * (FLR_MAX_Q + 3));
     if (e == cudaSuccess) e = cudaMemset(h->d_count, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e == cudaSuccess) {
         h->fwd_smem = flr::fwd_smem_bytes(h->p.q, h->p.radius);
         e = flr::fwd_prepare(h->p.q, h->p.radius, h->fwd_smem);
@@ -178,6 +181,7 @@ int flr_destroy(flr_handle *h)
     if (!h) return FLR_OK;
     cudaDeviceSynchronize();
     cudaFree(h->d_count);
+    cudaFree(h->d_status);
     cudaFree(h->d_shift);
     cudaFree(h->d_flags);
     cudaFree(h->d_coef);
@@ -273,6 +277,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
         aa.H = H;
         aa.W = W;
         aa.rc = h->p.coef_radius;
+        aa.status = h->d_status;
         FLR_CUDA(flr::launch_apply(q, aa, s), "apply kernel launch");
         ++h->n_apply;
     }
@@ -474,6 +479,12 @@ int flr_get_stats(flr_handle *h, flr_stats *out)
     FLR_CUDA(cudaMemcpy(&n, h->d_count, sizeof(n), cudaMemcpyDeviceToHost), "stats copy");
     out->flagged = n;
     out->resolved = h->p.pivot_ratio > 0.f ? (n < (unsigned long long)h->flag_cap ? n : (unsigned long long)h->flag_cap) : 0ull;
+    int status = 0;
+    FLR_CUDA(cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "stats copy");
+    if (status != 0) {
+        FLR_CUDA(cudaMemset(h->d_status, 0, sizeof(int)), "stats reset");
+        return FLR_ERR_TIMEOUT;
+    }
     return FLR_OK;
 }
 

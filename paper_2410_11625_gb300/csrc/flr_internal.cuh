@@ -119,6 +119,7 @@ struct ApplyArgs {
     const float *coef, *map_guide, *shift;
     float *out;
     int H, W, rc;
+    int *status;  // set to 1 if a bounded device wait ran out (may be NULL)
 };
 
 struct Fp64Args {

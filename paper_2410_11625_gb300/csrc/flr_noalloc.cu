@@ -170,6 +170,7 @@ extern "C" int flr_denoise_noalloc(const flr_params *p, const float *guide, cons
         aa.H = H;
         aa.W = W;
         aa.rc = p->coef_radius;
+        aa.status = nullptr;
         if (flr::launch_apply(q, aa, s) != cudaSuccess) return FLR_ERR_CUDA;
     }
     return FLR_OK;
