@@ -286,7 +286,7 @@ cudaError_t launch_apply_qr(const ApplyArgs &a, cudaStream_t st)
     std::memset(&ka, 0, sizeof(ka));
     ka.a = a;
     ka.use_tma = ((a.W & 3) == 0 && ((uintptr_t)a.coef & 15) == 0 &&
-                  tma::encode_planes_f32(&ka.tm, a.coef, a.W, a.H, 3 * (Q + 1), g.TS, g.THh) == cudaSuccess)
+                  tma::encode_planes_f32(&ka.tm, a.coef, a.W, a.H, 3 * (Q + 1), g.TS, g.THh, 1) == cudaSuccess)
                      ? 1
                      : 0;
     flr_apply_kernel<Q, RT><<<grid, kAThreads, smem, st>>>(ka);

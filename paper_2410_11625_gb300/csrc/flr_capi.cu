@@ -241,6 +241,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
     fa.gA = nullptr;
     fa.gS = nullptr;
     fa.geps = nullptr;
+    fa.status = h->d_status;
     dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
     FLR_CUDA(mark(h, s), "timing event");
     FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "forward kernel launch");
@@ -342,6 +343,7 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     fa.gA = nullptr;
     fa.gS = nullptr;
     fa.geps = nullptr;
+    fa.status = h->d_status;
     dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
     FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "backward: model kernel launch");
     if (h->p.pivot_ratio > 0.f) {
@@ -380,6 +382,7 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     fa.gA = gA;
     fa.gS = GS;
     fa.geps = geps;
+    fa.status = h->d_status;
     fa.force_coef = 0;
     FLR_CUDA(flr::launch_adj(q, fa, grid, h->adj_smem, s), "backward: adjoint kernel launch");
     // 4. adjoint of the window sums, the averaged models for the applied guide, contraction

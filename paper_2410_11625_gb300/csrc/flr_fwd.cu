@@ -9,6 +9,11 @@
 // With rc == 0 the model is applied to the centre pixel at once; otherwise (a, b) goes to
 // a coefficient plane set that the averaging kernel (flr_apply.cu) consumes.
 //
+// Staging: when rows are 16-byte aligned, one thread copies each batch's entering and
+// leaving input rows with four TMA box copies (guide and radiance planes, zero fill
+// outside the image) completing on an mbarrier; otherwise all threads issue asynchronous
+// copies.
+//
 // Layout of the work.  The path is bound by FP32 ALU issue, not by HBM: per pixel it
 // does ~60 products, ~280 window-sum adds and a ~300-FMA solve against 56 bytes of HBM
 // traffic.  One CTA owns a strip of kTW output columns and a segment of TH rows and walks
@@ -29,10 +34,12 @@
 // what the averaging and apply steps use.  A pixel whose Cholesky pivot ratio
 // d_j / M_jj falls to tau or below is appended to a flag list for the FP64 re-solve
 // (flr_fp64.cu).
+#include <cstring>
 #include <utility>
 
 #include "flr_device.cuh"
 #include "flr_internal.cuh"
+#include "tma.cuh"
 
 namespace flr {
 namespace {
@@ -218,23 +225,47 @@ struct FwdGeom {
     }
 };
 
+constexpr unsigned long long kFwdTimeoutNs = 1000000000ull;  // 1 s per wait
+
+// Kernel parameters: TMA maps of the guide [Q][H][W] and radiance [3][H][W] planes (boxes
+// of WSt columns x kB rows x all planes; valid when use_tma) and the forward arguments.
+struct alignas(128) FwdKArgs {
+    CUtensorMap tg, tr;
+    FwdArgs a;
+    int use_tma;
+};
+
 // Stage the input rows of kB walker steps: for step b, row yv + b + r enters the window
-// and row yv + b - r - 1 leaves it.  Layout [2][kB][Q+3][WSt] (0 = entering, 1 = leaving);
-// staged column j is global column x0 - RA + j; anything outside the image is zero.
+// and row yv + b - r - 1 leaves it.  Layout [2][Q+3][kB][WSt] (0 = entering, 1 = leaving;
+// then input plane, step); staged column j is global column x0 - RA + j; anything outside
+// the image is zero.
 template <int Q>
-__device__ __forceinline__ void stage_batch(float *stage, const FwdGeom &gm, const FwdArgs &a,
+__device__ __forceinline__ void stage_batch(float *stage, const FwdGeom &gm, const FwdKArgs &k, uint64_t *bar,
                                             int r, int yv, int x0, int warp, int lane)
 {
     constexpr int NS = Q + 3;
-    const size_t plane = (size_t)a.H * a.W;
+    const FwdArgs &a = k.a;
     const int xs0 = x0 - gm.RA;
+    if (k.use_tma) {
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads before the copies
+            tma::mbar_expect_tx(bar, (unsigned)(2 * NS * kB * gm.WSt * 4));
+            const size_t box = (size_t)kB * gm.WSt;
+            tma::load_3d(stage, &k.tg, xs0, yv + r, 0, bar);
+            tma::load_3d(stage + Q * box, &k.tr, xs0, yv + r, 0, bar);
+            tma::load_3d(stage + NS * box, &k.tg, xs0, yv - r - 1, 0, bar);
+            tma::load_3d(stage + (NS + Q) * box, &k.tr, xs0, yv - r - 1, 0, bar);
+        }
+        return;
+    }
+    const size_t plane = (size_t)a.H * a.W;
     const bool vec = (a.W & 3) == 0;  // 16-byte rows: every 4-column chunk is all in or all out
     for (int row = warp; row < 2 * kB * NS; row += kThreads / 32) {
         const int el = row / (kB * NS), rem = row - el * (kB * NS);
-        const int b = rem / NS, k = rem - b * NS;
+        const int kk = rem / kB, b = rem - kk * kB;
         const int y = el == 0 ? yv + b + r : yv + b - r - 1;
         const bool row_ok = y >= 0 && y < a.H;
-        const float *base = k < Q ? a.guide + (size_t)k * plane : a.rad + (size_t)(k - Q) * plane;
+        const float *base = kk < Q ? a.guide + (size_t)kk * plane : a.rad + (size_t)(kk - Q) * plane;
         const float *src_row = base + (size_t)(row_ok ? y : 0) * a.W;
         float *dst = stage + (size_t)row * gm.WSt;
         if (vec) {
@@ -252,6 +283,19 @@ __device__ __forceinline__ void stage_batch(float *stage, const FwdGeom &gm, con
         }
     }
     cp_async_commit();
+}
+
+// Wait for the rows staged by the n-th stage_batch call (bounded for the TMA path).
+__device__ __forceinline__ void stage_wait(const FwdKArgs &k, uint64_t *bar, int n, int *abort_flag)
+{
+    if (k.use_tma) {
+        if (!tma::wait_warp(bar, (uint32_t)(n & 1), kFwdTimeoutNs) && (threadIdx.x & 31) == 0) {
+            *abort_flag = 1;
+            if (k.a.status) atomicExch(k.a.status, 1);
+        }
+    } else {
+        cp_async_wait_all();
+    }
 }
 
 // Horizontal radius-r sums of one shared-memory row, in place: slot xo <- sum of
@@ -327,12 +371,14 @@ __device__ __forceinline__ void hsum_row(float *p, int r)
 }
 
 template <int Q, int RT, bool ADJ>
-__global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
+__global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_constant__ FwdKArgs ka)
 {
     using C = Chan<Q>;
     constexpr int NS = Q + 3;
     extern __shared__ __align__(16) float smem[];
     __shared__ float s_cta[NS], s_ref[NS];
+    __shared__ int s_abort;
+    const FwdArgs &a = ka.a;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int H = a.H, W = a.W;
@@ -342,12 +388,24 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
     const int y0 = blockIdx.y * a.TH;
     const int y1 = min(y0 + a.TH, H);
     const int nColWarps = (gm.Wi + 31) >> 5;
-    float *Vbuf = smem;                                   // [kB][NCH][VS]  window sums
-    float *stage = smem + (size_t)kB * C::NCH * gm.VS;    // [2][kB][NS][WSt] input rows
+    float *base = smem + (((128 - (tma::smem_addr(smem) & 127)) & 127) >> 2);  // 128-byte aligned
+    float *Vbuf = base;                                              // [kB][NCH][VS]  window sums
+    float *stage = base + ((size_t)kB * C::NCH * gm.VS + 31) / 32 * 32;  // [2][NS][kB][WSt] input rows
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stage + (size_t)2 * NS * kB * gm.WSt);
+    if (tid == 0) {
+        s_abort = 0;
+        if (ka.use_tma) {
+            tma::mbar_init(bar, 1);
+            tma::mbar_init_fence();
+        }
+    }
+    __syncthreads();
 
     const int first_row = y0 - r;  // first input row summed by this segment
     int yv = y0 - 2 * r;           // first virtual row: the walkers start from an empty window
-    stage_batch<Q>(stage, gm, a, r, yv, x0, warp, lane);
+    int nstaged = 0;               // stage_batch calls so far (mbarrier phase)
+    stage_batch<Q>(stage, gm, ka, bar, r, yv, x0, warp, lane);
+    ++nstaged;
 
     // reference shifts (overlaps the first copies)
     if (warp == 0) {
@@ -381,8 +439,9 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
     float geps_acc = 0.f;  // adjoint mode: this thread's share of d L / d eps
     for (; yv < y1; yv += kB) {
         // 1. V-pass over the staged rows
-        cp_async_wait_all();
+        stage_wait(ka, bar, nstaged - 1, &s_abort);
         __syncthreads();
+        if (s_abort) break;  // a copy never completed: issue nothing more on this barrier
         if (walker) {
 #pragma unroll 1
             for (int b = 0; b < kB; ++b) {
@@ -390,8 +449,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
                 if (yc < y1) {
                     const bool ein_ok = yc + r >= 0 && yc + r < H;
                     const bool lout_ok = yc - r - 1 >= first_row && yc - r - 1 >= 0;
-                    const float *se = stage + (size_t)(b * NS) * gm.WSt + scol;
-                    const float *sl = stage + (size_t)((kB + b) * NS) * gm.WSt + scol;
+                    const float *se = stage + (size_t)b * gm.WSt + scol;
+                    const float *sl = stage + (size_t)(NS * kB + b) * gm.WSt + scol;
                     float e[NS], l[NS];
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
@@ -400,11 +459,11 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
                     }
                     if (ein_ok) {
 #pragma unroll
-                        for (int k = 0; k < NS; ++k) e[k] = se[k * gm.WSt] - shl[k];
+                        for (int k = 0; k < NS; ++k) e[k] = se[(size_t)k * kB * gm.WSt] - shl[k];
                     }
                     if (lout_ok) {
 #pragma unroll
-                        for (int k = 0; k < NS; ++k) l[k] = sl[k * gm.WSt] - shl[k];
+                        for (int k = 0; k < NS; ++k) l[k] = sl[(size_t)k * kB * gm.WSt] - shl[k];
                     }
                     if (group == 0) walker_update<Q, 0, true>(V, e, l);
                     else if (group == 1) walker_update<Q, 1, true>(V, e, l);
@@ -415,7 +474,10 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
         }
         __syncthreads();
         // prefetch the next batch's rows while this one is summed and solved
-        if (yv + kB < y1) stage_batch<Q>(stage, gm, a, r, yv + kB, x0, warp, lane);
+        if (yv + kB < y1) {
+            stage_batch<Q>(stage, gm, ka, bar, r, yv + kB, x0, warp, lane);
+            ++nstaged;
+        }
         if (yv + kB - 1 < y0) continue;  // warm-up batch: nothing to solve yet
 
         // 2. H-pass, one thread per (row, channel)
@@ -474,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const FwdArgs a)
         }
         __syncthreads();
     }
-    cp_async_wait_all();
+    if (!ka.use_tma) cp_async_wait_all();
     if constexpr (ADJ) {
         double g = (double)geps_acc;
 #pragma unroll
@@ -490,7 +552,18 @@ __host__ __device__ constexpr bool specialised(int q, int r) { return q == 8 && 
 template <int Q, int RT, bool ADJ>
 cudaError_t launch_fwd_qr(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
-    flr_fwd_kernel<Q, RT, ADJ><<<grid, kThreads, smem, st>>>(a);
+    FwdKArgs ka;
+    std::memset(&ka, 0, sizeof(ka));
+    ka.a = a;
+    const FwdGeom gm(a.r, !ADJ && RT >= 0);
+    const bool aligned = (a.W & 3) == 0 && ((uintptr_t)a.guide & 15) == 0 && ((uintptr_t)a.rad & 15) == 0;
+    // boxes of all guide planes and all radiance planes: together the 2 * (Q + 3) * kB * WSt
+    // * 4 bytes per batch that stage_batch announces
+    ka.use_tma = aligned && tma::encode_planes_f32(&ka.tg, a.guide, a.W, a.H, Q, gm.WSt, kB, Q) == cudaSuccess &&
+                         tma::encode_planes_f32(&ka.tr, a.rad, a.W, a.H, 3, gm.WSt, kB, 3) == cudaSuccess
+                     ? 1
+                     : 0;
+    flr_fwd_kernel<Q, RT, ADJ><<<grid, kThreads, smem, st>>>(ka);
     return cudaGetLastError();
 }
 
@@ -525,7 +598,8 @@ template <int Q>
 size_t smem_q(int r, bool adj)
 {
     const FwdGeom gm(r, !adj && specialised(Q, r));
-    return sizeof(float) * ((size_t)kB * Chan<Q>::NCH * gm.VS + (size_t)2 * kB * (Q + 3) * gm.WSt);
+    // alignment slack, window sums (rounded to 128 bytes), staged rows, mbarrier
+    return 128 + sizeof(float) * (((size_t)kB * Chan<Q>::NCH * gm.VS + 31) / 32 * 32 + (size_t)2 * kB * (Q + 3) * gm.WSt) + 16;
 }
 
 }  // namespace

@@ -113,6 +113,7 @@ struct FwdArgs {
     const float *gA;   // [(Q+1)*3][H][W]: row 0 = G(b_k), rows 1..Q = G(a_k)
     float *gS;         // [NCH][H][W] in moment-channel order (see Chan)
     double *geps;      // accumulated d L / d eps
+    int *status = nullptr;  // set to 1 if a bounded device wait ran out (may be NULL)
 };
 
 struct ApplyArgs {

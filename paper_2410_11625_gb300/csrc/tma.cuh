@@ -24,15 +24,16 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encoder()
     return fn;
 }
 
-// 3-D map of float32 planes [P][H][W] (W innermost): box (bw, bh, 1), zero fill outside.
-// Needs W * 4 and the base address to be multiples of 16 bytes.
-inline cudaError_t encode_planes_f32(CUtensorMap *m, const float *base, int W, int H, int P, int bw, int bh)
+// 3-D map of float32 planes [P][H][W] (W innermost): box (bw, bh, bp) -- bw columns,
+// bh rows, bp planes -- zero fill outside.  One copy of the box transfers bw * bh * bp * 4
+// bytes.  Needs W * 4 and the base address to be multiples of 16 bytes.
+inline cudaError_t encode_planes_f32(CUtensorMap *m, const float *base, int W, int H, int P, int bw, int bh, int bp)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)P};
     const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bp};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
