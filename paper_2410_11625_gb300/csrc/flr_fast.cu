@@ -26,6 +26,7 @@
 
 #include "flr.h"
 #include "flr_fast_stages.cuh"
+#include "tma.cuh"
 
 namespace flr {
 namespace {
@@ -60,26 +61,191 @@ __global__ void __launch_bounds__(256) fast_apply_kernel(const FastArgs a)
         fast::stage_apply<Q>(a, t);
 }
 
+// ---- TMA version of the apply stage (rows 16-byte aligned) ------------------------------
+//
+// Persistent CTAs walk work items of kFW output columns; each item's map-guide rows arrive
+// by one TMA box copy into a two-stage ring (the next item loads while the current one is
+// computed), so the bytes in flight do not depend on registers per thread.  The copy
+// engine zero-fills outside the image.  Waits are bounded (1 s) and report through the
+// status word.
+constexpr int kFW = 128;
+constexpr unsigned long long kFastTimeoutNs = 1000000000ull;
+
+struct alignas(128) FastKArgs {
+    CUtensorMap t0;  // map-guide planes [Q][Ho][Wo], box (kFW, P, Q)
+    FastArgs a;
+};
+
+__device__ __forceinline__ float *align128(float *p)
+{
+    return p + (((128 - (tma::smem_addr(p) & 127)) & 127) >> 2);
+}
+
+// Stage 4 with TMA: item (cell row i, column chunk cx).  Cell row i is the P = F s output
+// rows [P i - P/2, P i + P/2), which all interpolate between the same two block rows; the
+// item loads those rows of the Q map-guide planes.  Thread t owns output column kFW cx + t:
+// it interpolates its corner models horizontally once per item (top and bottom block row),
+// then for each row vertically, and applies them.  The coordinates are the exact rational
+// ones of fast::stage_apply.
+template <int Q>
+__global__ void __launch_bounds__(kFW, 3) apply_tma_kernel(const __grid_constant__ FastKArgs k)
+{
+    constexpr int NC = 3 * (Q + 1), PMAX = 8, STAGE = Q * PMAX * kFW;
+    const FastArgs &a = k.a;
+    extern __shared__ __align__(16) float smem[];
+    float *base = align128(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * STAGE);
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int P = a.F * a.s, den = 2 * P;
+    const int ncx = (a.Wo + kFW - 1) / kFW, nitems = (a.Hb + 1) * ncx;
+    const size_t oplane = (size_t)a.Ho * a.Wo, bplane = (size_t)a.Hb * a.Wb;
+    if (tid == 0) {
+        s_abort = 0;
+        tma::mbar_init(bar, 1);
+        tma::mbar_init(bar + 1, 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int item, int st) {
+        const int ci = item / ncx, cx = item % ncx;
+        tma::mbar_expect_tx(bar + st, (unsigned)(Q * P * kFW * 4));
+        tma::load_3d(base + st * STAGE, &k.t0, cx * kFW, P * ci - P / 2, 0, bar + st);
+    };
+    if (tid == 0 && (int)blockIdx.x < nitems) issue(blockIdx.x, 0);
+    float sh[Q + 3];
+#pragma unroll
+    for (int q = 0; q < Q + 3; ++q) sh[q] = a.shift[q];
+    int it = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+        const int st = it & 1;
+        if (tid == 0 && item + (int)gridDim.x < nitems) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue(item + gridDim.x, st ^ 1);
+        }
+        if (!tma::wait_warp(bar + st, (uint32_t)((it >> 1) & 1), kFastTimeoutNs) && lane == 0) {
+            s_abort = 1;
+            if (a.status) atomicExch(a.status, 1);
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const float *T = base + st * STAGE;  // [Q][P][kFW]
+        const int ci = item / ncx, cx = item % ncx;
+        const int x = cx * kFW + tid;
+        const int ya = P * ci - P / 2;       // first output row of the cell (may be < 0)
+        if (x < a.Wo) {
+            // block rows of the cell (the same for all its rows)
+            const int yfirst = max(ya, 0);
+            const int ny0 = min(max(2 * yfirst + 1 - P, 0), (a.Hb - 1) * den);
+            const int i0 = min(ny0 / den, max(a.Hb - 2, 0)), i1 = min(i0 + 1, a.Hb - 1);
+            // block columns and weight of this column
+            const int r = (x + P / 2) / P;
+            const int jl = min(max(r - 1, 0), a.Wb - 1), jr = min(max(r, 0), a.Wb - 1);
+            const int nx = min(max(2 * x + 1 - P, 0), (a.Wb - 1) * den);
+            const float fx = fminf(fmaxf((float)(nx - (r - 1) * den) / (float)den, 0.f), 1.f);
+            float top[NC], dtb[NC];  // horizontally interpolated top row, bottom minus top
+            {
+                const size_t t0 = (size_t)i0 * a.Wb, t1 = (size_t)i1 * a.Wb;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float *pc = a.coef + c * bplane;
+                    const float l0 = __ldg(pc + t0 + jl), l1 = __ldg(pc + t1 + jl);
+                    const float d0 = __ldg(pc + t0 + jr) - l0, d1 = __ldg(pc + t1 + jr) - l1;
+                    top[c] = fmaf(fx, d0, l0);
+                    dtb[c] = fmaf(fx, d1, l1) - top[c];
+                }
+            }
+            for (int t = 0; t < P; ++t) {
+                const int yo = ya + t;
+                if (yo < 0 || yo >= a.Ho) continue;
+                const int ny = min(max(2 * yo + 1 - P, 0), (a.Hb - 1) * den);
+                const float fy = (float)(ny - i0 * den) / (float)den;
+                float z[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) z[i] = T[(i * P + t) * kFW + tid] - sh[i];
+                const size_t off = (size_t)yo * a.Wo + x;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float o = fmaf(fy, dtb[c], top[c]);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const int kk = 3 * (i + 1) + c;
+                        o = fmaf(fmaf(fy, dtb[kk], top[kk]), z[i], o);
+                    }
+                    a.out[c * oplane + off] = o + sh[Q + c];
+                }
+            }
+        }
+        __syncthreads();  // stage st is read; the next iteration may refill it
+    }
+}
+
+template <int Q>
+size_t apply_tma_smem()
+{
+    return 128 + sizeof(float) * 2 * (size_t)Q * 8 * kFW + 16;
+}
+
+int fast_n_sm()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 1;
+    }
+    return n;
+}
+
+template <int Q, int F>
+cudaError_t launch_moments(const FastArgs &a, cudaStream_t st)
+{
+    dim3 g1((a.Wi + 255) / 256, a.Hb);
+    block_moments_kernel<Q, F><<<g1, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t launch_apply_fast(const FastArgs &a, cudaStream_t st)
+{
+    const int P = a.F * a.s;
+    const bool aligned = (a.Wo & 3) == 0 && ((uintptr_t)a.map_guide & 15) == 0 && P <= 8;
+    if (aligned) {
+        FastKArgs k;
+        std::memset(&k, 0, sizeof(k));
+        k.a = a;
+        if (tma::encode_planes_f32(&k.t0, a.map_guide, a.Wo, a.Ho, Q, kFW, P, Q) == cudaSuccess) {
+            const size_t smem = apply_tma_smem<Q>();
+            cudaError_t e = cudaFuncSetAttribute(apply_tma_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            const int nitems = (a.Hb + 1) * ((a.Wo + kFW - 1) / kFW);
+            const int grid = nitems < 3 * fast_n_sm() ? nitems : 3 * fast_n_sm();  // three CTAs per SM
+            apply_tma_kernel<Q><<<grid, kFW, smem, st>>>(k);
+            return cudaGetLastError();
+        }
+    }
+    const size_t runs = (size_t)a.Ho * (a.Wo / (a.F * a.s) + 2);
+    fast_apply_kernel<Q><<<(unsigned)((runs + 255) / 256 < 16384 ? (runs + 255) / 256 : 16384), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int Q>
 cudaError_t launch_fast_q(const FastArgs &a, cudaStream_t st)
 {
-    dim3 g1((a.Wi + 255) / 256, a.Hb);
+    cudaError_t e;
     switch (a.F) {
-    case 2: block_moments_kernel<Q, 2><<<g1, 256, 0, st>>>(a); break;
-    case 4: block_moments_kernel<Q, 4><<<g1, 256, 0, st>>>(a); break;
-    case 8: block_moments_kernel<Q, 8><<<g1, 256, 0, st>>>(a); break;
+    case 2: e = launch_moments<Q, 2>(a, st); break;
+    case 4: e = launch_moments<Q, 4>(a, st); break;
+    case 8: e = launch_moments<Q, 8>(a, st); break;
     default: return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t nb = (size_t)a.Hb * a.Wb;
     blur_h_kernel<Q><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     blur_v_solve_kernel<Q><<<(unsigned)((nb + 127) / 128), 128, sizeof(float) * Chan<Q>::NCH * 128, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t runs = (size_t)a.Ho * (a.Wo / (a.F * a.s) + 2);
-    fast_apply_kernel<Q><<<(unsigned)((runs + 255) / 256 < 16384 ? (runs + 255) / 256 : 16384), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_apply_fast<Q>(a, st);
 }
 
 cudaError_t launch_fast(int q, const FastArgs &a, cudaStream_t st)
@@ -109,6 +275,7 @@ struct flr_fast_handle {
     size_t ws_blocks = 0;
     float *shift = nullptr;
     unsigned long long *count = nullptr;
+    int *status = nullptr;  // set by a kernel whose bounded wait ran out
     cudaStream_t last_stream = nullptr;
     // batch path: per-frame workspace, barrier words, status word
     float *bws = nullptr;
@@ -189,7 +356,8 @@ int flr_fast_create(const flr_fast_params *p, flr_fast_handle **out)
     for (int d = -p->taps; d <= p->taps; ++d)
         h->w[d + p->taps] = (float)std::exp(-(double)d * d / (2.0 * (double)p->sigma * p->sigma));
     if (cudaMalloc(&h->shift, sizeof(float) * (FLR_MAX_Q + 3)) != cudaSuccess ||
-        cudaMalloc(&h->count, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&h->count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->status, sizeof(int)) != cudaSuccess || cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
         flr_fast_destroy(h);
         return FLR_ERR_NOMEM;
     }
@@ -206,6 +374,7 @@ int flr_fast_destroy(flr_fast_handle *h)
     cudaFree(h->bar);
     cudaFree(h->shift);
     cudaFree(h->count);
+    cudaFree(h->status);
     delete h;
     return FLR_OK;
 }
@@ -250,6 +419,7 @@ int flr_fast_denoise(flr_fast_handle *h, const float *guide, const float *map_gu
     a.taps = h->p.taps;
     a.eps = h->p.eps;
     a.tau = h->p.pivot_ratio;
+    a.status = h->status;
     std::memcpy(a.w, h->w, sizeof(a.w));
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
@@ -341,6 +511,12 @@ int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out)
         return FLR_ERR_CUDA;
     out->flagged = n;
     out->resolved = h->p.pivot_ratio > 0.f ? n : 0ull;
+    int status = 0;
+    if (cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FLR_ERR_CUDA;
+    if (status != 0) {
+        if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) return FLR_ERR_CUDA;
+        return FLR_ERR_TIMEOUT;
+    }
     return FLR_OK;
 }
 

@@ -40,6 +40,7 @@ struct FastArgs {
     int Hi, Wi, Ho, Wo, Hb, Wb, F, s, taps;
     float eps, tau;
     float w[2 * kMaxTaps + 1];             // Gaussian weights
+    int *status = nullptr;                 // set to 1 if a bounded device wait ran out (may be NULL)
 };
 
 // 1. block moments.  Block (i, j) covers input rows [iF, iF+F) and columns [jF, jF+F).
@@ -313,17 +314,20 @@ __device__ __forceinline__ void stage_apply(const FastArgs &a, size_t t)
         const int i0 = min(ny / den, max(a.Hb - 2, 0)), i1 = min(i0 + 1, a.Hb - 1);
         const float fy = (float)(ny - i0 * den) / (float)den;
         const int jl = min(max(r - 1, 0), a.Wb - 1), jr = min(max(r, 0), a.Wb - 1);
-        float cl[NC], cr[NC];
+        // corner models: left values and right-minus-left differences of the two block rows
+        // (interpolated horizontally, then vertically, per pixel: the same order and the same
+        // roundings as the TMA apply kernel, so both paths agree bit for bit)
+        float l0[NC], d0[NC], l1[NC], d1[NC];
         {
             const size_t bl0 = (size_t)i0 * a.Wb + jl, bl1 = (size_t)i1 * a.Wb + jl;
             const size_t br0 = (size_t)i0 * a.Wb + jr, br1 = (size_t)i1 * a.Wb + jr;
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
                 const float *pl = a.coef + k * bplane;
-                const float l0 = __ldg(pl + bl0), l1 = __ldg(pl + bl1);
-                const float r0 = __ldg(pl + br0), r1 = __ldg(pl + br1);
-                cl[k] = fmaf(fy, l1 - l0, l0);
-                cr[k] = fmaf(fy, r1 - r0, r0);
+                l0[k] = __ldg(pl + bl0);
+                l1[k] = __ldg(pl + bl1);
+                d0[k] = __ldg(pl + br0) - l0[k];
+                d1[k] = __ldg(pl + br1) - l1[k];
             }
         }
         float sh[Q + 3];
@@ -357,11 +361,13 @@ __device__ __forceinline__ void stage_apply(const FastArgs &a, size_t t)
                 const float fx = fminf(fmaxf((float)(nx - (r - 1) * den) / (float)den, 0.f), 1.f);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float acc = fmaf(fx, cr[c] - cl[c], cl[c]);
+                    float top = fmaf(fx, d0[c], l0[c]);
+                    float acc = fmaf(fy, fmaf(fx, d1[c], l1[c]) - top, top);
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
                         const int k = 3 * (i + 1) + c;
-                        acc = fmaf(fmaf(fx, cr[k] - cl[k], cl[k]), z[i][u] - sh[i], acc);
+                        top = fmaf(fx, d0[k], l0[k]);
+                        acc = fmaf(fmaf(fy, fmaf(fx, d1[k], l1[k]) - top, top), z[i][u] - sh[i], acc);
                     }
                     o[c][u] = acc + sh[Q + c];
                 }
