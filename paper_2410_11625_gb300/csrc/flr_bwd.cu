@@ -13,7 +13,10 @@
 //             dz_j = Abar_j g_j                                    (the applied guide)
 // j in T_k <=> k in T_j for clipped square windows of one radius, so every adjoint of a
 // window sum is the same clipped box sum.
+#include <cstring>
+
 #include "flr_internal.cuh"
+#include "tma.cuh"
 
 namespace flr {
 namespace {
@@ -97,6 +100,132 @@ __global__ void __launch_bounds__(kBThreads) box_sum_kernel(const float *__restr
     }
 }
 
+// The same clipped box sum over many planes with TMA staging (rows 16-byte aligned): one CTA
+// per 64 x 32 output tile walks every plane; each plane's tile + halo arrives by one TMA box
+// copy (the copy engine zero-fills outside the image) into a double-buffered ring, so the
+// next plane loads while the current one is summed.  Waits are bounded (1 s).
+struct alignas(128) BoxKArgs {
+    CUtensorMap tm;  // [nplanes][H][W] float32, box (TS, THh, 1)
+    float *out;
+    int H, W, rad, nplanes;
+    int *status;
+};
+
+struct BoxGeom {
+    int RCA, TWa, THh, TS, HS;
+    __host__ __device__ BoxGeom(int rad)
+    {
+        RCA = (rad + 3) & ~3;  // staged columns start 16-byte aligned
+        TWa = kBW + 2 * RCA;
+        THh = kBH + 2 * rad;
+        TS = TWa + 4;          // row stride = 4 (mod 8) floats: conflict-free 128-bit phases
+        HS = kBW + 1;
+    }
+    __host__ __device__ int tile_floats() const { return (THh * TS + 31) / 32 * 32; }
+    __host__ __device__ size_t floats() const { return 32 + (size_t)2 * tile_floats() + (size_t)THh * HS + 8; }
+};
+
+constexpr unsigned long long kBoxTimeoutNs = 1000000000ull;
+
+template <int RT>
+__global__ void __launch_bounds__(kBThreads, 3) box_sum_tma_kernel(const __grid_constant__ BoxKArgs k)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int rad = RT >= 0 ? RT : k.rad;
+    const BoxGeom g(rad);
+    float *base = sm + (((128 - (tma::smem_addr(sm) & 127)) & 127) >> 2);
+    float *T0 = base, *T1 = base + g.tile_floats();
+    float *Hb = T1 + g.tile_floats();
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Hb + ((g.THh * g.HS + 1) & ~1));
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tx0 = blockIdx.x * kBW, ty0 = blockIdx.y * kBH;
+    const size_t plane = (size_t)k.H * k.W;
+    auto stage = [&](float *T, int p) {
+        if (tid == 0) {
+            uint64_t *b = bar + (p & 1);
+            tma::mbar_expect_tx(b, (unsigned)(g.THh * g.TS * 4));
+            tma::load_3d(T, &k.tm, tx0 - g.RCA, ty0 - rad, p, b);
+        }
+    };
+    if (tid == 0) {
+        s_abort = 0;
+        tma::mbar_init(bar, 1);
+        tma::mbar_init(bar + 1, 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    stage(T0, 0);
+    const int x = tid % kBW, run = tid / kBW;
+    const int gx = tx0 + x;
+    for (int p = 0; p < k.nplanes; ++p) {
+        float *Tc = (p & 1) ? T1 : T0;
+        if (p + 1 < k.nplanes) stage((p & 1) ? T0 : T1, p + 1);
+        if (!tma::wait_warp(bar + (p & 1), (uint32_t)((p >> 1) & 1), kBoxTimeoutNs) && lane == 0) {
+            s_abort = 1;
+            if (k.status) atomicExch(k.status, 1);
+        }
+        __syncthreads();
+        if (s_abort) {  // let a copy still in flight land before the CTA exits, then stop
+            if (p + 1 < k.nplanes && tid < 32)
+                tma::wait_warp(bar + ((p + 1) & 1), (uint32_t)(((p + 1) >> 1) & 1), kBoxTimeoutNs);
+            return;
+        }
+        // horizontal sums: 16 outputs per item, operands in registers; consecutive lanes take
+        // consecutive rows (16-byte loads at row stride 4 mod 8 floats: distinct banks)
+        for (int item = tid; item < g.THh * 4; item += kBThreads) {
+            const int xr = (item / g.THh) * 16, row = item % g.THh;
+            const float *q = Tc + row * g.TS + xr;
+            float *h = Hb + row * g.HS + xr;
+            if constexpr (RT >= 0) {
+                constexpr int RCA = (RT + 3) & ~3, XO = RCA - RT, N = 16 + 2 * RCA;
+                float v[N];
+#pragma unroll
+                for (int kk = 0; kk < N; kk += 4) {
+                    const float4 f = *reinterpret_cast<const float4 *>(q + kk);
+                    v[kk] = f.x;
+                    v[kk + 1] = f.y;
+                    v[kk + 2] = f.z;
+                    v[kk + 3] = f.w;
+                }
+                float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kk = 0; kk <= 2 * RT; ++kk) s4[kk & 3] += v[XO + kk];
+                float s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                h[0] = s;
+#pragma unroll
+                for (int t = 1; t < 16; ++t) {
+                    s += v[XO + t + 2 * RT] - v[XO + t - 1];
+                    h[t] = s;
+                }
+            } else {
+                const float *qq = q + (g.RCA - rad);
+                float s = 0.f;
+                for (int kk = 0; kk <= 2 * rad; ++kk) s += qq[kk];
+                h[0] = s;
+#pragma unroll
+                for (int t = 1; t < 16; ++t) {
+                    s += qq[t + 2 * rad] - qq[t - 1];
+                    h[t] = s;
+                }
+            }
+        }
+        __syncthreads();  // Hb complete; Tc may be refilled from here on
+        if (tid == 0) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        // vertical sums: thread = (column, run of 8 rows)
+        const float *q = Hb + (run * 8) * g.HS + x;
+        float s = 0.f;
+        for (int kk = 0; kk <= 2 * rad; ++kk) s += q[kk * g.HS];
+        float *dst = k.out + (size_t)p * plane;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (t > 0) s += q[(t + 2 * rad) * g.HS] - q[(t - 1) * g.HS];
+            const int gy = ty0 + run * 8 + t;
+            if (gx < k.W && gy < k.H) dst[(size_t)gy * k.W + gx] = s;
+        }
+    }
+}
+
 template <int Q>
 __global__ void bwd_contract_kernel(const BwdArgs a)
 {
@@ -171,8 +300,34 @@ cudaError_t launch_bwd_fields(int q, const float *g, const float *z, const float
     return cudaGetLastError();
 }
 
-cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st)
+template <int RT>
+cudaError_t launch_box_sum_tma(const BoxKArgs &k, cudaStream_t st)
 {
+    const BoxGeom g(k.rad);
+    const size_t smem = sizeof(float) * g.floats();
+    cudaError_t e = cudaFuncSetAttribute(box_sum_tma_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((k.W + kBW - 1) / kBW, (k.H + kBH - 1) / kBH);
+    box_sum_tma_kernel<RT><<<grid, kBThreads, smem, st>>>(k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st, int *status)
+{
+    if ((W & 3) == 0 && ((uintptr_t)in & 15) == 0 && nplanes > 0) {
+        BoxKArgs k;
+        std::memset(&k, 0, sizeof(k));
+        const BoxGeom g(rad);
+        if (tma::encode_planes_f32(&k.tm, in, W, H, nplanes, g.TS, g.THh, 1) == cudaSuccess) {
+            k.out = out;
+            k.H = H;
+            k.W = W;
+            k.rad = rad;
+            k.nplanes = nplanes;
+            k.status = status;
+            return rad == 8 ? launch_box_sum_tma<8>(k, st) : launch_box_sum_tma<-1>(k, st);
+        }
+    }
     const size_t smem = sizeof(float) * ((size_t)(kBH + 2 * rad) * (kBW + 2 * rad + 1) + (size_t)(kBH + 2 * rad) * (kBW + 1));
     cudaError_t e = cudaFuncSetAttribute(box_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -370,7 +370,7 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     FLR_CUDA(flr::launch_bwd_fields(q, grad_out, z, h->d_shift, F, H, W, rc, s), "backward: fields launch");
     const float *gA = F;
     if (rc > 0) {
-        FLR_CUDA(flr::launch_box_sum(F, GA, ncf, H, W, rc, s), "backward: average adjoint launch");
+        FLR_CUDA(flr::launch_box_sum(F, GA, ncf, H, W, rc, s, h->d_status), "backward: average adjoint launch");
         gA = GA;
     }
     // 3. per-pixel adjoint solve (moments recomputed) -> GS, d/d eps
@@ -386,10 +386,10 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     fa.force_coef = 0;
     FLR_CUDA(flr::launch_adj(q, fa, grid, h->adj_smem, s), "backward: adjoint kernel launch");
     // 4. adjoint of the window sums, the averaged models for the applied guide, contraction
-    FLR_CUDA(flr::launch_box_sum(GS, BS, nch, H, W, r, s), "backward: window-sum adjoint launch");
+    FLR_CUDA(flr::launch_box_sum(GS, BS, nch, H, W, r, s, h->d_status), "backward: window-sum adjoint launch");
     const float *BA = Acoef;
     if (rc > 0) {
-        FLR_CUDA(flr::launch_box_sum(Acoef, F, ncf, H, W, rc, s), "backward: model average launch");
+        FLR_CUDA(flr::launch_box_sum(Acoef, F, ncf, H, W, rc, s, h->d_status), "backward: model average launch");
         BA = F;
     }
     flr::BwdArgs ba;

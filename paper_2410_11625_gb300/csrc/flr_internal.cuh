@@ -154,7 +154,8 @@ cudaError_t launch_apply(int q, const ApplyArgs &a, cudaStream_t st);
 cudaError_t launch_fp64(int q, const Fp64Args &a, int n_sm, cudaStream_t st);
 cudaError_t launch_bwd_fields(int q, const float *g, const float *z, const float *shift, float *F, int H, int W,
                               int rc, cudaStream_t st);
-cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st);
+cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st,
+                           int *status = nullptr);
 cudaError_t launch_bwd_contract(int q, const BwdArgs &a, cudaStream_t st);
 namespace fast { struct FastArgs; }
 bool batch_supported(int q, int F);
