@@ -227,39 +227,51 @@ __global__ void __launch_bounds__(kBThreads, 3) box_sum_tma_kernel(const __grid_
 }
 
 template <int Q>
-__global__ void bwd_contract_kernel(const BwdArgs a)
+__global__ void __launch_bounds__(256) bwd_contract_kernel(const BwdArgs a)
 {
     using C = Chan<Q>;
     const int H = a.H, W = a.W;
     const size_t plane = (size_t)H * W;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < plane; p += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(p / W), x = (int)(p % W);
-        float xs[Q], ys[3];
+        // every input of this pixel is read once, up front (the outputs may not alias them)
+        float xs[Q], ys[3], gc[3];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) xs[i] = a.guide[i * plane + p] - a.shift[i];
+        for (int i = 0; i < Q; ++i) xs[i] = __ldg(a.guide + i * plane + p) - a.shift[i];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ys[c] = a.rad[c * plane + p] - a.shift[Q + c];
+        for (int c = 0; c < 3; ++c) {
+            ys[c] = __ldg(a.rad + c * plane + p) - a.shift[Q + c];
+            gc[c] = __ldg(a.g + c * plane + p);
+        }
+        float inv_m = 1.f;
+        if (a.rc > 0) {
+            const float ny = (float)(min(y + a.rc, H - 1) - max(y - a.rc, 0) + 1);
+            const float nx = (float)(min(x + a.rc, W - 1) - max(x - a.rc, 0) + 1);
+            inv_m = 1.0f / (ny * nx);
+        }
         const float *BS = a.BS;
+        float bxx[C::NXX];
+#pragma unroll
+        for (int t = 0; t < C::NXX; ++t) bxx[t] = __ldg(BS + (C::XX0 + t) * plane + p);
+        float bxy[Q][3];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) bxy[i][c] = __ldg(BS + C::xy(i, c) * plane + p);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            float d = BS[(C::X0 + i) * plane + p];
+            float d = __ldg(BS + (C::X0 + i) * plane + p);
 #pragma unroll
             for (int j = 0; j < Q; ++j) {
-                const int ch = i <= j ? C::xx(i, j) : C::xx(j, i);
-                d = fmaf(2.f * BS[ch * plane + p], xs[j], d);
+                const int t = (i <= j ? C::xx(i, j) : C::xx(j, i)) - C::XX0;
+                d = fmaf(2.f * bxx[t], xs[j], d);
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) d = fmaf(BS[C::xy(i, c) * plane + p], ys[c], d);
+            for (int c = 0; c < 3; ++c) d = fmaf(bxy[i][c], ys[c], d);
             // the applied guide: dz_i = sum_c Abar[i][c] g_c
-            float inv_m = 1.f;
-            if (a.rc > 0) {
-                const float ny = (float)(min(y + a.rc, H - 1) - max(y - a.rc, 0) + 1);
-                const float nx = (float)(min(x + a.rc, W - 1) - max(x - a.rc, 0) + 1);
-                inv_m = 1.0f / (ny * nx);
-            }
             float dz = 0.f;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dz = fmaf(a.BA[(3 * (i + 1) + c) * plane + p], a.g[c * plane + p], dz);
+            for (int c = 0; c < 3; ++c) dz = fmaf(__ldg(a.BA + (3 * (i + 1) + c) * plane + p), gc[c], dz);
             dz *= inv_m;
             if (a.separate_map) {
                 a.grad_guide[i * plane + p] = d;
@@ -270,9 +282,9 @@ __global__ void bwd_contract_kernel(const BwdArgs a)
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float d = BS[(C::Y0 + c) * plane + p];
+            float d = __ldg(BS + (C::Y0 + c) * plane + p);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) d = fmaf(BS[C::xy(i, c) * plane + p], xs[i], d);
+            for (int i = 0; i < Q; ++i) d = fmaf(bxy[i][c], xs[i], d);
             a.grad_rad[c * plane + p] = d;
         }
     }
@@ -338,7 +350,7 @@ cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int 
 
 cudaError_t launch_bwd_contract(int q, const BwdArgs &a, cudaStream_t st)
 {
-    const int grid = elem_grid((size_t)a.H * a.W);
+    const int grid = (int)(((size_t)a.H * a.W + 255) / 256);  // one thread per pixel
     switch (q) {
     case 1: bwd_contract_kernel<1><<<grid, 256, 0, st>>>(a); break;
     case 2: bwd_contract_kernel<2><<<grid, 256, 0, st>>>(a); break;

@@ -555,7 +555,7 @@ cudaError_t launch_fwd_qr(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t
     FwdKArgs ka;
     std::memset(&ka, 0, sizeof(ka));
     ka.a = a;
-    const FwdGeom gm(a.r, !ADJ && RT >= 0);
+    const FwdGeom gm(a.r, RT >= 0);
     const bool aligned = (a.W & 3) == 0 && ((uintptr_t)a.guide & 15) == 0 && ((uintptr_t)a.rad & 15) == 0;
     // boxes of all guide planes and all radiance planes: together the 2 * (Q + 3) * kB * WSt
     // * 4 bytes per batch that stage_batch announces
@@ -577,9 +577,9 @@ cudaError_t prepare_qr(size_t smem)
 template <int Q, bool ADJ>
 cudaError_t launch_fwd_q(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
-    if constexpr (Q == 8 && !ADJ) {
-        if (a.r == 8) return launch_fwd_qr<8, 8, false>(a, grid, smem, st);
-        if (a.r == 5) return launch_fwd_qr<8, 5, false>(a, grid, smem, st);
+    if constexpr (Q == 8) {
+        if (a.r == 8) return launch_fwd_qr<8, 8, ADJ>(a, grid, smem, st);
+        if (a.r == 5) return launch_fwd_qr<8, 5, ADJ>(a, grid, smem, st);
     }
     return launch_fwd_qr<Q, -1, ADJ>(a, grid, smem, st);
 }
@@ -587,9 +587,9 @@ cudaError_t launch_fwd_q(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t 
 template <int Q, bool ADJ>
 cudaError_t prepare_q(int r, size_t smem)
 {
-    if constexpr (Q == 8 && !ADJ) {
-        if (r == 8) return prepare_qr<8, 8, false>(smem);
-        if (r == 5) return prepare_qr<8, 5, false>(smem);
+    if constexpr (Q == 8) {
+        if (r == 8) return prepare_qr<8, 8, ADJ>(smem);
+        if (r == 5) return prepare_qr<8, 5, ADJ>(smem);
     }
     return prepare_qr<Q, -1, ADJ>(smem);
 }
@@ -597,7 +597,7 @@ cudaError_t prepare_q(int r, size_t smem)
 template <int Q>
 size_t smem_q(int r, bool adj)
 {
-    const FwdGeom gm(r, !adj && specialised(Q, r));
+    const FwdGeom gm(r, specialised(Q, r));
     // alignment slack, window sums (rounded to 128 bytes), staged rows, mbarrier
     return 128 + sizeof(float) * (((size_t)kB * Chan<Q>::NCH * gm.VS + 31) / 32 * 32 + (size_t)2 * kB * (Q + 3) * gm.WSt) + 16;
 }
