@@ -271,6 +271,16 @@ int flr_fast_batch_status(flr_fast_handle *h);
 int flr_barrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
 
 /*
+ * Self-test of the bounded mbarrier wait used by the TMA-staged and tensor-core kernels
+ * (every such wait gives up after a time limit and sets a status word instead of hanging):
+ * `ctas` CTAs each wait on an mbarrier whose phase never completes (one of two expected
+ * arrivals) and on one that does.  *status receives bit 0 if the first wait ran out (the
+ * expected result) and bit 1 if the second one did (a failure); so 1 is a pass.  No fault is
+ * involved.  Not a paper operation.  Errors: FLR_ERR_ARG, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_mbarrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
+
+/*
  * FLNR (Sec. 3.3, "Fast Local Neural Regression"): a U-Net maps the guides and the noisy
  * radiance, concatenated channel-wise (11 channels: Q = 8 guides, then RGB), to 8 enhanced
  * guide channels that FLR then uses (Fig. 2).  Layers, in order (3x3 convolutions stride 1,

@@ -263,6 +263,32 @@ cudaError_t launch_fast(int q, const FastArgs &a, cudaStream_t st)
     }
 }
 
+// Self-test of the bounded mbarrier wait the TMA and tensor-core kernels use: barrier 0
+// expects two arrivals and receives one, so its phase never completes and every warp's wait
+// must run out (status bit 0); barrier 1 expects one arrival and receives it, so the wait
+// must succeed (a timeout there sets bit 1).
+__global__ void mbarrier_selftest_kernel(int *status, unsigned long long timeout_ns)
+{
+    __shared__ uint64_t bar[2];
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar[0], 2);
+        tma::mbar_init(&bar[1], 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tma::smem_addr(&bar[0])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tma::smem_addr(&bar[1])) : "memory");
+    }
+    __syncthreads();
+    const bool done0 = tma::wait_warp(&bar[0], 0, timeout_ns);
+    const bool done1 = tma::wait_warp(&bar[1], 0, timeout_ns);
+    if ((threadIdx.x & 31) == 0) {
+        if (!done0) atomicOr(status, 1);
+        if (!done1) atomicOr(status, 2);
+    }
+}
+
 thread_local char g_fast_err[256] = "no error";
 
 }  // namespace
@@ -499,6 +525,22 @@ int flr_barrier_selftest(int ctas, unsigned long long timeout_ns, int *status)
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(status, w + 2, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(w);
+    return e == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+int flr_mbarrier_selftest(int ctas, unsigned long long timeout_ns, int *status)
+{
+    if (ctas <= 0 || ctas > 1024 || !status || timeout_ns > 10000000000ull) return FLR_ERR_ARG;
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return FLR_ERR_NOMEM;
+    cudaError_t e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        flr::mbarrier_selftest_kernel<<<ctas, 64>>>(d, timeout_ns);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
     return e == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
 }
 

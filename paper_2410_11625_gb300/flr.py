@@ -21,6 +21,7 @@ EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoi
            "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
            "flr_fast_denoise", "flr_fast_get_stats", "flr_denoise_batch", "flr_fast_reserve_batch",
            "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest",
+           "flr_mbarrier_selftest",
            "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
            "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_get_grads",
            "flnr_adam_step", "flnr_l1_loss", "flnr_layer", "flnr_status")
@@ -102,8 +103,9 @@ def load_library():
     lib.flr_fast_denoise_batch.argtypes = [vp, ip, ctypes.POINTER(FlrFrame), vp]
     lib.flr_fast_batch_status.argtypes = [vp]
     lib.flr_barrier_selftest.argtypes = [ip, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_int)]
+    lib.flr_mbarrier_selftest.argtypes = [ip, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_int)]
     for name in ("flr_denoise_batch", "flr_fast_reserve_batch", "flr_fast_denoise_batch",
-                 "flr_fast_batch_status", "flr_barrier_selftest"):
+                 "flr_fast_batch_status", "flr_barrier_selftest", "flr_mbarrier_selftest"):
         getattr(lib, name).restype = ctypes.c_int
     lib.flr_denoise_noalloc.argtypes = [ctypes.POINTER(FlrParams), fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_noalloc.restype = ctypes.c_int
@@ -335,6 +337,15 @@ class FastFLR:
         s = FlrStats()
         _check(load_library().flr_fast_get_stats(self._h, ctypes.byref(s)), "flr_fast_get_stats")
         return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+
+
+def mbarrier_selftest(ctas=4, timeout_ns=20_000_000):
+    """Status word of flr_mbarrier_selftest (1 = the never-completing wait ran out and the
+    completing one did not)."""
+    st = ctypes.c_int(0)
+    _check(load_library().flr_mbarrier_selftest(int(ctas), ctypes.c_ulonglong(timeout_ns), ctypes.byref(st)),
+           "flr_mbarrier_selftest")
+    return st.value
 
 
 def barrier_selftest(ctas=4, timeout_ns=50_000_000):

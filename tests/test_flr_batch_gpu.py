@@ -88,6 +88,18 @@ def test_bounded_wait_reports_timeout(flr):
     assert time.time() - t0 < 10.0
 
 
+def test_bounded_mbarrier_wait_reports_timeout(flr):
+    """The mbarrier wait of the TMA / tensor-core kernels gives up after its limit: a phase
+    that never completes sets bit 0 only (the completing one is not reported), in bounded
+    time, and the context stays usable afterwards."""
+    import torch
+    t0 = time.time()
+    assert flr.mbarrier_selftest(ctas=8, timeout_ns=20_000_000) == 1
+    assert time.time() - t0 < 10.0
+    x = torch.ones(16, device="cuda")
+    assert float((x * 2).sum().item()) == 32.0
+
+
 def test_per_pixel_batch_equals_per_frame(flr):
     import torch
     f = flr.FLR(q=8, radius=5, coef_radius=5)
