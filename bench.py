@@ -299,8 +299,9 @@ def flnr_inference_row(weights, dev_frames, torch, dev, timed, rows):
     rows["flnr_1080p"] = {"ms_per_frame": round(t_both, 4), "net_ms": round(t_net, 4), "flr_on_net_guides_ms": round(t_flr, 4),
                           "net_tflops": round(tflops, 2), "net_tensor_frac": round(tflops / peak, 4),
                           "net_macs_per_pixel": FLNR_MACS_PER_PIXEL,
-                          "what": "FLNR guide network (BF16 mma.sync implicit-GEMM convs, FP32 accumulation) + FP32 FLR "
-                                  "r=8 on its guides, 1920x1080; tensor fraction of measured dense bf16 peak"}
+                          "what": "FLNR guide network (BF16 tcgen05 implicit-GEMM convs with TMA-staged tiles, FP32 "
+                                  "accumulation in TMEM) + FP32 FLR r=8 on its guides, 1920x1080; tensor fraction of "
+                                  "measured dense bf16 peak"}
     f.close()
     net.close()
     return rows

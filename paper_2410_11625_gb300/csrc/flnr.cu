@@ -360,6 +360,79 @@ __device__ __forceinline__ bool mbar_wait_thread(uint32_t mbar, uint32_t parity)
     }
 }
 
+// Epilogue pieces shared by the tensor-core kernels.  tc_load_acc: one accumulator row (an
+// output pixel) from the warp's TMEM lane quarter, COUT columns from `taddr` on.
+template <int COUT>
+__device__ __forceinline__ void tc_load_acc(uint32_t taddr, float (&v)[COUT])
+{
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+        float q[16];
+        tmem_ld16(taddr + (uint32_t)c0, q);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[c0 + i] = q[i];
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+}
+
+// tc_store: bias, activation, optional ReLU mask, then bf16 NHWC stores (with the 2x2 pool of
+// the stored values when POOL: column pairs are lanes l, l ^ 1, row pairs lanes l, l ^ 8), or
+// sigmoid into planar fp32 (OUTM 1).  (n, yy, xx): the pixel; every lane of the warp calls it.
+template <int COUT, int ACT, int OUTM, bool MASK, bool POOL>
+__device__ __forceinline__ void tc_store(const ConvArgs &a, float (&v)[COUT], const float (&bias)[COUT], int n,
+                                         int yy, int xx, int lane)
+{
+    const bool in = yy < a.H && xx < a.W;
+    const size_t pix = ((size_t)n * a.H + yy) * a.W + xx;
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) {
+        v[c] += bias[c];
+        if (ACT == 1) v[c] = fmaxf(v[c], 0.f);
+    }
+    if (MASK && in) {
+#pragma unroll
+        for (int c8 = 0; c8 < COUT / 8; ++c8) {
+            const uint4 m = *reinterpret_cast<const uint4 *>(a.mask + pix * COUT + c8 * 8);
+            const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&m);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!(__bfloat162float(mh[i].x) > 0.f)) v[c8 * 8 + 2 * i] = 0.f;
+                if (!(__bfloat162float(mh[i].y) > 0.f)) v[c8 * 8 + 2 * i + 1] = 0.f;
+            }
+        }
+    }
+    if (OUTM == 0) {
+#pragma unroll
+        for (int c8 = 0; c8 < COUT / 8; ++c8) {
+            uint4 o;
+            __nv_bfloat162 *oh = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) oh[i] = __floats2bfloat162_rn(v[c8 * 8 + 2 * i], v[c8 * 8 + 2 * i + 1]);
+            if (in) *reinterpret_cast<uint4 *>(a.y + pix * a.ystride + c8 * 8) = o;
+            if (POOL) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float s0 = __bfloat162float(oh[i].x), s1 = __bfloat162float(oh[i].y);
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, 8);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, 8);
+                    oh[i] = __floats2bfloat162_rn(0.25f * s0, 0.25f * s1);
+                }
+                if (in && (lane & 9) == 0) {
+                    const size_t pp = ((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2;
+                    *reinterpret_cast<uint4 *>(a.yp + pp * COUT + c8 * 8) = o;
+                }
+            }
+        }
+    } else if (in) {
+        const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v[c]));
+    }
+}
+
 template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA, bool POOL>
 __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ TcArgs args)
 {
@@ -457,67 +530,9 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ Tc
     auto epilogue = [&](int j) {
         int n, ty0, tx0;
         tile_origin(j, n, ty0, tx0);
-        const int yy = ty0 + 4 * warp + (lane >> 3), xx = tx0 + (lane & 7);
-        const bool in = yy < a.H && xx < a.W;
-        const size_t pix = ((size_t)n * a.H + yy) * a.W + xx;
         float v[COUT];
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-            float q[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((j & 1) * COUT + c0), q);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[c0 + i] = q[i];
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-        asm volatile("tcgen05.fence::before_thread_sync;\n");
-#pragma unroll
-        for (int c = 0; c < COUT; ++c) {
-            v[c] += bias[c];
-            if (ACT == 1) v[c] = fmaxf(v[c], 0.f);
-        }
-        if (MASK && in) {
-#pragma unroll
-            for (int c8 = 0; c8 < COUT / 8; ++c8) {
-                const uint4 m = *reinterpret_cast<const uint4 *>(a.mask + pix * COUT + c8 * 8);
-                const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&m);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (!(__bfloat162float(mh[i].x) > 0.f)) v[c8 * 8 + 2 * i] = 0.f;
-                    if (!(__bfloat162float(mh[i].y) > 0.f)) v[c8 * 8 + 2 * i + 1] = 0.f;
-                }
-            }
-        }
-        if (OUTM == 0) {
-#pragma unroll
-            for (int c8 = 0; c8 < COUT / 8; ++c8) {
-                uint4 o;
-                __nv_bfloat162 *oh = reinterpret_cast<__nv_bfloat162 *>(&o);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) oh[i] = __floats2bfloat162_rn(v[c8 * 8 + 2 * i], v[c8 * 8 + 2 * i + 1]);
-                if (in) *reinterpret_cast<uint4 *>(a.y + pix * a.ystride + c8 * 8) = o;
-                if (POOL) {
-                    // 2x2 average of the stored values: column pairs are lanes l, l ^ 1, row
-                    // pairs lanes l, l ^ 8
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float s0 = __bfloat162float(oh[i].x), s1 = __bfloat162float(oh[i].y);
-                        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-                        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-                        s0 += __shfl_xor_sync(0xffffffffu, s0, 8);
-                        s1 += __shfl_xor_sync(0xffffffffu, s1, 8);
-                        oh[i] = __floats2bfloat162_rn(0.25f * s0, 0.25f * s1);
-                    }
-                    if (in && (lane & 9) == 0) {
-                        const size_t pp = ((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2;
-                        *reinterpret_cast<uint4 *>(a.yp + pp * COUT + c8 * 8) = o;
-                    }
-                }
-            }
-        } else if (in) {
-            const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v[c]));
-        }
+        tc_load_acc<COUT>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((j & 1) * COUT), v);
+        tc_store<COUT, ACT, OUTM, MASK, POOL>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7), lane);
     };
     auto fail = [&]() {
         atomicExch(&s_abort, 1);
@@ -570,6 +585,175 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ Tc
         for (int j = consumed; j < issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::COLS));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Warp-specialised tensor-core convolution (layers whose input is one tensor): no CTA-wide
+// barrier in the main loop.  Warp 4 (one lane) is the producer: it loads tile j into ring
+// stage j % NBUF with one TMA box copy per channel chunk once the MMAs of tile j - NBUF have
+// released the stage.  Warp 5 (one lane) issues tile j's MMAs into accumulator j & 1 once the
+// stage has landed and the epilogue has drained that accumulator, then commits them to the
+// stage's "empty" barrier and the accumulator's "full" barrier.  Warps 0-3 read the
+// accumulator rows of their TMEM lane quarter, release the accumulator, and run the epilogue.
+// The tile geometry and operand layouts are those of conv_tc_kernel.  Every wait is bounded.
+template <int CIN, int COUT, int KS>
+struct WsGeom {
+    static constexpr int TH = 16, TW = 8, P = KS / 2, SH = TH + 2 * P, SW = TW + 2 * P, C8 = CIN / 8;
+    static constexpr int NBUF = 4;
+    static constexpr int PS = (SH * SW * 16 + 127) / 128 * 128;
+    static constexpr int XBYTES = C8 * PS;
+    static constexpr int WBYTES = (KS * KS * C8 * COUT * 16 + 127) / 128 * 128;
+    static constexpr int TMA_BYTES = C8 * SH * SW * 16;
+    static constexpr int NBAR = 2 * NBUF + 4;  // full[NBUF], empty[NBUF], accf[2], acce[2]
+    static constexpr int SMEM = 128 + WBYTES + NBUF * XBYTES + NBAR * 8 + 16;
+    static constexpr int COLS = tmem_cols<2 * COUT>();
+};
+constexpr int kWsThreads = 192;
+
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool POOL>
+__global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_constant__ TcArgs args)
+{
+    using G = WsGeom<CIN, COUT, KS>;
+    constexpr int TH = G::TH, TW = G::TW, P = G::P, SW = G::SW, C8 = G::C8, NBUF = G::NBUF, PS = G::PS;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && 2 * COUT <= 256, "UMMA shape");
+    const ConvArgs &a = args.c;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    unsigned char *sw = base;
+    unsigned char *sx0 = base + G::WBYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sx0 + NBUF * G::XBYTES);
+    uint64_t *empty = full + NBUF, *accf = empty + NBUF, *acce = accf + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
+    __shared__ int s_issued, s_consumed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
+    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
+    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(G::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(empty + i)));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(accf + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(acce + i)));  // 4 epilogue warps
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.tm)) : "memory");
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    for (int i = tid; i < KS * KS * COUT * C8; i += kWsThreads) {
+        const int c8 = i % C8, row = i / C8, tap = row / COUT, co = row % COUT;
+        cp_async16(sw + ((tap * C8 + c8) * COUT + co) * 16, a.w + (size_t)row * CIN + c8 * 8, true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n");  // weights visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = *tslot;
+    auto fail = [&]() {
+        if (a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
+    };
+    auto origin = [&](int j, int &n, int &ty0, int &tx0) {
+        const int t = blockIdx.x + j * gridDim.x;
+        n = t / per_img;
+        const int r = t % per_img;
+        ty0 = (r / tiles_x) * TH;
+        tx0 = (r % tiles_x) * TW;
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {  // producer
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF;
+                if (j >= NBUF && !mbar_wait_thread(smem_u32(empty + st), (uint32_t)((j / NBUF - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                int n, ty0, tx0;
+                origin(j, n, ty0, tx0);
+                const uint32_t bar = smem_u32(full + st);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(G::TMA_BYTES) : "memory");
+                const uint32_t dst = smem_u32(sx0 + st * G::XBYTES);
+#pragma unroll
+                for (int k = 0; k < C8; ++k) tma_load_4d(dst + k * PS, &args.tm, k * 8, tx0 - P, ty0 - P, n, bar);
+                s_issued = j + 1;
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = umma_idesc(COUT);
+            const uint64_t adesc0 = umma_sdesc(smem_u32(sx0), PS, SW * 16);
+            const uint64_t bdesc0 = umma_sdesc(smem_u32(sw), COUT * 16, 128);
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF, acc = j & 1;
+                if (!mbar_wait_thread(smem_u32(full + st), (uint32_t)((j / NBUF) & 1))) {
+                    fail();
+                    break;
+                }
+                s_consumed = j + 1;
+                if (j >= 2 && !mbar_wait_thread(smem_u32(acce + acc), (uint32_t)((j / 2 - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                const uint64_t ab = adesc0 + (uint64_t)((st * G::XBYTES) >> 4);
+                const uint32_t d = tmem + (uint32_t)(acc * COUT);
+#pragma unroll
+                for (int tap = 0; tap < KS * KS; ++tap) {
+#pragma unroll
+                    for (int kk = 0; kk < C8 / 2; ++kk) {
+                        const uint32_t aoff = (uint32_t)((2 * kk * PS + ((tap / KS) * SW + tap % KS) * 16) >> 4);
+                        const uint32_t boff = (uint32_t)(((tap * C8 + 2 * kk) * COUT * 16) >> 4);
+                        umma_bf16(d, ab + aoff, bdesc0 + boff, idesc, (tap | kk) ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(empty + st)));
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(accf + acc)));
+            }
+        }
+    } else {  // epilogue warps 0-3: TMEM lane quarter = warp
+        float bias[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bias[c] = c < a.nbias ? a.bias[c] : 0.f;
+        for (int j = 0; j < mine; ++j) {
+            const int acc = j & 1;
+            if (!mbar_wait_warp(smem_u32(accf + acc), (uint32_t)((j / 2) & 1))) {
+                if (lane == 0) fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            float v[COUT];
+            tc_load_acc<COUT>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * COUT), v);
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
+            int n, ty0, tx0;
+            origin(j, n, ty0, tx0);
+            tc_store<COUT, ACT, OUTM, false, POOL>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7), lane);
+        }
+    }
+    __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (tid == 4 * 32) {  // after a failure: let copies still in flight land before the CTA exits
+        for (int j = s_consumed; j < s_issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
+    }
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n");
@@ -911,13 +1095,16 @@ cudaError_t conv_tc_launch(const ConvArgs &a, cudaStream_t st)
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        // the whole unified L1 / shared array as shared memory, so the residency below holds
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
         cudaFuncAttributes fa;
         if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-        const int by_regs = 65536 / (regs_per_warp * 4);
+        const int by_regs = (4 * (16384 / regs_per_warp)) / 4;  // four warps, one per sub-partition
         const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
         int r = kThreadsPerSm / 128;
         r = r < by_regs ? r : by_regs;
@@ -936,6 +1123,51 @@ cudaError_t conv_tc_launch(const ConvArgs &a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const long long cap = (long long)per_sm * n_sm;
     kern<<<(int)(ntiles < cap ? ntiles : cap), 128, smem, st>>>(ta);
+    return cudaGetLastError();
+}
+
+// Launch of the warp-specialised convolution; residency computed as for conv_tc_launch.
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool POOL = false>
+cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
+{
+    using G = WsGeom<CIN, COUT, KS>;
+    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreadsPerSm = 2048;
+    constexpr int tmem_cap = 512 / G::COLS;
+    constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
+    constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
+    static_assert(smem <= 227 * 1024, "warp-specialised conv tile does not fit in shared memory");
+    auto kern = conv_ws_kernel<CIN, COUT, KS, ACT, OUTM, POOL>;
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        // registers are split over the SM's four sub-partitions: warps per sub-partition first
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = (4 * (16384 / regs_per_warp)) / (kWsThreads / 32);
+        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
+        int r = kThreadsPerSm / kWsThreads;
+        r = r < by_regs ? r : by_regs;
+        r = r < by_smem ? r : by_smem;
+        r = r < tmem_cap ? r : tmem_cap;
+        if (r < 1) return cudaErrorInvalidConfiguration;
+        per_sm = r;
+    }
+    const long long ntiles = (long long)a.N * ((a.H + G::TH - 1) / G::TH) * ((a.W + G::TW - 1) / G::TW);
+    if (ntiles <= 0) return cudaSuccess;
+    TcArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.c = a;
+    cudaError_t e = make_tmap(&ta.tm, a.x, CIN, a.W, a.H, a.N, G::SW, G::SH);
+    if (e != cudaSuccess) return e;
+    const long long cap = (long long)per_sm * n_sm;
+    kern<<<(int)(ntiles < cap ? ntiles : cap), kWsThreads, smem, st>>>(ta);
     return cudaGetLastError();
 }
 
@@ -1127,29 +1359,29 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
         return c;
     };
     ConvArgs c;
-    FLNR_TRY((conv_tc_launch<16, 16, 3, 1, 0, false>(conv(n->x0, 0, n->a0, H, W), st)));
+    FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->x0, 0, n->a0, H, W), st)));
     c = conv(n->a0, 1, n->f0, H, W);
     c.yp = n->p0;  // 2x2 average pool of f0 for the encoder
-    FLNR_TRY((conv_tc_launch<16, 16, 1, 1, 0, false, 0, true>(c, st)));
-    FLNR_TRY((conv_tc_launch<16, 32, 3, 1, 0, false>(conv(n->p0, 2, n->a1, H2, W2), st)));
+    FLNR_TRY((conv_ws_launch<16, 16, 1, 1, 0, true>(c, st)));
+    FLNR_TRY((conv_ws_launch<16, 32, 3, 1, 0>(conv(n->p0, 2, n->a1, H2, W2), st)));
     c = conv(n->a1, 3, n->f1, H2, W2);
     c.yp = n->p1;
-    FLNR_TRY((conv_tc_launch<32, 32, 3, 1, 0, false, 0, true>(c, st)));
-    FLNR_TRY((conv_tc_launch<32, 64, 3, 1, 0, false>(conv(n->p1, 4, n->a2, H4, W4), st)));
-    FLNR_TRY((conv_tc_launch<64, 64, 3, 1, 0, false>(conv(n->a2, 5, n->f2, H4, W4), st)));
+    FLNR_TRY((conv_ws_launch<32, 32, 3, 1, 0, true>(c, st)));
+    FLNR_TRY((conv_ws_launch<32, 64, 3, 1, 0>(conv(n->p1, 4, n->a2, H4, W4), st)));
+    FLNR_TRY((conv_ws_launch<64, 64, 3, 1, 0>(conv(n->a2, 5, n->f2, H4, W4), st)));
     c = conv(n->f2, 6, n->a3, H2, W2);  // input up(f2) ++ f1, formed while staging
     c.x2 = n->f1;
     FLNR_TRY((conv_tc_launch<96, 32, 3, 1, 0, false, 64>(c, st)));
-    FLNR_TRY((conv_tc_launch<32, 32, 3, 1, 0, false>(conv(n->a3, 7, n->d1, H2, W2), st)));
+    FLNR_TRY((conv_ws_launch<32, 32, 3, 1, 0>(conv(n->a3, 7, n->d1, H2, W2), st)));
     c = conv(n->d1, 8, n->a4, H, W);  // input up(d1) ++ f0
     c.x2 = n->f0;
     FLNR_TRY((conv_tc_launch<48, 16, 3, 1, 0, false, 32>(c, st)));
-    FLNR_TRY((conv_tc_launch<16, 16, 3, 1, 0, false>(conv(n->a4, 9, n->d0, H, W), st)));
-    FLNR_TRY((conv_tc_launch<16, 16, 3, 1, 0, false>(conv(n->d0, 10, n->a5, H, W), st)));
+    FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->a4, 9, n->d0, H, W), st)));
+    FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->d0, 10, n->a5, H, W), st)));
     float *yf = guide_out ? guide_out : n->out;
     c = conv(n->a5, 11, nullptr, H, W);
     c.yf = yf;
-    FLNR_TRY((conv_tc_launch<16, 16, 1, 2, 1, false>(c, st)));
+    FLNR_TRY((conv_ws_launch<16, 16, 1, 2, 1>(c, st)));
     if (guide_out)
         FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return FLR_OK;
@@ -1250,7 +1482,7 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
         c.status = n->status;
         if constexpr (HEAD) {
             c.yf = (float *)out;
-            FLNR_TRY((conv_tc_launch<CI, CO, KS, 2, 1, false>(c, st)));
+            FLNR_TRY((conv_ws_launch<CI, CO, KS, 2, 1>(c, st)));
         } else {
             c.y = (bf *)out;
             if constexpr (CA > 0) {
@@ -1265,11 +1497,11 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
                 if (out2) {
                     if ((H | W) & 1) return FLR_ERR_ARG;
                     c.yp = (bf *)out2;
-                    FLNR_TRY((conv_tc_launch<CI, CO, KS, 1, 0, false, 0, true>(c, st)));
+                    FLNR_TRY((conv_ws_launch<CI, CO, KS, 1, 0, true>(c, st)));
                     return FLR_OK;
                 }
             }
-            FLNR_TRY((conv_tc_launch<CI, CO, KS, 1, 0, false>(c, st)));
+            FLNR_TRY((conv_ws_launch<CI, CO, KS, 1, 0>(c, st)));
         }
     } else if (op == FLNR_OP_DGRAD) {
         if (mask)

@@ -218,6 +218,10 @@ cudaError_t launch_apply_fast(const FastArgs &a, cudaStream_t st)
             const size_t smem = apply_tma_smem<Q>();
             cudaError_t e = cudaFuncSetAttribute(apply_tma_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
+            // three CTAs per SM need the whole unified L1 / shared array as shared memory
+            e = cudaFuncSetAttribute(apply_tma_kernel<Q>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return e;
             const int nitems = (a.Hb + 1) * ((a.Wo + kFW - 1) / kFW);
             const int grid = nitems < 3 * fast_n_sm() ? nitems : 3 * fast_n_sm();  // three CTAs per SM
             apply_tma_kernel<Q><<<grid, kFW, smem, st>>>(k);
