@@ -128,9 +128,16 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
 
 /*
  * The same pass on HOST images: copies guide, map_guide (if not NULL) and radiance to
- * handle-owned device staging, runs flr_denoise, copies the result back to `out`, and
- * waits for the stream.  Page-locked host memory gives asynchronous copies; pageable
- * memory works but is slower.  Errors as flr_denoise.
+ * handle-owned device staging, runs the FLR kernels, copies the result back to `out`, and
+ * waits.  Frames of 540 rows or more are processed in row bands of about 360 rows (at
+ * most 8; three at 1080 rows) so that the copies overlap the kernels: band k + 1 is copied in on a handle-owned stream while
+ * band k's kernels run on `stream`, and band k's output is copied out on a second handle-
+ * owned stream while band k + 1 runs (the copies start after the work already queued on
+ * `stream`).  The bands choose their own segment heights and sample the frame reference
+ * from the first band, so the result equals flr_denoise's to FP32 rounding (not bit for
+ * bit; both meet the same bar against an FP64 solve); smaller frames run exactly
+ * flr_denoise.  Page-locked host memory gives asynchronous copies; pageable memory works
+ * but is slower.  Errors as flr_denoise.
  */
 int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
                      const float *radiance, float *out, int H, int W, void *stream);

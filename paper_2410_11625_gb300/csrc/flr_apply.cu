@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const __grid_co
     uint64_t *bar = reinterpret_cast<uint64_t *>(Hb + ((g.THh * g.HS + 1) & ~1));  // [2] TMA arrivals
     __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx0 = blockIdx.x * kAW, ty0 = blockIdx.y * kAH;
+    const int row_hi = a.row_hi < 0 ? H : min(a.row_hi, H);
+    const int tx0 = blockIdx.x * kAW, ty0 = a.row_lo + blockIdx.y * kAH;
     const int x = tid % kAW, run = tid / kAW;
     const int gx = tx0 + x;
     const size_t plane = (size_t)H * W;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const __grid_co
 #pragma unroll
         for (int t = 0; t < kARun; ++t) {
             const int gy = ty0 + run * kARun + t;
-            if (gy < H) {
+            if (gy < row_hi) {
                 const float ny = (float)(min(gy + rc, H - 1) - max(gy - rc, 0) + 1);
                 const float inv_m = 1.0f / (nx * ny);
 #pragma unroll
@@ -281,7 +282,9 @@ cudaError_t launch_apply_qr(const ApplyArgs &a, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(flr_apply_kernel<Q, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.W + kAW - 1) / kAW, (a.H + kAH - 1) / kAH);
+    const int rows = (a.row_hi < 0 ? a.H : a.row_hi) - a.row_lo;
+    if (rows <= 0) return cudaSuccess;
+    dim3 grid((a.W + kAW - 1) / kAW, (rows + kAH - 1) / kAH);
     ApplyKArgs ka;
     std::memset(&ka, 0, sizeof(ka));
     ka.a = a;

@@ -43,9 +43,11 @@ __global__ void __launch_bounds__(kDThreads) flr_fp64_kernel(const Fp64Args a)
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
     const unsigned long long cnt = *a.flag_count;
     const int n = (int)(cnt < (unsigned long long)a.flag_cap ? cnt : (unsigned long long)a.flag_cap);
+    const unsigned long long st0 = a.flag_start ? *a.flag_start : 0ull;
+    const int start = (int)(st0 < (unsigned long long)n ? st0 : (unsigned long long)n);
     const int H = a.H, W = a.W, r = a.r;
     const size_t plane = (size_t)H * W;
-    for (int e = gw; e < n; e += nw) {
+    for (int e = start + gw; e < n; e += nw) {
         const int idx = a.flag_list[e];
         const int y = idx / W, x = idx % W;
         const int ylo = max(0, y - r), yhi = min(H - 1, y + r);

@@ -385,8 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
     const int r = RT >= 0 ? RT : a.r;
     const FwdGeom gm(r, RT >= 0);
     const int x0 = blockIdx.x * kTW;
-    const int y0 = blockIdx.y * a.TH;
-    const int y1 = min(y0 + a.TH, H);
+    const int row_hi = a.row_hi < 0 ? H : min(a.row_hi, H);
+    const int y0 = a.row_lo + blockIdx.y * a.TH;
+    const int y1 = min(y0 + a.TH, row_hi);
+    const int ref_rows = a.ref_rows > 0 ? min(a.ref_rows, H) : H;
     const int nColWarps = (gm.Wi + 31) >> 5;
     float *base = smem + (((128 - (tma::smem_addr(smem) & 127)) & 127) >> 2);  // 128-byte aligned
     float *Vbuf = base;                                              // [kB][NCH][VS]  window sums
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
 
     // reference shifts (overlaps the first copies)
     if (warp == 0) {
-        sample_mean<Q>(s_ref, a.guide, a.rad, H, W, 0, H, 0, W, lane);
+        sample_mean<Q>(s_ref, a.guide, a.rad, H, W, 0, ref_rows, 0, W, lane);
     } else if (warp == 1) {
         sample_mean<Q>(s_cta, a.guide, a.rad, H, W, max(0, y0 - r), min(H, y1 + r), max(0, x0 - r),
                        min(W, x0 + kTW + r), lane);

@@ -183,6 +183,58 @@ def test_deterministic_and_host_path_matches(flr):
     assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("H,W,rc,kind,map_kind,pivot", [
+    (600, 200, 8, "rendered", None, 1e-3), (600, 200, 0, "uniform", None, 1e-3),
+    (600, 200, 6, "rendered", "perturbed", 1e-3), (600, 200, 4, "rendered", None, 1.0),
+    (600, 200, 0, "uniform", None, 1.0), (1100, 96, 8, "rendered", None, 1e-3),
+    (1100, 96, 3, "uniform", None, 1.0),
+])
+def test_banded_host_path_matches_oracle(flr, H, W, rc, kind, map_kind, pivot):
+    """Frames of 540 rows or more take the banded host path (two bands at 600 rows, three
+    at 1100): the copies of row bands
+    overlap the kernels, each band has its own segment height and the frame reference is
+    sampled from the first band.  Only the shifts change, so it meets the same parity bar
+    against the FP64 oracle as the device path.  pivot = 1 flags every pixel, so every
+    band's FP64 re-solve must pick up exactly its own flags (with rc = 0 the output is the
+    FP64 solve itself: 2e-6; with rc > 0 its models are averaged in FP32: the parity bar)."""
+    import torch
+    g, y = synth.render(5, H, W) if kind == "rendered" else synth.random_frame(30 + rc, H, W, 8)
+    z = None
+    if map_kind == "perturbed":  # the models applied to a second guide set at the same pixels
+        z = (g + synth.random_frame(9, H, W, 8)[0] * 0.05).astype(np.float32)
+    ref = oracle.flr_forward(g, y, 8, 1e-3, coef_radius=rc, map_guide=z)
+    f = flr.FLR(q=8, radius=8, coef_radius=rc, eps=1e-3, pivot_ratio=pivot)
+    dev = f.denoise(to_dev(g), to_dev(y), map_guide=None if z is None else to_dev(z)).cpu().numpy()
+    n_dev = f.stats()["flagged"]
+    host = f.denoise_host(g, y, map_guide=z)
+    st = f.stats()
+    torch.cuda.synchronize()
+    f.close()
+    assert np.all(np.isfinite(host))
+    for got in (dev, host):
+        if pivot >= 1.0 and rc == 0:  # FP64 results written directly
+            assert rel_err(got, ref) <= 2e-6
+        elif z is not None:  # the bar of test_separate_map_guide_rendered
+            assert np.max(np.abs(got - ref)) <= 1e-4 * np.sqrt(np.mean(ref ** 2))
+        else:
+            assert rel_err(got, ref) <= TOL
+    if pivot >= 1.0:
+        assert n_dev == H * W and st["flagged"] == H * W and st["resolved"] == H * W
+
+
+def test_rendered_unaveraged_with_tighter_pivot(flr):
+    """rc = 0 on rendered scene 5 (600x200, r = 8): with pivot_ratio 1e-3 nothing is flagged
+    and a few pixels reach 2.7e-4 against the oracle (windows whose mean lies far from the
+    CTA reference compared with their spread lose FP32 precision in the moments, which
+    the pivot ratio does not see).  pivot_ratio 0.03 re-solves those windows in FP64 and
+    the frame meets the parity bar."""
+    g, y = synth.render(5, 600, 200)
+    ref = oracle.flr_forward(g, y, 8, 1e-3, coef_radius=0)
+    got, st = run_gpu(flr, g, y, 8, 0, 1e-3, pivot_ratio=0.03, stats=True)
+    assert st["flagged"] > 0 and st["resolved"] == st["flagged"]
+    assert rel_err(got, ref) <= TOL
+
+
 def test_misaligned_pointer_is_rejected(flr):
     import torch
     g, y = synth.random_frame(1, 16, 16, 8)
