@@ -1,7 +1,8 @@
 // flnr.cu -- the FLNR guide network (Sec. 3.3) on sm_103a: BF16 implicit-GEMM convolutions
-// on the tensor cores (mma.sync m16n8k16, FP32 accumulation), its backward pass (dgrad as a
-// convolution with rotated, transposed weights; wgrad as a per-tap GEMM over pixels),
-// Adam on FP32 master weights, and the flnr_* entry points of include/flr.h.
+// with FP32 accumulation -- the forward pass on the fifth-generation tensor cores (tcgen05,
+// TMA-staged tiles, accumulators in tensor memory), the backward pass with mma.sync m16n8k16
+// (dgrad as a convolution with rotated, transposed weights; wgrad as a per-tap GEMM over
+// pixels) -- Adam on FP32 master weights, and the flnr_* entry points of include/flr.h.
 //
 // Network (weights and order as oracle/flnr_ref.py): 11 inputs (8 guides + noisy RGB)
 //   in0 3x3 11->16 ReLU, in1 1x1 16->16 ReLU                                   f0 (H)
@@ -235,10 +236,10 @@ __global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
 // (ky, kx) of chunk 2kk: 8-row groups (output rows) SW * 16 bytes apart, the two K halves
 // (chunks 2kk, 2kk + 1) SH * SW * 16 bytes apart.  No im2col copy is made.  The weights are
 // staged once per CTA as [tap][c8][COUT][8]: operand B (COUT x 16, K-major) has 8-row groups
-// 128 bytes apart and K halves COUT * 16 bytes apart.  Thread 0 issues the taps x CIN/16 MMAs
-// of a tile and commits them to an mbarrier; the four warps then read the accumulator rows of
+// 128 bytes apart and K halves COUT * 16 bytes apart.  One thread issues the taps x CIN/16
+// MMAs of a tile and commits them to an mbarrier; four warps then read the accumulator rows of
 // their TMEM lane quarter (one output pixel per thread) and run the epilogue, while the next
-// tile's input is already loading.  Every wait is bounded by the global timer.
+// tiles' inputs are already loading.  Every wait is bounded by the global timer.
 #define FLNR_STATUS_TIMEOUT 1
 constexpr unsigned long long kTcTimeoutNs = 1000000000ull;  // 1 s per wait
 
@@ -314,19 +315,6 @@ constexpr int tmem_cols()
 {
     return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
 }
-
-template <int CIN, int COUT, int KS, int CA>
-struct TcGeom {
-    static constexpr int TH = 16, TW = 8, P = KS / 2, SH = TH + 2 * P, SW = TW + 2 * P, C8 = CIN / 8;
-    static constexpr int NBUF = 3;                                // input ring: tiles i, i + 1, i + 2
-    static constexpr int PS = (SH * SW * 16 + 127) / 128 * 128;   // one channel-chunk plane [SH][SW][8]
-    static constexpr int XBYTES = C8 * PS;                        // one input buffer
-    static constexpr int WBYTES = (KS * KS * C8 * COUT * 16 + 127) / 128 * 128;
-    static constexpr int TMA_C8 = (CIN - CA) / 8;                 // chunks loaded by TMA (the rest: upsampled)
-    static constexpr int TMA_BYTES = TMA_C8 * SH * SW * 16;
-    static constexpr int SMEM = 128 + WBYTES + NBUF * XBYTES + 64;  // alignment slack, mbarriers, TMEM slot
-    static constexpr int COLS = tmem_cols<2 * COUT>();            // two accumulators of COUT columns
-};
 
 // Kernel parameters: the tensor map (4-D: channels, W, H, N) of the operand that TMA stages
 // (x, or the skip x2 of a decoder layer) and the convolution arguments.
@@ -433,165 +421,6 @@ __device__ __forceinline__ void tc_store(const ConvArgs &a, float (&v)[COUT], co
     }
 }
 
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA, bool POOL>
-__global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ TcArgs args)
-{
-    using G = TcGeom<CIN, COUT, KS, CA>;
-    constexpr int TH = G::TH, TW = G::TW, P = G::P, SH = G::SH, SW = G::SW, C8 = G::C8, NBUF = G::NBUF, PS = G::PS;
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && 2 * COUT <= 256, "UMMA shape");
-    const ConvArgs &a = args.c;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    unsigned char *sw = base;                        // weights [tap][c8][COUT][8]
-    unsigned char *sx0 = base + G::WBYTES;           // NBUF input buffers of C8 planes [SH][SW][8]
-    uint64_t *full = reinterpret_cast<uint64_t *>(sx0 + NBUF * G::XBYTES);  // [NBUF] TMA arrivals
-    uint64_t *mmab = full + NBUF;                                           // [2] MMA completion
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mmab + 2);
-    __shared__ int s_abort;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
-    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
-    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // tiles of this CTA
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                     "r"(G::COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-    }
-    if (tid == 0) {
-        for (int i = 0; i < NBUF + 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
-        asm volatile("fence.mbarrier_init.release.cluster;\n");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.tm)) : "memory");
-        s_abort = 0;
-    }
-    // weights: global [tap][COUT][CIN] -> shared [tap][c8][COUT][8]
-    for (int i = tid; i < KS * KS * COUT * C8; i += 128) {
-        const int c8 = i % C8, row = i / C8, tap = row / COUT, co = row % COUT;
-        cp_async16(sw + ((tap * C8 + c8) * COUT + co) * 16, a.w + (size_t)row * CIN + c8 * 8, true);
-    }
-    auto tile_origin = [&](int j, int &n, int &ty0, int &tx0) {
-        const int t = blockIdx.x + j * gridDim.x;
-        n = t / per_img;
-        const int r = t % per_img;
-        ty0 = (r / tiles_x) * TH;
-        tx0 = (r % tiles_x) * TW;
-    };
-    // TMA part of tile j (thread 0): one 4-D box (8 channels, SW, SH, 1) per channel chunk;
-    // the halo outside the image is zero-filled by the copy engine
-    auto stage_tma = [&](int j) {
-        if (j >= mine) return;
-        int n, ty0, tx0;
-        tile_origin(j, n, ty0, tx0);
-        const uint32_t bar = smem_u32(full + j % NBUF);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(G::TMA_BYTES) : "memory");
-        const uint32_t dst = smem_u32(sx0 + (j % NBUF) * G::XBYTES);
-#pragma unroll
-        for (int k = 0; k < G::TMA_C8; ++k)
-            tma_load_4d(dst + (CA / 8 + k) * PS, &args.tm, k * 8, tx0 - P, ty0 - P, n, bar);
-    };
-    // upsampled part of a decoder input (CA > 0, all threads): nearest 2x of x [N][H/2][W/2][CA]
-    auto stage_up = [&](int j) {
-        if (CA == 0 || j >= mine) return;
-        int n, ty0, tx0;
-        tile_origin(j, n, ty0, tx0);
-        constexpr int CA8 = CA > 0 ? CA / 8 : 1;
-        unsigned char *sx = sx0 + (j % NBUF) * G::XBYTES;
-        for (int i = tid; i < SH * SW * CA8; i += 128) {
-            const int pix = i / CA8, c8 = i % CA8;
-            const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
-            const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const bf16 *src = in ? a.x + (((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2) * CA + c8 * 8 : a.x;
-            cp_async16(sx + c8 * PS + pix * 16, src, in);
-        }
-    };
-    __syncthreads();  // barriers initialised before the first TMA arrives on them
-    if (tid == 0) {
-        stage_tma(0);
-        stage_tma(1);
-    }
-    stage_up(0);
-    cp_async_commit();  // group: weights + upsampled part of tile 0
-    stage_up(1);
-    cp_async_commit();
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    const uint32_t tmem = *tslot;
-    const uint32_t mmab_a = smem_u32(mmab);
-    constexpr uint32_t idesc = umma_idesc(COUT);
-    const uint64_t adesc0 = umma_sdesc(smem_u32(sx0), PS, SW * 16);
-    const uint64_t bdesc0 = umma_sdesc(smem_u32(sw), COUT * 16, 128);
-    float bias[COUT];
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) bias[c] = c < a.nbias ? a.bias[c] : 0.f;
-
-    // epilogue of this CTA's j-th tile from accumulator j & 1: thread (warp w, lane l) owns
-    // accumulator row 32w + l = pixel (4w + l / 8, l % 8) of the tile
-    auto epilogue = [&](int j) {
-        int n, ty0, tx0;
-        tile_origin(j, n, ty0, tx0);
-        float v[COUT];
-        tc_load_acc<COUT>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((j & 1) * COUT), v);
-        tc_store<COUT, ACT, OUTM, MASK, POOL>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7), lane);
-    };
-    auto fail = [&]() {
-        atomicExch(&s_abort, 1);
-        if (a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
-    };
-    auto wait_mma = [&](int j) {  // MMAs of tile j complete (bounded)
-        if (!mbar_wait_warp(mmab_a + 8 * (j & 1), (uint32_t)((j >> 1) & 1)) && lane == 0) fail();
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-    };
-
-    // software pipeline: the MMAs of tile j run while tile j - 1's epilogue runs and tiles
-    // j + 1 and j + 2 load
-    int consumed = 0;  // tiles whose TMA arrival thread 0 has waited for
-    for (int j = 0; j < mine; ++j) {
-        cp_async_wait<1>();  // all groups but the newest: weights and tile j's upsampled part
-        asm volatile("fence.proxy.async.shared::cta;\n");  // thread-written bytes visible to the tensor core
-        __syncthreads();
-        if (s_abort) break;
-        if (tid == 0) {
-            if (!mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1))) fail();
-            consumed = j + 1;
-            asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint64_t ab = adesc0 + (uint64_t)(((j % NBUF) * G::XBYTES) >> 4);
-            const uint32_t d = tmem + (uint32_t)((j & 1) * COUT);
-#pragma unroll
-            for (int tap = 0; tap < KS * KS; ++tap) {
-#pragma unroll
-                for (int kk = 0; kk < C8 / 2; ++kk) {
-                    const uint32_t aoff = (uint32_t)((2 * kk * PS + ((tap / KS) * SW + tap % KS) * 16) >> 4);
-                    const uint32_t boff = (uint32_t)(((tap * C8 + 2 * kk) * COUT * 16) >> 4);
-                    umma_bf16(d, ab + aoff, bdesc0 + boff, idesc, (tap | kk) ? 1u : 0u);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                mmab_a + 8 * (j & 1)));
-        }
-        if (j >= 1) wait_mma(j - 1);  // frees tile j - 1's input buffer and accumulator
-        if (tid == 0) stage_tma(j + 2);  // into the buffer tile j - 1 used
-        stage_up(j + 2);
-        cp_async_commit();
-        if (j >= 1) epilogue(j - 1);
-    }
-    if (mine > 0 && !s_abort) {
-        wait_mma(mine - 1);
-        epilogue(mine - 1);
-    }
-    cp_async_wait<0>();
-    if (tid == 0) {  // after an abort: let the TMA loads still in flight land before the CTA exits
-        const int issued = mine < consumed + 2 ? mine : consumed + 2;
-        for (int j = consumed; j < issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::COLS));
-    }
-}
-
 // ---------------------------------------------------------------------------------------
 // Warp-specialised tensor-core convolution (layers whose input is one tensor): no CTA-wide
 // barrier in the main loop.  Warp 4 (one lane) is the producer: it loads tile j into ring
@@ -600,7 +429,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ Tc
 // stage has landed and the epilogue has drained that accumulator, then commits them to the
 // stage's "empty" barrier and the accumulator's "full" barrier.  Warps 0-3 read the
 // accumulator rows of their TMEM lane quarter, release the accumulator, and run the epilogue.
-// The tile geometry and operand layouts are those of conv_tc_kernel.  Every wait is bounded.
+// The tile geometry and operand layouts are those described above.  Every wait is bounded.
 template <int CIN, int COUT, int KS>
 struct WsGeom {
     static constexpr int TH = 16, TW = 8, P = KS / 2, SH = TH + 2 * P, SW = TW + 2 * P, C8 = CIN / 8;
@@ -746,6 +575,226 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_consta
             int n, ty0, tx0;
             origin(j, n, ty0, tx0);
             tc_store<COUT, ACT, OUTM, false, POOL>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7), lane);
+        }
+    }
+    __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (tid == 4 * 32) {  // after a failure: let copies still in flight land before the CTA exits
+        for (int j = s_consumed; j < s_issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::COLS));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Decoder convolution (3x3, ReLU) on up2(lo) ++ skip without forming the upsampled map.
+// A stage covers 32 x 16 output pixels: a 16 x 8 block of low-resolution positions (i0 + g,
+// j0 + r) and its four parity classes (a, b), output pixel (2(i0 + g) + a, 2(j0 + r) + b),
+// one 128-row accumulator per class (row 8g + r).  For tap (dy, dx), t = a + dy - 1 and
+// u = b + dx - 1, every pixel of class (a, b) reads the low-resolution map at
+// (i0 + g + t/2, j0 + r + u/2) (floor division) and the skip at full-resolution pixel
+// (2(i0 + g + t/2) + (t mod 2), 2(j0 + r + u/2) + (u mod 2)).  Rows of a class step by one
+// low-resolution position in both operands, so both are plain K-major tiles:
+//   lo    CA/8 planes [18][10][8] (rows i0 - 1 .. i0 + 16, columns j0 - 1 .. j0 + 8), one TMA
+//         box copy each;
+//   skip  its four parity planes (a', b') x CB/8 chunks [18][10][8] (rows i0 - 1 .. i0 + 16
+//         of row parity a', columns j0 - 1 .. j0 + 8 of column parity b'), one TMA box copy
+//         each from a 5-D view (channels of a column pair, column pairs, row parity, row
+//         pairs, images) in which the start channel b' * CB + 8k selects the column parity.
+// The products are those of the convolution on the concatenated map; only their order of
+// accumulation differs.  Roles and waits as conv_ws_kernel; the MMA lane issues the four
+// classes of a stage into one of two accumulator sets (4 * COUT columns each).
+template <int CA, int CB, int COUT, int NBUF>
+struct UpGeom {
+    static constexpr int SH = 18, SW = 10;                       // staged rows and columns
+    static constexpr int PS = (SH * SW * 16 + 127) / 128 * 128;  // one chunk plane [SH][SW][8]
+    static constexpr int CA8 = CA / 8, CB8 = CB / 8, C8 = CA8 + CB8;
+    static constexpr int PLANES = CA8 + 4 * CB8;                 // lo chunks, then skip (a', b', chunk)
+    static constexpr int XBYTES = PLANES * PS;
+    static constexpr int TMA_BYTES = PLANES * SH * SW * 16;
+    static constexpr int WBYTES = (9 * C8 * COUT * 16 + 127) / 128 * 128;
+    static constexpr int NBAR = 2 * NBUF + 4;
+    static constexpr int SMEM = 128 + WBYTES + NBUF * XBYTES + NBAR * 8 + 16;
+    static constexpr int COLS = tmem_cols<8 * COUT>();          // two sets of four class accumulators
+};
+
+struct alignas(128) UpArgs {
+    CUtensorMap tlo, tskip;
+    ConvArgs c;  // x = lo [N][H/2][W/2][CA], x2 = skip [N][H][W][CB], H and W even
+};
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+        : "memory");
+}
+
+template <int CA, int CB, int COUT, int NBUF>
+__global__ void __launch_bounds__(kWsThreads) conv_up_kernel(const __grid_constant__ UpArgs args)
+{
+    using G = UpGeom<CA, CB, COUT, NBUF>;
+    constexpr int PS = G::PS, SW = G::SW, CA8 = G::CA8, CB8 = G::CB8, C8 = G::C8;
+    static_assert(CA % 16 == 0 && CB % 16 == 0 && COUT % 16 == 0 && 8 * COUT <= 256, "UMMA shape");
+    const ConvArgs &a = args.c;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    unsigned char *sw = base;
+    unsigned char *sx0 = base + G::WBYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sx0 + NBUF * G::XBYTES);
+    uint64_t *empty = full + NBUF, *accf = empty + NBUF, *acce = accf + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
+    __shared__ int s_issued, s_consumed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int HL = a.H / 2, WL = a.W / 2;
+    const int tiles_x = (WL + 7) / 8, tiles_y = (HL + 15) / 16;
+    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
+    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(G::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(empty + i)));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(accf + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(acce + i)));  // 4 epilogue warps
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.tlo)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.tskip)) : "memory");
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    // weights: global [tap][COUT][CA + CB] -> shared [tap][c8][COUT][8] (lo chunks first)
+    for (int i = tid; i < 9 * COUT * C8; i += kWsThreads) {
+        const int c8 = i % C8, row = i / C8, tap = row / COUT, co = row % COUT;
+        cp_async16(sw + ((tap * C8 + c8) * COUT + co) * 16, a.w + (size_t)row * (CA + CB) + c8 * 8, true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n");  // weights visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = *tslot;
+    auto fail = [&]() {
+        if (a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
+    };
+    auto origin = [&](int j, int &n, int &i0, int &j0) {
+        const int t = blockIdx.x + j * gridDim.x;
+        n = t / per_img;
+        const int r = t % per_img;
+        i0 = (r / tiles_x) * 16;
+        j0 = (r % tiles_x) * 8;
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {  // producer
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF;
+                if (j >= NBUF && !mbar_wait_thread(smem_u32(empty + st), (uint32_t)((j / NBUF - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                int n, i0, j0;
+                origin(j, n, i0, j0);
+                const uint32_t bar = smem_u32(full + st);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(G::TMA_BYTES) : "memory");
+                const uint32_t dst = smem_u32(sx0 + st * G::XBYTES);
+#pragma unroll
+                for (int k = 0; k < CA8; ++k) tma_load_4d(dst + k * PS, &args.tlo, 8 * k, j0 - 1, i0 - 1, n, bar);
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+#pragma unroll
+                    for (int k = 0; k < CB8; ++k)
+                        tma_load_5d(dst + (CA8 + pp * CB8 + k) * PS, &args.tskip, (pp & 1) * CB + 8 * k, j0 - 1, pp >> 1,
+                                    i0 - 1, n, bar);
+                }
+                s_issued = j + 1;
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = umma_idesc(COUT);
+            const uint64_t adesc0 = umma_sdesc(smem_u32(sx0), PS, SW * 16);
+            const uint64_t bdesc0 = umma_sdesc(smem_u32(sw), COUT * 16, 128);
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF, acc = j & 1;
+                if (!mbar_wait_thread(smem_u32(full + st), (uint32_t)((j / NBUF) & 1))) {
+                    fail();
+                    break;
+                }
+                s_consumed = j + 1;
+                if (j >= 2 && !mbar_wait_thread(smem_u32(acce + acc), (uint32_t)((j / 2 - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                const uint64_t ab = adesc0 + (uint64_t)((st * G::XBYTES) >> 4);
+#pragma unroll
+                for (int cls = 0; cls < 4; ++cls) {
+                    const uint32_t d = tmem + (uint32_t)((acc * 4 + cls) * COUT);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int t = (cls >> 1) + tap / 3 - 1, u = (cls & 1) + tap % 3 - 1;  // -1 .. 2
+                        const int oy = t >> 1, ox = u >> 1, pp = (t & 1) * 2 + (u & 1);
+                        const int pos = ((oy + 1) * SW + (ox + 1)) * 16;
+#pragma unroll
+                        for (int kk = 0; kk < CA8 / 2; ++kk) {
+                            const uint32_t aoff = (uint32_t)((2 * kk * PS + pos) >> 4);
+                            const uint32_t boff = (uint32_t)(((tap * C8 + 2 * kk) * COUT * 16) >> 4);
+                            umma_bf16(d, ab + aoff, bdesc0 + boff, idesc, (tap | kk) ? 1u : 0u);
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < CB8 / 2; ++kk) {
+                            const uint32_t aoff = (uint32_t)(((CA8 + pp * CB8 + 2 * kk) * PS + pos) >> 4);
+                            const uint32_t boff = (uint32_t)(((tap * C8 + CA8 + 2 * kk) * COUT * 16) >> 4);
+                            umma_bf16(d, ab + aoff, bdesc0 + boff, idesc, 1u);
+                        }
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(empty + st)));
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(accf + acc)));
+            }
+        }
+    } else {  // epilogue warps 0-3: TMEM lane quarter = warp; row 32w + l = position (4w + l/8, l%8)
+        float bias[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bias[c] = c < a.nbias ? a.bias[c] : 0.f;
+        const int g = 4 * warp + (lane >> 3), r = lane & 7;
+        for (int j = 0; j < mine; ++j) {
+            const int acc = j & 1;
+            if (!mbar_wait_warp(smem_u32(accf + acc), (uint32_t)((j / 2) & 1))) {
+                if (lane == 0) fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            int n, i0, j0;
+            origin(j, n, i0, j0);
+#pragma unroll 1
+            for (int cls = 0; cls < 4; ++cls) {
+                float v[COUT];
+                tc_load_acc<COUT>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((acc * 4 + cls) * COUT), v);
+                if (cls == 3) {
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
+                }
+                tc_store<COUT, 1, 0, false, false>(a, v, bias, n, 2 * (i0 + g) + (cls >> 1), 2 * (j0 + r) + (cls & 1), lane);
+            }
         }
     }
     __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
@@ -1042,11 +1091,6 @@ cudaError_t conv_launch(const ConvArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Launch of the tensor-core convolution.  The occupancy API reports one CTA per SM for
-// kernels that allocate tensor memory, so the resident count is computed here from the
-// kernel's registers, shared memory and threads, and capped at 512 / (TMEM columns per CTA);
-// where threads alone would allow more CTAs than TMEM can hold, the shared-memory request is
-// raised so that no more can be resident (an allocation never has to wait for another CTA).
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 {
@@ -1076,57 +1120,29 @@ cudaError_t make_tmap(CUtensorMap *m, const void *base, int C, int W, int H, int
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Launch of the tensor-core convolution.  The occupancy API reports one CTA per SM for
+// 5-D map of an NHWC bf16 tensor [N][H][W][C] (H, W even) that stages one parity plane per
+// box: dims (2C channels of a column pair, W/2 column pairs, 2 row parities, H/2 row pairs,
+// N); box (8, bw, 1, bh, 1).  The start channel b * C + 8k selects column parity b, chunk k.
+cudaError_t make_tmap_parity(CUtensorMap *m, const void *base, int C, int W, int H, int N, int bw, int bh)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {(cuuint64_t)2 * C, (cuuint64_t)W / 2, 2, (cuuint64_t)H / 2, (cuuint64_t)N};
+    const cuuint64_t strides[4] = {(cuuint64_t)C * 4, (cuuint64_t)W * C * 2, (cuuint64_t)W * C * 4,
+                                   (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[5] = {8, (cuuint32_t)bw, 1, (cuuint32_t)bh, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Launch of the warp-specialised convolution.  The occupancy API reports one CTA per SM for
 // kernels that allocate tensor memory, so the resident count is computed here from the
 // kernel's registers, shared memory and threads, and capped at 512 / (TMEM columns per CTA);
 // where threads alone would allow more CTAs than TMEM can hold, the shared-memory request is
 // raised so that no more can be resident (an allocation never has to wait for another CTA).
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA = 0, bool POOL = false>
-cudaError_t conv_tc_launch(const ConvArgs &a, cudaStream_t st)
-{
-    using G = TcGeom<CIN, COUT, KS, CA>;
-    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreadsPerSm = 2048;
-    constexpr int tmem_cap = 512 / G::COLS;
-    constexpr int min_smem = tmem_cap < kThreadsPerSm / 128 ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
-    constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
-    static_assert(smem <= 227 * 1024, "tensor-core conv tile does not fit in shared memory");
-    auto kern = conv_tc_kernel<CIN, COUT, KS, ACT, OUTM, MASK, CA, POOL>;
-    static int per_sm = 0, n_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        // the whole unified L1 / shared array as shared memory, so the residency below holds
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        cudaFuncAttributes fa;
-        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-        const int by_regs = (4 * (16384 / regs_per_warp)) / 4;  // four warps, one per sub-partition
-        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
-        int r = kThreadsPerSm / 128;
-        r = r < by_regs ? r : by_regs;
-        r = r < by_smem ? r : by_smem;
-        r = r < tmem_cap ? r : tmem_cap;
-        if (r < 1) return cudaErrorInvalidConfiguration;
-        per_sm = r;
-    }
-    const long long ntiles = (long long)a.N * ((a.H + G::TH - 1) / G::TH) * ((a.W + G::TW - 1) / G::TW);
-    if (ntiles <= 0) return cudaSuccess;
-    TcArgs ta;
-    std::memset(&ta, 0, sizeof(ta));
-    ta.c = a;
-    cudaError_t e = CA > 0 ? make_tmap(&ta.tm, a.x2, CIN - CA, a.W, a.H, a.N, G::SW, G::SH)
-                           : make_tmap(&ta.tm, a.x, CIN, a.W, a.H, a.N, G::SW, G::SH);
-    if (e != cudaSuccess) return e;
-    const long long cap = (long long)per_sm * n_sm;
-    kern<<<(int)(ntiles < cap ? ntiles : cap), 128, smem, st>>>(ta);
-    return cudaGetLastError();
-}
-
-// Launch of the warp-specialised convolution; residency computed as for conv_tc_launch.
 template <int CIN, int COUT, int KS, int ACT, int OUTM, bool POOL = false>
 cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
 {
@@ -1168,6 +1184,53 @@ cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const long long cap = (long long)per_sm * n_sm;
     kern<<<(int)(ntiles < cap ? ntiles : cap), kWsThreads, smem, st>>>(ta);
+    return cudaGetLastError();
+}
+
+// Launch of the parity-class decoder convolution (a.x = lo, a.x2 = skip; H, W even);
+// residency computed as for conv_ws_launch.
+template <int CA, int CB, int COUT, int NBUF>
+cudaError_t conv_up_launch(const ConvArgs &a, cudaStream_t st)
+{
+    using G = UpGeom<CA, CB, COUT, NBUF>;
+    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreadsPerSm = 2048;
+    constexpr int tmem_cap = 512 / G::COLS;
+    constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
+    constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
+    static_assert(smem <= 227 * 1024, "decoder conv stage does not fit in shared memory");
+    auto kern = conv_up_kernel<CA, CB, COUT, NBUF>;
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = (4 * (16384 / regs_per_warp)) / (kWsThreads / 32);
+        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
+        int r = kThreadsPerSm / kWsThreads;
+        r = r < by_regs ? r : by_regs;
+        r = r < by_smem ? r : by_smem;
+        r = r < tmem_cap ? r : tmem_cap;
+        if (r < 1) return cudaErrorInvalidConfiguration;
+        per_sm = r;
+    }
+    if ((a.H | a.W) & 1) return cudaErrorInvalidValue;
+    const long long ntiles = (long long)a.N * ((a.H / 2 + 15) / 16) * ((a.W / 2 + 7) / 8);
+    if (ntiles <= 0) return cudaSuccess;
+    UpArgs ua;
+    std::memset(&ua, 0, sizeof(ua));
+    ua.c = a;
+    cudaError_t e = make_tmap(&ua.tlo, a.x, CA, a.W / 2, a.H / 2, a.N, G::SW, G::SH);
+    if (e != cudaSuccess) return e;
+    if ((e = make_tmap_parity(&ua.tskip, a.x2, CB, a.W, a.H, a.N, G::SW, G::SH)) != cudaSuccess) return e;
+    const long long cap = (long long)per_sm * n_sm;
+    kern<<<(int)(ntiles < cap ? ntiles : cap), kWsThreads, smem, st>>>(ua);
     return cudaGetLastError();
 }
 
@@ -1371,11 +1434,11 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     FLNR_TRY((conv_ws_launch<64, 64, 3, 1, 0>(conv(n->a2, 5, n->f2, H4, W4), st)));
     c = conv(n->f2, 6, n->a3, H2, W2);  // input up(f2) ++ f1, formed while staging
     c.x2 = n->f1;
-    FLNR_TRY((conv_tc_launch<96, 32, 3, 1, 0, false, 64>(c, st)));
+    FLNR_TRY((conv_up_launch<64, 32, 32, 2>(c, st)));
     FLNR_TRY((conv_ws_launch<32, 32, 3, 1, 0>(conv(n->a3, 7, n->d1, H2, W2), st)));
     c = conv(n->d1, 8, n->a4, H, W);  // input up(d1) ++ f0
     c.x2 = n->f0;
-    FLNR_TRY((conv_tc_launch<48, 16, 3, 1, 0, false, 32>(c, st)));
+    FLNR_TRY((conv_up_launch<32, 16, 16, 2>(c, st)));
     FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->a4, 9, n->d0, H, W), st)));
     FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->d0, 10, n->a5, H, W), st)));
     float *yf = guide_out ? guide_out : n->out;
@@ -1489,7 +1552,7 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
                 if (b) {
                     if ((H | W) & 1) return FLR_ERR_ARG;
                     c.x2 = (const bf *)b;
-                    FLNR_TRY((conv_tc_launch<CI, CO, KS, 1, 0, false, CA>(c, st)));
+                    FLNR_TRY((conv_up_launch<CA, CI - CA, CO, 2>(c, st)));
                     return FLR_OK;
                 }
             }

@@ -98,9 +98,11 @@ def test_layer_forward(net, l, N, H, W):
 
 
 @pytest.mark.parametrize("l,ca", [(6, 64), (8, 32)])
-@pytest.mark.parametrize("N,H,W", SIZES)
+@pytest.mark.parametrize("N,H,W", SIZES + [(1, 544, 400)])
 def test_decoder_layer_forms_the_concatenation_on_load(net, l, ca, N, H, W):
-    """Layers 6 and 8 read up2(lo) ++ skip directly (the network's fused form)."""
+    """Layers 6 and 8 read up2(lo) ++ skip directly (the network's fused form: the four
+    parity classes of each output block read the low-resolution map and the skip's parity
+    planes).  544 x 400 gives every CTA several blocks."""
     name, cin, cout, k = flnr.LAYERS[l]
     rng = np.random.default_rng(4000 * l + H)
     p = params_with_bias(11)
