@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) flr_batch_kernel(const __gri
 {
     extern __shared__ float sS[];  // [NCH][kBatchThreads] for the solve stage
     const unsigned nblocks = gridDim.x;
-    // stage 1: block moments; item -> (frame, block row, 256-column chunk)
+    // stage 1: block moments; item -> (frame, block row, 512-column chunk)
     for (unsigned long long it = blockIdx.x; it < b.off[0][b.n]; it += gridDim.x) {
         const int f = frame_of(b.off[0], b.n, it);
         const FastArgs &a = b.f[f];

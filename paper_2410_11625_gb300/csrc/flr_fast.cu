@@ -3,8 +3,9 @@
 //
 // The paper's four steps, as four kernels:
 //   1. block_moments: outer products of the shifted inputs summed over F x F blocks of the
-//      input grid (the strided box filter);  one thread per input column walks the F rows
-//      of its block row, then a shuffle tree over the F lanes of a block reduces them;
+//      input grid (the strided box filter);  one thread per pair of input columns walks the
+//      F rows of its block row, then a shuffle tree over the F / 2 lanes of a block reduces
+//      them;
 //   2. blur_h:  horizontal Gaussian over the block grid (one thread per channel and block);
 //   3. blur_v_solve: vertical Gaussian, then the centred ridge model of every block in
 //      registers (the window sums staged per thread in shared memory); a block whose
@@ -35,7 +36,7 @@ using fast::FastArgs;
 using fast::kMaxTaps;
 
 template <int Q, int F>
-__global__ void __launch_bounds__(256) block_moments_kernel(const FastArgs a)
+__global__ void __launch_bounds__(256, 2) block_moments_kernel(const FastArgs a)
 {
     fast::stage_moments<Q, F>(a, blockIdx.y, blockIdx.x);
 }
@@ -200,7 +201,7 @@ int fast_n_sm()
 template <int Q, int F>
 cudaError_t launch_moments(const FastArgs &a, cudaStream_t st)
 {
-    dim3 g1((a.Wi + 255) / 256, a.Hb);
+    dim3 g1(fast::moment_chunks(a.Wi), a.Hb);
     block_moments_kernel<Q, F><<<g1, 256, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -44,12 +44,15 @@ struct FastArgs {
 };
 
 // 1. block moments.  Block (i, j) covers input rows [iF, iF+F) and columns [jF, jF+F).
-// Work item (by, cx): block row by, input columns [256 cx, 256 cx + 256); 256 threads.
+// Work item (by, cx): block row by, input columns [512 cx, 512 cx + 512); 256 threads, each
+// summing two adjacent columns over the F rows (one 8-byte load per plane and row when the
+// rows are 8-byte aligned), then a shuffle tree over the F / 2 lanes of a block.
 template <int Q, int F>
 __device__ __forceinline__ void stage_moments(const FastArgs &a, int by, int cx)
 {
     using C = Chan<Q>;
-    constexpr int NS = Q + 3;
+    constexpr int NS = Q + 3, LPB = F / 2;  // lanes per block
+    static_assert(F >= 2 && 32 % F == 0, "block width");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (by == 0 && cx == 0 && warp == 0) {
         // the frame reference the models are expressed in (used by the solve and apply)
@@ -58,10 +61,10 @@ __device__ __forceinline__ void stage_moments(const FastArgs &a, int by, int cx)
         __syncwarp();
         if (lane < NS) a.shift[lane] = s_ref[lane];
     }
-    const int x = cx * 256 + tid;
+    const int x = cx * 512 + 2 * tid;  // this thread's columns x, x + 1
     const size_t plane = (size_t)a.Hi * a.Wi;
     const int y0 = by * F, y1 = min(y0 + F, a.Hi);
-    // the block's reference: its top-left input pixel (column of lane (lane & ~(F-1)))
+    // the block's reference: its top-left input pixel (column x of lane (lane & ~(LPB-1)))
     float ref[NS];
     {
         const size_t off0 = (size_t)y0 * a.Wi + min(x, a.Wi - 1);
@@ -70,31 +73,57 @@ __device__ __forceinline__ void stage_moments(const FastArgs &a, int by, int cx)
 #pragma unroll
         for (int c = 0; c < 3; ++c) ref[Q + c] = __ldg(a.rad + c * plane + off0);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) ref[k] = __shfl_sync(0xffffffffu, ref[k], lane & ~(F - 1));
+        for (int k = 0; k < NS; ++k) ref[k] = __shfl_sync(0xffffffffu, ref[k], lane & ~(LPB - 1));
     }
     float acc[C::NCH];
 #pragma unroll
     for (int c = 0; c < C::NCH; ++c) acc[c] = 0.f;
     if (x < a.Wi) {
+        // with an even width, x + 1 < Wi and the 8-byte loads are aligned (x even, planes
+        // 16-byte aligned)
+        const bool vec = (a.Wi & 1) == 0;
+        const bool two = x + 1 < a.Wi;
 #pragma unroll
         for (int yy = 0; yy < F; ++yy) {
             const int y = y0 + yy;
             if (y >= y1) break;
             const size_t off = (size_t)y * a.Wi + x;
-            float v[NS];
+            float v0[NS], v1[NS];
+            if (vec) {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) v[k] = __ldg(a.guide + k * plane + off) - ref[k];
+                for (int k = 0; k < Q; ++k) {
+                    const float2 g = __ldg(reinterpret_cast<const float2 *>(a.guide + k * plane + off));
+                    v0[k] = g.x - ref[k];
+                    v1[k] = g.y - ref[k];
+                }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[Q + c] = __ldg(a.rad + c * plane + off) - ref[Q + c];
-            moments_all<Q>(acc, v, std::make_integer_sequence<int, C::NCH>{});
+                for (int c = 0; c < 3; ++c) {
+                    const float2 g = __ldg(reinterpret_cast<const float2 *>(a.rad + c * plane + off));
+                    v0[Q + c] = g.x - ref[Q + c];
+                    v1[Q + c] = g.y - ref[Q + c];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    v0[k] = __ldg(a.guide + k * plane + off) - ref[k];
+                    v1[k] = two ? __ldg(a.guide + k * plane + off + 1) - ref[k] : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    v0[Q + c] = __ldg(a.rad + c * plane + off) - ref[Q + c];
+                    v1[Q + c] = two ? __ldg(a.rad + c * plane + off + 1) - ref[Q + c] : 0.f;
+                }
+            }
+            moments_all<Q>(acc, v0, std::make_integer_sequence<int, C::NCH>{});
+            moments_all<Q>(acc, v1, std::make_integer_sequence<int, C::NCH>{});
         }
     }
-    // reduce over the F lanes of each block (blocks never straddle a warp: 32 % F == 0)
+    // reduce over the LPB lanes of each block (blocks never straddle a warp: 32 % LPB == 0)
 #pragma unroll
     for (int ch = 0; ch < C::NCH; ++ch)
 #pragma unroll
-        for (int o = 1; o < F; o <<= 1) acc[ch] += __shfl_xor_sync(0xffffffffu, acc[ch], o);
-    if ((lane & (F - 1)) == 0 && x < a.Wi) {
+        for (int o = 1; o < LPB; o <<= 1) acc[ch] += __shfl_xor_sync(0xffffffffu, acc[ch], o);
+    if ((lane & (LPB - 1)) == 0 && x < a.Wi) {
         const int bx = x / F;
         const size_t bplane = (size_t)a.Hb * a.Wb;
         const size_t boff = (size_t)by * a.Wb + bx;
@@ -390,7 +419,7 @@ __device__ __forceinline__ void stage_apply(const FastArgs &a, size_t t)
 }
 
 // Work-item counts of each stage for one frame (256 threads per item).
-__host__ __device__ inline int moment_chunks(int Wi) { return (Wi + 255) / 256; }
+__host__ __device__ inline int moment_chunks(int Wi) { return (Wi + 511) / 512; }
 inline size_t items_moments(const FastArgs &a) { return (size_t)a.Hb * moment_chunks(a.Wi); }
 inline size_t items_blocks(const FastArgs &a) { return ((size_t)a.Hb * a.Wb + 255) / 256; }
 inline size_t items_apply(const FastArgs &a) { return ((size_t)a.Ho * (a.Wo / (a.F * a.s) + 2) + 255) / 256; }
