@@ -591,6 +591,247 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------------------
+// Two layers in one pass: a KS x KS convolution (ReLU) followed by a 1x1 convolution of its
+// output (in1 after in0, o1 after o0).  The first layer's tile never reaches HBM: the
+// epilogue warps write its bias + ReLU + bfloat16 values into shared memory as the K-major
+// A operand of the 1x1 MMA ([chunk][128 pixels][8 channels]), the MMA lane issues that one
+// MMA into a second pair of accumulators, and the epilogue warps finish the tile from it
+// (ReLU and the 2x2 pool for in1, sigmoid into planar FP32 for o1).  Roles as
+// conv_ws_kernel; the MMA lane issues tile j's convolution, then tile j - 1's 1x1.
+// Barriers: full/empty per input stage, accf/acce per first accumulator, a2full (the A
+// operand of the 1x1 written, four epilogue warps), acc2f (1x1 committed) and acc2e (its
+// accumulator drained, four warps), all per accumulator slot j & 1.
+struct alignas(128) TailArgs {
+    CUtensorMap tm;
+    ConvArgs c;   // first layer: x, w, bias, nbias, N, H, W, status; y (may be NULL), ystride
+    ConvArgs c2;  // 1x1 layer: w, bias, nbias, N, H, W and the outputs (y, ystride, yp / yf)
+};
+
+template <int CIN, int COUT, int KS, int COUT2>
+struct TailGeom {
+    using G1 = WsGeom<CIN, COUT, KS>;
+    static constexpr int NBUF = G1::NBUF;
+    static constexpr int A2BYTES = (COUT / 8) * 128 * 16;             // one 1x1 A operand
+    static constexpr int W2BYTES = ((COUT / 8) * COUT2 * 16 + 127) / 128 * 128;
+    static constexpr int NBAR = 2 * NBUF + 10;  // full, empty, accf, acce, a2full, acc2f, acc2e
+    static constexpr int SMEM = 128 + G1::WBYTES + W2BYTES + NBUF * G1::XBYTES + 2 * A2BYTES + NBAR * 8 + 16;
+    static constexpr int COLS = tmem_cols<2 * COUT + 2 * COUT2>();
+};
+
+template <int CIN, int COUT, int KS, int COUT2, int ACT2, int OUTM2, bool POOL2>
+__global__ void __launch_bounds__(kWsThreads) conv_tail_kernel(const __grid_constant__ TailArgs args)
+{
+    using T = TailGeom<CIN, COUT, KS, COUT2>;
+    using G = typename T::G1;
+    constexpr int TH = G::TH, TW = G::TW, P = G::P, SW = G::SW, C8 = G::C8, NBUF = G::NBUF, PS = G::PS;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT2 % 16 == 0 && 2 * COUT + 2 * COUT2 <= 256, "UMMA shape");
+    const ConvArgs &a = args.c;
+    const ConvArgs &a2 = args.c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    unsigned char *sw = base;
+    unsigned char *sw2 = sw + G::WBYTES;
+    unsigned char *sa2 = sw2 + T::W2BYTES;                   // [2][COUT/8][128][8] 1x1 A operands
+    unsigned char *sx0 = sa2 + 2 * T::A2BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sx0 + NBUF * G::XBYTES);
+    uint64_t *empty = full + NBUF, *accf = empty + NBUF, *acce = accf + 2;
+    uint64_t *a2full = acce + 2, *acc2f = a2full + 2, *acc2e = acc2f + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acc2e + 2);
+    __shared__ int s_issued, s_consumed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
+    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
+    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(T::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(empty + i)));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(accf + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(acce + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(a2full + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(acc2f + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(acc2e + i)));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.tm)) : "memory");
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    for (int i = tid; i < KS * KS * COUT * C8; i += kWsThreads) {
+        const int c8 = i % C8, row = i / C8, tap = row / COUT, co = row % COUT;
+        cp_async16(sw + ((tap * C8 + c8) * COUT + co) * 16, a.w + (size_t)row * CIN + c8 * 8, true);
+    }
+    for (int i = tid; i < COUT2 * (COUT / 8); i += kWsThreads) {  // 1x1 weights [COUT2][COUT] -> [c8][COUT2][8]
+        const int c8 = i % (COUT / 8), co = i / (COUT / 8);
+        cp_async16(sw2 + (c8 * COUT2 + co) * 16, a2.w + (size_t)co * COUT + c8 * 8, true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n");  // weights visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = *tslot;
+    const uint32_t tmem2 = tmem + (uint32_t)(2 * COUT);  // the 1x1 accumulators
+    auto fail = [&]() {
+        if (a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
+    };
+    auto origin = [&](int j, int &n, int &ty0, int &tx0) {
+        const int t = blockIdx.x + j * gridDim.x;
+        n = t / per_img;
+        const int r = t % per_img;
+        ty0 = (r / tiles_x) * TH;
+        tx0 = (r % tiles_x) * TW;
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {  // producer
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF;
+                if (j >= NBUF && !mbar_wait_thread(smem_u32(empty + st), (uint32_t)((j / NBUF - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                int n, ty0, tx0;
+                origin(j, n, ty0, tx0);
+                const uint32_t bar = smem_u32(full + st);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(G::TMA_BYTES) : "memory");
+                const uint32_t dst = smem_u32(sx0 + st * G::XBYTES);
+#pragma unroll
+                for (int k = 0; k < C8; ++k) tma_load_4d(dst + k * PS, &args.tm, k * 8, tx0 - P, ty0 - P, n, bar);
+                s_issued = j + 1;
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = umma_idesc(COUT), idesc2 = umma_idesc(COUT2);
+            const uint64_t adesc0 = umma_sdesc(smem_u32(sx0), PS, SW * 16);
+            const uint64_t bdesc0 = umma_sdesc(smem_u32(sw), COUT * 16, 128);
+            const uint64_t a2desc0 = umma_sdesc(smem_u32(sa2), 128 * 16, 128);
+            const uint64_t b2desc0 = umma_sdesc(smem_u32(sw2), COUT2 * 16, 128);
+            // the 1x1 of tile t: its A operand written, its accumulator slot drained
+            auto tail = [&](int t) -> bool {
+                const int sl = t & 1;
+                if (!mbar_wait_thread(smem_u32(a2full + sl), (uint32_t)((t >> 1) & 1))) return false;
+                if (t >= 2 && !mbar_wait_thread(smem_u32(acc2e + sl), (uint32_t)(((t >> 1) - 1) & 1))) return false;
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                const uint32_t d = tmem2 + (uint32_t)(sl * COUT2);
+                const uint64_t ab = a2desc0 + (uint64_t)((sl * T::A2BYTES) >> 4);
+#pragma unroll
+                for (int kk = 0; kk < COUT / 16; ++kk)
+                    umma_bf16(d, ab + (uint64_t)((2 * kk * 128 * 16) >> 4), b2desc0 + (uint64_t)((2 * kk * COUT2 * 16) >> 4),
+                              idesc2, kk ? 1u : 0u);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(acc2f + sl)));
+                return true;
+            };
+            bool ok = true;
+            for (int j = 0; j < mine && ok; ++j) {
+                const int st = j % NBUF, acc = j & 1;
+                if (!mbar_wait_thread(smem_u32(full + st), (uint32_t)((j / NBUF) & 1))) {
+                    ok = false;
+                    break;
+                }
+                s_consumed = j + 1;
+                if (j >= 2 && !mbar_wait_thread(smem_u32(acce + acc), (uint32_t)((j / 2 - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                const uint64_t ab = adesc0 + (uint64_t)((st * G::XBYTES) >> 4);
+                const uint32_t d = tmem + (uint32_t)(acc * COUT);
+#pragma unroll
+                for (int tap = 0; tap < KS * KS; ++tap) {
+#pragma unroll
+                    for (int kk = 0; kk < C8 / 2; ++kk) {
+                        const uint32_t aoff = (uint32_t)((2 * kk * PS + ((tap / KS) * SW + tap % KS) * 16) >> 4);
+                        const uint32_t boff = (uint32_t)(((tap * C8 + 2 * kk) * COUT * 16) >> 4);
+                        umma_bf16(d, ab + aoff, bdesc0 + boff, idesc, (tap | kk) ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(empty + st)));
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(accf + acc)));
+                if (j >= 1) ok = tail(j - 1);
+            }
+            if (ok && mine > 0) ok = tail(mine - 1);
+            if (!ok) fail();
+        }
+    } else {  // epilogue warps 0-3: TMEM lane quarter = warp; row 32w + l = pixel (4w + l/8, l%8)
+        float bias[COUT], bias2[COUT2];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bias[c] = c < a.nbias ? a.bias[c] : 0.f;
+#pragma unroll
+        for (int c = 0; c < COUT2; ++c) bias2[c] = c < a2.nbias ? a2.bias[c] : 0.f;
+        const int m = 32 * warp + lane;
+        for (int j = 0; j < mine; ++j) {
+            const int acc = j & 1;
+            if (!mbar_wait_warp(smem_u32(accf + acc), (uint32_t)((j / 2) & 1))) {
+                if (lane == 0) fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            float v[COUT];
+            tc_load_acc<COUT>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * COUT), v);
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
+            int n, ty0, tx0;
+            origin(j, n, ty0, tx0);
+            const int yy = ty0 + 4 * warp + (lane >> 3), xx = tx0 + (lane & 7);
+            const bool in = yy < a.H && xx < a.W;
+            const size_t pix = ((size_t)n * a.H + yy) * a.W + xx;
+            // first layer's bias + ReLU, rounded to bfloat16: the 1x1's A operand row m, and
+            // (when a.y is set) the first layer's stored output, which the backward pass reads
+            unsigned char *arow = sa2 + acc * T::A2BYTES + m * 16;
+#pragma unroll
+            for (int c8 = 0; c8 < COUT / 8; ++c8) {
+                uint4 o;
+                __nv_bfloat162 *oh = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    oh[i] = __floats2bfloat162_rn(fmaxf(v[c8 * 8 + 2 * i] + bias[c8 * 8 + 2 * i], 0.f),
+                                                  fmaxf(v[c8 * 8 + 2 * i + 1] + bias[c8 * 8 + 2 * i + 1], 0.f));
+                *reinterpret_cast<uint4 *>(arow + c8 * 128 * 16) = o;
+                if (a.y && in) *reinterpret_cast<uint4 *>(a.y + pix * a.ystride + c8 * 8) = o;
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor core
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(a2full + acc)) : "memory");
+            if (!mbar_wait_warp(smem_u32(acc2f + acc), (uint32_t)((j / 2) & 1))) {
+                if (lane == 0) fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            float v2[COUT2];
+            tc_load_acc<COUT2>(tmem2 + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * COUT2), v2);
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acc2e + acc)) : "memory");
+            tc_store<COUT2, ACT2, OUTM2, false, POOL2>(a2, v2, bias2, n, yy, xx, lane);
+        }
+    }
+    __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (tid == 4 * 32) {  // after a failure: let copies still in flight land before the CTA exits
+        for (int j = s_consumed; j < s_issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(T::COLS));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Decoder convolution (3x3, ReLU) on up2(lo) ++ skip without forming the upsampled map.
 // A stage covers 32 x 16 output pixels: a 16 x 8 block of low-resolution positions (i0 + g,
 // j0 + r) and its four parity classes (a, b), output pixel (2(i0 + g) + a, 2(j0 + r) + b),
@@ -1187,6 +1428,53 @@ cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Launch of the fused KS x KS + 1x1 pair (c: first layer, c2: the 1x1 layer); residency
+// computed as for conv_ws_launch.
+template <int CIN, int COUT, int KS, int COUT2, int ACT2, int OUTM2, bool POOL2>
+cudaError_t conv_tail_launch(const ConvArgs &c, const ConvArgs &c2, cudaStream_t st)
+{
+    using T = TailGeom<CIN, COUT, KS, COUT2>;
+    using G = typename T::G1;
+    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreadsPerSm = 2048;
+    constexpr int tmem_cap = 512 / T::COLS;
+    constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
+    constexpr size_t smem = (size_t)(T::SMEM > min_smem ? T::SMEM : min_smem);
+    static_assert(smem <= 227 * 1024, "fused conv stage does not fit in shared memory");
+    auto kern = conv_tail_kernel<CIN, COUT, KS, COUT2, ACT2, OUTM2, POOL2>;
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = (4 * (16384 / regs_per_warp)) / (kWsThreads / 32);
+        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
+        int r = kThreadsPerSm / kWsThreads;
+        r = r < by_regs ? r : by_regs;
+        r = r < by_smem ? r : by_smem;
+        r = r < tmem_cap ? r : tmem_cap;
+        if (r < 1) return cudaErrorInvalidConfiguration;
+        per_sm = r;
+    }
+    const long long ntiles = (long long)c.N * ((c.H + G::TH - 1) / G::TH) * ((c.W + G::TW - 1) / G::TW);
+    if (ntiles <= 0) return cudaSuccess;
+    TailArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.c = c;
+    ta.c2 = c2;
+    cudaError_t e = make_tmap(&ta.tm, c.x, CIN, c.W, c.H, c.N, G::SW, G::SH);
+    if (e != cudaSuccess) return e;
+    const long long cap = (long long)per_sm * n_sm;
+    kern<<<(int)(ntiles < cap ? ntiles : cap), kWsThreads, smem, st>>>(ta);
+    return cudaGetLastError();
+}
+
 // Launch of the parity-class decoder convolution (a.x = lo, a.x2 = skip; H, W even);
 // residency computed as for conv_ws_launch.
 template <int CA, int CB, int COUT, int NBUF>
@@ -1422,10 +1710,10 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
         return c;
     };
     ConvArgs c;
-    FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->x0, 0, n->a0, H, W), st)));
     c = conv(n->a0, 1, n->f0, H, W);
     c.yp = n->p0;  // 2x2 average pool of f0 for the encoder
-    FLNR_TRY((conv_ws_launch<16, 16, 1, 1, 0, true>(c, st)));
+    // in0 and in1 in one pass (a0, which the backward pass reads, is still stored)
+    FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 1, 0, true>(conv(n->x0, 0, n->a0, H, W), c, st)));
     FLNR_TRY((conv_ws_launch<16, 32, 3, 1, 0>(conv(n->p0, 2, n->a1, H2, W2), st)));
     c = conv(n->a1, 3, n->f1, H2, W2);
     c.yp = n->p1;
@@ -1440,11 +1728,11 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     c.x2 = n->f0;
     FLNR_TRY((conv_up_launch<32, 16, 16, 2>(c, st)));
     FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->a4, 9, n->d0, H, W), st)));
-    FLNR_TRY((conv_ws_launch<16, 16, 3, 1, 0>(conv(n->d0, 10, n->a5, H, W), st)));
     float *yf = guide_out ? guide_out : n->out;
     c = conv(n->a5, 11, nullptr, H, W);
     c.yf = yf;
-    FLNR_TRY((conv_ws_launch<16, 16, 1, 2, 1>(c, st)));
+    // o0 and the head o1 (sigmoid into planar FP32) in one pass; a5 is still stored
+    FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 2, 1, false>(conv(n->d0, 10, n->a5, H, W), c, st)));
     if (guide_out)
         FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return FLR_OK;
