@@ -101,7 +101,7 @@ __device__ __forceinline__ void load_tile(float *T, const ApplyGeom &g, const fl
 }
 
 template <int Q, int RT>
-__global__ void __launch_bounds__(kAThreads, 3) flr_apply_kernel(const __grid_constant__ ApplyKArgs ka)
+__global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_constant__ ApplyKArgs ka)
 {
     extern __shared__ __align__(16) float sm[];
     const ApplyArgs &a = ka.a;
@@ -281,6 +281,10 @@ cudaError_t launch_apply_qr(const ApplyArgs &a, cudaStream_t st)
     const size_t smem = sizeof(float) * g.floats();
     cudaError_t e = cudaFuncSetAttribute(flr_apply_kernel<Q, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e != cudaSuccess) return e;
+    // four CTAs per SM (64 registers each) need most of the unified L1 / shared array
+    e = cudaFuncSetAttribute(flr_apply_kernel<Q, RT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     const int rows = (a.row_hi < 0 ? a.H : a.row_hi) - a.row_lo;
     if (rows <= 0) return cudaSuccess;

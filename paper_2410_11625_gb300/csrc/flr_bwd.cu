@@ -128,7 +128,7 @@ struct BoxGeom {
 constexpr unsigned long long kBoxTimeoutNs = 1000000000ull;
 
 template <int RT>
-__global__ void __launch_bounds__(kBThreads, 3) box_sum_tma_kernel(const __grid_constant__ BoxKArgs k)
+__global__ void __launch_bounds__(kBThreads, 4) box_sum_tma_kernel(const __grid_constant__ BoxKArgs k)
 {
     extern __shared__ __align__(16) float sm[];
     const int rad = RT >= 0 ? RT : k.rad;
@@ -318,6 +318,10 @@ cudaError_t launch_box_sum_tma(const BoxKArgs &k, cudaStream_t st)
     const BoxGeom g(k.rad);
     const size_t smem = sizeof(float) * g.floats();
     cudaError_t e = cudaFuncSetAttribute(box_sum_tma_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // four CTAs per SM need most of the unified L1 / shared array as shared memory
+    e = cudaFuncSetAttribute(box_sum_tma_kernel<RT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     dim3 grid((k.W + kBW - 1) / kBW, (k.H + kBH - 1) / kBH);
     box_sum_tma_kernel<RT><<<grid, kBThreads, smem, st>>>(k);

@@ -397,8 +397,9 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     // 4. adjoint of the window sums, the averaged models for the applied guide, contraction
     FLR_CUDA(flr::launch_box_sum(GS, BS, nch, H, W, r, s, h->d_status), "backward: window-sum adjoint launch");
     const float *BA = Acoef;
-    if (rc > 0) {
-        FLR_CUDA(flr::launch_box_sum(Acoef, F, ncf, H, W, rc, s, h->d_status), "backward: model average launch");
+    if (rc > 0) {  // the averaged a (planes 3 .. ncf - 1); the contraction reads no averaged bias
+        FLR_CUDA(flr::launch_box_sum(Acoef + 3 * px, F + 3 * px, ncf - 3, H, W, rc, s, h->d_status),
+                 "backward: model average launch");
         BA = F;
     }
     flr::BwdArgs ba;
