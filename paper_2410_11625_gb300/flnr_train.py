@@ -62,12 +62,17 @@ def sample_batch(rng, scenes, batch, crop):
 class Trainer:
     """Holds the network, the FLR handle and the device buffers of one batch shape."""
 
-    def __init__(self, weights, batch=16, crop=128, radius=8, eps=1e-3, lr=1e-3, device="cuda"):
+    def __init__(self, weights, batch=16, crop=128, radius=8, eps=1e-3, lr=1e-3, device="cuda", graph=True):
         import torch
         self.B, self.c, self.lr = batch, crop, lr
         self.net = _flnr.FLNR(batch * crop * crop, weights)
-        self.flr = _flr.FLR(q=8, radius=radius, eps=eps)
-        self.flr.reserve(crop, crop)
+        # one FLR handle and stream per crop: the crops' FLR passes and adjoints (small
+        # grids each) run concurrently, and no two of them share a handle's workspace
+        self.flrs = [_flr.FLR(q=8, radius=radius, eps=eps) for _ in range(batch)]
+        for f in self.flrs:
+            f.reserve(crop, crop)
+        self.flr = self.flrs[0]
+        self.streams = [torch.cuda.Stream() for _ in range(batch)]
         opt = dict(dtype=torch.float32, device=device)
         self.x_host = torch.empty((batch, 11, crop, crop), dtype=torch.float32).pin_memory()
         self.r_host = torch.empty((batch, 3, crop, crop), dtype=torch.float32).pin_memory()
@@ -76,24 +81,63 @@ class Trainer:
         self.guides = torch.empty((batch, 8, crop, crop), **opt)
         self.out = torch.empty((batch, 3, crop, crop), **opt)
         self.g_guides = torch.empty((batch, 8, crop, crop), **opt)
-        self.g_rad = torch.empty((3, crop, crop), **opt)
+        self.g_rad = torch.empty((batch, 3, crop, crop), **opt)
         self.steps = 0
+        # After two eager warm-up steps the device part of a step (network forward, FLR per
+        # crop, L1, FLR adjoint per crop, network backward: about 200 launches on B + 1
+        # streams) is captured once in a CUDA graph and replayed.  The batch's H2D copy and Adam stay outside the
+        # graph: the host buffer is refilled every step, and the step count and learning rate
+        # enter Adam's arguments.
+        self.use_graph = graph
+        self.graph = None
+        self.loss_static = None
+        self.h2d_done = torch.cuda.Event()
+        self.h2d_pending = False
+
+    def _per_crop(self, fn):
+        """Runs fn(b) for every crop on its own stream, forked from and joined back into
+        the current stream."""
+        import torch
+        cur = torch.cuda.current_stream()
+        for b in range(self.B):
+            self.streams[b].wait_stream(cur)
+            with torch.cuda.stream(self.streams[b]):
+                fn(b)
+        for b in range(self.B):
+            cur.wait_stream(self.streams[b])
+
+    def _device_step(self):
+        """Forward, loss and gradients of the batch already on the device; returns the loss."""
+        self.net.forward(self.x, out=self.guides)
+        self._per_crop(lambda b: self.flrs[b].denoise(self.guides[b], self.x[b, 8:11], out=self.out[b]))
+        loss, g_out = _flnr.l1_loss(self.out, self.ref)
+        self._per_crop(lambda b: self.flrs[b].backward(self.guides[b], self.x[b, 8:11], g_out[b],
+                                                      grad_guide=self.g_guides[b], grad_radiance=self.g_rad[b]))
+        self.net.zero_grads(self.x)
+        self.net.backward(self.g_guides)
+        return loss
 
     def step(self, xs, rs):
         """One optimisation step on host crops; returns the loss as a device tensor."""
+        import torch
+        if self.h2d_pending:
+            self.h2d_done.synchronize()  # the previous step's copies have read the host buffers
         self.x_host.numpy()[...] = xs
         self.r_host.numpy()[...] = rs
         self.x.copy_(self.x_host, non_blocking=True)
         self.ref.copy_(self.r_host, non_blocking=True)
-        self.net.forward(self.x, out=self.guides)
-        for b in range(self.B):
-            self.flr.denoise(self.guides[b], self.x[b, 8:11], out=self.out[b])
-        loss, g_out = _flnr.l1_loss(self.out, self.ref)
-        for b in range(self.B):
-            self.flr.backward(self.guides[b], self.x[b, 8:11], g_out[b], grad_guide=self.g_guides[b],
-                              grad_radiance=self.g_rad)
-        self.net.zero_grads(self.x)
-        self.net.backward(self.g_guides)
+        self.h2d_done.record()
+        self.h2d_pending = True
+        if self.graph is None and self.use_graph and self.steps >= 2:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+                self.loss_static = self._device_step()
+            self.graph = graph
+        if self.graph is not None:
+            self.graph.replay()
+            loss = self.loss_static.clone()
+        else:
+            loss = self._device_step()
         self.steps += 1
         self.net.adam_step(self.steps, lr=self.lr, stream_of=self.x)
         return loss
