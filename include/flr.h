@@ -324,9 +324,11 @@ int flnr_get_weights(flnr_net *net, float *host, size_t count);
 int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, int H, int W, void *stream);
 
 /*
- * One layer of the network by itself, with the network's current weights: the same
- * kernels flnr_guide_forward and flnr_guide_backward launch for that layer (Sec. 3.3), so
- * that each can be checked on its own.  layer = 0..11 in the order above.  Tensors are
+ * One layer of the network by itself, with the network's current weights: the kernels
+ * flnr_guide_forward and flnr_guide_backward use for that layer (Sec. 3.3), so that each
+ * can be checked on its own.  (flnr_guide_forward runs in0 with in1, and o0 with o1, as
+ * one fused pass each; the products and their order are those of the separate layers.)
+ * layer = 0..11 in the order above.  Tensors are
  * device NHWC bfloat16 (raw 16-bit patterns) with channel counts padded to multiples of
  * 16: CinP = 16 * ceil(Cin / 16), CoutP likewise; the padding channels of the outputs are
  * written (as zero where the padded weights are zero).
@@ -334,8 +336,10 @@ int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, 
  *                    or, for layer 11, float32 planar [N][8][H][W] = sigmoid(conv(x) + b).
  *                    Layers 6 and 8 with b != NULL: a = the half-resolution decoder input
  *                    [N][H/2][W/2][64 or 32] and b = the skip [N][H][W][32 or 16]; the
- *                    kernel forms their concatenation (nearest 2x upsampling of a, then b)
- *                    while loading, as the network does.  Layers 1 and 3 with out2 != NULL:
+ *                    result is the convolution of their concatenation (nearest 2x
+ *                    upsampling of a, then b), which the kernel never forms: each output
+ *                    parity class reads a and the skip's parity planes directly, as the
+ *                    network does.  Layers 1 and 3 with out2 != NULL:
  *                    out2 [N][H/2][W/2][CoutP] also receives the 2x2 average of the stored
  *                    bf16 outputs, rounded to bf16, as the network's encoder reads it.
  *                    Both fused forms need H and W even.
