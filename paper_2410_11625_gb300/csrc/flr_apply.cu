@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_co
     float *Hb = T1 + g.tile_floats();  // [THh][HS]   horizontal sums
     uint64_t *bar = reinterpret_cast<uint64_t *>(Hb + ((g.THh * g.HS + 1) & ~1));  // [2] TMA arrivals
     __shared__ int s_abort;
+    __shared__ float s_shift[Q + 3];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row_hi = a.row_hi < 0 ? H : min(a.row_hi, H);
     const int tx0 = blockIdx.x * kAW, ty0 = a.row_lo + blockIdx.y * kAH;
@@ -150,8 +151,20 @@ __global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_co
             tma::mbar_init_fence();
         }
     }
+    if (tid < Q + 3) s_shift[tid] = a.shift[tid];
     __syncthreads();
     stage(T0, 0);
+    // the map-guide values of model row i + 1 are prefetched into L1 while row i is summed
+    auto prefetch_z = [&](int i) {
+        if (i < 1 || i > Q || gx >= W) return;
+#pragma unroll
+        for (int t = 0; t < kARun; ++t) {
+            const int gy = ty0 + run * kARun + t;
+            if (gy < H)
+                asm volatile("prefetch.global.L1 [%0];\n" ::"l"(a.map_guide + (size_t)(i - 1) * plane + (size_t)gy * W + gx));
+        }
+    };
+    prefetch_z(1);
     for (int i = 0; i <= Q; ++i) {
         float zf[kARun];
 #pragma unroll
@@ -160,10 +173,11 @@ __global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_co
             zf[t] = 1.f;
             if (i > 0) {
                 zf[t] = (gx < W && gy < H)
-                            ? __ldg(a.map_guide + (size_t)(i - 1) * plane + (size_t)gy * W + gx) - a.shift[i - 1]
+                            ? __ldg(a.map_guide + (size_t)(i - 1) * plane + (size_t)gy * W + gx) - s_shift[i - 1]
                             : 0.f;
             }
         }
+        prefetch_z(i + 1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int p = 3 * i + c;
@@ -268,7 +282,7 @@ __global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_co
                 const float inv_m = 1.0f / (nx * ny);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    a.out[c * plane + (size_t)gy * W + gx] = fmaf(acc[c][t], inv_m, a.shift[Q + c]);
+                    a.out[c * plane + (size_t)gy * W + gx] = fmaf(acc[c][t], inv_m, s_shift[Q + c]);
             }
         }
     }
