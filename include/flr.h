@@ -66,9 +66,12 @@ typedef struct flr_params {
 } flr_params;
 
 typedef struct flr_stats {
-    unsigned long long flagged;  /* pixels of the last call whose pivot fell below tau */
-    unsigned long long resolved; /* of those, pixels re-solved in FP64 (the rest overflowed
-                                    the flag list and kept their FP32 solution) */
+    unsigned long long flagged;   /* pixels of the last call whose pivot fell below tau */
+    unsigned long long resolved;  /* of those, pixels re-solved in FP64 (the rest overflowed
+                                     the flag list and kept their FP32 solution) */
+    unsigned long long nonfinite; /* output values (pixel x channel) of the last call that are
+                                     NaN or infinite: non-finite inputs are not sanitised and
+                                     propagate through every window that holds them */
 } flr_stats;
 
 typedef struct flr_handle flr_handle;
@@ -231,7 +234,8 @@ int flr_fast_destroy(flr_fast_handle *h);
 int flr_fast_denoise(flr_fast_handle *h, const float *guide, const float *map_guide,
                      const float *radiance, float *out, int Hi, int Wi, void *stream);
 
-/* Blocks of the last call whose pivot fell below the threshold (re-solved in FP64). */
+/* Blocks of the last call whose pivot fell below the threshold (re-solved in FP64); the
+ * fast path does not count non-finite outputs (nonfinite = 0). */
 int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out);
 
 /* One frame of a batch: device pointers as in flr_denoise / flr_fast_denoise. */

@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_co
     }
     if (gx < W) {
         const float nx = (float)(min(gx + rc, W - 1) - max(gx - rc, 0) + 1);
+        int bad = 0;
 #pragma unroll
         for (int t = 0; t < kARun; ++t) {
             const int gy = ty0 + run * kARun + t;
@@ -281,10 +282,14 @@ __global__ void __launch_bounds__(kAThreads, 4) flr_apply_kernel(const __grid_co
                 const float ny = (float)(min(gy + rc, H - 1) - max(gy - rc, 0) + 1);
                 const float inv_m = 1.0f / (nx * ny);
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    a.out[c * plane + (size_t)gy * W + gx] = fmaf(acc[c][t], inv_m, s_shift[Q + c]);
+                for (int c = 0; c < 3; ++c) {
+                    const float o = fmaf(acc[c][t], inv_m, s_shift[Q + c]);
+                    a.out[c * plane + (size_t)gy * W + gx] = o;
+                    bad += !isfinite(o);
+                }
             }
         }
+        if (bad && a.nonfinite) atomicAdd(a.nonfinite, (unsigned long long)bad);
     }
 }
 

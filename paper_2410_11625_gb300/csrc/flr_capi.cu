@@ -38,7 +38,7 @@ struct flr_handle {
     flr_params p;
     int device = 0;
     int n_sm = 0;
-    unsigned long long *d_count = nullptr;  // flagged-pixel counter
+    unsigned long long *d_count = nullptr;  // [0] flagged pixels, [1] non-finite output values
     int *d_status = nullptr;                // set by a kernel whose bounded wait ran out
     float *d_shift = nullptr;               // frame reference shift, Q+3 floats
     int *d_flags = nullptr;                 // flag list
@@ -159,9 +159,9 @@ int flr_create(const flr_params *params, flr_handle **out)
     h->p = *params;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_count, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_shift, sizeof(float) * (FLR_MAX_Q + 3));
-    if (e == cudaSuccess) e = cudaMemset(h->d_count, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_count, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e == cudaSuccess) {
@@ -227,7 +227,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
     if (st != FLR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
-    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), s), "reset counter");
+    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(unsigned long long), s), "reset counters");
 
     flr::FwdArgs fa;
     fa.guide = guide;
@@ -251,6 +251,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
     fa.gS = nullptr;
     fa.geps = nullptr;
     fa.status = h->d_status;
+    fa.nonfinite = h->d_count + 1;
     dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
     FLR_CUDA(mark(h, s), "timing event");
     FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "forward kernel launch");
@@ -274,6 +275,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
         da.flag_list = h->d_flags;
         da.flag_cap = h->flag_cap;
         da.force_coef = 0;
+        da.nonfinite = h->d_count + 1;
         FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "fp64 re-solve launch");
         ++h->n_fp64;
     }
@@ -288,6 +290,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
         aa.W = W;
         aa.rc = h->p.coef_radius;
         aa.status = h->d_status;
+        aa.nonfinite = h->d_count + 1;
         FLR_CUDA(flr::launch_apply(q, aa, s), "apply kernel launch");
         ++h->n_apply;
     }
@@ -330,7 +333,7 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     const int r = h->p.radius, rc = h->p.coef_radius;
 
     // 1. models A_k (forward kernel, coefficient output forced), FP64 re-solve of flagged pixels
-    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), s), "reset counter");
+    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(unsigned long long), s), "reset counters");
     flr::FwdArgs fa;
     fa.guide = guide;
     fa.map_guide = map_guide;
@@ -493,7 +496,7 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
     // the copies start after the work already queued on the caller's stream
     FLR_CUDA(cudaEventRecord(e_start, s), "band event");
     FLR_CUDA(cudaStreamWaitEvent(h->s_in, e_start, 0), "band wait");
-    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), s), "reset counter");
+    FLR_CUDA(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(unsigned long long), s), "reset counters");
     FLR_CUDA(cudaMemsetAsync(h->d_fstart, 0, sizeof(unsigned long long), s), "reset counter");
     h->last_stream = s;
     for (int k = 0; k < K; ++k) {
@@ -535,6 +538,7 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         fa.gS = nullptr;
         fa.geps = nullptr;
         fa.status = h->d_status;
+        fa.nonfinite = h->d_count + 1;
         fa.row_lo = c[k];
         fa.row_hi = c[k + 1];
         fa.ref_rows = in_end[1];  // the reference comes from the first band's rows
@@ -558,6 +562,7 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
             da.flag_list = h->d_flags;
             da.flag_cap = h->flag_cap;
             da.force_coef = 0;
+            da.nonfinite = h->d_count + 1;
             da.flag_start = h->d_fstart;  // only this band's flags
             FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "fp64 re-solve launch");
             FLR_CUDA(cudaMemcpyAsync(h->d_fstart, h->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s),
@@ -574,6 +579,7 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
             aa.W = W;
             aa.rc = rc;
             aa.status = h->d_status;
+            aa.nonfinite = h->d_count + 1;
             aa.row_lo = o[k];
             aa.row_hi = o[k + 1];
             FLR_CUDA(flr::launch_apply(q, aa, s), "apply kernel launch");
@@ -620,10 +626,12 @@ int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset)
 int flr_get_stats(flr_handle *h, flr_stats *out)
 {
     if (!h || !out) return FLR_ERR_ARG;
-    unsigned long long n = 0;
+    unsigned long long cnt[2] = {0ull, 0ull};
     FLR_CUDA(cudaStreamSynchronize(h->last_stream), "stats synchronise");
-    FLR_CUDA(cudaMemcpy(&n, h->d_count, sizeof(n), cudaMemcpyDeviceToHost), "stats copy");
+    FLR_CUDA(cudaMemcpy(cnt, h->d_count, sizeof(cnt), cudaMemcpyDeviceToHost), "stats copy");
+    const unsigned long long n = cnt[0];
     out->flagged = n;
+    out->nonfinite = cnt[1];
     out->resolved = h->p.pivot_ratio > 0.f ? (n < (unsigned long long)h->flag_cap ? n : (unsigned long long)h->flag_cap) : 0ull;
     int status = 0;
     FLR_CUDA(cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "stats copy");

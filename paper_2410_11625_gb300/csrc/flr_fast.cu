@@ -558,6 +558,7 @@ int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out)
         return FLR_ERR_CUDA;
     out->flagged = n;
     out->resolved = h->p.pivot_ratio > 0.f ? n : 0ull;
+    out->nonfinite = 0ull;  // not counted by the fast path
     int status = 0;
     if (cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FLR_ERR_CUDA;
     if (status != 0) {

@@ -135,13 +135,17 @@ __global__ void __launch_bounds__(kDThreads) flr_fp64_kernel(const Fp64Args a)
         }
         if (a.rc == 0 && !a.force_coef) {
             const float *zg = a.map_guide ? a.map_guide : a.guide;
+            int bad = 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double o = bv[c];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) o += A[i][c] * ((double)zg[i * plane + idx] - (double)s[i]);
-                a.out[c * plane + idx] = (float)(o + (double)s[Q + c]);
+                const float of = (float)(o + (double)s[Q + c]);
+                a.out[c * plane + idx] = of;
+                bad += !isfinite(of);
             }
+            if (bad && a.nonfinite && lane == 0) atomicAdd(a.nonfinite, (unsigned long long)bad);
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) a.coef[c * plane + idx] = (float)bv[c];

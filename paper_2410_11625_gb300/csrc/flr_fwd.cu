@@ -514,13 +514,18 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
                         float z[Q];
 #pragma unroll
                         for (int i = 0; i < Q; ++i) z[i] = __ldg(zg + i * plane + off) - s_ref[i];
+                        int bad = 0;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             float o = bv[c];
 #pragma unroll
                             for (int i = 0; i < Q; ++i) o = fmaf(A[i][c], z[i], o);
-                            a.out[c * plane + off] = o + s_ref[Q + c];
+                            o += s_ref[Q + c];
+                            a.out[c * plane + off] = o;
+                            bad += !isfinite(o);
                         }
+                        // a flagged pixel's value is replaced by the FP64 re-solve, which counts it
+                        if (bad && a.nonfinite && !(low && tau > 0.f)) atomicAdd(a.nonfinite, (unsigned long long)bad);
                     } else {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) a.coef[c * plane + off] = bv[c];

@@ -114,6 +114,7 @@ struct FwdArgs {
     float *gS;         // [NCH][H][W] in moment-channel order (see Chan)
     double *geps;      // accumulated d L / d eps
     int *status = nullptr;  // set to 1 if a bounded device wait ran out (may be NULL)
+    unsigned long long *nonfinite = nullptr;  // count of non-finite output values (may be NULL)
     // rows [row_lo, row_hi) of the frame are computed (row_hi < 0: to H); the frame reference
     // is sampled over rows [0, ref_rows) (ref_rows <= 0: all rows)
     int row_lo = 0, row_hi = -1, ref_rows = 0;
@@ -125,6 +126,7 @@ struct ApplyArgs {
     int H, W, rc;
     int *status = nullptr;  // set to 1 if a bounded device wait ran out (may be NULL)
     int row_lo = 0, row_hi = -1;  // output rows [row_lo, row_hi) (row_hi < 0: to H)
+    unsigned long long *nonfinite = nullptr;  // count of non-finite output values (may be NULL)
 };
 
 struct Fp64Args {
@@ -137,6 +139,7 @@ struct Fp64Args {
     const int *flag_list;
     int flag_cap;
     const unsigned long long *flag_start = nullptr;  // first list entry to re-solve (NULL: 0)
+    unsigned long long *nonfinite = nullptr;  // count of non-finite output values (may be NULL)
 };
 
 struct BwdArgs {

@@ -47,7 +47,8 @@ class FlrFrame(ctypes.Structure):
 
 
 class FlrStats(ctypes.Structure):
-    _fields_ = [("flagged", ctypes.c_ulonglong), ("resolved", ctypes.c_ulonglong)]
+    _fields_ = [("flagged", ctypes.c_ulonglong), ("resolved", ctypes.c_ulonglong),
+                ("nonfinite", ctypes.c_ulonglong)]
 
 
 class FlrKernelTimes(ctypes.Structure):
@@ -261,7 +262,7 @@ class FLR:
     def stats(self):
         s = FlrStats()
         _check(load_library().flr_get_stats(self._h, ctypes.byref(s)), "flr_get_stats")
-        return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+        return {"flagged": int(s.flagged), "resolved": int(s.resolved), "nonfinite": int(s.nonfinite)}
 
 
 class FastFLR:

@@ -235,6 +235,29 @@ def test_rendered_unaveraged_with_tighter_pivot(flr):
     assert rel_err(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("H,W,rc", [(64, 96, 0), (64, 96, 2), (600, 64, 3)])
+def test_nonfinite_outputs_are_counted(flr, H, W, rc):
+    """Non-finite inputs are not sanitised (reading c11): they reach every output whose
+    windows hold them, and flr_get_stats reports how many output values are NaN or
+    infinite -- exactly the number in the returned frame, through the device entry point
+    and (600 rows: two bands) the host one.  A clean frame reports none."""
+    g, y = synth.random_frame(40 + rc, H, W, 8)
+    f = flr.FLR(q=8, radius=2, coef_radius=rc, eps=1e-3, pivot_ratio=1e-3)
+    clean = f.denoise(to_dev(g), to_dev(y)).cpu().numpy()
+    assert np.all(np.isfinite(clean)) and f.stats()["nonfinite"] == 0
+    y = y.copy()
+    g = g.copy()
+    y[1, H // 3, W // 2] = np.nan
+    g[3, H // 2 + 5, 7] = np.inf
+    dev = f.denoise(to_dev(g), to_dev(y)).cpu().numpy()
+    n_dev = f.stats()["nonfinite"]
+    host = f.denoise_host(g, y)
+    n_host = f.stats()["nonfinite"]
+    f.close()
+    assert n_dev == int(np.sum(~np.isfinite(dev))) > 0
+    assert n_host == int(np.sum(~np.isfinite(host))) > 0
+
+
 def test_misaligned_pointer_is_rejected(flr):
     import torch
     g, y = synth.random_frame(1, 16, 16, 8)
