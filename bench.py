@@ -148,7 +148,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """Rank, world size and local rank from the torchrun environment; for N > 1 one process
+    group (NCCL on the GPUs; the CPU tests use gloo).  It carries only the barrier and the
+    max-reduce of the timed region: the replicas share no data."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -157,9 +160,17 @@ def dist_setup(n_gpus):
         raise SystemExit(f"--gpus {n_gpus} but WORLD_SIZE={world}: launch N>1 with torchrun")
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
+
+
+def frame_seeds(rank):
+    """Scene seeds of a rank's rotating frames: every replica renders its own frames."""
+    return [1 + N_FRAMES * rank + i for i in range(N_FRAMES)]
 
 
 def reduce_max(x, world):
@@ -167,7 +178,8 @@ def reduce_max(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -318,7 +330,7 @@ def run_ours(args):
     build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    frames = [synth.render(1 + N_FRAMES * rank + i, H, W) for i in range(N_FRAMES)]
+    frames = [synth.render(seed, H, W) for seed in frame_seeds(rank)]
     dev_frames = [(torch.from_numpy(g).to(dev), torch.from_numpy(y).to(dev)) for g, y in frames]
     host_frames = [(torch.from_numpy(g).pin_memory(), torch.from_numpy(y).pin_memory()) for g, y in frames]
     out = torch.empty((3, H, W), dtype=torch.float32, device=dev)
