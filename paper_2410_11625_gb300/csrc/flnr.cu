@@ -64,15 +64,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Convolution (stride 1, zero padding KS/2) as an implicit GEMM on the tensor cores.
-// x [N][H][W][CIN] bf16, w [taps][COUT][CIN] bf16, bias [COUT] fp32.
-// Output: OUTM 0 -> y [N][H][W][ystride] bf16 at channel offset 0 (ACT 1 = ReLU);
-//         OUTM 1 -> yf planar fp32 [N][8][H][W], sigmoid of channels 0..7.
-// MASK: multiply the result by (mask > 0), mask [N][H][W][COUT] bf16 (the ReLU of the layer
-// input, for input gradients).
-// CA > 0: the input is the concatenation of the nearest 2x upsampling of x [N][H/2][W/2][CA]
-// (channels 0..CA-1) and x2 [N][H][W][CIN-CA] (the rest), formed while staging.
-// POOL: also writes yp [N][H/2][W/2][COUT], the 2x2 average of the bf16 outputs (H, W even).
+// Arguments of the convolution kernels (stride 1, zero padding KS/2, implicit GEMM on the
+// tensor cores).  x [N][H][W][CIN] bf16, w [taps][COUT][CIN] bf16, bias [COUT] fp32.  The
+// kernels' template parameters select the epilogue:
+//   OUTM 0 -> y [N][H][W][ystride] bf16 at channel offset 0 (ACT 1 = ReLU);
+//   OUTM 1 -> yf planar fp32 [N][8][H][W], sigmoid of channels 0..7;
+//   MASK   -> the result times (mask > 0), mask [N][H][W][COUT] bf16 (the ReLU of the
+//             layer input, for input gradients);
+//   POOL   -> also yp [N][H/2][W/2][COUT], the 2x2 average of the bf16 outputs (H, W even).
+// The decoder kernel reads x as the half-resolution map [N][H/2][W/2][CA] and x2 as the
+// skip [N][H][W][CIN-CA] of the concatenated input up2(x) ++ x2.
 struct ConvArgs {
     const bf16 *x, *w, *mask;
     const float *bias;
@@ -85,11 +86,13 @@ struct ConvArgs {
     int *status;  // tensor-core path: set to FLNR_STATUS_TIMEOUT if a completion wait ran out
 };
 
-// Persistent CTAs: the weights are staged in shared memory once per CTA; the CTA then walks
-// tiles of TH = 2 * WARPS rows by 16 pixels, the next tile's input (with halo) loading by
-// cp.async while the current one is computed.  Warp w owns rows 2w, 2w+1 of the tile: two
-// m16 fragments (16 pixels of a row each) times COUT/8 n8 fragments.
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA, bool POOL, int WARPS>
+// The input-gradient convolution of the backward pass (warp-level mma.sync): persistent
+// CTAs stage the weights in shared memory once; a CTA then walks tiles of TH = 2 * WARPS
+// rows by 16 pixels, the next tile's input (with halo) loading by cp.async while the
+// current one is computed.  Warp w owns rows 2w, 2w+1 of the tile: two m16 fragments (16
+// pixels of a row each) times COUT/8 n8 fragments.  Output: bf16 NHWC at channel offset 0,
+// times (mask > 0) when MASK.
+template <int CIN, int COUT, int KS, bool MASK, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
 {
     constexpr int NTH = WARPS * 32, TH = 2 * WARPS, TW = 16, P = KS / 2;
@@ -114,15 +117,7 @@ __global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
             const int pix = i / C8, c8 = i % C8;
             const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
             const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const bf16 *src = a.x;
-            if (in) {
-                if (CA > 0 && c8 < CA / 8)
-                    src = a.x + (((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2) * CA + c8 * 8;
-                else if (CA > 0)
-                    src = a.x2 + (((size_t)n * a.H + yy) * a.W + xx) * (CIN - CA) + (c8 - CA / 8) * 8;
-                else
-                    src = a.x + (((size_t)n * a.H + yy) * a.W + xx) * CIN + c8 * 8;
-            }
+            const bf16 *src = in ? a.x + (((size_t)n * a.H + yy) * a.W + xx) * CIN + c8 * 8 : a.x;
             cp_async16(sx + pix * CS + c8 * 8, src, in);
         }
     };
@@ -180,7 +175,6 @@ __global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 const int c = nt * 8 + 2 * q;
-                float ps0 = 0.f, ps1 = 0.f;  // pooled sums (POOL)
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt) {
                     const int yy = ty0 + 2 * warp + mt;
@@ -188,35 +182,12 @@ __global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
                     const size_t pix = img + (size_t)yy * a.W + xx;
                     float v0 = acc[mt][nt][2 * half] + (c < a.nbias ? a.bias[c] : 0.f);
                     float v1 = acc[mt][nt][2 * half + 1] + (c + 1 < a.nbias ? a.bias[c + 1] : 0.f);
-                    if (ACT == 1) {
-                        v0 = fmaxf(v0, 0.f);
-                        v1 = fmaxf(v1, 0.f);
-                    }
                     if (MASK && in) {
                         const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + c);
                         if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
                         if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
                     }
-                    if (OUTM == 0) {
-                        const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
-                        if (in) *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ystride + c) = o;
-                        ps0 += __bfloat162float(o.x);
-                        ps1 += __bfloat162float(o.y);
-                    } else if (c < 8 && in) {
-                        const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
-                        a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v0));
-                        a.yf[((size_t)n * 8 + c + 1) * hw + off] = 1.f / (1.f + expf(-v1));
-                    }
-                }
-                if (POOL) {
-                    // pixel pairs (g, g + 1) sit in lanes 4 apart
-                    ps0 += __shfl_xor_sync(0xffffffffu, ps0, 4);
-                    ps1 += __shfl_xor_sync(0xffffffffu, ps1, 4);
-                    const int yy = ty0 + 2 * warp;
-                    if ((g & 1) == 0 && yy < a.H && xx < a.W) {
-                        const size_t pp = ((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2;
-                        *reinterpret_cast<__nv_bfloat162 *>(a.yp + pp * COUT + c) = __floats2bfloat162_rn(0.25f * ps0, 0.25f * ps1);
-                    }
+                    if (in) *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ystride + c) = __floats2bfloat162_rn(v0, v1);
                 }
             }
         }
@@ -1308,13 +1279,13 @@ int egrid(size_t n) { return (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 81
 
 // ---------------------------------------------------------------------------------------
 // Launch helpers for the template instantiations the network uses.
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK, int CA = 0, bool POOL = false, int WARPS = 8>
+template <int CIN, int COUT, int KS, bool MASK, int WARPS = 8>
 cudaError_t conv_launch(const ConvArgs &a, cudaStream_t st)
 {
     constexpr int P = KS / 2, TH = 2 * WARPS, TW = 16;
     constexpr size_t smem = sizeof(bf16) * ((size_t)KS * KS * COUT * (CIN + 8) + 2 * (size_t)(TH + 2 * P) * (TW + 2 * P) * (CIN + 8));
     static_assert(smem <= 227 * 1024, "conv tile does not fit in shared memory");
-    auto kern = conv_kernel<CIN, COUT, KS, ACT, OUTM, MASK, CA, POOL, WARPS>;
+    auto kern = conv_kernel<CIN, COUT, KS, MASK, WARPS>;
     static int per_sm = 0, n_sm = 0;  // occupancy of this instantiation, computed once
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1755,52 +1726,52 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
     sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W);
     FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, 8, ns, st)));
     bgrad(n->gA, (long long)P, 16, 8, 11);
-    FLNR_TRY((conv_launch<16, 16, 1, 0, 0, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((conv_launch<16, 16, 1, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
     FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, ns, st)));
     bgrad(n->gB, (long long)P, 16, 16, 10);
-    FLNR_TRY((conv_launch<16, 16, 3, 0, 0, true>({n->gB, n->wd[10], n->d0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((conv_launch<16, 16, 3, true>({n->gB, n->wd[10], n->d0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
     // decoder level 0
     FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, ns, st)));
     bgrad(n->gA, (long long)P, 16, 16, 9);
-    FLNR_TRY((conv_launch<16, 16, 3, 0, 0, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((conv_launch<16, 16, 3, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
     upcat_kernel<<<egrid(P * 6), 256, 0, st>>>(n->d1, n->f0, n->c0, N, H, W, 32, 16);  // d0a's input
     FLNR_TRY(cudaGetLastError());
     FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, ns, st)));
     bgrad(n->gB, (long long)P, 16, 16, 8);
-    FLNR_TRY((conv_launch<16, 48, 3, 0, 0, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, st)));
+    FLNR_TRY((conv_launch<16, 48, 3, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, st)));
     upcat_bwd_kernel<<<egrid(P * 48), 256, 0, st>>>(n->gC, n->d1, n->gLo, n->gskip0, N, H, W, 32, 16);  // gLo = dz(d1b)
     // decoder level 1 (H/2)
     const size_t P2 = P / 4;
     FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, ns, st)));
     bgrad(n->gLo, (long long)P2, 32, 32, 7);
-    FLNR_TRY((conv_launch<32, 32, 3, 0, 0, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
+    FLNR_TRY((conv_launch<32, 32, 3, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
     upcat_kernel<<<egrid(P2 * 12), 256, 0, st>>>(n->f2, n->f1, n->c1, N, H2, W2, 64, 32);  // d1a's input
     FLNR_TRY(cudaGetLastError());
     FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, ns, st)));
     bgrad(n->gA, (long long)P2, 32, 32, 6);
-    FLNR_TRY((conv_launch<32, 96, 3, 0, 0, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, st)));
+    FLNR_TRY((conv_launch<32, 96, 3, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, st)));
     upcat_bwd_kernel<<<egrid(P2 * 96), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
     // encoder level 2 (H/4)
     const size_t P4 = P / 16;
     FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gLo, gw(5), N, H4, W4, 64, 64, ns, st)));
     bgrad(n->gLo, (long long)P4, 64, 64, 5);
-    FLNR_TRY((conv_launch<64, 64, 3, 0, 0, true>({n->gLo, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H4, W4, 64}, st)));
+    FLNR_TRY((conv_launch<64, 64, 3, true>({n->gLo, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H4, W4, 64}, st)));
     FLNR_TRY((wgrad_launch<32, 64, 3>(n->p1, n->gA, gw(4), N, H4, W4, 32, 64, ns, st)));
     bgrad(n->gA, (long long)P4, 64, 64, 4);
-    FLNR_TRY((conv_launch<64, 32, 3, 0, 0, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H4, W4, 32}, st)));
+    FLNR_TRY((conv_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H4, W4, 32}, st)));
     pool_bwd_kernel<<<egrid(P2 * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gLo, N, H2, W2, 32);  // dz(e1b)
     // encoder level 1 (H/2)
     FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gLo, gw(3), N, H2, W2, 32, 32, ns, st)));
     bgrad(n->gLo, (long long)P2, 32, 32, 3);
-    FLNR_TRY((conv_launch<32, 32, 3, 0, 0, true>({n->gLo, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
+    FLNR_TRY((conv_launch<32, 32, 3, true>({n->gLo, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
     FLNR_TRY((wgrad_launch<16, 32, 3>(n->p0, n->gA, gw(2), N, H2, W2, 16, 32, ns, st)));
     bgrad(n->gA, (long long)P2, 32, 32, 2);
-    FLNR_TRY((conv_launch<32, 16, 3, 0, 0, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 16}, st)));
+    FLNR_TRY((conv_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 16}, st)));
     pool_bwd_kernel<<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
     // input projection (H)
     FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, ns, st)));
     bgrad(n->gLo, (long long)P, 16, 16, 1);
-    FLNR_TRY((conv_launch<16, 16, 1, 0, 0, true>({n->gLo, n->wd[1], n->a0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((conv_launch<16, 16, 1, true>({n->gLo, n->wd[1], n->a0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
     FLNR_TRY((wgrad_launch<16, 16, 3>(n->x0, n->gA, gw(0), N, H, W, 11, 16, ns, st)));
     bgrad(n->gA, (long long)P, 16, 16, 0);
     return cudaGetLastError() == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
@@ -1856,9 +1827,9 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
         }
     } else if (op == FLNR_OP_DGRAD) {
         if (mask)
-            FLNR_TRY((conv_launch<CO, CI, KS, 0, 0, true>({(const bf *)a, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+            FLNR_TRY((conv_launch<CO, CI, KS, true>({(const bf *)a, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
         else
-            FLNR_TRY((conv_launch<CO, CI, KS, 0, 0, false>({(const bf *)a, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+            FLNR_TRY((conv_launch<CO, CI, KS, false>({(const bf *)a, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
     } else {
         FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, (const bf *)b, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->n_sm, st)));
         bias_grad_kernel<<<64, 256, 0, st>>>((const bf *)b, n->g + n->poff[l][1], P, CO, d.cout);
