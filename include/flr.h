@@ -145,6 +145,20 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
 int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
                      const float *radiance, float *out, int H, int W, void *stream);
 
+/* Most row bands flr_denoise_host cuts a frame into. */
+#define FLR_HOST_MAX_BANDS 8
+
+/*
+ * The row bands flr_denoise_host uses for a frame of H rows (host arithmetic only, no
+ * device call; not a paper operation: it exposes the host path's plan to tests).  Returns
+ * K >= 1 and fills K + 1 entries of each array: band k computes the models of rows
+ * [c[k], c[k+1]), copies in input rows [in_end[k], in_end[k+1]) (so rows below
+ * in_end[k+1] = min(H, c[k+1] + radius) are on the device when it runs) and writes output
+ * rows [out_lo[k], out_lo[k+1]) (c[k] - coef_radius inside the frame).  The arrays need
+ * FLR_HOST_MAX_BANDS + 1 entries.  Errors: FLR_ERR_ARG.
+ */
+int flr_host_band_plan(int H, int radius, int coef_radius, int *c, int *in_end, int *out_lo);
+
 /*
  * Statistics of the last flr_denoise on this handle.  Waits for that call's stream.
  * Returns FLR_ERR_TIMEOUT (after filling *out) if a kernel of an earlier call on this

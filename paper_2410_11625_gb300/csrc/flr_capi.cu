@@ -104,6 +104,26 @@ int choose_segment_rows(int H, int W, int r, int n_sm)
     return best_th;
 }
 
+// Row bands of the host entry point (see flr_denoise_host): band k computes the models of
+// rows [c_k, c_k+1), needs input rows below in_end_k+1 (copied in as rows [in_end_k,
+// in_end_k+1)) and writes output rows [o_k, o_k+1).  Returns the number of bands K; the
+// arrays hold K + 1 entries (K <= FLR_HOST_MAX_BANDS).  Bands of about 360 rows: a band's
+// kernels lose efficiency as it gets shorter (each segment re-fills its window and a short
+// band fills fewer CTAs), while fewer bands expose more of the first copy; at 1920x1080
+// three bands measured 0.74 ms per frame against 0.96 (one), 0.79 (two), 0.75 (four) and
+// 0.93 (eight).
+int band_plan(int H, int r, int rc, int *c, int *in_end, int *o)
+{
+    const int K = std::max(1, std::min(FLR_HOST_MAX_BANDS, (H + 180) / 360));
+    for (int k = 0; k <= K; ++k) c[k] = k == K ? H : (int)((long long)H * k / K) / flr::kB * flr::kB;
+    for (int k = 0; k <= K; ++k) {
+        in_end[k] = std::min(H, c[k] + r);
+        o[k] = (k == 0 || k == K || rc == 0) ? c[k] : std::max(0, c[k] - rc);
+    }
+    in_end[0] = 0;
+    return K;
+}
+
 int validate_params(const flr_params *p)
 {
     if (!p) return FLR_ERR_ARG;
@@ -458,12 +478,9 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
     // overlaps the kernels of band k + 1 (separate copy-in and copy-out streams).  Band k's
     // kernels compute the models of rows [c_k, c_k+1) from input rows up to c_k+1 + r and
     // apply the averaged models to rows [c_k - rc, c_k+1 - rc); each band has its own segment
-    // height.  One band (small frames) is exactly flr_denoise.  Bands of about 360 rows: a
-    // band's kernels lose efficiency as it gets shorter (each segment re-fills its window
-    // and a short band fills fewer CTAs), while fewer bands expose more of the first copy;
-    // at 1920x1080 three bands measured 0.74 ms per frame against 0.96 (one), 0.79 (two),
-    // 0.75 (four) and 0.93 (eight).
-    const int K = std::max(1, std::min(8, (H + 180) / 360));
+    // height.  One band (small frames) is exactly flr_denoise.  The bands: band_plan.
+    int c[FLR_HOST_MAX_BANDS + 1], in_end[FLR_HOST_MAX_BANDS + 1], o[FLR_HOST_MAX_BANDS + 1];
+    const int K = band_plan(H, r, rc, c, in_end, o);
     if (K == 1) {
         FLR_CUDA(cudaMemcpyAsync(dg, guide, sizeof(float) * q * px, cudaMemcpyHostToDevice, s), "h2d guide");
         if (map_guide)
@@ -481,18 +498,11 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         FLR_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "copy stream");
         FLR_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "copy stream");
         FLR_CUDA(cudaMalloc(&h->d_fstart, sizeof(unsigned long long)), "re-solve index");
-        h->band_ev.resize(2 * 8 + 1);
+        h->band_ev.resize(2 * FLR_HOST_MAX_BANDS + 1);
         for (auto &e : h->band_ev) FLR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "band event");
     }
-    std::vector<int> c(K + 1), in_end(K + 1), o(K + 1);
-    for (int k = 0; k <= K; ++k) c[k] = k == K ? H : (int)((long long)H * k / K) / flr::kB * flr::kB;
-    for (int k = 0; k <= K; ++k) {
-        in_end[k] = std::min(H, c[k] + r);
-        o[k] = (k == 0 || k == K || rc == 0) ? c[k] : std::max(0, c[k] - rc);
-    }
-    in_end[0] = 0;
     const size_t plane_b = px * sizeof(float);
-    cudaEvent_t e_start = h->band_ev[16];
+    cudaEvent_t e_start = h->band_ev[2 * FLR_HOST_MAX_BANDS];
     // the copies start after the work already queued on the caller's stream
     FLR_CUDA(cudaEventRecord(e_start, s), "band event");
     FLR_CUDA(cudaStreamWaitEvent(h->s_in, e_start, 0), "band wait");
@@ -598,6 +608,12 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
     FLR_CUDA(cudaStreamSynchronize(h->s_out), "host-path synchronise");
     FLR_CUDA(cudaStreamSynchronize(s), "host-path synchronise");
     return FLR_OK;
+}
+
+int flr_host_band_plan(int H, int radius, int coef_radius, int *c, int *in_end, int *out_lo)
+{
+    if (H <= 0 || radius < 0 || coef_radius < 0 || !c || !in_end || !out_lo) return FLR_ERR_ARG;
+    return band_plan(H, radius, coef_radius, c, in_end, out_lo);
 }
 
 int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset)

@@ -21,12 +21,13 @@ EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoi
            "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
            "flr_fast_denoise", "flr_fast_get_stats", "flr_denoise_batch", "flr_fast_reserve_batch",
            "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest",
-           "flr_mbarrier_selftest",
+           "flr_mbarrier_selftest", "flr_host_band_plan",
            "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
            "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_get_grads",
            "flnr_adam_step", "flnr_l1_loss", "flnr_layer", "flnr_status")
 BATCH_TIMEOUT = 1
 FLAG_TIMING = 1
+HOST_MAX_BANDS = 8  # FLR_HOST_MAX_BANDS
 
 
 class FlrParams(ctypes.Structure):
@@ -89,6 +90,7 @@ def load_library():
     lib.flr_reserve.argtypes = [vp, ip, ip]
     lib.flr_denoise.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_host.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_host_band_plan.argtypes = [ip, ip, ip, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.flr_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
     lib.flr_get_kernel_times.argtypes = [vp, ctypes.POINTER(FlrKernelTimes), ip]
     lib.flr_backward.argtypes = [vp, fp, fp, fp, fp, fp, fp, fp, vp, ip, ip, vp]
@@ -338,6 +340,17 @@ class FastFLR:
         s = FlrStats()
         _check(load_library().flr_fast_get_stats(self._h, ctypes.byref(s)), "flr_fast_get_stats")
         return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+
+
+def host_band_plan(H, radius, coef_radius):
+    """The row bands flr_denoise_host uses for H rows: lists c, in_end, out_lo of K + 1
+    entries (host arithmetic only; see flr_host_band_plan)."""
+    import numpy as np
+    c, e, o = (np.zeros(HOST_MAX_BANDS + 1, np.int32) for _ in range(3))
+    K = load_library().flr_host_band_plan(int(H), int(radius), int(coef_radius), c.ctypes.data, e.ctypes.data,
+                                          o.ctypes.data)
+    _check(min(K, 0), "flr_host_band_plan")
+    return c[:K + 1].tolist(), e[:K + 1].tolist(), o[:K + 1].tolist()
 
 
 def mbarrier_selftest(ctas=4, timeout_ns=20_000_000):

@@ -64,3 +64,26 @@ def test_null_arguments_are_rejected(lib):
     assert lib.flr_reserve(None, 8, 8) == -1
     assert lib.flr_get_stats(None, None) == -1
     assert lib.flr_get_kernel_times(None, None, 0) == -1
+
+
+@pytest.mark.parametrize("r,rc", [(8, 8), (8, 0), (5, 5), (16, 3), (0, 0), (2, 16)])
+def test_host_band_plan_covers_every_row_once(lib, r, rc):
+    """flr_denoise_host's bands (host arithmetic only): the input copies and the output
+    bands each partition the rows; a band's models need only input rows already copied;
+    its averaged outputs need only models of earlier or current bands (below c[k+1])."""
+    from paper_2410_11625_gb300 import flr
+    for H in (1, 96, 539, 540, 600, 1080, 1100, 1440, 2160, 4320):
+        c, e, o = flr.host_band_plan(H, r, rc)
+        K = len(c) - 1
+        assert K == max(1, min(flr.HOST_MAX_BANDS, (H + 180) // 360))
+        assert c[0] == 0 and c[K] == H and all(c[k] < c[k + 1] for k in range(K))
+        assert all(c[k] % 4 == 0 for k in range(K))  # segment rows stay multiples of kB
+        assert e[0] == 0 and e[K] == H and all(e[k] <= e[k + 1] for k in range(K))
+        assert o[0] == 0 and o[K] == H and all(o[k] < o[k + 1] for k in range(K))
+        for k in range(K):
+            assert e[k + 1] >= min(H, c[k + 1] + r)   # inputs of band k's windows
+            assert o[k + 1] <= e[k + 1]               # its map-guide rows
+            if k + 1 < K:
+                assert o[k + 1] + rc <= c[k + 1]      # averaging windows of its outputs
+            if rc == 0:
+                assert o[k] == c[k]
