@@ -67,11 +67,13 @@ class Trainer:
         self.B, self.c, self.lr = batch, crop, lr
         self.net = _flnr.FLNR(batch * crop * crop, weights)
         # one FLR handle and stream per crop: the crops' FLR passes and adjoints (small
-        # grids each) run concurrently, and no two of them share a handle's workspace
+        # grids each) run concurrently, and no two of them share a handle's workspace.
+        # These handles only ever see crops, so their buffers never move once the step is
+        # captured in a graph; `flr` is a separate handle for evaluation at other sizes.
         self.flrs = [_flr.FLR(q=8, radius=radius, eps=eps) for _ in range(batch)]
         for f in self.flrs:
             f.reserve(crop, crop)
-        self.flr = self.flrs[0]
+        self.flr = _flr.FLR(q=8, radius=radius, eps=eps)
         self.streams = [torch.cuda.Stream() for _ in range(batch)]
         opt = dict(dtype=torch.float32, device=device)
         self.x_host = torch.empty((batch, 11, crop, crop), dtype=torch.float32).pin_memory()
