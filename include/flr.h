@@ -43,7 +43,8 @@ typedef enum flr_status {
     FLR_ERR_CUDA = -3,        /* a CUDA runtime call failed (see flr_last_cuda_error) */
     FLR_ERR_UNSUPPORTED = -4, /* q or a radius outside what this build supports */
     FLR_ERR_NOMEM = -5,       /* a workspace allocation failed */
-    FLR_ERR_TIMEOUT = -6      /* a device-side wait ran out of time (flr_fast_batch_status) */
+    FLR_ERR_TIMEOUT = -6      /* a bounded device-side wait ran out of time (reported by
+                                 flr_get_stats, flr_fast_batch_status, flnr_status) */
 } flr_status;
 
 /* Largest guide count and window radii the kernels are built for. */
