@@ -5,9 +5,9 @@ Besides the headline, `rows` reports the other parts of the path: the FLR adjoin
 paper's fast FLR, joint 2x upsampling, batched serving, and FLNR (training on rendered
 crops, PSNR against high-spp references on held-out rooms, 1080p inference time).
 
-One step = one full FLR pass (windowed moments, per-pixel Cholesky solve, FP64 re-solve
-of flagged pixels, coefficient averaging and apply) over one frame whose inputs are
-already in HBM.  Four rendered frames rotate, so every step reads inputs larger than L2.
+One step = one full FLR pass over one frame whose inputs are already in HBM: the fused
+kernel (windowed moments, per-pixel Cholesky solve, coefficient averaging and apply) and
+the FP64 correction of flagged pixels.  Four rendered frames rotate, so every step reads inputs larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,19 +39,27 @@ WORKLOAD = ("FLR forward, 1920x1080, Q=8 rendered guides (albedo RGB, normal xyz
             "1spp albedo-demodulated indirect RGB, r=8, rc=8, eps=1e-3, pivot ratio 1e-3")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES = 152, 128
-FWD_SOURCES = ["paper_2410_11625_gb300/csrc/flr_fwd.cu", "paper_2410_11625_gb300/csrc/flr_internal.cuh"]
-FWD_PROFILE = os.path.join(ROOT, "profiles", "flr_fwd_1080p_r8.txt")
+FWD_SOURCES = ["paper_2410_11625_gb300/csrc/flr_fused.cu", "paper_2410_11625_gb300/csrc/flr_internal.cuh"]
+FWD_PROFILE = os.path.join(ROOT, "profiles", "flr_fused_1080p_r8.txt")
 
 
 def fwd_flops_per_pixel(q: int) -> int:
-    """Algorithmic FP32 flops of the forward kernel per pixel (FMA = 2)."""
+    """Algorithmic FP32 flops per pixel of the per-pixel model (FMA = 2): products, window
+    sums, centring, Cholesky, three triangular solves and the bias."""
     products = q * (q + 1) // 2 + 3 * q                 # x x^T upper triangle and x y^T
     box_sums = 4 * (products + q + 3)                   # 2 passes x (add + subtract)
     centring = (q + 3) + 2 * (q * (q + 1) // 2 + 3 * q) + q
     chol = 2 * (q * (q - 1) // 2 + sum((q - 1 - j) * j for j in range(q))) + q * (q - 1) // 2 + 2 * q
     solves = 6 * q * q                                  # 3 RHS x (forward + backward)
-    bias = 3 * 2 * q + 3 * (2 * q + 2)                  # b = mu_y - a^T mu, shift re-expression
+    bias = 3 * 2 * q                                    # b = mu_y - a^T mu
     return products + box_sums + centring + chol + solves + bias
+
+
+def path_flops_per_pixel(q: int, rc: int) -> int:
+    """The whole FLR path per output pixel: the model, then (rc > 0) the box average of its
+    3 (q + 1) coefficients (2 passes x add + subtract), and the apply (3 x (q + 1) FMA)."""
+    average = 4 * 3 * (q + 1) if rc > 0 else 0
+    return fwd_flops_per_pixel(q) + average + 2 * 3 * (q + 1)
 
 
 def frame_bytes(q: int) -> int:
@@ -76,8 +84,8 @@ def sha_of(paths):
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the forward kernel from the committed ncu summary, if the
-    kernel source has not changed since it was captured; else None."""
+    """DRAM bytes per launch of the fused forward kernel from the committed ncu summary, if
+    the kernel source has not changed since it was captured; else None."""
     try:
         text = open(FWD_PROFILE).read()
     except OSError:
@@ -198,6 +206,47 @@ def cpu_oracle_band(frame, rows):
     t = time.perf_counter()
     oracle.flr_forward(g[:, y0:y0 + rows], y[:, y0:y0 + rows], R, EPS, coef_radius=RC)
     return time.perf_counter() - t
+
+
+def cpu_baseline(frame):
+    """The FP64 oracle on whole 1080p frames: all host cores (median of 5 runs after one
+    warm-up) and one core (median of 3); about 25 s of CPU work on 16 Arm cores."""
+    import oracle
+    n_all = os.cpu_count() or 1
+    oracle.set_threads(n_all)
+    cpu_oracle_band(frame, H)
+    t_all = statistics.median(cpu_oracle_band(frame, H) for _ in range(5))
+    oracle.set_threads(1)
+    t_one = statistics.median(cpu_oracle_band(frame, H) for _ in range(3))
+    oracle.set_threads(n_all)
+    return {"value": round(t_all * 1e3, 2), "unit": UNIT, "cores": n_all, "kind": "oracle",
+            "sample": f"FP64 oracle on whole {W}x{H} frames (r=8, rc=8): median of 5 runs on {n_all} threads",
+            "single_thread": {"value": round(t_one * 1e3, 2), "unit": UNIT, "cores": 1,
+                              "sample": "the same frame, median of 3 runs on one thread"}}
+
+
+def sampled_parity(got, frame, blocks=12, B=32, seed=0):
+    """max relative error (c7 metric) of the timed frame's result against the oracle on
+    sampled B x B blocks (corners, edges, random interior), each computed by the oracle on
+    the block plus its radius-(r + rc) halo, which holds every input its outputs depend on."""
+    import numpy as np
+
+    import oracle
+    g, y = frame
+    rng = np.random.default_rng(seed)
+    halo = R + RC
+    where = [(0, 0), (0, W - B), (H - B, 0), (H - B, W - B)]
+    where += [(int(rng.integers(0, H - B)), int(rng.integers(0, W - B))) for _ in range(blocks - 4)]
+    worst = 0.0
+    for by, bx in where:
+        y0, y1 = max(0, by - halo), min(H, by + B + halo)
+        x0, x1 = max(0, bx - halo), min(W, bx + B + halo)
+        ref = oracle.flr_forward(g[:, y0:y1, x0:x1], y[:, y0:y1, x0:x1], R, EPS, coef_radius=RC)
+        ref = ref[:, by - y0:by - y0 + B, bx - x0:bx - x0 + B]
+        part = np.asarray(got[:, by:by + B, bx:bx + B], np.float64)
+        rms = np.sqrt(np.mean(ref ** 2))
+        worst = max(worst, float(np.max(np.abs(part - ref) / np.maximum(np.abs(ref), 0.01 * rms))))
+    return worst, len(where)
 
 
 def serving_batch(flr, torch, np, dev, stream, n_iter=100):
@@ -414,24 +463,27 @@ def run_ours(args):
     if rank == 0 and "flnr" in want:
         rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps))
 
+    # parity of the timed configuration: the last timed frame against the oracle on blocks
+    f2 = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
+    res = f2.denoise(*dev_frames[0], out=out).cpu().numpy()
+    f2.close()
+    # measured FP32 FMA rate, the denominator of the ALU roofline
+    fma_tflops, fma_ms = flr.fp32_fma_peak(20000)
+
     if rank != 0:
         return
     peaks, peak_src = load_peaks()
+    max_rel, n_blocks = sampled_parity(res, frames[0])
     value = t_ms / (args.steps * world)
     fwd_avg_ms = kt["fwd_ms"] / max(1, kt["fwd_n"])
-    flops = fwd_flops_per_pixel(Q) * H * W
+    flops = path_flops_per_pixel(Q, RC) * H * W
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    nominal = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (fwd_avg_ms * 1e-3) / 1e12
     hbm_peak = float(peaks["hbm_gbs"])
     frame_gbs = frame_bytes(Q) / (value * 1e-3) / 1e9
     traffic = profiled_traffic()
-
-    # CPU baseline: the oracle on a quarter-frame band, scaled to a frame
-    import oracle
-    band = H // 4
-    cpu_s = cpu_oracle_band(frames[0], band)
-    cpu_ms = cpu_s * 1e3 * (H / band)
+    cpu = cpu_baseline(frames[0])
 
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
@@ -445,24 +497,26 @@ def run_ours(args):
         "e2e": {"value": round(e2e_s * 1e3 / (n_e2e * world), 5), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * H * W * (Q + 3), "d2h_bytes_per_step": 4 * H * W * 3,
                 "steps": n_e2e, "api": "flr_denoise_host (page-locked host buffers)"},
-        "roofline": {"bound": "alu", "kernel": "flr_fwd_kernel<8>", "achieved": round(achieved, 3),
-                     "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
+        "roofline": {"bound": "alu", "kernel": "flr_fused_kernel<8,8,8>", "achieved": round(achieved, 3),
+                     "peak": round(fma_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / fma_tflops, 4),
                      "traffic": traffic,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz ({peak_src} max clock)",
-                     "flops_per_pixel": fwd_flops_per_pixel(Q), "avg_launch_ms": round(fwd_avg_ms, 5)},
+                     "peak_source": (f"measured: flr_fp32_fma_peak, independent FP32 FMA chains on every SM "
+                                     f"({fma_ms:.2f} ms run); nominal 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                                     f"= {nominal:.1f}"),
+                     "flops_per_pixel": path_flops_per_pixel(Q, RC), "avg_launch_ms": round(fwd_avg_ms, 5)},
         "hbm": {"algorithmic_bytes_per_frame": frame_bytes(Q), "achieved_gbs": round(frame_gbs, 1),
                 "peak_gbs": hbm_peak, "frac": round(frame_gbs / hbm_peak, 4),
                 "peak_source": f"{peak_src} copy bandwidth"},
-        "cpu_baseline": {"value": round(cpu_ms, 2), "unit": UNIT, "cores": oracle.threads(),
-                         "kind": "oracle",
-                         "sample": f"FP64 oracle on a {W}x{band} row band (r=8, rc=8), scaled x{H / band:g}"},
+        "parity": {"max_rel_err": float(f"{max_rel:.3e}"), "bar": 1e-4, "blocks": n_blocks,
+                   "what": "the timed configuration's result on frame seed 1 vs the FP64 oracle, 32x32 blocks "
+                           "(corners + random) with their radius-16 halo, c7 metric"},
+        "cpu_baseline": cpu,
         "gpu_launches": int(kt["fwd_n"] + kt["fp64_n"] + kt["apply_n"]),
         "flagged_pixels_last_frame": flagged,
     }
     line["kernels"] = {
-        "flr_fwd": {"launches": kt["fwd_n"], "avg_ms": round(kt["fwd_ms"] / max(1, kt["fwd_n"]), 5)},
-        "flr_fp64": {"launches": kt["fp64_n"], "avg_ms": round(kt["fp64_ms"] / max(1, kt["fp64_n"]), 5)},
-        "flr_apply": {"launches": kt["apply_n"], "avg_ms": round(kt["apply_ms"] / max(1, kt["apply_n"]), 5)},
+        "flr_fused": {"launches": kt["fwd_n"], "avg_ms": round(kt["fwd_ms"] / max(1, kt["fwd_n"]), 5)},
+        "flr_fused_fix": {"launches": kt["fp64_n"], "avg_ms": round(kt["fp64_ms"] / max(1, kt["fp64_n"]), 5)},
     }
     line["rows"] = rows
     if clk is not None:

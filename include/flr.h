@@ -400,6 +400,16 @@ int flnr_adam_step(flnr_net *net, float lr, float beta1, float beta2, float eps,
  */
 int flnr_l1_loss(const float *pred, const float *ref, float *grad, float *loss, size_t count, void *stream);
 
+/*
+ * Measured FP32 FMA throughput of the current device, for the roofline of the per-pixel FLR
+ * path, which is bound by the FP32 ALUs (not a paper operation).  Runs `iters` x 16 rounds of
+ * 8 independent FMA chains in 4 x 256 threads per SM, four times, and reports the fastest of
+ * the last three runs: *ms its duration (CUDA events) and *tflops = flops / time, one FMA
+ * counting 2 flops.  Synchronous; allocates and frees one small buffer.
+ * Errors: FLR_ERR_ARG, FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_fp32_fma_peak(int iters, double *tflops, double *ms);
+
 /* Human-readable name of a status code (static storage). */
 const char *flr_status_string(int status);
 

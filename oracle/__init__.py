@@ -61,6 +61,8 @@ def _load():
         lib.flr_oracle_fast.restype = ctypes.c_int
         lib.flr_oracle_threads.argtypes = []
         lib.flr_oracle_threads.restype = ctypes.c_int
+        lib.flr_oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.flr_oracle_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -84,6 +86,11 @@ class OracleError(RuntimeError):
 def threads() -> int:
     """Threads the oracle's parallel loops use."""
     return int(_load().flr_oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's parallel loops from now on (for timing; results do not change)."""
+    _load().flr_oracle_set_threads(int(n))
 
 
 def flr_forward(guide, radiance, radius, eps, coef_radius=0, map_guide=None,

@@ -262,6 +262,17 @@ int flr_oracle_threads(void)
 #endif
 }
 
+/* Set the number of threads of the parallel loops (timing only; no arithmetic depends on it:
+ * every loop writes disjoint outputs). */
+void flr_oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /*
  * FLR backward pass in FP64: the gradient of L = <grad_out, I> with respect to the guides,
  * the map guides, the radiance and eps, for the forward pass above.

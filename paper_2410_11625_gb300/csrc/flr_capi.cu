@@ -1,6 +1,8 @@
 // flr_capi.cu -- the extern "C" boundary of libflr.so (declared in include/flr.h):
-// argument validation, handle and workspace management, and the launch sequence
-//   forward kernel -> FP64 re-solve of flagged pixels -> coefficient averaging + apply.
+// argument validation, handle and workspace management, and the launch sequences
+//   fused forward kernel (moments, solve, averaging, apply) -> FP64 correction of flagged
+//   pixels, for the compiled (q, r, rc) instances with 16-byte rows (flr_fused.cu);
+//   otherwise forward kernel -> FP64 re-solve of flagged pixels -> averaging + apply.
 // No exception and no abort crosses the ABI: every failure is a negative flr_status.
 #include <cuda_runtime.h>
 
@@ -34,6 +36,74 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
+namespace flr {
+namespace host {
+
+// Rows per segment of the forward kernel: minimise (waves of CTAs) x (rows walked,
+// including the 2r warm-up rows of every segment).
+int choose_segment_rows(int H, int W, int r, int n_sm)
+{
+    const int strips = (W + flr::kTW - 1) / flr::kTW;
+    int best_th = H, best_cost = -1;
+    for (int segs = 1; segs <= 256; ++segs) {
+        int th = (H + segs - 1) / segs;
+        th = (th + flr::kB - 1) / flr::kB * flr::kB;
+        const int real_segs = (H + th - 1) / th;
+        const long long waves = ((long long)strips * real_segs + n_sm - 1) / n_sm;
+        const long long cost = waves * (th + 2 * r);
+        if (best_cost < 0 || cost < best_cost) { best_cost = (int)cost; best_th = th; }
+        if (th <= flr::kB) break;
+    }
+    return best_th;
+}
+
+// Launch plan of the fused forward kernel over `rows` output rows: strips of TW columns, and
+// the segment height that minimises (waves of CTAs, one CTA per SM) x (rows walked per
+// segment, including the 2 (r + rc) warm-up rows).
+FusedPlan fused_plan(int rows, int W, int r, int rc, int n_sm)
+{
+    FusedPlan p;
+    p.TW = flr::fused_tile_width(rc);
+    p.strips = (W + p.TW - 1) / p.TW;
+    int best_th = rows;
+    long long best = -1;
+    for (int segs = 1; segs <= 512; ++segs) {
+        int th = (rows + segs - 1) / segs;
+        th = (th + 3) / 4 * 4;
+        const int real = (rows + th - 1) / th;
+        const long long waves = ((long long)p.strips * real + n_sm - 1) / n_sm;
+        const long long cost = waves * (th + 2 * r + 2 * rc);
+        if (best < 0 || cost < best) { best = cost; best_th = th; }
+        if (th <= 4) break;
+    }
+    p.TH = best_th;
+    p.segs = (rows + p.TH - 1) / p.TH;
+    p.cap = (p.TW + 2 * rc) * (p.TH + 2 * rc);
+    return p;
+}
+
+// Whether a call can take the fused path: a compiled instance, rows of 16-byte multiples
+// (TMA), 16-byte aligned images.
+bool fused_ok(const flr_params &p, int W, const void *g, const void *mg, const void *rad, const void *out)
+{
+    return flr::fused_supported(p.q, p.radius, p.coef_radius) && (W % 4) == 0 && aligned16(g) && aligned16(rad) &&
+           aligned16(out) && (!mg || aligned16(mg));
+}
+
+int validate_params(const flr_params *p)
+{
+    if (!p) return FLR_ERR_ARG;
+    if ((p->flags & ~FLR_FLAG_TIMING) != 0u || !(p->eps >= 0.f) || p->radius < 0 || p->coef_radius < 0) return FLR_ERR_ARG;
+    if (p->pivot_ratio != p->pivot_ratio) return FLR_ERR_ARG;
+    if (p->q < 1 || p->q > FLR_MAX_Q || p->radius > FLR_MAX_RADIUS ||
+        p->coef_radius > FLR_MAX_COEF_RADIUS)
+        return FLR_ERR_UNSUPPORTED;
+    return FLR_OK;
+}
+
+}  // namespace host
+}  // namespace flr
+
 struct flr_handle {
     flr_params p;
     int device = 0;
@@ -60,9 +130,22 @@ struct flr_handle {
     unsigned long long n_fwd = 0, n_fp64 = 0, n_apply = 0;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
+    // fused path (flr_fused.cu): per-CTA flag lists, entry counts and reference shifts
+    int *d_flist = nullptr;
+    size_t flist_ints = 0;
+    int *d_fcount = nullptr;
+    float *d_fshift = nullptr;
+    int fcta = 0;
+    bool last_fused = false;  // the last forward call took the fused path
 };
 
 namespace {
+
+using flr::host::FusedPlan;
+using flr::host::choose_segment_rows;
+using flr::host::fused_ok;
+using flr::host::fused_plan;
+using flr::host::validate_params;
 
 int grow(flr_handle *h, int H, int W)
 {
@@ -86,22 +169,86 @@ int grow(flr_handle *h, int H, int W)
     return FLR_OK;
 }
 
-// Rows per segment of the forward kernel: minimise (waves of CTAs) x (rows walked,
-// including the 2r warm-up rows of every segment).
-int choose_segment_rows(int H, int W, int r, int n_sm)
+// With FLR_FLAG_TIMING: the next event of the handle's pool, recorded on stream s.
+cudaError_t mark(flr_handle *h, cudaStream_t s)
 {
-    const int strips = (W + flr::kTW - 1) / flr::kTW;
-    int best_th = H, best_cost = -1;
-    for (int segs = 1; segs <= 256; ++segs) {
-        int th = (H + segs - 1) / segs;
-        th = (th + flr::kB - 1) / flr::kB * flr::kB;
-        const int real_segs = (H + th - 1) / th;
-        const long long waves = ((long long)strips * real_segs + n_sm - 1) / n_sm;
-        const long long cost = waves * (th + 2 * r);
-        if (best_cost < 0 || cost < best_cost) { best_cost = (int)cost; best_th = th; }
-        if (th <= flr::kB) break;
+    if (!(h->p.flags & FLR_FLAG_TIMING)) return cudaSuccess;
+    if (h->events_used == h->events.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        h->events.push_back(ev);
     }
-    return best_th;
+    return cudaEventRecord(h->events[h->events_used++], s);
+}
+
+int grow_fused(flr_handle *h, const FusedPlan &pl)
+{
+    const int ncta = pl.strips * pl.segs;
+    const size_t ints = (size_t)ncta * pl.cap;
+    if (ncta > h->fcta) {
+        cudaFree(h->d_fcount);
+        cudaFree(h->d_fshift);
+        h->d_fcount = nullptr;
+        h->d_fshift = nullptr;
+        h->fcta = 0;
+        if (cudaMalloc(&h->d_fcount, ncta * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->d_fshift, (size_t)ncta * (FLR_MAX_Q + 3) * sizeof(float)) != cudaSuccess)
+            return FLR_ERR_NOMEM;
+        h->fcta = ncta;
+    }
+    if (ints > h->flist_ints && h->p.pivot_ratio > 0.f) {
+        cudaFree(h->d_flist);
+        h->d_flist = nullptr;
+        h->flist_ints = 0;
+        if (cudaMalloc(&h->d_flist, ints * sizeof(int)) != cudaSuccess) return FLR_ERR_NOMEM;
+        h->flist_ints = ints;
+    }
+    return FLR_OK;
+}
+
+// The fused forward kernel over output rows [row_lo, row_hi), then (pivot test on) the FP64
+// correction of its flagged pixels.  Timing marks bracket each kernel (apply: none).
+int run_fused(flr_handle *h, const float *guide, const float *map_guide, const float *radiance, float *out, int H,
+              int W, int row_lo, int row_hi, cudaStream_t s)
+{
+    const FusedPlan pl = fused_plan(row_hi - row_lo, W, h->p.radius, h->p.coef_radius, h->n_sm);
+    int st = grow_fused(h, pl);
+    if (st != FLR_OK) return st;
+    flr::FusedArgs fa;
+    fa.guide = guide;
+    fa.map_guide = map_guide;
+    fa.rad = radiance;
+    fa.out = out;
+    fa.H = H;
+    fa.W = W;
+    fa.r = h->p.radius;
+    fa.rc = h->p.coef_radius;
+    fa.eps = h->p.eps;
+    fa.tau = h->p.pivot_ratio;
+    fa.TH = pl.TH;
+    fa.row_lo = row_lo;
+    fa.row_hi = row_hi;
+    fa.list = h->d_flist;
+    fa.list_cap = h->p.pivot_ratio > 0.f ? pl.cap : 0;
+    fa.list_count = h->d_fcount;
+    fa.cta_shift = h->d_fshift;
+    fa.flag_count = h->d_count;
+    fa.nonfinite = h->d_count + 1;
+    fa.status = h->d_status;
+    const dim3 grid(pl.strips, pl.segs);
+    FLR_CUDA(mark(h, s), "timing event");
+    FLR_CUDA(flr::launch_fused(h->p.q, fa, grid, s), "fused forward kernel launch");
+    ++h->n_fwd;
+    FLR_CUDA(mark(h, s), "timing event");
+    if (h->p.pivot_ratio > 0.f) {
+        FLR_CUDA(flr::launch_fused_fix(h->p.q, fa, grid, s), "fp64 correction launch");
+        ++h->n_fp64;
+    }
+    FLR_CUDA(mark(h, s), "timing event");
+    FLR_CUDA(mark(h, s), "timing event");
+    h->last_fused = true;
+    return FLR_OK;
 }
 
 // Row bands of the host entry point (see flr_denoise_host): band k computes the models of
@@ -122,30 +269,6 @@ int band_plan(int H, int r, int rc, int *c, int *in_end, int *o)
     }
     in_end[0] = 0;
     return K;
-}
-
-int validate_params(const flr_params *p)
-{
-    if (!p) return FLR_ERR_ARG;
-    if ((p->flags & ~FLR_FLAG_TIMING) != 0u || !(p->eps >= 0.f) || p->radius < 0 || p->coef_radius < 0) return FLR_ERR_ARG;
-    if (p->pivot_ratio != p->pivot_ratio) return FLR_ERR_ARG;
-    if (p->q < 1 || p->q > FLR_MAX_Q || p->radius > FLR_MAX_RADIUS ||
-        p->coef_radius > FLR_MAX_COEF_RADIUS)
-        return FLR_ERR_UNSUPPORTED;
-    return FLR_OK;
-}
-
-// With FLR_FLAG_TIMING: the next event of the handle's pool, recorded on stream s.
-cudaError_t mark(flr_handle *h, cudaStream_t s)
-{
-    if (!(h->p.flags & FLR_FLAG_TIMING)) return cudaSuccess;
-    if (h->events_used == h->events.size()) {
-        cudaEvent_t ev;
-        cudaError_t e = cudaEventCreate(&ev);
-        if (e != cudaSuccess) return e;
-        h->events.push_back(ev);
-    }
-    return cudaEventRecord(h->events[h->events_used++], s);
 }
 
 }  // namespace
@@ -216,6 +339,9 @@ int flr_destroy(flr_handle *h)
     cudaFree(h->d_coef);
     cudaFree(h->stage);
     cudaFree(h->bwd);
+    cudaFree(h->d_flist);
+    cudaFree(h->d_fcount);
+    cudaFree(h->d_fshift);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     delete h;
     return FLR_OK;
@@ -224,6 +350,8 @@ int flr_destroy(flr_handle *h)
 int flr_reserve(flr_handle *h, int H, int W)
 {
     if (!h || H <= 0 || W <= 0) return FLR_ERR_ARG;
+    if (flr::fused_supported(h->p.q, h->p.radius, h->p.coef_radius) && W % 4 == 0)
+        return grow_fused(h, fused_plan(H, W, h->p.radius, h->p.coef_radius, h->n_sm));
     return grow(h, H, W);
 }
 
@@ -243,11 +371,14 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
     };
     if (overlaps(guide, q * px) || overlaps(map_guide, q * px) || overlaps(radiance, 3 * px))
         return FLR_ERR_ARG;
-    int st = grow(h, H, W);
-    if (st != FLR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
     FLR_CUDA(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(unsigned long long), s), "reset counters");
+    if (fused_ok(h->p, W, guide, map_guide, radiance, out))
+        return run_fused(h, guide, map_guide, radiance, out, H, W, 0, H, s);
+    h->last_fused = false;
+    int st = grow(h, H, W);
+    if (st != FLR_OK) return st;
 
     flr::FwdArgs fa;
     fa.guide = guide;
@@ -492,8 +623,10 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         FLR_CUDA(cudaStreamSynchronize(s), "host-path synchronise");
         return FLR_OK;
     }
-    int st = grow(h, H, W);
-    if (st != FLR_OK) return st;
+    if (!fused_ok(h->p, W, dg, map_guide ? dm : nullptr, dr, dout)) {
+        int st = grow(h, H, W);
+        if (st != FLR_OK) return st;
+    }
     if (!h->s_in) {
         FLR_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "copy stream");
         FLR_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "copy stream");
@@ -525,6 +658,20 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         }
         FLR_CUDA(cudaEventRecord(h->band_ev[2 * k], h->s_in), "band event");
         FLR_CUDA(cudaStreamWaitEvent(s, h->band_ev[2 * k], 0), "band wait");
+        if (fused_ok(h->p, W, dg, map_guide ? dm : nullptr, dr, dout)) {  // outputs [o_k, o_k+1) in one pass
+            int sf = run_fused(h, dg, map_guide ? dm : nullptr, dr, dout, H, W, o[k], o[k + 1], s);
+            if (sf != FLR_OK) return sf;
+            FLR_CUDA(cudaEventRecord(h->band_ev[2 * k + 1], s), "band event");
+            FLR_CUDA(cudaStreamWaitEvent(h->s_out, h->band_ev[2 * k + 1], 0), "band wait");
+            const int oa = o[k], ob = o[k + 1];
+            if (ob > oa) {
+                const size_t off = (size_t)oa * W * sizeof(float), bytes = (size_t)(ob - oa) * W * sizeof(float);
+                FLR_CUDA(cudaMemcpy2DAsync((char *)out + off, plane_b, (const char *)dout + off, plane_b, bytes, 3,
+                                           cudaMemcpyDeviceToHost, h->s_out), "d2h out band");
+            }
+            continue;
+        }
+        h->last_fused = false;
         // models of rows [c_k, c_k+1)
         flr::FwdArgs fa;
         fa.guide = dg;
@@ -648,7 +795,10 @@ int flr_get_stats(flr_handle *h, flr_stats *out)
     const unsigned long long n = cnt[0];
     out->flagged = n;
     out->nonfinite = cnt[1];
-    out->resolved = h->p.pivot_ratio > 0.f ? (n < (unsigned long long)h->flag_cap ? n : (unsigned long long)h->flag_cap) : 0ull;
+    if (h->last_fused)  // the fused path lists every flagged pixel: no capacity limit
+        out->resolved = h->p.pivot_ratio > 0.f ? n : 0ull;
+    else
+        out->resolved = h->p.pivot_ratio > 0.f ? (n < (unsigned long long)h->flag_cap ? n : (unsigned long long)h->flag_cap) : 0ull;
     int status = 0;
     FLR_CUDA(cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "stats copy");
     if (status != 0) {

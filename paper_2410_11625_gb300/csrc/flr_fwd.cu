@@ -35,6 +35,7 @@
 // d_j / M_jj falls to tau or below is appended to a flag list for the FP64 re-solve
 // (flr_fp64.cu).
 #include <cstring>
+#include <mutex>
 #include <utility>
 
 #include "flr_device.cuh"
@@ -574,11 +575,24 @@ cudaError_t launch_fwd_qr(const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t
     return cudaGetLastError();
 }
 
+// The dynamic shared memory a kernel instance may use is a per-device attribute shared by
+// every handle (the generic instance serves every radius): it is only ever raised, to the
+// largest size requested so far on that device, so a later request for less never takes
+// memory from an instance already configured for more.
 template <int Q, int RT, bool ADJ>
 cudaError_t prepare_qr(size_t smem)
 {
-    return cudaFuncSetAttribute(flr_fwd_kernel<Q, RT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    static std::mutex mu;
+    static size_t granted[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= granted[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(flr_fwd_kernel<Q, RT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) granted[dev] = smem;
+    return e;
 }
 
 template <int Q, bool ADJ>

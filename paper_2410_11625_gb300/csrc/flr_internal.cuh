@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "flr.h"
+
 namespace flr {
 
 // ---- moment channels ---------------------------------------------------------------
@@ -151,7 +153,42 @@ struct BwdArgs {
     int separate_map;                      // the map guide is not the model guide
 };
 
+// Arguments of the fused forward kernel (flr_fused.cu) and of its FP64 correction kernel.
+struct FusedArgs {
+    const float *guide, *map_guide, *rad;
+    float *out;
+    int H, W, r, rc;
+    float eps, tau;
+    int TH;                          // output rows per segment (grid.y segments)
+    int row_lo = 0, row_hi = -1;     // output rows [row_lo, row_hi) (row_hi < 0: to H)
+    int *list;                       // flagged pixels: CTA c's entries at list + c * list_cap
+    int list_cap;                    // >= the pixels one CTA solves, (TW + 2 rc) (TH + 2 rc)
+    int *list_count;                 // entries per CTA, written by every CTA of the launch
+    float *cta_shift;                // per CTA: its reference shift, Q + 3 floats
+    unsigned long long *flag_count = nullptr;  // flagged pixels owned by a CTA (fix kernel)
+    unsigned long long *nonfinite = nullptr;   // non-finite output values (may be NULL)
+    int *status = nullptr;                     // set to 1 if a bounded wait ran out (may be NULL)
+};
+
+// Host-side plan and checks shared by the entry points of flr_capi.cu and flr_noalloc.cu
+// (defined in flr_capi.cu).
+namespace host {
+int validate_params(const flr_params *p);
+int choose_segment_rows(int H, int W, int r, int n_sm);
+// Launch plan of the fused forward kernel over `rows` output rows: strips of TW columns and
+// segments of TH rows; cap = pixels one CTA solves, (TW + 2 rc)(TH + 2 rc).
+struct FusedPlan {
+    int TW, TH, strips, segs, cap;
+};
+FusedPlan fused_plan(int rows, int W, int r, int rc, int n_sm);
+bool fused_ok(const flr_params &p, int W, const void *g, const void *mg, const void *rad, const void *out);
+}  // namespace host
+
 // Host-side launchers (defined in the .cu files; q is dispatched to a template).
+bool fused_supported(int q, int r, int rc);
+int fused_tile_width(int rc);
+cudaError_t launch_fused(int q, const FusedArgs &a, dim3 grid, cudaStream_t st);
+cudaError_t launch_fused_fix(int q, const FusedArgs &a, dim3 grid, cudaStream_t st);
 cudaError_t launch_fwd(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st);
 cudaError_t launch_adj(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st);
 cudaError_t adj_prepare(int q, int r, size_t smem);

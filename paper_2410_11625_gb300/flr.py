@@ -24,7 +24,7 @@ EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoi
            "flr_mbarrier_selftest", "flr_host_band_plan",
            "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
            "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_get_grads",
-           "flnr_adam_step", "flnr_l1_loss", "flnr_layer", "flnr_status")
+           "flnr_adam_step", "flnr_l1_loss", "flnr_layer", "flnr_status", "flr_fp32_fma_peak")
 BATCH_TIMEOUT = 1
 FLAG_TIMING = 1
 HOST_MAX_BANDS = 8  # FLR_HOST_MAX_BANDS
@@ -110,6 +110,8 @@ def load_library():
     for name in ("flr_denoise_batch", "flr_fast_reserve_batch", "flr_fast_denoise_batch",
                  "flr_fast_batch_status", "flr_barrier_selftest", "flr_mbarrier_selftest"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.flr_fp32_fma_peak.argtypes = [ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.flr_fp32_fma_peak.restype = ctypes.c_int
     lib.flr_denoise_noalloc.argtypes = [ctypes.POINTER(FlrParams), fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_noalloc.restype = ctypes.c_int
     lib.flr_status_string.argtypes = [ip]
@@ -340,6 +342,13 @@ class FastFLR:
         s = FlrStats()
         _check(load_library().flr_fast_get_stats(self._h, ctypes.byref(s)), "flr_fast_get_stats")
         return {"flagged": int(s.flagged), "resolved": int(s.resolved)}
+
+
+def fp32_fma_peak(iters=20000):
+    """Measured FP32 FMA rate of the current device: (TFLOP/s, ms of the timed run)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().flr_fp32_fma_peak(int(iters), ctypes.byref(tf), ctypes.byref(ms)), "flr_fp32_fma_peak")
+    return tf.value, ms.value
 
 
 def host_band_plan(H, radius, coef_radius):
