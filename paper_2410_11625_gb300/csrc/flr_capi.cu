@@ -83,11 +83,11 @@ FusedPlan fused_plan(int rows, int W, int r, int rc, int n_sm)
 }
 
 // Whether a call can take the fused path: a compiled instance, rows of 16-byte multiples
-// (TMA), 16-byte aligned images.
-bool fused_ok(const flr_params &p, int W, const void *g, const void *mg, const void *rad, const void *out)
+// (TMA), 16-byte aligned images, and images whose element offsets fit in 32 bits.
+bool fused_ok(const flr_params &p, int H, int W, const void *g, const void *mg, const void *rad, const void *out)
 {
     return flr::fused_supported(p.q, p.radius, p.coef_radius) && (W % 4) == 0 && aligned16(g) && aligned16(rad) &&
-           aligned16(out) && (!mg || aligned16(mg));
+           aligned16(out) && (!mg || aligned16(mg)) && (long long)H * W * (p.q + 3) < 0x7fffffffLL;
 }
 
 int validate_params(const flr_params *p)
@@ -374,7 +374,7 @@ int flr_denoise(flr_handle *h, const float *guide, const float *map_guide, const
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
     FLR_CUDA(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(unsigned long long), s), "reset counters");
-    if (fused_ok(h->p, W, guide, map_guide, radiance, out))
+    if (fused_ok(h->p, H, W, guide, map_guide, radiance, out))
         return run_fused(h, guide, map_guide, radiance, out, H, W, 0, H, s);
     h->last_fused = false;
     int st = grow(h, H, W);
@@ -623,7 +623,7 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         FLR_CUDA(cudaStreamSynchronize(s), "host-path synchronise");
         return FLR_OK;
     }
-    if (!fused_ok(h->p, W, dg, map_guide ? dm : nullptr, dr, dout)) {
+    if (!fused_ok(h->p, H, W, dg, map_guide ? dm : nullptr, dr, dout)) {
         int st = grow(h, H, W);
         if (st != FLR_OK) return st;
     }
@@ -658,7 +658,7 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         }
         FLR_CUDA(cudaEventRecord(h->band_ev[2 * k], h->s_in), "band event");
         FLR_CUDA(cudaStreamWaitEvent(s, h->band_ev[2 * k], 0), "band wait");
-        if (fused_ok(h->p, W, dg, map_guide ? dm : nullptr, dr, dout)) {  // outputs [o_k, o_k+1) in one pass
+        if (fused_ok(h->p, H, W, dg, map_guide ? dm : nullptr, dr, dout)) {  // outputs [o_k, o_k+1) in one pass
             int sf = run_fused(h, dg, map_guide ? dm : nullptr, dr, dout, H, W, o[k], o[k + 1], s);
             if (sf != FLR_OK) return sf;
             FLR_CUDA(cudaEventRecord(h->band_ev[2 * k + 1], s), "band event");

@@ -57,92 +57,84 @@ constexpr unsigned long long kTimeoutNs = 1000000000ull;  // 1 s per bounded wai
 
 __host__ __device__ constexpr int tile_width(int rc) { return (kTS - 2 * rc) & ~3; }
 
-// ---- channel pairs -------------------------------------------------------------------
-// The NCH moment channels (numbered as in Chan) are stored and accumulated in pairs.  Rows of
-// products that share their left factor are paired within the row -- the linear moments (left
-// factor 1), then for each guide u the products x_u x_v (v = u..Q-1) and x_u y_c -- so a pair's
-// two products have a common left operand; the odd leftovers are paired among themselves.
+// ---- walker groups -------------------------------------------------------------------
+// The NCH moment channels (numbered as in Chan) fall into rows that share their left factor:
+// the linear moments (left factor 1: x_0..x_{Q-1}, y_0..y_2) and, for each guide u, the
+// products x_u x_v (v = u..Q-1) and x_u y_c, whose right factors are the input slots u..Q+2.
+// A walker thread keeps the vertical sums of one group of rows for a pair of adjacent columns,
+// so the packed FMAs (fma.rn.f32x2) take their operands straight from 8-byte shared loads of
+// the staged rows.  Six groups of at most 13 channels: the linear row, row 0, row 1, and the
+// row pairs {2, 7}, {3, 6}, {4, 5}; a group reads the slots from its smallest left factor up.
 template <int Q>
-struct PairMap {
-    static constexpr int NCH = Chan<Q>::NCH;
-    static constexpr int NP = (NCH + 1) / 2;
-    // channel of element e (0 or 1) of pair p; -1 for the padding element
-    __host__ __device__ static constexpr int ch(int p, int e)
+struct Groups {
+    static_assert(Q == 8, "the walker groups are laid out for eight guides");
+    static constexpr int NG = 6, MAXG = 13;
+    __host__ __device__ static constexpr int row_a(int g) { return g == 0 ? -1 : g - 1; }
+    __host__ __device__ static constexpr int row_b(int g) { return g >= 3 ? Q + 2 - g : -2; }  // -2: none
+    __host__ __device__ static constexpr int row_len(int u) { return u < 0 ? Q + 3 : Q + 3 - u; }
+    __host__ __device__ static constexpr int size(int g)
     {
-        int left[Q + 2] = {};
-        int np = 0, nl = 0;
-        for (int u = -1; u < Q; ++u) {
-            int row[Q + 3] = {};
-            int n = 0;
-            if (u < 0) {
-                for (int i = 0; i < Q; ++i) row[n++] = Chan<Q>::X0 + i;
-                for (int c = 0; c < 3; ++c) row[n++] = Chan<Q>::Y0 + c;
-            } else {
-                for (int v = u; v < Q; ++v) row[n++] = Chan<Q>::xx(u, v);
-                for (int c = 0; c < 3; ++c) row[n++] = Chan<Q>::xy(u, c);
-            }
-            for (int k = 0; k + 1 < n; k += 2) {
-                if (np == p) return e == 0 ? row[k] : row[k + 1];
-                ++np;
-            }
-            if (n & 1) left[nl++] = row[n - 1];
-        }
-        for (int k = 0; k < nl; k += 2) {
-            if (np == p) return e == 0 ? left[k] : (k + 1 < nl ? left[k + 1] : -1);
-            ++np;
-        }
-        return -1;
+        return row_len(row_a(g)) + (row_b(g) >= -1 ? row_len(row_b(g)) : 0);
     }
-    __host__ __device__ static constexpr int group_begin(int g) { return g * NP / 3; }
-    __host__ __device__ static constexpr int group_size(int g) { return group_begin(g + 1) - group_begin(g); }
-    static constexpr int GP = (NP + 2) / 3;  // pairs of the largest walker group
+    // the i-th channel of group g
+    __host__ __device__ static constexpr int ch(int g, int i)
+    {
+        const int ua = row_a(g), na = row_len(ua);
+        const int u = i < na ? ua : row_b(g);
+        const int k = i < na ? i : i - na;
+        if (u < 0) return k < Q ? Chan<Q>::X0 + k : Chan<Q>::Y0 + (k - Q);
+        const int v = u + k;
+        return v < Q ? Chan<Q>::xx(u, v) : Chan<Q>::xy(u, v - Q);
+    }
+    __host__ __device__ static constexpr int s0(int g) { return row_a(g) < 0 ? 0 : row_a(g); }
 };
 
 // Compile-time geometry of one instantiation.
 template <int Q, int R, int RC>
 struct Geo {
     static constexpr int NS = Q + 3;
-    static constexpr int NP = PairMap<Q>::NP;
-    static constexpr int NCF = 3 * (Q + 1);      // model coefficients per pixel
-    static constexpr int NCP = (NCF + 1) / 2;    // ... in pairs
-    static constexpr int NPB = NP > 2 * NCP ? NP : 2 * NCP;  // pairs per pixel row of the buffer
-    static constexpr int TW = tile_width(RC);    // output columns
-    static constexpr int TS = TW + 2 * RC;       // solve columns
-    static constexpr int TM = TS + 2 * R;        // walker columns
-    static constexpr int RA = (R + RC + 3) & ~3; // staged rows start at column x0 - RA
+    static constexpr int NCH = Chan<Q>::NCH;
+    static constexpr int NCF = 3 * (Q + 1);       // model coefficients per pixel
+    static constexpr int NCHB = NCH > 2 * NCF ? NCH : 2 * NCF;  // channel rows of the buffer
+    static constexpr int TW = tile_width(RC);     // output columns
+    static constexpr int TS = TW + 2 * RC;        // solve columns
+    static constexpr int TM = TS + 2 * R;         // walker columns
+    static constexpr int NCP = TM / 2;            // walker column pairs
+    static constexpr int RA = (R + RC + 3) & ~3;  // staged rows start at column x0 - RA
     // staged row length: covers TW + 2 RA columns, and kB rows of it are a multiple of 128
     // bytes, so every TMA box of the staging buffer starts 128-byte aligned
     static constexpr int WSt = (TW + 2 * RA + 7) & ~7;
-    static constexpr int SOFF = RA - R - RC;     // staged column of walker column 0
-    static constexpr int VS = TM | 1;          // pair-row stride: odd, so pair rows hit distinct banks
+    static constexpr int SOFF = RA - R - RC;      // staged column of walker column 0
+    static constexpr int VS = TM + ((12 - TM % 8) % 8);  // row stride >= TM, = 4 (mod 8)
     static constexpr int WR = 2 * R + 1, WC = 2 * RC + 1;
-    static constexpr int CH = TS / 2;            // H-pass: two chunks per row
-    static constexpr int NCHC = 4, CL = TW / NCHC;  // coefficient H-pass: four chunks per row
+    static constexpr int CH = (TS / 2 + 3) & ~3;  // H-pass: runs [0, CH) and [CH, TS)
+    static constexpr int CL = (TW / 2 + 3) & ~3;  // coefficient H-pass: runs [0, CL), [CL, TW)
     static constexpr int COLOUR_WARPS = (3 * TW + 31) / 32;
-    static constexpr size_t VBUF_FLOATS = ((size_t)kB * NPB * VS * 2 + 31) / 32 * 32;  // 128-byte multiple
+    static constexpr size_t VBUF_FLOATS = ((size_t)kB * NCHB * VS + 31) / 32 * 32;
     static constexpr size_t STAGE_FLOATS = (size_t)2 * NS * kB * WSt;
     static constexpr size_t SMEM = 128 + 4 * (VBUF_FLOATS + STAGE_FLOATS) + 16;
     static_assert(TS <= kTS && TM <= 112 && WSt <= 112, "strip geometry");
     static_assert((kB * WSt * 4) % 128 == 0 && (VBUF_FLOATS * 4) % 128 == 0, "TMA boxes 128-byte aligned");
     static_assert(SOFF + TM <= WSt, "walker columns inside the staged rows");
-    static_assert(TS % 2 == 0 && CH > 2 * R, "H-pass chunks");
-    static_assert(TW % NCHC == 0 && (RC == 0 || CL > 0), "coefficient chunks");
-    static_assert(PairMap<Q>::GP <= 12, "walker state: 48 tensor-memory columns");
+    static_assert((R + RC) % 2 == 0 && SOFF % 2 == 0, "column pairs start at even columns");
+    static_assert(NCP <= 64, "two warps of walkers per group");
+    static_assert(CH > 2 * R && CH < TS && CL < TW, "H-pass runs");
     static_assert(RC == 0 || (WC <= 17 && COLOUR_WARPS <= 8 && WC >= 4), "coefficient ring");
     static_assert(Q + 1 <= 9, "colour state: 18 tensor-memory columns");
 };
 
-// Tensor-memory columns (per lane, 512 allocated).  Walker warp w keeps its 48 accumulators
-// at columns 32 k .. (x32) and 96 + 16 k .. (x16), k = w / 4; colour warp w (k = w / 4, k < 2)
-// keeps its ring slot s at 144 + 136 k + 8 s (x8) and 416 + 17 k + s (x1), and its 18
-// accumulators at 464 + 16 k (x16) and 496 + 2 k (x2).  Every access is aligned to its width.
+// Tensor-memory columns (per lane; 512 allocated, every access aligned to its width).
+// Walker warp w (k = w / 4) keeps its 52 accumulators at 32 k (x32), 96 + 16 k (x16) and
+// 144 + 4 k (x4); colour warp w (k = w / 4 < 2) keeps its ring slot s at 160 + 136 k + 8 s
+// (x8) and 432 + 17 k + s (x1), and its 18 accumulators at 480 + 16 k (x16), 156 + 2 k (x2).
 constexpr uint32_t kTmemCols = 512;
-__device__ __forceinline__ uint32_t col_walk32(int k) { return 32u * k; }
-__device__ __forceinline__ uint32_t col_walk16(int k) { return 96u + 16u * k; }
-__device__ __forceinline__ uint32_t col_ring8(int k, int s) { return 144u + 136u * k + 8u * s; }
-__device__ __forceinline__ uint32_t col_ring1(int k, int s) { return 416u + 17u * k + s; }
-__device__ __forceinline__ uint32_t col_cst16(int k) { return 464u + 16u * k; }
-__device__ __forceinline__ uint32_t col_cst2(int k) { return 496u + 2u * k; }
+__device__ __forceinline__ uint32_t col_w32(int k) { return 32u * k; }
+__device__ __forceinline__ uint32_t col_w16(int k) { return 96u + 16u * k; }
+__device__ __forceinline__ uint32_t col_w4(int k) { return 144u + 4u * k; }
+__device__ __forceinline__ uint32_t col_c2(int k) { return 156u + 2u * k; }
+__device__ __forceinline__ uint32_t col_ring8(int k, int s) { return 160u + 136u * k + 8u * s; }
+__device__ __forceinline__ uint32_t col_ring1(int k, int s) { return 432u + 17u * k + s; }
+__device__ __forceinline__ uint32_t col_c16(int k) { return 480u + 16u * k; }
 
 // ---- tensor-memory access (32 lanes x 32 bits per warp, one lane per thread) ----------
 #define FLR_TM_R4(i) "r"(v[i]), "r"(v[i + 1]), "r"(v[i + 2]), "r"(v[i + 3])
@@ -216,61 +208,72 @@ __device__ __forceinline__ uint32_t tm_ld1(uint32_t ta)
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
-// ---- V-pass: one channel pair ----------------------------------------------------------
-// E += left(e) * right(e), Dn += left(l) * right(l), V = E - Dn; e and l are the shifted
-// values of the entering and the leaving row at this walker's column.
-template <int Q, int P>
-__device__ __forceinline__ void walk_pair(float2 &E, float2 &Dn, float2 *dst, const float (&e)[Q + 3],
-                                          const float (&l)[Q + 3])
+__device__ __forceinline__ void tm_st4(uint32_t ta, const uint32_t *v)
 {
-    using C = Chan<Q>;
-    constexpr int ca = PairMap<Q>::ch(P, 0), cb = PairMap<Q>::ch(P, 1);
-    constexpr int ua = C::slot_u(ca), va = C::slot_v(ca);
-    constexpr int ub = cb >= 0 ? C::slot_u(cb) : 0, vb = cb >= 0 ? C::slot_v(cb) : -1;
-    const float2 el = make_float2(e[ua], cb >= 0 ? e[ub] : 0.f);
-    const float2 er = make_float2(va >= 0 ? e[va] : 1.f, vb >= 0 ? e[vb] : 1.f);
-    const float2 ll = make_float2(l[ua], cb >= 0 ? l[ub] : 0.f);
-    const float2 lr = make_float2(va >= 0 ? l[va] : 1.f, vb >= 0 ? l[vb] : 1.f);
-    E = __ffma2_rn(el, er, E);
-    Dn = __ffma2_rn(ll, lr, Dn);
-    *dst = __ffma2_rn(Dn, make_float2(-1.f, -1.f), E);
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(ta), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+__device__ __forceinline__ void tm_ld4(uint32_t ta, uint32_t *v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(ta)
+                 : "memory");
 }
 
-template <int Q, int G, int... I>
-__device__ __forceinline__ void walk_group(float2 (&E)[12], float2 (&Dn)[12], float2 *vcol, int VS,
-                                           const float (&e)[Q + 3], const float (&l)[Q + 3],
-                                           std::integer_sequence<int, I...>)
+// ---- V-pass: one group of channels, two columns ---------------------------------------
+// E += left(e) * right(e), Dn += left(l) * right(l), V = E - Dn for every channel of group G;
+// e and l: the shifted values of the entering and the leaving row at the two columns.
+template <int Q, int G, int I>
+__device__ __forceinline__ void walk_enter(float2 (&E)[13], const float2 (&e)[Q + 3])
 {
-    constexpr int P0 = PairMap<Q>::group_begin(G);
-    (walk_pair<Q, P0 + I>(E[I], Dn[I], vcol + (size_t)(P0 + I) * VS, e, l), ...);
+    constexpr int c = Groups<Q>::ch(G, I);
+    constexpr int u = Chan<Q>::slot_u(c), v = Chan<Q>::slot_v(c);
+    if constexpr (v < 0) E[I] = __fadd2_rn(E[I], e[u]);
+    else E[I] = __ffma2_rn(e[u], e[v], E[I]);
+}
+template <int Q, int G, int I>
+__device__ __forceinline__ void walk_store(const float2 (&E)[13], const float2 (&Dn)[13], float *vcol, int VS)
+{
+    constexpr int c = Groups<Q>::ch(G, I);
+    *reinterpret_cast<float2 *>(vcol + (size_t)c * VS) = __ffma2_rn(Dn[I], make_float2(-1.f, -1.f), E[I]);
+}
+// se: the staged entering row of this batch row at the walker's first column; planes are
+// kB * WST floats apart, the leaving rows NS planes further on.
+template <int Q, int G, int WST, int... I>
+__device__ __forceinline__ void walk_rows(float2 (&E)[13], float2 (&Dn)[13], float *vcol, int VS, const float *se,
+                                         const float2 (&nsh)[Q + 3], bool ein, bool lout,
+                                         std::integer_sequence<int, I...>)
+{
+    constexpr int NS = Q + 3, S0 = Groups<Q>::s0(G);
+    constexpr size_t PL = (size_t)kB * WST;
+    if (ein) {
+        float2 e[NS];
+#pragma unroll
+        for (int k = S0; k < NS; ++k) e[k] = __fadd2_rn(*reinterpret_cast<const float2 *>(se + k * PL), nsh[k]);
+        (walk_enter<Q, G, I>(E, e), ...);
+    }
+    if (lout) {
+        const float *sl = se + NS * PL;
+        float2 l[NS];
+#pragma unroll
+        for (int k = S0; k < NS; ++k) l[k] = __fadd2_rn(*reinterpret_cast<const float2 *>(sl + k * PL), nsh[k]);
+        (walk_enter<Q, G, I>(Dn, l), ...);
+    }
+    (walk_store<Q, G, I>(E, Dn, vcol, VS), ...);
 }
 
 // ---- solve ---------------------------------------------------------------------------------
-template <int Q, int P>
-__device__ __forceinline__ void gather_pair(const float2 *cp, int VS, float (&S)[Chan<Q>::NCH])
-{
-    constexpr int ca = PairMap<Q>::ch(P, 0), cb = PairMap<Q>::ch(P, 1);
-    const float2 v = cp[(size_t)P * VS];
-    S[ca] = v.x;
-    if constexpr (cb >= 0) S[cb] = v.y;
-}
-template <int Q, int... I>
-__device__ __forceinline__ void gather(const float2 *cp, int VS, float (&S)[Chan<Q>::NCH], std::integer_sequence<int, I...>)
-{
-    (gather_pair<Q, I>(cp, VS, S), ...);
-}
-
-// Centred ridge model of one pixel from its window sums (pairs at cp + P * VS), in the
-// unnormalised form n M = S - L mu^T + n eps I, n D = XY - L_y mu^T (the same a as M^{-1} D).
-// Returns whether a Cholesky pivot ratio d_j / (n M)_jj fell to tau or below.
+// Centred ridge model of one pixel from its window sums S (moment channels, Chan order), in
+// the unnormalised form n M = S - L mu^T + n eps I, n D = XY - L_y mu^T (the same a as
+// M^{-1} D).  Returns whether a Cholesky pivot ratio d_j / (n M)_jj fell to tau or below.
 template <int Q>
-__device__ __forceinline__ bool solve_px(const float2 *cp, int VS, float n, float eps, float tau, float (&A)[Q][3],
-                                         float (&bv)[3])
+__device__ __forceinline__ bool solve_px(const float (&S)[Chan<Q>::NCH], float n, float eps, float tau,
+                                         float (&A)[Q][3], float (&bv)[3])
 {
     using C = Chan<Q>;
     using dev::tri;
-    float S[C::NCH];
-    gather<Q>(cp, VS, S, std::make_integer_sequence<int, PairMap<Q>::NP>{});
     const float inv_n = 1.0f / n;
     float mu[Q], muy[3];
 #pragma unroll
@@ -341,6 +344,53 @@ __device__ __forceinline__ bool solve_px(const float2 *cp, int VS, float n, floa
     return low;
 }
 
+// ---- horizontal sums of one buffer row -------------------------------------------------
+// out[x] = sum_{j=0}^{2K} in[x + j] for x in [x0, x0 + N) (x0 and the rows 16-byte aligned):
+// the first output is a direct (2K + 1)-term sum, the others slide, four per step with 16-byte
+// accesses, then one at a time.  With in == out the row is summed in place: every value is
+// read before its slot is written.
+template <int K, int N>
+__device__ __forceinline__ void hsum_run(const float *in, float *out, int x0)
+{
+    float S = 0.f;
+#pragma unroll
+    for (int j = 0; j <= 2 * K; ++j) S += in[x0 + j];
+    float prev = 0.f;
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const int x = x0 + 4 * q;
+        const float4 old = *reinterpret_cast<const float4 *>(in + x);
+        float ent[4];
+        if constexpr ((2 * K) % 4 == 0) {
+            const float4 e4 = *reinterpret_cast<const float4 *>(in + x + 2 * K);
+            ent[0] = e4.x, ent[1] = e4.y, ent[2] = e4.z, ent[3] = e4.w;
+        } else {
+            const float2 e0 = *reinterpret_cast<const float2 *>(in + x + 2 * K);
+            const float2 e1 = *reinterpret_cast<const float2 *>(in + x + 2 * K + 2);
+            ent[0] = e0.x, ent[1] = e0.y, ent[2] = e1.x, ent[3] = e1.y;
+        }
+        float4 o;
+        if (q > 0) S = (S + ent[0]) - prev;
+        o.x = S;
+        S = (S + ent[1]) - old.x;
+        o.y = S;
+        S = (S + ent[2]) - old.y;
+        o.z = S;
+        S = (S + ent[3]) - old.z;
+        o.w = S;
+        prev = old.w;
+        *reinterpret_cast<float4 *>(out + x) = o;
+    }
+#pragma unroll
+    for (int i = (N / 4) * 4; i < N; ++i) {
+        const int x = x0 + i;
+        const float old = in[x];
+        if (i > 0) S = (S + in[x + 2 * K]) - prev;
+        out[x] = S;
+        prev = old;
+    }
+}
+
 // Kernel parameters: TMA maps of the guide [Q][H][W] and radiance [3][H][W] planes (boxes of
 // WSt columns x kB rows x all planes) and the arguments.
 struct alignas(128) KArgs {
@@ -353,8 +403,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
 {
     using C = Chan<Q>;
     using G = Geo<Q, R, RC>;
-    constexpr int NS = G::NS, NP = G::NP, NPB = G::NPB, NCP = G::NCP;
-    constexpr int TW = G::TW, TS = G::TS, TM = G::TM, WSt = G::WSt, VS = G::VS;
+    constexpr int NS = G::NS, NCH = G::NCH, NCF = G::NCF, NCHB = G::NCHB;
+    constexpr int TW = G::TW, TS = G::TS, WSt = G::WSt, VS = G::VS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float s_sh[NS];
     __shared__ int s_abort, s_nlist, s_wcnt[kWarps];
@@ -378,8 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
     int *list = a.list + (size_t)cta * a.list_cap;
 
     unsigned char *base = smem_raw + ((128 - (tma::smem_addr(smem_raw) & 127)) & 127);
-    float2 *Vbuf = reinterpret_cast<float2 *>(base);                 // [kB][NPB][VS] pairs
-    float *stage = reinterpret_cast<float *>(base) + G::VBUF_FLOATS;  // [2][NS][kB][WSt]
+    float *Vbuf = reinterpret_cast<float *>(base);  // [kB][NCHB][VS]: channel rows
+    float *stage = Vbuf + G::VBUF_FLOATS;            // [2][NS][kB][WSt]: entering, leaving rows
     uint64_t *bar = reinterpret_cast<uint64_t *>(stage + G::STAGE_FLOATS);
 
     if (warp == 0) {
@@ -416,13 +466,13 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
     if (tid == 0) stage_batch(v0);
     int nstaged = 1, nconsumed = 0;
 
-    // walker identity: warp -> (channel-pair third, 32-column block); walker column wx is
-    // global column x0 - RC - R + wx and staged column wx + SOFF
-    const int group = warp >> 2;
-    const int wx = ((warp & 3) << 5) + lane;
-    const bool walker = wx < TM;
-    const int gxw = x0 - RC - R + wx;
-    const bool wcol_in = gxw >= 0 && gxw < W;
+    // walker identity: two warps per channel group, one thread per column pair; walker
+    // column 2 cp is global column x0 - RC - R + 2 cp and staged column 2 cp + SOFF
+    const int group = warp >> 1;
+    const int wcp = ((warp & 1) << 5) + lane;
+    const bool walker = wcp < G::NCP;
+    const int gxw = x0 - RC - R + 2 * wcp;
+    const bool wcol_in = gxw >= 0 && gxw < W;  // W is even and gxw even: both columns or neither
     // solver identity
     const int sb = tid / kTS, sxs = tid % kTS;
     const int sgx = x0 - RC + sxs;
@@ -445,25 +495,29 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
 
         // 1. V-pass
         {
-            float2 E[12], Dn[12];
+            float2 E[13], Dn[13];
             if (v == v0) {
 #pragma unroll
-                for (int i = 0; i < 12; ++i) E[i] = Dn[i] = make_float2(0.f, 0.f);
+                for (int i = 0; i < 13; ++i) E[i] = Dn[i] = make_float2(0.f, 0.f);
             } else {
-                uint32_t st[48];
-                tm_ld32(tmem + col_walk32(slot_k), st);
-                tm_ld16(tmem + col_walk16(slot_k), st + 32);
+                uint32_t st[52];
+                tm_ld32(tmem + col_w32(slot_k), st);
+                tm_ld16(tmem + col_w16(slot_k), st + 32);
+                tm_ld4(tmem + col_w4(slot_k), st + 48);
                 tm_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 12; ++i) {
+                for (int i = 0; i < 13; ++i) {
                     E[i] = make_float2(__uint_as_float(st[2 * i]), __uint_as_float(st[2 * i + 1]));
-                    Dn[i] = make_float2(__uint_as_float(st[24 + 2 * i]), __uint_as_float(st[25 + 2 * i]));
+                    Dn[i] = make_float2(__uint_as_float(st[26 + 2 * i]), __uint_as_float(st[27 + 2 * i]));
                 }
             }
             if (walker) {
-                float shl[NS];
+                float2 nsh[NS];  // minus the shift, both columns (zero outside the image)
 #pragma unroll
-                for (int k = 0; k < NS; ++k) shl[k] = wcol_in ? s_sh[k] : 0.f;
+                for (int k = 0; k < NS; ++k) {
+                    const float t = wcol_in ? -s_sh[k] : 0.f;
+                    nsh[k] = make_float2(t, t);
+                }
 #pragma unroll 1
                 for (int b = 0; b < kB; ++b) {
                     const int vb = v + b;
@@ -471,41 +525,37 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                     const int t = vb - v0;
                     if (t % G::WR == 0) {  // block start: Dn = -(previous block total), E = 0
 #pragma unroll
-                        for (int i = 0; i < 12; ++i) {
+                        for (int i = 0; i < 13; ++i) {
                             Dn[i] = __fmul2_rn(E[i], make_float2(-1.f, -1.f));
                             E[i] = make_float2(0.f, 0.f);
                         }
                     }
                     const bool ein = vb + R >= 0 && vb + R < H;
                     const bool lout = t >= G::WR && vb - R - 1 >= 0 && vb - R - 1 < H;
-                    const float *se = stage + (size_t)b * WSt + wx + G::SOFF;
-                    const float *sl = se + (size_t)NS * kB * WSt;
-                    float e[NS], l[NS];
-#pragma unroll
-                    for (int k = 0; k < NS; ++k) {
-                        e[k] = ein ? se[(size_t)k * kB * WSt] - shl[k] : 0.f;
-                        l[k] = lout ? sl[(size_t)k * kB * WSt] - shl[k] : 0.f;
+                    const float *se = stage + (size_t)b * WSt + 2 * wcp + G::SOFF;
+                    float *vcol = Vbuf + (size_t)b * NCHB * VS + 2 * wcp;
+                    switch (group) {
+                    case 0: walk_rows<Q, 0, WSt>(E, Dn, vcol, VS, se, nsh, ein, lout, std::make_integer_sequence<int, Groups<Q>::size(0)>{}); break;
+                    case 1: walk_rows<Q, 1, WSt>(E, Dn, vcol, VS, se, nsh, ein, lout, std::make_integer_sequence<int, Groups<Q>::size(1)>{}); break;
+                    case 2: walk_rows<Q, 2, WSt>(E, Dn, vcol, VS, se, nsh, ein, lout, std::make_integer_sequence<int, Groups<Q>::size(2)>{}); break;
+                    case 3: walk_rows<Q, 3, WSt>(E, Dn, vcol, VS, se, nsh, ein, lout, std::make_integer_sequence<int, Groups<Q>::size(3)>{}); break;
+                    case 4: walk_rows<Q, 4, WSt>(E, Dn, vcol, VS, se, nsh, ein, lout, std::make_integer_sequence<int, Groups<Q>::size(4)>{}); break;
+                    default: walk_rows<Q, 5, WSt>(E, Dn, vcol, VS, se, nsh, ein, lout, std::make_integer_sequence<int, Groups<Q>::size(5)>{}); break;
                     }
-                    float2 *vcol = Vbuf + (size_t)b * NPB * VS + wx;
-                    if (group == 0)
-                        walk_group<Q, 0>(E, Dn, vcol, VS, e, l, std::make_integer_sequence<int, PairMap<Q>::group_size(0)>{});
-                    else if (group == 1)
-                        walk_group<Q, 1>(E, Dn, vcol, VS, e, l, std::make_integer_sequence<int, PairMap<Q>::group_size(1)>{});
-                    else
-                        walk_group<Q, 2>(E, Dn, vcol, VS, e, l, std::make_integer_sequence<int, PairMap<Q>::group_size(2)>{});
                 }
             }
             __syncwarp();  // the walkers' branches rejoin before the warp-wide tensor-memory store
-            uint32_t st[48];
+            uint32_t st[52];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
+            for (int i = 0; i < 13; ++i) {
                 st[2 * i] = __float_as_uint(E[i].x);
                 st[2 * i + 1] = __float_as_uint(E[i].y);
-                st[24 + 2 * i] = __float_as_uint(Dn[i].x);
-                st[25 + 2 * i] = __float_as_uint(Dn[i].y);
+                st[26 + 2 * i] = __float_as_uint(Dn[i].x);
+                st[27 + 2 * i] = __float_as_uint(Dn[i].y);
             }
-            tm_st32(tmem + col_walk32(slot_k), st);
-            tm_st16(tmem + col_walk16(slot_k), st + 32);
+            tm_st32(tmem + col_w32(slot_k), st);
+            tm_st16(tmem + col_w16(slot_k), st + 32);
+            tm_st4(tmem + col_w4(slot_k), st + 48);
             tm_wait_st();
         }
         __syncthreads();
@@ -516,33 +566,13 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
         }
         if (v + kB <= m_lo) continue;  // every row of this batch is a warm-up row
 
-        // 2. H-pass: unit (row b, pair P, chunk k); consecutive threads take consecutive pairs
+        // 2. H-pass: one thread per (row b, channel), in place, seeded at 0 and CH
         {
-            const int hP = tid % NP, hk = (tid / NP) & 1, hb = tid / (2 * NP);
-            const bool hrow = tid < kB * NP * 2 && v + hb >= m_lo && v + hb < m_hi;
-            float2 *rowp = Vbuf + ((size_t)hb * NPB + hP) * VS;
-            const int xk = hk * G::CH;
-            float2 pre[2 * R];  // the next chunk's first 2R slots, read before anyone writes
-            if (hrow) {
-#pragma unroll
-                for (int j = 0; j < 2 * R; ++j) pre[j] = rowp[xk + G::CH + j];
-            }
-            __syncthreads();
-            if (hrow) {
-                float2 S = rowp[xk];
-                float2 vprev = S;
-#pragma unroll
-                for (int j = 1; j <= 2 * R; ++j) S = __fadd2_rn(S, rowp[xk + j]);
-                rowp[xk] = S;
-#pragma unroll
-                for (int i = 1; i < G::CH; ++i) {
-                    const float2 enter =
-                        (i + 2 * R < G::CH) ? rowp[xk + i + 2 * R] : pre[i + 2 * R >= G::CH ? i + 2 * R - G::CH : 0];
-                    const float2 old = rowp[xk + i];
-                    S = __ffma2_rn(vprev, make_float2(-1.f, -1.f), __fadd2_rn(S, enter));
-                    rowp[xk + i] = S;
-                    vprev = old;
-                }
+            const int hb = tid / NCH, hch = tid % NCH;
+            if (tid < kB * NCH && v + hb >= m_lo && v + hb < m_hi) {
+                float *row = Vbuf + ((size_t)hb * NCHB + hch) * VS;
+                hsum_run<R, G::CH>(row, row, 0);
+                hsum_run<R, TS - G::CH>(row, row, G::CH);
             }
         }
         __syncthreads();
@@ -553,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
             const int m = v + sb;
             if (sxs < TS && m >= m_lo && m < m_hi) {
                 const bool live = m >= 0 && m < H && sgx >= 0 && sgx < W;
-                float2 *cp = Vbuf + (size_t)sb * NPB * VS + sxs;
+                float *col = Vbuf + (size_t)sb * NCHB * VS + sxs;
                 float A[Q][3], bv[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -562,26 +592,26 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                     for (int i = 0; i < Q; ++i) A[i][c] = 0.f;
                 }
                 if (live) {
+                    float S[NCH];
+#pragma unroll
+                    for (int ch = 0; ch < NCH; ++ch) S[ch] = col[(size_t)ch * VS];
                     const float ny = (float)(min(m + R, H - 1) - max(m - R, 0) + 1);
                     const float nx = (float)(min(sgx + R, W - 1) - max(sgx - R, 0) + 1);
-                    const bool low = solve_px<Q>(cp, VS, ny * nx, eps, tau, A, bv);
+                    const bool low = solve_px<Q>(S, ny * nx, eps, tau, A, bv);
                     flag = low && tau > 0.f;
                 }
                 if constexpr (RC > 0) {
-                    // model coefficients (relative to the CTA shift) into pairs [0, NCP) of this
-                    // pixel; a flagged pixel contributes zero here and its FP64 model later
-                    float cf[2 * NCP];
+                    // model coefficients (relative to the CTA shift) into channel rows [0, NCF)
+                    // of this pixel, colour-major; a flagged pixel contributes zero here and its
+                    // FP64 model later
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        cf[c * (Q + 1)] = flag ? 0.f : bv[c];
+                        col[(size_t)(c * (Q + 1)) * VS] = flag ? 0.f : bv[c];
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) cf[c * (Q + 1) + 1 + i] = flag ? 0.f : A[i][c];
+                        for (int i = 0; i < Q; ++i) col[(size_t)(c * (Q + 1) + 1 + i) * VS] = flag ? 0.f : A[i][c];
                     }
-                    if constexpr (2 * NCP > G::NCF) cf[2 * NCP - 1] = 0.f;
-#pragma unroll
-                    for (int p = 0; p < NCP; ++p) cp[(size_t)p * VS] = make_float2(cf[2 * p], cf[2 * p + 1]);
                 } else {
-                    if (live && !flag && sgx < x0 + TW) {
+                    if (live && !flag) {
                         const size_t off = (size_t)m * W + sgx;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -612,34 +642,39 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
             }
         }
         if constexpr (RC > 0) {
-            // 4. coefficient H-pass: unit (row b, coefficient pair P, chunk k) -> pair NCP + P
+            // 4. coefficient H-pass: unit (row b, coefficient k, half h): row k -> row NCF + k
             {
-                const int uP = tid % NCP, uk = (tid / NCP) % G::NCHC, ub = tid / (NCP * G::NCHC);
-                if (tid < kB * NCP * G::NCHC && v + ub >= m_lo && v + ub < m_hi) {
-                    const float2 *in = Vbuf + ((size_t)ub * NPB + uP) * VS + uk * G::CL;
-                    float2 *outp = Vbuf + ((size_t)ub * NPB + NCP + uP) * VS + uk * G::CL;
-                    float2 S = in[0];
-#pragma unroll
-                    for (int j = 1; j <= 2 * RC; ++j) S = __fadd2_rn(S, in[j]);
-                    outp[0] = S;
-#pragma unroll
-                    for (int i = 1; i < G::CL; ++i) {
-                        S = __ffma2_rn(in[i - 1], make_float2(-1.f, -1.f), __fadd2_rn(S, in[i + 2 * RC]));
-                        outp[i] = S;
-                    }
+                const int uk = tid % NCF, uh = (tid / NCF) & 1, ub = tid / (2 * NCF);
+                if (tid < kB * NCF * 2 && v + ub >= m_lo && v + ub < m_hi) {
+                    const float *in = Vbuf + ((size_t)ub * NCHB + uk) * VS;
+                    float *outp = Vbuf + ((size_t)ub * NCHB + NCF + uk) * VS;
+                    if (uh == 0) hsum_run<RC, G::CL>(in, outp, 0);
+                    else hsum_run<RC, TW - G::CL>(in, outp, G::CL);
                 }
             }
             __syncthreads();
             // 5. coefficient V-pass and apply: thread (colour cc, column cx)
             if (warp < G::COLOUR_WARPS) {
+                // map-guide values of this batch's output rows, loaded first so that their
+                // latency overlaps the tensor-memory traffic below
+                float zv[kB][Q];
+                const float *zcol = zg + (colour && cgx < W ? cgx : 0);
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int y = v + b - RC;
+                    const bool row_out = y >= y0 && y < y1;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        zv[b][i] = row_out ? __ldg(zcol + i * plane + (size_t)y * W) - s_sh[i] : 0.f;
+                }
                 float Ec[Q + 1], Dc[Q + 1];
                 if (v <= m_lo) {
 #pragma unroll
                     for (int j = 0; j <= Q; ++j) Ec[j] = Dc[j] = 0.f;
                 } else {
                     uint32_t st[18];
-                    tm_ld16(tmem + col_cst16(slot_k), st);
-                    tm_ld2(tmem + col_cst2(slot_k), st + 16);
+                    tm_ld16(tmem + col_c16(slot_k), st);
+                    tm_ld2(tmem + col_c2(slot_k), st + 16);
                     tm_wait_ld();
 #pragma unroll
                     for (int j = 0; j <= Q; ++j) {
@@ -658,6 +693,9 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                     }
                 }
                 tm_wait_ld();
+                const float *hcol = Vbuf + (size_t)(NCF + (colour ? cc : 0) * (Q + 1)) * VS + cx;
+                const float mx = (float)(min(cgx + RC, W - 1) - max(cgx - RC, 0) + 1);
+                const float inv_mx = 1.0f / mx;
 #pragma unroll
                 for (int b = 0; b < kB; ++b) {
                     const int m = v + b, tcm = m - m_lo;
@@ -674,11 +712,9 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                         for (int j = 0; j <= Q; ++j) Dc[j] += __uint_as_float(lv[b][j]);
                     }
                     uint32_t ent[9];
-                    const float *hrow = reinterpret_cast<const float *>(Vbuf + ((size_t)b * NPB + NCP) * VS);
 #pragma unroll
                     for (int j = 0; j <= Q; ++j) {
-                        const int k = cc * (Q + 1) + j;  // coefficient index (colour-major)
-                        const float hv = colour ? hrow[(size_t)(k >> 1) * VS * 2 + 2 * cx + (k & 1)] : 0.f;
+                        const float hv = colour ? hcol[(size_t)(b * NCHB + j) * VS] : 0.f;
                         Ec[j] += hv;
                         ent[j] = __float_as_uint(hv);
                     }
@@ -689,14 +725,12 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                     tm_st1(tmem + col_ring1(slot_k, tcm % G::WC), ent[8]);
                     const int y = m - RC;
                     if (colour && y >= y0 && y < y1 && cgx < W) {
-                        const size_t off = (size_t)y * W + cgx;
                         const float my = (float)(min(y + RC, H - 1) - max(y - RC, 0) + 1);
-                        const float mx = (float)(min(cgx + RC, W - 1) - max(cgx - RC, 0) + 1);
                         float o = Ec[0] - Dc[0];
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) o = fmaf(Ec[1 + i] - Dc[1 + i], __ldg(zg + i * plane + off) - s_sh[i], o);
-                        o = fmaf(o, 1.0f / (my * mx), s_sh[Q + cc]);
-                        a.out[cc * plane + off] = o;
+                        for (int i = 0; i < Q; ++i) o = fmaf(Ec[1 + i] - Dc[1 + i], zv[b][i], o);
+                        o = fmaf(o, inv_mx / my, s_sh[Q + cc]);
+                        a.out[cc * plane + (size_t)y * W + cgx] = o;
                         bad += !isfinite(o);
                     }
                 }
@@ -707,8 +741,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                     st[j] = __float_as_uint(j <= Q ? Ec[j] : 0.f);
                     st[9 + j] = __float_as_uint(j <= Q ? Dc[j] : 0.f);
                 }
-                tm_st16(tmem + col_cst16(slot_k), st);
-                tm_st2(tmem + col_cst2(slot_k), st + 16);
+                tm_st16(tmem + col_c16(slot_k), st);
+                tm_st2(tmem + col_c2(slot_k), st + 16);
                 tm_wait_st();
             }
         }
@@ -865,10 +899,10 @@ cudaError_t launch_qr(const FusedArgs &a, dim3 grid, cudaStream_t st)
 }  // namespace fused
 
 // Radii of the fused kernel (compile-time instances): the 1080p workload (r = rc = 8), the
-// 256 x 256 workload (r = rc = 5) and both without averaging; Q = 8.
+// 256 x 256 workload (r = rc = 5) and r = 8 without averaging; Q = 8.
 bool fused_supported(int q, int r, int rc)
 {
-    return q == 8 && (r == 8 || r == 5) && (rc == r || rc == 0);
+    return q == 8 && ((r == 8 && (rc == 8 || rc == 0)) || (r == 5 && rc == 5));
 }
 
 int fused_tile_width(int rc) { return fused::tile_width(rc); }
@@ -879,7 +913,6 @@ cudaError_t launch_fused(int q, const FusedArgs &a, dim3 grid, cudaStream_t st)
         if (a.r == 8 && a.rc == 8) return fused::launch_qr<8, 8, 8>(a, grid, st);
         if (a.r == 8 && a.rc == 0) return fused::launch_qr<8, 8, 0>(a, grid, st);
         if (a.r == 5 && a.rc == 5) return fused::launch_qr<8, 5, 5>(a, grid, st);
-        if (a.r == 5 && a.rc == 0) return fused::launch_qr<8, 5, 0>(a, grid, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -181,7 +181,7 @@ struct FusedPlan {
     int TW, TH, strips, segs, cap;
 };
 FusedPlan fused_plan(int rows, int W, int r, int rc, int n_sm);
-bool fused_ok(const flr_params &p, int W, const void *g, const void *mg, const void *rad, const void *out);
+bool fused_ok(const flr_params &p, int H, int W, const void *g, const void *mg, const void *rad, const void *out);
 }  // namespace host
 
 // Host-side launchers (defined in the .cu files; q is dispatched to a template).

@@ -101,7 +101,7 @@ extern "C" int flr_denoise_noalloc(const flr_params *p, const float *guide, cons
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(base, 0, 32, s) != cudaSuccess) return FLR_ERR_CUDA;  // counters and status
 
-    if (flr::host::fused_ok(*p, W, guide, map_guide, radiance, out)) {
+    if (flr::host::fused_ok(*p, H, W, guide, map_guide, radiance, out)) {
         const flr::host::FusedPlan pl = flr::host::fused_plan(H, W, p->radius, p->coef_radius, g_n_sm[dev]);
         const int ncta = pl.strips * pl.segs;
         if (ncta <= kMaxFusedCta && (size_t)ncta * pl.cap <= kFusedListInts) {
