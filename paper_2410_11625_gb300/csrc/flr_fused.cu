@@ -112,7 +112,10 @@ struct Geo {
     static constexpr int COLOUR_WARPS = (3 * TW + 31) / 32;
     static constexpr size_t VBUF_FLOATS = ((size_t)kB * NCHB * VS + 31) / 32 * 32;
     static constexpr size_t STAGE_FLOATS = (size_t)2 * NS * kB * WSt;
-    static constexpr size_t SMEM = 128 + 4 * (VBUF_FLOATS + STAGE_FLOATS) + 16;
+    // map-guide rows of a batch's output rows (the apply reads them), double-buffered
+    static constexpr size_t ZBUF_FLOATS = RC > 0 ? ((size_t)Q * kB * TW + 31) / 32 * 32 : 0;
+    static constexpr unsigned ZBYTES = (unsigned)(Q * kB * TW * 4);
+    static constexpr size_t SMEM = 128 + 4 * (VBUF_FLOATS + STAGE_FLOATS + 2 * ZBUF_FLOATS) + 16;
     static_assert(TS <= kTS && TM <= 112 && WSt <= 112, "strip geometry");
     static_assert((kB * WSt * 4) % 128 == 0 && (VBUF_FLOATS * 4) % 128 == 0, "TMA boxes 128-byte aligned");
     static_assert(SOFF + TM <= WSt, "walker columns inside the staged rows");
@@ -345,56 +348,62 @@ __device__ __forceinline__ bool solve_px(const float (&S)[Chan<Q>::NCH], float n
 }
 
 // ---- horizontal sums of one buffer row -------------------------------------------------
-// out[x] = sum_{j=0}^{2K} in[x + j] for x in [x0, x0 + N) (x0 and the rows 16-byte aligned):
-// the first output is a direct (2K + 1)-term sum, the others slide, four per step with 16-byte
-// accesses, then one at a time.  With in == out the row is summed in place: every value is
-// read before its slot is written.
+// out[x] = sum_{j=0}^{2K} in[x + j] for x in [x0, x0 + N) (x0 and the rows 16-byte aligned).
+// The run's N + 2K input values are read from shared memory once, with 16-byte loads, into
+// registers before anything is written (so in == out sums the row in place).  The first
+// output is a direct (2K + 1)-term sum; the others add the differences
+// d(x) = in[x + 2K] - in[x - 1], four per step as prefix sums of the step's differences, so
+// the dependent chain is one add per four outputs.
 template <int K, int N>
 __device__ __forceinline__ void hsum_run(const float *in, float *out, int x0)
 {
-    float S = 0.f;
+    constexpr int NV = N + 2 * K;
+    float v[NV];
 #pragma unroll
-    for (int j = 0; j <= 2 * K; ++j) S += in[x0 + j];
-    float prev = 0.f;
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q) {
-        const int x = x0 + 4 * q;
-        const float4 old = *reinterpret_cast<const float4 *>(in + x);
-        float ent[4];
-        if constexpr ((2 * K) % 4 == 0) {
-            const float4 e4 = *reinterpret_cast<const float4 *>(in + x + 2 * K);
-            ent[0] = e4.x, ent[1] = e4.y, ent[2] = e4.z, ent[3] = e4.w;
+    for (int j = 0; j < NV; j += 4) {
+        if (j + 3 < NV) {
+            const float4 t = *reinterpret_cast<const float4 *>(in + x0 + j);
+            v[j] = t.x, v[j + 1] = t.y, v[j + 2] = t.z, v[j + 3] = t.w;
         } else {
-            const float2 e0 = *reinterpret_cast<const float2 *>(in + x + 2 * K);
-            const float2 e1 = *reinterpret_cast<const float2 *>(in + x + 2 * K + 2);
-            ent[0] = e0.x, ent[1] = e0.y, ent[2] = e1.x, ent[3] = e1.y;
+#pragma unroll
+            for (int i = j; i < NV; ++i) v[i] = in[x0 + i];
         }
-        float4 o;
-        if (q > 0) S = (S + ent[0]) - prev;
-        o.x = S;
-        S = (S + ent[1]) - old.x;
-        o.y = S;
-        S = (S + ent[2]) - old.y;
-        o.z = S;
-        S = (S + ent[3]) - old.z;
-        o.w = S;
-        prev = old.w;
-        *reinterpret_cast<float4 *>(out + x) = o;
+    }
+    float S;
+    {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j <= 2 * K; ++j) t[j & 3] += v[j];
+        S = (t[0] + t[1]) + (t[2] + t[3]);
     }
 #pragma unroll
-    for (int i = (N / 4) * 4; i < N; ++i) {
-        const int x = x0 + i;
-        const float old = in[x];
-        if (i > 0) S = (S + in[x + 2 * K]) - prev;
-        out[x] = S;
-        prev = old;
+    for (int x = 0; x < N; x += 4) {
+        float d[4], o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int xo = x + k;
+            d[k] = (xo > 0 && xo < N) ? v[xo + 2 * K] - v[xo - 1] : 0.f;
+        }
+        const float p1 = d[0], p2 = p1 + d[1], p3 = p2 + d[2], p4 = p3 + d[3];
+        o[0] = S + p1;
+        o[1] = S + p2;
+        o[2] = S + p3;
+        o[3] = S + p4;
+        S = o[3];
+        if (x + 3 < N) {
+            *reinterpret_cast<float4 *>(out + x0 + x) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x + k < N) out[x0 + x + k] = o[k];
+        }
     }
 }
 
 // Kernel parameters: TMA maps of the guide [Q][H][W] and radiance [3][H][W] planes (boxes of
 // WSt columns x kB rows x all planes) and the arguments.
 struct alignas(128) KArgs {
-    CUtensorMap tg, tr;
+    CUtensorMap tg, tr, tz;  // tz: the map guide, boxes of TW columns x kB rows x Q planes
     FusedArgs a;
 };
 
@@ -430,7 +439,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
     unsigned char *base = smem_raw + ((128 - (tma::smem_addr(smem_raw) & 127)) & 127);
     float *Vbuf = reinterpret_cast<float *>(base);  // [kB][NCHB][VS]: channel rows
     float *stage = Vbuf + G::VBUF_FLOATS;            // [2][NS][kB][WSt]: entering, leaving rows
-    uint64_t *bar = reinterpret_cast<uint64_t *>(stage + G::STAGE_FLOATS);
+    float *zbuf = stage + G::STAGE_FLOATS;           // [2][Q][kB][TW]: map-guide rows of the outputs
+    uint64_t *bar = reinterpret_cast<uint64_t *>(zbuf + 2 * G::ZBUF_FLOATS);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tma::smem_addr(&s_tmem)),
@@ -454,14 +464,16 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
     const int slot_k = warp >> 2;
 
     // stage the entering (vb + R) and leaving (vb - R - 1) input rows of batch v
+    // and, with averaging, the map-guide rows of its output rows v - RC .. into zbuf[batch & 1]
     auto stage_batch = [&](int v) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads before the copies
-        tma::mbar_expect_tx(bar, (unsigned)(2 * NS * kB * WSt * 4));
+        tma::mbar_expect_tx(bar, (unsigned)(2 * NS * kB * WSt * 4) + (RC > 0 ? G::ZBYTES : 0u));
         const size_t box = (size_t)kB * WSt;
         tma::load_3d(stage, &ka.tg, x0 - G::RA, v + R, 0, bar);
         tma::load_3d(stage + Q * box, &ka.tr, x0 - G::RA, v + R, 0, bar);
         tma::load_3d(stage + NS * box, &ka.tg, x0 - G::RA, v - R - 1, 0, bar);
         tma::load_3d(stage + (NS + Q) * box, &ka.tr, x0 - G::RA, v - R - 1, 0, bar);
+        if constexpr (RC > 0) tma::load_3d(zbuf + ((v - v0) / kB & 1) * G::ZBUF_FLOATS, &ka.tz, x0, v - RC, 0, bar);
     };
     if (tid == 0) stage_batch(v0);
     int nstaged = 1, nconsumed = 0;
@@ -657,16 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
             if (warp < G::COLOUR_WARPS) {
                 // map-guide values of this batch's output rows, loaded first so that their
                 // latency overlaps the tensor-memory traffic below
-                float zv[kB][Q];
-                const float *zcol = zg + (colour && cgx < W ? cgx : 0);
-#pragma unroll
-                for (int b = 0; b < kB; ++b) {
-                    const int y = v + b - RC;
-                    const bool row_out = y >= y0 && y < y1;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i)
-                        zv[b][i] = row_out ? __ldg(zcol + i * plane + (size_t)y * W) - s_sh[i] : 0.f;
-                }
+                const float *zb = zbuf + ((v - v0) / kB & 1) * G::ZBUF_FLOATS + (colour ? cx : 0);
                 float Ec[Q + 1], Dc[Q + 1];
                 if (v <= m_lo) {
 #pragma unroll
@@ -728,7 +731,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                         const float my = (float)(min(y + RC, H - 1) - max(y - RC, 0) + 1);
                         float o = Ec[0] - Dc[0];
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) o = fmaf(Ec[1 + i] - Dc[1 + i], zv[b][i], o);
+                        for (int i = 0; i < Q; ++i)
+                            o = fmaf(Ec[1 + i] - Dc[1 + i], zb[(i * kB + b) * TW] - s_sh[i], o);
                         o = fmaf(o, inv_mx / my, s_sh[Q + cc]);
                         a.out[cc * plane + (size_t)y * W + cgx] = o;
                         bad += !isfinite(o);
@@ -890,7 +894,9 @@ cudaError_t launch_qr(const FusedArgs &a, dim3 grid, cudaStream_t st)
     std::memset(&ka, 0, sizeof(ka));
     ka.a = a;
     if (tma::encode_planes_f32(&ka.tg, a.guide, a.W, a.H, Q, G::WSt, kB, Q) != cudaSuccess ||
-        tma::encode_planes_f32(&ka.tr, a.rad, a.W, a.H, 3, G::WSt, kB, 3) != cudaSuccess)
+        tma::encode_planes_f32(&ka.tr, a.rad, a.W, a.H, 3, G::WSt, kB, 3) != cudaSuccess ||
+        tma::encode_planes_f32(&ka.tz, a.map_guide ? a.map_guide : a.guide, a.W, a.H, Q, G::TW, kB, Q) !=
+            cudaSuccess)
         return cudaErrorInvalidValue;
     flr_fused_kernel<Q, R, RC><<<grid, kThreads, G::SMEM, st>>>(ka);
     return cudaGetLastError();
