@@ -779,7 +779,7 @@ template <int Q>
 __global__ void __launch_bounds__(kFixThreads) flr_fused_fix_kernel(const FusedArgs a)
 {
     constexpr int NS = Q + 3, NCF = 3 * (Q + 1);
-    __shared__ float s_model[kFixWarps][NCF];
+    __shared__ double s_model[kFixWarps][NCF];
     __shared__ float s_sh[NS];
     __shared__ unsigned long long s_cnt[2];
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
@@ -812,9 +812,9 @@ __global__ void __launch_bounds__(kFixThreads) flr_fused_fix_kernel(const FusedA
             if (lane == 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    s_model[warp][c * (Q + 1)] = (float)bv[c];
+                    s_model[warp][c * (Q + 1)] = bv[c];
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) s_model[warp][c * (Q + 1) + 1 + i] = (float)A[i][c];
+                    for (int i = 0; i < Q; ++i) s_model[warp][c * (Q + 1) + 1 + i] = A[i][c];
                 }
             }
         }
@@ -822,12 +822,11 @@ __global__ void __launch_bounds__(kFixThreads) flr_fused_fix_kernel(const FusedA
         const int ne = min(kFixWarps, n - e0);
         for (int k = 0; k < ne; ++k) {
             const int idx = list[e0 + k], py = idx / W, px = idx % W;
-            const float *md = s_model[k];
+            const double *md = s_model[k];
             if (rc == 0) {
                 if (tid < 3 && py >= y0 && py < y1 && px >= x0 && px < x1) {
-                    double o = (double)md[tid * (Q + 1)];
-                    for (int i = 0; i < Q; ++i)
-                        o += (double)md[tid * (Q + 1) + 1 + i] * ((double)zg[i * plane + idx] - (double)s_sh[i]);
+                    double o = md[tid * (Q + 1)];
+                    for (int i = 0; i < Q; ++i) o += md[tid * (Q + 1) + 1 + i] * ((double)zg[i * plane + idx] - (double)s_sh[i]);
                     const float of = (float)(o + (double)s_sh[Q + tid]);
                     a.out[tid * plane + idx] = of;
                     dbad += !isfinite(of);
@@ -840,13 +839,13 @@ __global__ void __launch_bounds__(kFixThreads) flr_fused_fix_kernel(const FusedA
                     const size_t off = (size_t)yy * W + xx;
                     const float my = (float)(min(yy + rc, H - 1) - max(yy - rc, 0) + 1);
                     const float mx = (float)(min(xx + rc, W - 1) - max(xx - rc, 0) + 1);
-                    float zz[Q];
-                    for (int i = 0; i < Q; ++i) zz[i] = __ldg(zg + i * plane + off) - s_sh[i];
+                    double zz[Q];
+                    for (int i = 0; i < Q; ++i) zz[i] = (double)__ldg(zg + i * plane + off) - (double)s_sh[i];
                     for (int c = 0; c < 3; ++c) {
-                        float o = md[c * (Q + 1)];
-                        for (int i = 0; i < Q; ++i) o = fmaf(md[c * (Q + 1) + 1 + i], zz[i], o);
+                        double o = md[c * (Q + 1)];
+                        for (int i = 0; i < Q; ++i) o += md[c * (Q + 1) + 1 + i] * zz[i];
                         const float old = a.out[c * plane + off];
-                        const float nw = fmaf(o, 1.0f / (my * mx), old);
+                        const float nw = (float)((double)old + o / ((double)my * (double)mx));
                         a.out[c * plane + off] = nw;
                         dbad += (long long)!isfinite(nw) - (long long)!isfinite(old);
                     }
