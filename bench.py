@@ -292,6 +292,46 @@ def serving_batch(flr, torch, np, dev, stream, n_iter=100):
             "what": "flr_fast_denoise_batch: one persistent cooperative kernel, 4 stages x 8 frames"}
 
 
+def serving_batch_flnr(torch, np, dev, weights, n_iter=100):
+    """The same 8 frames with the FLNR guide network in the step (config of the batched serving
+    pattern: FP32 FLR plus the BF16 guide CNN): per frame size, the network's forward over the
+    half-resolution inputs gives the model guides, then one persistent fast-FLR launch; the
+    step is one captured CUDA graph."""
+    import synth
+    from paper_2410_11625_gb300 import serving
+    sizes = [(720, 1280), (1080, 1920), (1440, 2560)]
+    groups = []
+    for i, (Ho, Wo) in enumerate(sizes):
+        g, y = synth.render(100 + i, Ho, Wo)
+        n = 3 if i < 2 else 2
+        lo = np.concatenate([g[:, ::2, ::2], y[:, ::2, ::2]])
+        x = torch.from_numpy(np.ascontiguousarray(np.repeat(lo[None], n, axis=0))).to(dev)
+        z = torch.from_numpy(np.ascontiguousarray(np.repeat(g[None], n, axis=0))).to(dev)
+        groups.append((x, z, torch.empty((n, 3, Ho, Wo), device=dev)))
+    b = serving.GuidedBatch(groups, weights, factor=4)
+    for _ in range(5):
+        b.run()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_iter)]
+    for e0, e1 in evs:
+        e0.record(b.stream)
+        b.run()
+        e1.record(b.stream)
+    b.stream.synchronize()
+    lat = sorted(e0.elapsed_time(e1) for e0, e1 in evs)
+    status = b.status()
+    b.close()
+    px = 3 * 1280 * 720 + 3 * 1920 * 1080 + 2 * 2560 * 1440
+    mean = sum(lat) / len(lat)
+    return {"frames": 8, "outputs": "3x 1280x720, 3x 1920x1080, 2x 2560x1440", "inputs": "half resolution",
+            "launches_per_batch": "3 network forward passes (one per frame size, 8 kernels each) + 1 persistent FLR",
+            "graph": True, "batch_latency_ms_p50": round(lat[len(lat) // 2], 4),
+            "batch_latency_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
+            "frames_per_s": round(8 / (mean * 1e-3), 1), "output_mpix_per_s": round(px / (mean * 1e-3) / 1e6, 1),
+            "status": "ok" if status == 0 else "timeout",
+            "what": "serving.GuidedBatch: FLNR (BF16 tcgen05) model guides at half resolution + "
+                    "flr_fast_denoise_batch, one CUDA graph"}
+
+
 ROW_NAMES = ("backward", "fast", "joint", "serving", "flnr")
 
 # FLNR network (Sec. 3.3): multiply-accumulates per full-resolution pixel, layer by layer
@@ -460,6 +500,8 @@ def run_ours(args):
                                            "what": "Sec. 3.2.1: 960x540 radiance and model guides, 1920x1080 map guide and output"}
     if "serving" in want:
         rows["batch_serving"] = serving_batch(flr, torch, np, dev, stream)
+        from paper_2410_11625_gb300 import flnr as _flnr
+        rows["batch_serving_flnr"] = serving_batch_flnr(torch, np, dev, _flnr.init_weights(0))
     if rank == 0 and "flnr" in want:
         rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps))
 

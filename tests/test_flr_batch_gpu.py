@@ -112,3 +112,41 @@ def test_per_pixel_batch_equals_per_frame(flr):
     for (g, y, _, o) in frames:
         assert torch.equal(f.denoise(g, y), o)
     f.close()
+
+
+def test_batch_with_guide_network(flr):
+    """The serving step with the FLNR guide network (serving.GuidedBatch): per frame size,
+    the network's forward pass over the half-resolution inputs gives the model guides, then
+    one persistent fast-FLR launch does joint denoising and 2x upsampling of every frame;
+    the step is a captured CUDA graph, replayed twice.  The guides equal a separate forward
+    pass of the network, bit for bit, and each frame's result meets the FP64 oracle of fast
+    FLR run on those guides (the map guide differs from the model guide: the absolute bar
+    of the joint-upsampling tests)."""
+    import torch
+
+    from paper_2410_11625_gb300 import flnr, serving
+    weights = flnr.init_weights(3)
+    groups = []
+    for i, (h, w) in enumerate([(32, 48), (48, 64)]):
+        xs, zs = [], []
+        for j in range(2):
+            g_lo, y_lo = synth.render(40 + 2 * i + j, h, w)
+            g_hi, _ = synth.render(40 + 2 * i + j, 2 * h, 2 * w)
+            xs.append(np.concatenate([g_lo, y_lo]))
+            zs.append(g_hi)
+        groups.append((torch.from_numpy(np.stack(xs)).cuda(), torch.from_numpy(np.stack(zs)).cuda(),
+                       torch.empty((2, 3, 2 * h, 2 * w), device="cuda")))
+    b = serving.GuidedBatch(groups, weights, factor=4)
+    b.run()
+    b.run()
+    assert b.status() == 0
+    net = flnr.FLNR(2 * 48 * 64, weights)
+    for (x, z, o), e in zip(groups, b.enh):
+        assert torch.equal(net.forward(x), e)
+        for n in range(x.shape[0]):
+            ref = oracle.flr_fast(e[n].cpu().numpy(), x[n, 8:].cpu().numpy(), factor=4,
+                                  map_guide=z[n].cpu().numpy(), scale=2)
+            got = o[n].cpu().numpy()
+            assert np.max(np.abs(got - ref)) <= TOL * np.sqrt(np.mean(ref ** 2))
+    net.close()
+    b.close()
