@@ -6,20 +6,22 @@ The network maps the 11 input channels (Q = 8 guides and the noisy RGB radiance,
 concatenated channel-wise, Sec. 3.3) to 8 enhanced guide channels through a 3-level U-Net
 (Sec. 3.3's blocks; widths 16 / 32 / 64, ReLU as the activation):
   input              guides X unchanged, radiance Y as log(1 + max(Y, 0))
-  input projection   conv3x3 11->16, ReLU;  conv1x1 16->16, ReLU              -> f0 (H)
-  encoder level 1    avgpool 2x2;  conv3x3 16->32, ReLU;  conv3x3 32->32, ReLU -> f1 (H/2)
-  encoder level 2    avgpool 2x2;  conv3x3 32->64, ReLU;  conv3x3 64->64, ReLU -> f2 (H/4)
+  input projection   conv3x3 11->16, ReLU;  conv1x1 16->16, ReLU                    -> f0 (H)
+  encoder level 1    conv3x3 16->32, ReLU;  conv3x3 32->32 stride 2, ReLU           -> f1 (H/2)
+  encoder level 2    conv3x3 32->64, ReLU;  conv3x3 64->64 stride 2, ReLU           -> f2 (H/4)
   decoder level 1    nearest 2x up(f2) ++ f1;  conv3x3 96->32, ReLU;  conv3x3 32->32, ReLU -> d1
   decoder level 0    nearest 2x up(d1) ++ f0;  conv3x3 48->16, ReLU;  conv3x3 16->16, ReLU -> d0
-  output             conv3x3 16->16, ReLU;  conv1x1 16->8;  sigmoid          -> X'
-All 3x3 convolutions have stride 1 and zero padding 1.  H and W must be multiples of 4.
+  output             conv3x3 16->16, ReLU;  conv1x1 16->8;  sigmoid                -> X'
+Sec. 3.3: each encoder block is two 3x3 convolutions, the second striding by 2 to
+downsample (no separate pooling).  Every 3x3 convolution has zero padding 1; a stride-2 one
+gives output (i, j) from inputs (2i + u - 1, 2j + v - 1).  H and W must be multiples of 4.
 Weights are [Cout][Cin][kh][kw] with a bias per output channel.
 
 `bf16_storage=True` takes the network's rounding decisions in the precision a BF16
-implementation stores (every product and sum still in float64): the input, the weights,
-each ReLU output and each pooled map are rounded to bfloat16 (round to nearest even) on
-the forward pass; on the reverse pass the gradient with respect to each pre-activation,
-each pooled map and each concatenation is rounded to bfloat16.  The ReLU masks are then
+implementation stores (every product and sum still in float64): the input, the weights and
+each ReLU output are rounded to bfloat16 (round to nearest even) on the forward pass; on
+the reverse pass the gradient with respect to each pre-activation and each concatenation is
+rounded to bfloat16.  The ReLU masks are then
 the same on both sides, which the comparison of gradients needs: a mask decided
 differently at one pixel changes that pixel's whole contribution to a weight gradient.
 """
@@ -87,21 +89,18 @@ def forward(x, params, bf16_storage=False):
     R = _RoundValue.apply if bf16_storage else (lambda t: t)
     G = _RoundGrad.apply if bf16_storage else (lambda t: t)
 
-    def conv(t, name, relu):
+    def conv(t, name, relu, stride=1):
         w, b = R(params[name + ".w"]), params[name + ".b"]
-        z = G(F.conv2d(t, w, b, padding=w.shape[-1] // 2))
+        z = G(F.conv2d(t, w, b, stride=stride, padding=w.shape[-1] // 2))
         return R(F.relu(z)) if relu else z
-
-    def pool(t):
-        return G(R(F.avg_pool2d(t, 2)))
 
     def upcat(lo, skip):
         return G(torch.cat([F.interpolate(lo, scale_factor=2, mode="nearest"), skip], dim=1))
 
     x = torch.cat([x[:, :8], torch.log1p(torch.clamp(x[:, 8:], min=0.0))], dim=1)
     f0 = conv(conv(R(x), "in0", True), "in1", True)
-    f1 = conv(conv(pool(f0), "e1a", True), "e1b", True)
-    f2 = conv(conv(pool(f1), "e2a", True), "e2b", True)
+    f1 = conv(conv(f0, "e1a", True), "e1b", True, stride=2)
+    f2 = conv(conv(f1, "e2a", True), "e2b", True, stride=2)
     d1 = conv(conv(upcat(f2, f1), "d1a", True), "d1b", True)
     d0 = conv(conv(upcat(d1, f0), "d0a", True), "d0b", True)
     return torch.sigmoid(conv(conv(d0, "o0", True), "o1", False))
@@ -122,16 +121,19 @@ def forward_backward(x, params, grad_out, bf16_storage=False):
     return out.detach().numpy(), grads
 
 
-def conv2d_direct(x, w, b):
-    """Reference 2-D convolution by explicit summation (stride 1, zero padding k//2):
-    y[n, o, i, j] = b[o] + sum_{c, u, v} w[o, c, u, v] x[n, c, i + u - k//2, j + v - k//2]."""
+def conv2d_direct(x, w, b, stride=1):
+    """Reference 2-D convolution by explicit summation (zero padding k//2):
+    y[n, o, i, j] = b[o] + sum_{c, u, v} w[o, c, u, v] x[n, c, s i + u - k//2, s j + v - k//2]
+    for output (i, j), i < ceil(H / s), j < ceil(W / s)."""
     N, C, H, W = x.shape
     O, _, k, _ = w.shape
     p = k // 2
-    xp = np.zeros((N, C, H + 2 * p, W + 2 * p))
+    Ho, Wo = (H + stride - 1) // stride, (W + stride - 1) // stride
+    xp = np.zeros((N, C, H + 2 * p + stride, W + 2 * p + stride))
     xp[:, :, p:p + H, p:p + W] = x
-    y = np.zeros((N, O, H, W)) + b[None, :, None, None]
+    y = np.zeros((N, O, Ho, Wo)) + b[None, :, None, None]
     for u in range(k):
         for v in range(k):
-            y += np.einsum("oc,nchw->nohw", w[:, :, u, v], xp[:, :, u:u + H, v:v + W])
+            tap = xp[:, :, u:u + stride * Ho:stride, v:v + stride * Wo:stride]
+            y += np.einsum("oc,nchw->nohw", w[:, :, u, v], tap)
     return y

@@ -1,7 +1,9 @@
 """Pins of the FLNR network oracle (oracle/flnr_ref.py, PyTorch CPU float64).
 
 * torch's conv2d as used (cross-correlation, zero padding k//2) equals an explicit
-  summation over taps, for 3x3 and 1x1 kernels;
+  summation over taps, for 3x3 and 1x1 kernels, at stride 1 and at the encoder's stride 2
+  (Sec. 3.3), which is also the stride-1 result at even rows and columns and, on a tiny
+  input, a pure-Python loop over every output, channel and tap;
 * the autograd gradients equal Richardson central differences of the forward pass, for
   weights, biases of several layers and the input (steps of 1e-6 keep every ReLU on one
   side of its kink);
@@ -25,6 +27,41 @@ def test_conv_matches_explicit_sum(k):
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
+@pytest.mark.parametrize("H,W", [(8, 12), (9, 7)])
+def test_stride_two_conv_matches_explicit_sum_and_subsampling(H, W):
+    rng = np.random.default_rng(H * W)
+    x = rng.normal(size=(2, 5, H, W))
+    w = rng.normal(size=(4, 5, 3, 3))
+    b = rng.normal(size=4)
+    ref = flnr_ref.conv2d_direct(x, w, b, stride=2)
+    assert ref.shape == (2, 4, (H + 1) // 2, (W + 1) // 2)
+    got = torch.nn.functional.conv2d(torch.tensor(x), torch.tensor(w), torch.tensor(b), stride=2, padding=1).numpy()
+    assert np.max(np.abs(got - ref)) < 1e-12
+    full = flnr_ref.conv2d_direct(x, w, b)
+    assert np.max(np.abs(full[:, :, ::2, ::2] - ref)) < 1e-12
+
+
+def test_stride_two_conv_brute_force():
+    """Output (i, j) of a stride-2 3x3 convolution with zero padding 1 reads inputs
+    (2i - 1 .. 2i + 1, 2j - 1 .. 2j + 1); written out element by element."""
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(1, 2, 5, 6))
+    w = rng.normal(size=(3, 2, 3, 3))
+    b = rng.normal(size=3)
+    ref = flnr_ref.conv2d_direct(x, w, b, stride=2)
+    for o in range(3):
+        for i in range(3):
+            for j in range(3):
+                acc = b[o]
+                for c in range(2):
+                    for u in range(3):
+                        for v in range(3):
+                            yy, xx = 2 * i + u - 1, 2 * j + v - 1
+                            if 0 <= yy < 5 and 0 <= xx < 6:
+                                acc += w[o, c, u, v] * x[0, c, yy, xx]
+                assert abs(acc - ref[0, o, i, j]) < 1e-12
+
+
 def test_gradients_match_finite_differences():
     rng = np.random.default_rng(1)
     params = {k: v.astype(np.float64) for k, v in flnr_ref.init_weights(3).items()}
@@ -44,7 +81,8 @@ def test_gradients_match_finite_differences():
         return (4 * (f(h / 2) - f(-h / 2)) / h - (f(h) - f(-h)) / (2 * h)) / 3
 
     for name, idx in [("in0.w", (3, 7, 1, 2)), ("e2b.w", (10, 20, 0, 1)), ("d1a.w", (5, 70, 2, 2)),
-                      ("o1.w", (6, 9, 0, 0)), ("o0.b", (4,)), ("e1a.b", (17,))]:
+                      ("o1.w", (6, 9, 0, 0)), ("o0.b", (4,)), ("e1a.b", (17,)), ("e1b.w", (2, 9, 2, 0)),
+                      ("e2a.w", (40, 3, 1, 1)), ("e1b.b", (30,))]:
         def f(t, name=name, idx=idx):
             p = dict(params)
             p[name] = params[name].copy()
@@ -83,7 +121,7 @@ def test_bf16_rounding_is_nearest_even():
 def test_bf16_storage_forward_matches_explicit_rounding():
     """The emulated forward equals a numpy restatement: log(1 + max(Y, 0)) radiance input,
     explicit-sum convolutions in float64 with bit-level bfloat16 rounding of the input,
-    weights, ReLU outputs and pooled maps (Sec. 3.3's network)."""
+    weights and ReLU outputs (Sec. 3.3's network, stride-2 encoder convolutions)."""
     rng = np.random.default_rng(7)
     params = flnr_ref.init_weights(4)
     for k in params:
@@ -94,21 +132,18 @@ def test_bf16_storage_forward_matches_explicit_rounding():
     pt = {k: torch.tensor(v.astype(np.float64)) for k, v in params.items()}
     got = flnr_ref.forward(torch.tensor(x), pt, bf16_storage=True).numpy()
 
-    def conv(t, n, relu=True):
-        z = flnr_ref.conv2d_direct(t, bf16_bits(params[n + ".w"]), params[n + ".b"].astype(np.float64))
+    def conv(t, n, relu=True, stride=1):
+        z = flnr_ref.conv2d_direct(t, bf16_bits(params[n + ".w"]), params[n + ".b"].astype(np.float64),
+                                   stride=stride)
         return bf16_bits(np.maximum(z, 0.0)) if relu else z
-
-    def pool(t):
-        N, C, H, W = t.shape
-        return bf16_bits(t.reshape(N, C, H // 2, 2, W // 2, 2).mean(axis=(3, 5)))
 
     def up(t):
         return t.repeat(2, axis=2).repeat(2, axis=3)
 
     xin = np.concatenate([x[:, :8], np.log1p(np.maximum(x[:, 8:], 0.0))], axis=1)
     f0 = conv(conv(bf16_bits(xin), "in0"), "in1")
-    f1 = conv(conv(pool(f0), "e1a"), "e1b")
-    f2 = conv(conv(pool(f1), "e2a"), "e2b")
+    f1 = conv(conv(f0, "e1a"), "e1b", stride=2)
+    f2 = conv(conv(f1, "e2a"), "e2b", stride=2)
     d1 = conv(conv(np.concatenate([up(f2), f1], 1), "d1a"), "d1b")
     d0 = conv(conv(np.concatenate([up(d1), f0], 1), "d0a"), "d0b")
     ref = 1.0 / (1.0 + np.exp(-conv(conv(d0, "o0"), "o1", relu=False)))
