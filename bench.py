@@ -335,9 +335,11 @@ def serving_batch_flnr(torch, np, dev, weights, n_iter=100):
 ROW_NAMES = ("backward", "fast", "joint", "serving", "flnr")
 
 # FLNR network (Sec. 3.3): multiply-accumulates per full-resolution pixel, layer by layer
-# (Cin x Cout x k^2, divided by 4 at half and 16 at quarter resolution)
-FLNR_MACS_PER_PIXEL = (11 * 16 * 9 + 16 * 16 + (16 * 32 * 9 + 32 * 32 * 9) / 4 + (32 * 64 * 9 + 64 * 64 * 9) / 16
-                       + (96 * 32 * 9 + 32 * 32 * 9) / 4 + 48 * 16 * 9 + 16 * 16 * 9 + 16 * 16 * 9 + 16 * 8)
+# (Cin x Cout x k^2 per output pixel, divided by 4 at half and 16 at quarter resolution; the
+# stride-2 encoder convolutions e1b and e2b produce half- and quarter-resolution outputs)
+FLNR_MACS_PER_PIXEL = (11 * 16 * 9 + 16 * 16 + 16 * 32 * 9 + (32 * 32 * 9) / 4 + (32 * 64 * 9) / 4
+                       + (64 * 64 * 9) / 16 + (96 * 32 * 9 + 32 * 32 * 9) / 4 + 48 * 16 * 9 + 16 * 16 * 9
+                       + 16 * 16 * 9 + 16 * 8)
 
 
 def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):

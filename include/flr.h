@@ -309,11 +309,13 @@ int flr_mbarrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
 /*
  * FLNR (Sec. 3.3, "Fast Local Neural Regression"): a U-Net maps the guides and the noisy
  * radiance, concatenated channel-wise (11 channels: Q = 8 guides, then RGB), to 8 enhanced
- * guide channels that FLR then uses (Fig. 2).  Layers, in order (3x3 convolutions stride 1,
- * zero padding 1; ReLU unless stated):
- *   in0 3x3 11->16, in1 1x1 16->16 | avgpool, e1a 3x3 16->32, e1b 3x3 32->32 |
- *   avgpool, e2a 3x3 32->64, e2b 3x3 64->64 | up2 ++ e1b: d1a 3x3 96->32, d1b 3x3 32->32 |
+ * guide channels that FLR then uses (Fig. 2).  Layers, in order (3x3 convolutions with zero
+ * padding 1, stride 1 unless stated; ReLU unless stated):
+ *   in0 3x3 11->16, in1 1x1 16->16 | e1a 3x3 16->32, e1b 3x3 32->32 stride 2 |
+ *   e2a 3x3 32->64, e2b 3x3 64->64 stride 2 | up2 ++ e1b: d1a 3x3 96->32, d1b 3x3 32->32 |
  *   up2 ++ in1: d0a 3x3 48->16, d0b 3x3 16->16 | o0 3x3 16->16, o1 1x1 16->8 + sigmoid.
+ * Each encoder block downsamples with its second convolution (stride 2, Sec. 3.3): output
+ * (i, j) reads inputs (2i - 1 .. 2i + 1, 2j - 1 .. 2j + 1).
  * The network reads the radiance channels as log(1 + max(Y, 0)) (fireflies stay bounded).
  * BF16 convolutions on the tensor cores with FP32 accumulation (forward: tcgen05 UMMA with
  * accumulators in tensor memory; backward: warp-level MMA); FP32 master weights.
@@ -347,27 +349,28 @@ int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, 
  * flnr_guide_forward and flnr_guide_backward use for that layer (Sec. 3.3), so that each
  * can be checked on its own.  (flnr_guide_forward runs in0 with in1, and o0 with o1, as
  * one fused pass each; the products and their order are those of the separate layers.)
- * layer = 0..11 in the order above.  Tensors are
+ * layer = 0..11 in the order above; (N, H, W) is the layer's input size.  Tensors are
  * device NHWC bfloat16 (raw 16-bit patterns) with channel counts padded to multiples of
  * 16: CinP = 16 * ceil(Cin / 16), CoutP likewise; the padding channels of the outputs are
- * written (as zero where the padded weights are zero).
- *   FLNR_OP_FORWARD  a = x [N][H][W][CinP]; out = y [N][H][W][CoutP] = bf16(ReLU(conv(x) + b)),
+ * written (as zero where the padded weights are zero).  The output size (Ho, Wo) is
+ * (H, W), or (H/2, W/2) for the stride-2 layers 3 and 5 (which need H and W even).
+ *   FLNR_OP_FORWARD  a = x [N][H][W][CinP]; out = y [N][Ho][Wo][CoutP] = bf16(ReLU(conv(x) + b)),
  *                    or, for layer 11, float32 planar [N][8][H][W] = sigmoid(conv(x) + b).
  *                    Layers 6 and 8 with b != NULL: a = the half-resolution decoder input
  *                    [N][H/2][W/2][64 or 32] and b = the skip [N][H][W][32 or 16]; the
  *                    result is the convolution of their concatenation (nearest 2x
  *                    upsampling of a, then b), which the kernel never forms: each output
  *                    parity class reads a and the skip's parity planes directly, as the
- *                    network does.  Layers 1 and 3 with out2 != NULL:
- *                    out2 [N][H/2][W/2][CoutP] also receives the 2x2 average of the stored
- *                    bf16 outputs, rounded to bf16, as the network's encoder reads it.
- *                    Both fused forms need H and W even.
- *   FLNR_OP_DGRAD    a = dz [N][H][W][CoutP] (gradient w.r.t. the layer's pre-activation);
+ *                    network does (H and W even).
+ *   FLNR_OP_DGRAD    a = dz [N][Ho][Wo][CoutP] (gradient w.r.t. the layer's pre-activation);
  *                    mask = [N][H][W][CinP] or NULL; out = dx [N][H][W][CinP] =
  *                    bf16((mask > 0) * transposed convolution of dz)
- *   FLNR_OP_WGRAD    a = x, b = dz; adds dL/dW and dL/db of the layer into the gradient
- *                    buffer (flnr_get_grads / flnr_zero_grads)
- * Runs on `stream` without waiting.  Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
+ *   FLNR_OP_WGRAD    a = x [N][H][W][CinP], b = dz [N][Ho][Wo][CoutP]; adds dL/dW and dL/db
+ *                    of the layer into the gradient buffer (flnr_get_grads / flnr_zero_grads)
+ * For layers 3 and 5 the two gradient ops first spread dz onto the input grid (zeros at odd
+ * rows and columns) in the network's scratch, which must hold N*H*W*CoutP values
+ * (N*H*W*CoutP <= 48 * max_pixels, else FLR_ERR_UNSUPPORTED).
+ * Runs on `stream` without waiting.  Errors: FLR_ERR_ARG, FLR_ERR_UNSUPPORTED, FLR_ERR_CUDA.
  */
 /*
  * Waits for the device and reports whether a tensor-core kernel of this network ran out of
@@ -381,7 +384,7 @@ int flnr_status(flnr_net *net);
 #define FLNR_OP_DGRAD 1
 #define FLNR_OP_WGRAD 2
 int flnr_layer(flnr_net *net, int layer, int op, const void *a, const void *b, const void *mask, void *out,
-               void *out2, int N, int H, int W, void *stream);
+               int N, int H, int W, void *stream);
 
 /*
  * Backward pass of the last forward: grad_out [N][8][H][W] = dL/d(enhanced guides);

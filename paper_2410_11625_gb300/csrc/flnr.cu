@@ -6,8 +6,8 @@
 //
 // Network (weights and order as oracle/flnr_ref.py): 11 inputs (8 guides + noisy RGB)
 //   in0 3x3 11->16 ReLU, in1 1x1 16->16 ReLU                                   f0 (H)
-//   avgpool, e1a 3x3 16->32 ReLU, e1b 3x3 32->32 ReLU                          f1 (H/2)
-//   avgpool, e2a 3x3 32->64 ReLU, e2b 3x3 64->64 ReLU                          f2 (H/4)
+//   e1a 3x3 16->32 ReLU, e1b 3x3 32->32 stride 2 ReLU                          f1 (H/2)
+//   e2a 3x3 32->64 ReLU, e2b 3x3 64->64 stride 2 ReLU                          f2 (H/4)
 //   up(f2) ++ f1, d1a 3x3 96->32 ReLU, d1b 3x3 32->32 ReLU                     d1 (H/2)
 //   up(d1) ++ f0, d0a 3x3 48->16 ReLU, d0b 3x3 16->16 ReLU                     d0 (H)
 //   o0 3x3 16->16 ReLU, o1 1x1 16->8, sigmoid                                  X' (8 ch)
@@ -71,7 +71,6 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //   OUTM 1 -> yf planar fp32 [N][8][H][W], sigmoid of channels 0..7;
 //   MASK   -> the result times (mask > 0), mask [N][H][W][COUT] bf16 (the ReLU of the
 //             layer input, for input gradients);
-//   POOL   -> also yp [N][H/2][W/2][COUT], the 2x2 average of the bf16 outputs (H, W even).
 // The decoder kernel reads x as the half-resolution map [N][H/2][W/2][CA] and x2 as the
 // skip [N][H][W][CIN-CA] of the concatenated input up2(x) ++ x2.
 struct ConvArgs {
@@ -82,7 +81,6 @@ struct ConvArgs {
     int N, H, W, ystride;
     int nbias;  // valid bias entries (the true output channels); 0 without bias
     const bf16 *x2;
-    bf16 *yp;
     int *status;  // tensor-core path: set to FLNR_STATUS_TIMEOUT if a completion wait ran out
 };
 
@@ -335,12 +333,11 @@ __device__ __forceinline__ void tc_load_acc(uint32_t taddr, float (&v)[COUT])
     asm volatile("tcgen05.fence::before_thread_sync;\n");
 }
 
-// tc_store: bias, activation, optional ReLU mask, then bf16 NHWC stores (with the 2x2 pool of
-// the stored values when POOL: column pairs are lanes l, l ^ 1, row pairs lanes l, l ^ 8), or
-// sigmoid into planar fp32 (OUTM 1).  (n, yy, xx): the pixel; every lane of the warp calls it.
-template <int COUT, int ACT, int OUTM, bool MASK, bool POOL>
+// tc_store: bias, activation, optional ReLU mask, then bf16 NHWC stores, or sigmoid into
+// planar fp32 (OUTM 1).  (n, yy, xx): the output pixel of an [N][a.H][a.W] map.
+template <int COUT, int ACT, int OUTM, bool MASK>
 __device__ __forceinline__ void tc_store(const ConvArgs &a, float (&v)[COUT], const float (&bias)[COUT], int n,
-                                         int yy, int xx, int lane)
+                                         int yy, int xx)
 {
     const bool in = yy < a.H && xx < a.W;
     const size_t pix = ((size_t)n * a.H + yy) * a.W + xx;
@@ -369,21 +366,6 @@ __device__ __forceinline__ void tc_store(const ConvArgs &a, float (&v)[COUT], co
 #pragma unroll
             for (int i = 0; i < 4; ++i) oh[i] = __floats2bfloat162_rn(v[c8 * 8 + 2 * i], v[c8 * 8 + 2 * i + 1]);
             if (in) *reinterpret_cast<uint4 *>(a.y + pix * a.ystride + c8 * 8) = o;
-            if (POOL) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float s0 = __bfloat162float(oh[i].x), s1 = __bfloat162float(oh[i].y);
-                    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-                    s0 += __shfl_xor_sync(0xffffffffu, s0, 8);
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, 8);
-                    oh[i] = __floats2bfloat162_rn(0.25f * s0, 0.25f * s1);
-                }
-                if (in && (lane & 9) == 0) {
-                    const size_t pp = ((size_t)n * (a.H / 2) + yy / 2) * (a.W / 2) + xx / 2;
-                    *reinterpret_cast<uint4 *>(a.yp + pp * COUT + c8 * 8) = o;
-                }
-            }
         }
     } else if (in) {
         const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
@@ -415,7 +397,7 @@ struct WsGeom {
 };
 constexpr int kWsThreads = 192;
 
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool POOL>
+template <int CIN, int COUT, int KS, int ACT, int OUTM>
 __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_constant__ TcArgs args)
 {
     using G = WsGeom<CIN, COUT, KS>;
@@ -545,7 +527,7 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_consta
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
             int n, ty0, tx0;
             origin(j, n, ty0, tx0);
-            tc_store<COUT, ACT, OUTM, false, POOL>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7), lane);
+            tc_store<COUT, ACT, OUTM, false>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7));
         }
     }
     __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
@@ -567,7 +549,7 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_consta
 // epilogue warps write its bias + ReLU + bfloat16 values into shared memory as the K-major
 // A operand of the 1x1 MMA ([chunk][128 pixels][8 channels]), the MMA lane issues that one
 // MMA into a second pair of accumulators, and the epilogue warps finish the tile from it
-// (ReLU and the 2x2 pool for in1, sigmoid into planar FP32 for o1).  Roles as
+// (ReLU and BF16 for in1, sigmoid into planar FP32 for o1).  Roles as
 // conv_ws_kernel; the MMA lane issues tile j's convolution, then tile j - 1's 1x1.
 // Barriers: full/empty per input stage, accf/acce per first accumulator, a2full (the A
 // operand of the 1x1 written, four epilogue warps), acc2f (1x1 committed) and acc2e (its
@@ -575,7 +557,7 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_consta
 struct alignas(128) TailArgs {
     CUtensorMap tm;
     ConvArgs c;   // first layer: x, w, bias, nbias, N, H, W, status; y (may be NULL), ystride
-    ConvArgs c2;  // 1x1 layer: w, bias, nbias, N, H, W and the outputs (y, ystride, yp / yf)
+    ConvArgs c2;  // 1x1 layer: w, bias, nbias, N, H, W and the outputs (y, ystride / yf)
 };
 
 template <int CIN, int COUT, int KS, int COUT2>
@@ -589,7 +571,7 @@ struct TailGeom {
     static constexpr int COLS = tmem_cols<2 * COUT + 2 * COUT2>();
 };
 
-template <int CIN, int COUT, int KS, int COUT2, int ACT2, int OUTM2, bool POOL2>
+template <int CIN, int COUT, int KS, int COUT2, int ACT2, int OUTM2>
 __global__ void __launch_bounds__(kWsThreads) conv_tail_kernel(const __grid_constant__ TailArgs args)
 {
     using T = TailGeom<CIN, COUT, KS, COUT2>;
@@ -786,7 +768,7 @@ __global__ void __launch_bounds__(kWsThreads) conv_tail_kernel(const __grid_cons
             tc_load_acc<COUT2>(tmem2 + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * COUT2), v2);
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acc2e + acc)) : "memory");
-            tc_store<COUT2, ACT2, OUTM2, false, POOL2>(a2, v2, bias2, n, yy, xx, lane);
+            tc_store<COUT2, ACT2, OUTM2, false>(a2, v2, bias2, n, yy, xx);
         }
     }
     __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
@@ -1005,8 +987,205 @@ __global__ void __launch_bounds__(kWsThreads) conv_up_kernel(const __grid_consta
                     __syncwarp();
                     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
                 }
-                tc_store<COUT, 1, 0, false, false>(a, v, bias, n, 2 * (i0 + g) + (cls >> 1), 2 * (j0 + r) + (cls & 1), lane);
+                tc_store<COUT, 1, 0, false>(a, v, bias, n, 2 * (i0 + g) + (cls >> 1), 2 * (j0 + r) + (cls & 1));
             }
+        }
+    }
+    __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (tid == 4 * 32) {  // after a failure: let copies still in flight land before the CTA exits
+        for (int j = s_consumed; j < s_issued; ++j) mbar_wait_thread(smem_u32(full + j % NBUF), (uint32_t)((j / NBUF) & 1));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::COLS));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Stride-2 3x3 convolution (the second convolution of an encoder block, Sec. 3.3; ReLU):
+// output pixel (oy, ox) of the [N][H/2][W/2] map reads input pixels (2oy + u - 1,
+// 2ox + v - 1) of the [N][H][W] input (H, W even), so only the kept outputs are computed.
+// A tile is 16 x 8 output pixels (oy0 + g, ox0 + r), accumulator row 8g + r.  Its input is
+// staged per 8-channel chunk as four parity planes: rows 2i + pr for row pairs
+// i = oy0 - 1 .. oy0 + 15, and columns 2j + pc for column pairs j = ox0 .. ox0 + 7 (even
+// columns, pc = 0, planes [17][8][8]) or j = ox0 - 1 .. ox0 + 7 (odd columns, pc = 1, planes
+// [17][9][8]).  Tap u reads row parity pr = (u != 1) at row offset (u != 0); tap v reads
+// column parity pc = (v != 1) at column offset (v == 2) of its plane.  Consecutive output
+// pixels step by one pair, so every tap's operand is a plain K-major tile of the staged
+// planes: 9 taps x CIN/16 MMAs per tile, no products for the dropped positions.  The planes
+// come from two 5-D views of the NHWC input (channels of a column pair, column pairs, row
+// parity, row pairs, images), boxes 8 and 9 pairs wide; the start channel pc * CIN + 8k
+// selects the column parity.  Roles, waits and epilogue as conv_ws_kernel.
+template <int CIN, int COUT, int NBUF_>
+struct S2Geom {
+    static constexpr int TH = 16, TW = 8, SH = TH + 1, WE = TW, WO = TW + 1, C8 = CIN / 8, NBUF = NBUF_;
+    static constexpr int PSE = (SH * WE * 16 + 127) / 128 * 128;  // even-column plane [SH][WE][8]
+    static constexpr int PSO = (SH * WO * 16 + 127) / 128 * 128;  // odd-column plane [SH][WO][8]
+    static constexpr int ROWP = C8 * (PSE + PSO);                  // one row parity: even chunks, odd chunks
+    static constexpr int XBYTES = 2 * ROWP;
+    static constexpr int TMA_BYTES = 2 * C8 * SH * (WE + WO) * 16;
+    static constexpr int WBYTES = (9 * C8 * COUT * 16 + 127) / 128 * 128;
+    static constexpr int NBAR = 2 * NBUF + 4;
+    static constexpr int SMEM = 128 + WBYTES + NBUF * XBYTES + NBAR * 8 + 16;
+    static constexpr int COLS = tmem_cols<2 * COUT>();
+    static_assert(PSE % 128 == 0 && PSO % 128 == 0, "TMA destinations 128-byte aligned");
+};
+
+struct alignas(128) S2Args {
+    CUtensorMap te, to;  // even-column and odd-column views of the input
+    ConvArgs c;          // x [N][H][W][CIN] (H, W: the input's size), y [N][H/2][W/2][ystride]
+};
+
+template <int CIN, int COUT, int NBUF>
+__global__ void __launch_bounds__(kWsThreads) conv_s2_kernel(const __grid_constant__ S2Args args)
+{
+    using G = S2Geom<CIN, COUT, NBUF>;
+    constexpr int TH = G::TH, TW = G::TW, C8 = G::C8, PSE = G::PSE, PSO = G::PSO, ROWP = G::ROWP;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && 2 * COUT <= 256, "UMMA shape");
+    const ConvArgs &a = args.c;
+    ConvArgs ao = a;  // the output map
+    ao.H = a.H / 2;
+    ao.W = a.W / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    unsigned char *sw = base;
+    unsigned char *sx0 = base + G::WBYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sx0 + NBUF * G::XBYTES);
+    uint64_t *empty = full + NBUF, *accf = empty + NBUF, *acce = accf + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
+    __shared__ int s_issued, s_consumed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (ao.W + TW - 1) / TW, tiles_y = (ao.H + TH - 1) / TH;
+    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
+    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(G::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(empty + i)));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(accf + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(acce + i)));  // 4 epilogue warps
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.te)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&args.to)) : "memory");
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    for (int i = tid; i < 9 * COUT * C8; i += kWsThreads) {
+        const int c8 = i % C8, row = i / C8, tap = row / COUT, co = row % COUT;
+        cp_async16(sw + ((tap * C8 + c8) * COUT + co) * 16, a.w + (size_t)row * CIN + c8 * 8, true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n");  // weights visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = *tslot;
+    auto fail = [&]() {
+        if (a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
+    };
+    auto origin = [&](int j, int &n, int &oy0, int &ox0) {
+        const int t = blockIdx.x + j * gridDim.x;
+        n = t / per_img;
+        const int r = t % per_img;
+        oy0 = (r / tiles_x) * TH;
+        ox0 = (r % tiles_x) * TW;
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {  // producer
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF;
+                if (j >= NBUF && !mbar_wait_thread(smem_u32(empty + st), (uint32_t)((j / NBUF - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                int n, oy0, ox0;
+                origin(j, n, oy0, ox0);
+                const uint32_t bar = smem_u32(full + st);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(G::TMA_BYTES) : "memory");
+                const uint32_t dst = smem_u32(sx0 + st * G::XBYTES);
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+#pragma unroll
+                    for (int k = 0; k < C8; ++k)
+                        tma_load_5d(dst + pr * ROWP + k * PSE, &args.te, 8 * k, ox0, pr, oy0 - 1, n, bar);
+#pragma unroll
+                    for (int k = 0; k < C8; ++k)
+                        tma_load_5d(dst + pr * ROWP + C8 * PSE + k * PSO, &args.to, CIN + 8 * k, ox0 - 1, pr, oy0 - 1, n, bar);
+                }
+                s_issued = j + 1;
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = umma_idesc(COUT);
+            const uint64_t adesc_e = umma_sdesc(smem_u32(sx0), PSE, G::WE * 16);
+            const uint64_t adesc_o = umma_sdesc(smem_u32(sx0), PSO, G::WO * 16);
+            const uint64_t bdesc0 = umma_sdesc(smem_u32(sw), COUT * 16, 128);
+            for (int j = 0; j < mine; ++j) {
+                const int st = j % NBUF, acc = j & 1;
+                if (!mbar_wait_thread(smem_u32(full + st), (uint32_t)((j / NBUF) & 1))) {
+                    fail();
+                    break;
+                }
+                s_consumed = j + 1;
+                if (j >= 2 && !mbar_wait_thread(smem_u32(acce + acc), (uint32_t)((j / 2 - 1) & 1))) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                const uint32_t sbase = (uint32_t)(st * G::XBYTES);
+                const uint32_t d = tmem + (uint32_t)(acc * COUT);
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int u = tap / 3, v = tap % 3;
+                    const int pr = u != 1, pc = v != 1, ro = u != 0, co = v == 2;
+#pragma unroll
+                    for (int kk = 0; kk < C8 / 2; ++kk) {
+                        const uint32_t off = pc ? sbase + pr * ROWP + C8 * PSE + 2 * kk * PSO + (ro * G::WO + co) * 16
+                                                : sbase + pr * ROWP + 2 * kk * PSE + ro * G::WE * 16;
+                        const uint64_t ad = (pc ? adesc_o : adesc_e) + (uint64_t)(off >> 4);
+                        const uint32_t boff = (uint32_t)(((tap * C8 + 2 * kk) * COUT * 16) >> 4);
+                        umma_bf16(d, ad, bdesc0 + boff, idesc, (tap | kk) ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(empty + st)));
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(accf + acc)));
+            }
+        }
+    } else {  // epilogue warps 0-3: TMEM lane quarter = warp
+        float bias[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bias[c] = c < a.nbias ? a.bias[c] : 0.f;
+        for (int j = 0; j < mine; ++j) {
+            const int acc = j & 1;
+            if (!mbar_wait_warp(smem_u32(accf + acc), (uint32_t)((j / 2) & 1))) {
+                if (lane == 0) fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            float v[COUT];
+            tc_load_acc<COUT>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * COUT), v);
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
+            int n, oy0, ox0;
+            origin(j, n, oy0, ox0);
+            tc_store<COUT, 1, 0, false>(ao, v, bias, n, oy0 + 4 * warp + (lane >> 3), ox0 + (lane & 7));
         }
     }
     __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
@@ -1195,17 +1374,29 @@ __global__ void upcat_bwd_kernel(const bf16 *gy, const bf16 *lo, bf16 *g_lo, flo
     }
 }
 
-// gradient of a ReLU feature used by a pool and a skip: g = mask(f) * (g_skip + up(g_pool) / 4)
-__global__ void pool_bwd_kernel(const float *g_skip, const bf16 *g_pool, const bf16 *f, bf16 *g, int N, int H, int W, int C)
+// Gradient with respect to the pre-activation of a layer whose ReLU output f [N][Ho][Wo][C]
+// feeds the next encoder convolution (gradient g_path, bf16) and, when g_skip is given, a
+// decoder skip (fp32): dz = mask(f) * (g_skip + g_path); no mask when f is NULL.  S = 2 (the
+// layer strides by 2): dz is written zero-upsampled onto the layer's input grid
+// [N][2Ho][2Wo][C], nonzero only at even rows and columns, so that the stride-1 input- and
+// weight-gradient kernels at the input's size give the stride-2 layer's gradients.
+template <int S>
+__global__ void join_bwd_kernel(const float *g_skip, const bf16 *g_path, const bf16 *f, bf16 *dz, int N, int Ho, int Wo,
+                                int C)
 {
+    const int H = S * Ho, W = S * Wo;
     const size_t total = (size_t)N * H * W * C;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(e % C);
         const size_t p = e / C;
         const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((size_t)W * H));
-        const float gp = __bfloat162float(g_pool[(((size_t)n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c]);
-        const float v = g_skip[e] + 0.25f * gp;
-        g[e] = __float2bfloat16(__bfloat162float(f[e]) > 0.f ? v : 0.f);
+        float v = 0.f;
+        if (S == 1 || ((x | y) & 1) == 0) {
+            const size_t q = (((size_t)n * Ho + y / S) * Wo + x / S) * C + c;
+            v = __bfloat162float(g_path[q]) + (g_skip ? g_skip[q] : 0.f);
+            if (f && !(__bfloat162float(f[q]) > 0.f)) v = 0.f;
+        }
+        dz[e] = __float2bfloat16(v);
     }
 }
 
@@ -1355,7 +1546,7 @@ cudaError_t make_tmap_parity(CUtensorMap *m, const void *base, int C, int W, int
 // kernel's registers, shared memory and threads, and capped at 512 / (TMEM columns per CTA);
 // where threads alone would allow more CTAs than TMEM can hold, the shared-memory request is
 // raised so that no more can be resident (an allocation never has to wait for another CTA).
-template <int CIN, int COUT, int KS, int ACT, int OUTM, bool POOL = false>
+template <int CIN, int COUT, int KS, int ACT, int OUTM>
 cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
 {
     using G = WsGeom<CIN, COUT, KS>;
@@ -1364,7 +1555,7 @@ cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
     constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
     constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
     static_assert(smem <= 227 * 1024, "warp-specialised conv tile does not fit in shared memory");
-    auto kern = conv_ws_kernel<CIN, COUT, KS, ACT, OUTM, POOL>;
+    auto kern = conv_ws_kernel<CIN, COUT, KS, ACT, OUTM>;
     static int per_sm = 0, n_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1401,7 +1592,7 @@ cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
 
 // Launch of the fused KS x KS + 1x1 pair (c: first layer, c2: the 1x1 layer); residency
 // computed as for conv_ws_launch.
-template <int CIN, int COUT, int KS, int COUT2, int ACT2, int OUTM2, bool POOL2>
+template <int CIN, int COUT, int KS, int COUT2, int ACT2, int OUTM2>
 cudaError_t conv_tail_launch(const ConvArgs &c, const ConvArgs &c2, cudaStream_t st)
 {
     using T = TailGeom<CIN, COUT, KS, COUT2>;
@@ -1411,7 +1602,7 @@ cudaError_t conv_tail_launch(const ConvArgs &c, const ConvArgs &c2, cudaStream_t
     constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
     constexpr size_t smem = (size_t)(T::SMEM > min_smem ? T::SMEM : min_smem);
     static_assert(smem <= 227 * 1024, "fused conv stage does not fit in shared memory");
-    auto kern = conv_tail_kernel<CIN, COUT, KS, COUT2, ACT2, OUTM2, POOL2>;
+    auto kern = conv_tail_kernel<CIN, COUT, KS, COUT2, ACT2, OUTM2>;
     static int per_sm = 0, n_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1493,6 +1684,53 @@ cudaError_t conv_up_launch(const ConvArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Launch of the stride-2 convolution (a.H, a.W: the input's size, both even; output at half
+// size); residency computed as for conv_ws_launch.
+template <int CIN, int COUT, int NBUF>
+cudaError_t conv_s2_launch(const ConvArgs &a, cudaStream_t st)
+{
+    using G = S2Geom<CIN, COUT, NBUF>;
+    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreadsPerSm = 2048;
+    constexpr int tmem_cap = 512 / G::COLS;
+    constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
+    constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
+    static_assert(smem <= 227 * 1024, "stride-2 conv stage does not fit in shared memory");
+    auto kern = conv_s2_kernel<CIN, COUT, NBUF>;
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = (4 * (16384 / regs_per_warp)) / (kWsThreads / 32);
+        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
+        int r = kThreadsPerSm / kWsThreads;
+        r = r < by_regs ? r : by_regs;
+        r = r < by_smem ? r : by_smem;
+        r = r < tmem_cap ? r : tmem_cap;
+        if (r < 1) return cudaErrorInvalidConfiguration;
+        per_sm = r;
+    }
+    if ((a.H | a.W) & 1) return cudaErrorInvalidValue;
+    const long long ntiles = (long long)a.N * ((a.H / 2 + G::TH - 1) / G::TH) * ((a.W / 2 + G::TW - 1) / G::TW);
+    if (ntiles <= 0) return cudaSuccess;
+    S2Args sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.c = a;
+    cudaError_t e = make_tmap_parity(&sa.te, a.x, CIN, a.W, a.H, a.N, G::WE, G::SH);
+    if (e != cudaSuccess) return e;
+    if ((e = make_tmap_parity(&sa.to, a.x, CIN, a.W, a.H, a.N, G::WO, G::SH)) != cudaSuccess) return e;
+    const long long cap = (long long)per_sm * n_sm;
+    kern<<<(int)(ntiles < cap ? ntiles : cap), kWsThreads, smem, st>>>(sa);
+    return cudaGetLastError();
+}
+
 template <int CIN, int COUT, int KS>
 cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H, int W, int cin_true, int cout_true,
                          int n_sm, cudaStream_t st)
@@ -1521,7 +1759,7 @@ struct flnr_net {
     __nv_bfloat16 *wf[flnr::kNL] = {}, *wd[flnr::kNL] = {};          // bf16 forward / dgrad weights
     std::vector<void *> bufs;
     // activations (bf16 NHWC) and gradients
-    __nv_bfloat16 *x0, *a0, *f0, *p0, *a1, *f1, *p1, *a2, *f2, *c1, *a3, *d1, *c0, *a4, *d0, *a5;
+    __nv_bfloat16 *x0, *a0, *f0, *a1, *f1, *a2, *f2, *c1, *a3, *d1, *c0, *a4, *d0, *a5;
     __nv_bfloat16 *gA, *gB, *gC, *gLo;  // gradient scratch (largest: 48 channels at full res)
     float *gskip0, *gskip1;             // skip gradients (fp32)
     float *out = nullptr;               // last forward output, planar fp32 [N][8][H][W]
@@ -1596,9 +1834,9 @@ int flnr_create(int max_pixels, flnr_net **out)
         const size_t e = (size_t)d.k * d.k * flnr::pad16(d.cin) * flnr::pad16(d.cout);
         st |= nalloc(n, &n->wf[l], e) | nalloc(n, &n->wd[l], e);
     }
-    st |= nalloc(n, &n->x0, P * 16) | nalloc(n, &n->a0, P * 16) | nalloc(n, &n->f0, P * 16) | nalloc(n, &n->p0, P2 * 16);
-    st |= nalloc(n, &n->a1, P2 * 32) | nalloc(n, &n->f1, P2 * 32) | nalloc(n, &n->p1, P4 * 32);
-    st |= nalloc(n, &n->a2, P4 * 64) | nalloc(n, &n->f2, P4 * 64) | nalloc(n, &n->c1, P2 * 96);
+    st |= nalloc(n, &n->x0, P * 16) | nalloc(n, &n->a0, P * 16) | nalloc(n, &n->f0, P * 16);
+    st |= nalloc(n, &n->a1, P * 32) | nalloc(n, &n->f1, P2 * 32);
+    st |= nalloc(n, &n->a2, P2 * 64) | nalloc(n, &n->f2, P4 * 64) | nalloc(n, &n->c1, P2 * 96);
     st |= nalloc(n, &n->a3, P2 * 32) | nalloc(n, &n->d1, P2 * 32) | nalloc(n, &n->c0, P * 48);
     st |= nalloc(n, &n->a4, P * 16) | nalloc(n, &n->d0, P * 16) | nalloc(n, &n->a5, P * 16);
     st |= nalloc(n, &n->gA, P * 48) | nalloc(n, &n->gB, P * 48) | nalloc(n, &n->gC, P * 48) | nalloc(n, &n->gLo, P * 16);
@@ -1669,7 +1907,7 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     n->H = H;
     n->W = W;
     const size_t P = (size_t)N * H * W;
-    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const int H2 = H / 2, W2 = W / 2;
     auto bias = [&](int l) { return n->w + n->poff[l][1]; };
     pack_input_kernel<<<egrid(P), 256, 0, st>>>(in, n->x0, N, H, W);
     FLNR_TRY(cudaGetLastError());
@@ -1681,16 +1919,13 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
         return c;
     };
     ConvArgs c;
-    c = conv(n->a0, 1, n->f0, H, W);
-    c.yp = n->p0;  // 2x2 average pool of f0 for the encoder
     // in0 and in1 in one pass (a0, which the backward pass reads, is still stored)
-    FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 1, 0, true>(conv(n->x0, 0, n->a0, H, W), c, st)));
-    FLNR_TRY((conv_ws_launch<16, 32, 3, 1, 0>(conv(n->p0, 2, n->a1, H2, W2), st)));
-    c = conv(n->a1, 3, n->f1, H2, W2);
-    c.yp = n->p1;
-    FLNR_TRY((conv_ws_launch<32, 32, 3, 1, 0, true>(c, st)));
-    FLNR_TRY((conv_ws_launch<32, 64, 3, 1, 0>(conv(n->p1, 4, n->a2, H4, W4), st)));
-    FLNR_TRY((conv_ws_launch<64, 64, 3, 1, 0>(conv(n->a2, 5, n->f2, H4, W4), st)));
+    FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 1, 0>(conv(n->x0, 0, n->a0, H, W), conv(n->a0, 1, n->f0, H, W), st)));
+    // encoder blocks: a 3x3 convolution, then a stride-2 one (sizes passed: the input's)
+    FLNR_TRY((conv_ws_launch<16, 32, 3, 1, 0>(conv(n->f0, 2, n->a1, H, W), st)));
+    FLNR_TRY((conv_s2_launch<32, 32, 2>(conv(n->a1, 3, n->f1, H, W), st)));
+    FLNR_TRY((conv_ws_launch<32, 64, 3, 1, 0>(conv(n->f1, 4, n->a2, H2, W2), st)));
+    FLNR_TRY((conv_s2_launch<64, 64, 2>(conv(n->a2, 5, n->f2, H2, W2), st)));
     c = conv(n->f2, 6, n->a3, H2, W2);  // input up(f2) ++ f1, formed while staging
     c.x2 = n->f1;
     FLNR_TRY((conv_up_launch<64, 32, 32, 2>(c, st)));
@@ -1703,7 +1938,7 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     c = conv(n->a5, 11, nullptr, H, W);
     c.yf = yf;
     // o0 and the head o1 (sigmoid into planar FP32) in one pass; a5 is still stored
-    FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 2, 1, false>(conv(n->d0, 10, n->a5, H, W), c, st)));
+    FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 2, 1>(conv(n->d0, 10, n->a5, H, W), c, st)));
     if (guide_out)
         FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return FLR_OK;
@@ -1751,23 +1986,28 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
     bgrad(n->gA, (long long)P2, 32, 32, 6);
     FLNR_TRY((conv_launch<32, 96, 3, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, st)));
     upcat_bwd_kernel<<<egrid(P2 * 96), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
-    // encoder level 2 (H/4)
+    // encoder level 2: e2b (stride 2, H/2 -> H/4), then e2a (H/2).  A stride-2 layer's
+    // gradients are those of the stride-1 kernels at its input's size on dz zero-upsampled
+    // onto that grid.
     const size_t P4 = P / 16;
-    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gLo, gw(5), N, H4, W4, 64, 64, ns, st)));
     bgrad(n->gLo, (long long)P4, 64, 64, 5);
-    FLNR_TRY((conv_launch<64, 64, 3, true>({n->gLo, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H4, W4, 64}, st)));
-    FLNR_TRY((wgrad_launch<32, 64, 3>(n->p1, n->gA, gw(4), N, H4, W4, 32, 64, ns, st)));
-    bgrad(n->gA, (long long)P4, 64, 64, 4);
-    FLNR_TRY((conv_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H4, W4, 32}, st)));
-    pool_bwd_kernel<<<egrid(P2 * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gLo, N, H2, W2, 32);  // dz(e1b)
-    // encoder level 1 (H/2)
-    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gLo, gw(3), N, H2, W2, 32, 32, ns, st)));
-    bgrad(n->gLo, (long long)P2, 32, 32, 3);
-    FLNR_TRY((conv_launch<32, 32, 3, true>({n->gLo, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
-    FLNR_TRY((wgrad_launch<16, 32, 3>(n->p0, n->gA, gw(2), N, H2, W2, 16, 32, ns, st)));
-    bgrad(n->gA, (long long)P2, 32, 32, 2);
-    FLNR_TRY((conv_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 16}, st)));
-    pool_bwd_kernel<<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
+    join_bwd_kernel<2><<<egrid(P2 * 64), 256, 0, st>>>(nullptr, n->gLo, nullptr, n->gB, N, H4, W4, 64);
+    FLNR_TRY(cudaGetLastError());
+    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gB, gw(5), N, H2, W2, 64, 64, ns, st)));
+    FLNR_TRY((conv_launch<64, 64, 3, true>({n->gB, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H2, W2, 64}, st)));
+    FLNR_TRY((wgrad_launch<32, 64, 3>(n->f1, n->gA, gw(4), N, H2, W2, 32, 64, ns, st)));
+    bgrad(n->gA, (long long)P2, 64, 64, 4);
+    FLNR_TRY((conv_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 32}, st)));
+    // encoder level 1: e1b (stride 2, H -> H/2; f1 also feeds the d1a skip), then e1a (H)
+    join_bwd_kernel<2><<<egrid(P * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gC, N, H2, W2, 32);
+    FLNR_TRY(cudaGetLastError());
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gC, gw(3), N, H, W, 32, 32, ns, st)));
+    bgrad(n->gC, (long long)P, 32, 32, 3);
+    FLNR_TRY((conv_launch<32, 32, 3, true>({n->gC, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H, W, 32}, st)));
+    FLNR_TRY((wgrad_launch<16, 32, 3>(n->f0, n->gA, gw(2), N, H, W, 16, 32, ns, st)));
+    bgrad(n->gA, (long long)P, 32, 32, 2);
+    FLNR_TRY((conv_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    join_bwd_kernel<1><<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
     // input projection (H)
     FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, ns, st)));
     bgrad(n->gLo, (long long)P, 16, 16, 1);
@@ -1782,10 +2022,11 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
 namespace {
 
 // One layer's kernels by themselves (flnr_layer): CI / CO are the padded channel counts, CA
-// the upsampled part of a decoder input, POOL whether the layer's output feeds a pool.
-template <int CI, int CO, int KS, int CA, bool POOL, bool HEAD = false>
-int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const void *mask, void *out, void *out2,
-              int N, int H, int W, cudaStream_t st)
+// the upsampled part of a decoder input, S2 whether the layer strides by 2 (N, H, W: the
+// layer's input size).
+template <int CI, int CO, int KS, int CA, bool S2, bool HEAD = false>
+int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const void *mask, void *out, int N, int H,
+              int W, cudaStream_t st)
 {
     using namespace flnr;
     using bf = __nv_bfloat16;
@@ -1815,24 +2056,31 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
                     return FLR_OK;
                 }
             }
-            if constexpr (POOL) {
-                if (out2) {
-                    if ((H | W) & 1) return FLR_ERR_ARG;
-                    c.yp = (bf *)out2;
-                    FLNR_TRY((conv_ws_launch<CI, CO, KS, 1, 0, true>(c, st)));
-                    return FLR_OK;
-                }
+            if constexpr (S2) {
+                if ((H | W) & 1) return FLR_ERR_ARG;
+                FLNR_TRY((conv_s2_launch<CI, CO, 2>(c, st)));
+            } else {
+                FLNR_TRY((conv_ws_launch<CI, CO, KS, 1, 0>(c, st)));
             }
-            FLNR_TRY((conv_ws_launch<CI, CO, KS, 1, 0>(c, st)));
         }
-    } else if (op == FLNR_OP_DGRAD) {
+        return FLR_OK;
+    }
+    const bf *dz = (const bf *)(op == FLNR_OP_DGRAD ? a : b);
+    if constexpr (S2) {  // dz [N][H/2][W/2][CO], zero-upsampled onto the input grid in scratch
+        if ((H | W) & 1) return FLR_ERR_ARG;
+        if (P * CO > (long long)n->max_pix * 48) return FLR_ERR_UNSUPPORTED;
+        join_bwd_kernel<2><<<egrid((size_t)P * CO), 256, 0, st>>>(nullptr, dz, nullptr, n->gC, N, H / 2, W / 2, CO);
+        FLNR_TRY(cudaGetLastError());
+        dz = n->gC;
+    }
+    if (op == FLNR_OP_DGRAD) {
         if (mask)
-            FLNR_TRY((conv_launch<CO, CI, KS, true>({(const bf *)a, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+            FLNR_TRY((conv_launch<CO, CI, KS, true>({dz, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
         else
-            FLNR_TRY((conv_launch<CO, CI, KS, false>({(const bf *)a, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+            FLNR_TRY((conv_launch<CO, CI, KS, false>({dz, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
     } else {
-        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, (const bf *)b, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->n_sm, st)));
-        bias_grad_kernel<<<64, 256, 0, st>>>((const bf *)b, n->g + n->poff[l][1], P, CO, d.cout);
+        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->n_sm, st)));
+        bias_grad_kernel<<<64, 256, 0, st>>>(dz, n->g + n->poff[l][1], P, CO, d.cout);
         FLNR_TRY(cudaGetLastError());
     }
     return FLR_OK;
@@ -1842,8 +2090,8 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
 
 extern "C" {
 
-int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, const void *mask, void *out, void *out2,
-               int N, int H, int W, void *stream)
+int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, const void *mask, void *out, int N,
+               int H, int W, void *stream)
 {
     if (!n || layer < 0 || layer >= flnr::kNL || op < FLNR_OP_FORWARD || op > FLNR_OP_WGRAD || !a || N <= 0 ||
         H <= 0 || W <= 0)
@@ -1853,18 +2101,18 @@ int flnr_layer(flnr_net *n, int layer, int op, const void *a, const void *b, con
     if (!n->weights_fresh) return FLR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     switch (layer) {
-    case 0: return layer_ops<16, 16, 3, 0, false>(n, 0, op, a, b, mask, out, out2, N, H, W, st);
-    case 1: return layer_ops<16, 16, 1, 0, true>(n, 1, op, a, b, mask, out, out2, N, H, W, st);
-    case 2: return layer_ops<16, 32, 3, 0, false>(n, 2, op, a, b, mask, out, out2, N, H, W, st);
-    case 3: return layer_ops<32, 32, 3, 0, true>(n, 3, op, a, b, mask, out, out2, N, H, W, st);
-    case 4: return layer_ops<32, 64, 3, 0, false>(n, 4, op, a, b, mask, out, out2, N, H, W, st);
-    case 5: return layer_ops<64, 64, 3, 0, false>(n, 5, op, a, b, mask, out, out2, N, H, W, st);
-    case 6: return layer_ops<96, 32, 3, 64, false>(n, 6, op, a, b, mask, out, out2, N, H, W, st);
-    case 7: return layer_ops<32, 32, 3, 0, false>(n, 7, op, a, b, mask, out, out2, N, H, W, st);
-    case 8: return layer_ops<48, 16, 3, 32, false>(n, 8, op, a, b, mask, out, out2, N, H, W, st);
-    case 9: return layer_ops<16, 16, 3, 0, false>(n, 9, op, a, b, mask, out, out2, N, H, W, st);
-    case 10: return layer_ops<16, 16, 3, 0, false>(n, 10, op, a, b, mask, out, out2, N, H, W, st);
-    default: return layer_ops<16, 16, 1, 0, false, true>(n, 11, op, a, b, mask, out, out2, N, H, W, st);
+    case 0: return layer_ops<16, 16, 3, 0, false>(n, 0, op, a, b, mask, out, N, H, W, st);
+    case 1: return layer_ops<16, 16, 1, 0, false>(n, 1, op, a, b, mask, out, N, H, W, st);
+    case 2: return layer_ops<16, 32, 3, 0, false>(n, 2, op, a, b, mask, out, N, H, W, st);
+    case 3: return layer_ops<32, 32, 3, 0, true>(n, 3, op, a, b, mask, out, N, H, W, st);
+    case 4: return layer_ops<32, 64, 3, 0, false>(n, 4, op, a, b, mask, out, N, H, W, st);
+    case 5: return layer_ops<64, 64, 3, 0, true>(n, 5, op, a, b, mask, out, N, H, W, st);
+    case 6: return layer_ops<96, 32, 3, 64, false>(n, 6, op, a, b, mask, out, N, H, W, st);
+    case 7: return layer_ops<32, 32, 3, 0, false>(n, 7, op, a, b, mask, out, N, H, W, st);
+    case 8: return layer_ops<48, 16, 3, 32, false>(n, 8, op, a, b, mask, out, N, H, W, st);
+    case 9: return layer_ops<16, 16, 3, 0, false>(n, 9, op, a, b, mask, out, N, H, W, st);
+    case 10: return layer_ops<16, 16, 3, 0, false>(n, 10, op, a, b, mask, out, N, H, W, st);
+    default: return layer_ops<16, 16, 1, 0, false, true>(n, 11, op, a, b, mask, out, N, H, W, st);
     }
 }
 

@@ -36,7 +36,7 @@ def _lib():
         lib.flnr_zero_grads.argtypes = [vp, vp]
         lib.flnr_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ip, vp]
         lib.flnr_l1_loss.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
-        lib.flnr_layer.argtypes = [vp, ip, ip, vp, vp, vp, vp, vp, ip, ip, ip, vp]
+        lib.flnr_layer.argtypes = [vp, ip, ip, vp, vp, vp, vp, ip, ip, ip, vp]
         lib.flnr_status.argtypes = [vp]
         for name in ("flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights", "flnr_get_grads",
                      "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_adam_step",
@@ -142,14 +142,15 @@ class FLNR:
         """Waits for the device; raises if a tensor-core kernel's bounded wait ran out."""
         _flr._check(_lib().flnr_status(self._h), "flnr_status")
 
-    def layer(self, layer, op, a, b=None, mask=None, out=None, out2=None, size=None):
-        """One layer's kernels by themselves (flnr_layer): a, b, mask, out, out2 are CUDA
-        bfloat16 NHWC tensors with padded channels (out float32 planar for layer 11's
-        forward); the shape [N, H, W] comes from `a`, or from `size` when `a` is the
-        half-resolution input of a decoder layer."""
+    def layer(self, layer, op, a, b=None, mask=None, out=None, size=None):
+        """One layer's kernels by themselves (flnr_layer): a, b, mask, out are CUDA bfloat16
+        NHWC tensors with padded channels (out float32 planar for layer 11's forward).  The
+        layer's input size [N, H, W] comes from `a`, or from `size` when `a` is not at that
+        size (the half-resolution input of a decoder layer, or the gradient dz of a stride-2
+        layer)."""
         N, H, W = (int(v) for v in (size if size is not None else a.shape[:3]))
         ptr = (lambda t: None if t is None else ctypes.c_void_p(t.data_ptr()))
-        _flr._check(_lib().flnr_layer(self._h, int(layer), int(op), ptr(a), ptr(b), ptr(mask), ptr(out), ptr(out2),
+        _flr._check(_lib().flnr_layer(self._h, int(layer), int(op), ptr(a), ptr(b), ptr(mask), ptr(out),
                                       N, H, W, _stream(a)), "flnr_layer")
         return out
 

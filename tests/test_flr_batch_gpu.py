@@ -118,24 +118,29 @@ def test_batch_with_guide_network(flr):
     """The serving step with the FLNR guide network (serving.GuidedBatch): per frame size,
     the network's forward pass over the half-resolution inputs gives the model guides, then
     one persistent fast-FLR launch does joint denoising and 2x upsampling of every frame;
-    the step is a captured CUDA graph, replayed twice.  The guides equal a separate forward
-    pass of the network, bit for bit, and each frame's result meets the FP64 oracle of fast
-    FLR run on those guides (the map guide differs from the model guide: the absolute bar
-    of the joint-upsampling tests)."""
+    the step is a captured CUDA graph, replayed twice.  The map guides are the same
+    network's output on the full-resolution inputs (guides from one distribution, as the
+    model and map guides of FLNR are).  The model guides equal a separate forward pass of
+    the network, bit for bit, and each frame's result meets the FP64 oracle of fast FLR run
+    on those guides (the map guide differs from the model guide: the absolute bar of the
+    joint-upsampling tests)."""
     import torch
 
     from paper_2410_11625_gb300 import flnr, serving
     weights = flnr.init_weights(3)
+    hi_net = flnr.FLNR(2 * 96 * 128, weights)
     groups = []
     for i, (h, w) in enumerate([(32, 48), (48, 64)]):
-        xs, zs = [], []
+        xs, xs_hi = [], []
         for j in range(2):
             g_lo, y_lo = synth.render(40 + 2 * i + j, h, w)
-            g_hi, _ = synth.render(40 + 2 * i + j, 2 * h, 2 * w)
+            g_hi, y_hi = synth.render(40 + 2 * i + j, 2 * h, 2 * w)
             xs.append(np.concatenate([g_lo, y_lo]))
-            zs.append(g_hi)
-        groups.append((torch.from_numpy(np.stack(xs)).cuda(), torch.from_numpy(np.stack(zs)).cuda(),
-                       torch.empty((2, 3, 2 * h, 2 * w), device="cuda")))
+            xs_hi.append(np.concatenate([g_hi, y_hi]))
+        z = hi_net.forward(torch.from_numpy(np.stack(xs_hi)).cuda()).clone()
+        groups.append((torch.from_numpy(np.stack(xs)).cuda(), z, torch.empty((2, 3, 2 * h, 2 * w), device="cuda")))
+    torch.cuda.synchronize()
+    hi_net.close()
     b = serving.GuidedBatch(groups, weights, factor=4)
     b.run()
     b.run()
