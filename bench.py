@@ -351,7 +351,8 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
         return flnr_inference_row(flnr.init_weights(0), dev_frames, torch, dev, timed, rows)
     t0 = time.perf_counter()
     scenes = flnr_train.render_scenes(range(1, 33), 192, 192, ref_spp=1024, noise=8)
-    held_out = flnr_train.render_scenes(range(flnr_train.EVAL_SEED0, flnr_train.EVAL_SEED0 + 6), 256, 256,
+    n_eval = 16
+    held_out = flnr_train.render_scenes(range(flnr_train.EVAL_SEED0, flnr_train.EVAL_SEED0 + n_eval), 256, 256,
                                         ref_spp=1024)
     t_render = time.perf_counter() - t0
     tr = flnr_train.Trainer(flnr.init_weights(0), batch=16, crop=128, lr=2e-3)
@@ -365,7 +366,10 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
         "psnr_flr_db": round(float(np.mean(p_flr)), 3), "psnr_flnr_db": round(float(np.mean(p_net)), 3),
         "gain_db": round(float(np.mean(p_net) - np.mean(p_flr)), 3),
         "per_scene_gain_db": [round(a - b, 2) for a, b in zip(p_net, p_flr)],
-        "what": (f"held-out rooms (seeds 1000000..1000005, 256x256) vs 1024 spp references, albedo-modulated, "
+        "psnr_flr_per_scene_db": [round(float(a), 2) for a in p_flr],
+        "rooms_improved": int(sum(a > b for a, b in zip(p_net, p_flr))),
+        "what": (f"{n_eval} held-out rooms (seeds {flnr_train.EVAL_SEED0}..{flnr_train.EVAL_SEED0 + n_eval - 1}, "
+                 f"256x256) vs 1024 spp references, albedo-modulated, "
                  f"clamped to [0,1]; network trained here for {train_steps} steps (batch 16 x 128^2 crops of 32 "
                  f"rooms, 8 noise realisations each, L1, Adam lr 2e-3 cosine to 1e-4) in {t_train:.1f} s; "
                  f"rendering {t_render:.1f} s on the host"),

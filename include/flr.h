@@ -387,10 +387,16 @@ int flnr_layer(flnr_net *net, int layer, int op, const void *a, const void *b, c
                int N, int H, int W, void *stream);
 
 /*
- * Backward pass of the last forward: grad_out [N][8][H][W] = dL/d(enhanced guides);
- * ACCUMULATES the parameter gradients (flnr_zero_grads clears them).
+ * Backward pass of the last forward (Sec. 3.3's network trained end to end through FLR):
+ * grad_out [N][8][H][W] = dL/d(enhanced guides), planar float32 (device).  ACCUMULATES the
+ * parameter gradients (flnr_zero_grads clears them).  grad_in (device, may be NULL)
+ * receives dL/d(in), [N][11][H][W] planar float32, overwritten: the guide channels'
+ * gradients, and for the radiance channels the gradient through log(1 + max(Y, 0)), i.e.
+ * times 1 / (1 + Y) for Y > 0 and 0 for Y <= 0 (evaluated from the stored bfloat16 input).
+ * Values carry the bfloat16 storage of the backward pass.  Runs on `stream`.
+ * Errors: FLR_ERR_ARG (no forward yet), FLR_ERR_CUDA.
  */
-int flnr_guide_backward(flnr_net *net, const float *grad_out, void *stream);
+int flnr_guide_backward(flnr_net *net, const float *grad_out, float *grad_in, void *stream);
 int flnr_zero_grads(flnr_net *net, void *stream);
 int flnr_get_grads(flnr_net *net, float *host, size_t count);
 

@@ -1,8 +1,9 @@
 // flnr.cu -- the FLNR guide network (Sec. 3.3) on sm_103a: BF16 implicit-GEMM convolutions
-// with FP32 accumulation -- the forward pass on the fifth-generation tensor cores (tcgen05,
-// TMA-staged tiles, accumulators in tensor memory), the backward pass with mma.sync m16n8k16
-// (dgrad as a convolution with rotated, transposed weights; wgrad as a per-tap GEMM over
-// pixels) -- Adam on FP32 master weights, and the flnr_* entry points of include/flr.h.
+// with FP32 accumulation on the fifth-generation tensor cores (tcgen05, accumulators in
+// tensor memory) for the forward pass and for training -- input gradients as convolutions
+// with rotated, transposed weights on the forward's TMA-staged kernel, weight gradients as
+// one GEMM over pixels per layer with the operands transposed on chip -- Adam on FP32
+// master weights, and the flnr_* entry points of include/flr.h.
 //
 // Network (weights and order as oracle/flnr_ref.py): 11 inputs (8 guides + noisy RGB)
 //   in0 3x3 11->16 ReLU, in1 1x1 16->16 ReLU                                   f0 (H)
@@ -41,19 +42,6 @@ constexpr LayerDef kLayers[kNL] = {
 __host__ __device__ constexpr int pad16(int c) { return (c + 15) / 16 * 16; }
 
 // ---------------------------------------------------------------------------------------
-// Tensor-core primitive: D = A (16x16, row) * B (16x8, col) + C, BF16 inputs, FP32 accum.
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-// ---------------------------------------------------------------------------------------
 // Asynchronous 16-byte global -> shared copies (zero fill when !valid).
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
 {
@@ -83,116 +71,6 @@ struct ConvArgs {
     const bf16 *x2;
     int *status;  // tensor-core path: set to FLNR_STATUS_TIMEOUT if a completion wait ran out
 };
-
-// The input-gradient convolution of the backward pass (warp-level mma.sync): persistent
-// CTAs stage the weights in shared memory once; a CTA then walks tiles of TH = 2 * WARPS
-// rows by 16 pixels, the next tile's input (with halo) loading by cp.async while the
-// current one is computed.  Warp w owns rows 2w, 2w+1 of the tile: two m16 fragments (16
-// pixels of a row each) times COUT/8 n8 fragments.  Output: bf16 NHWC at channel offset 0,
-// times (mask > 0) when MASK.
-template <int CIN, int COUT, int KS, bool MASK, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) conv_kernel(const ConvArgs a)
-{
-    constexpr int NTH = WARPS * 32, TH = 2 * WARPS, TW = 16, P = KS / 2;
-    constexpr int SH = TH + 2 * P, SW = TW + 2 * P;
-    constexpr int CS = CIN + 8;  // padded pixel stride: conflict-free fragment loads
-    constexpr int NT = COUT / 8, C8 = CIN / 8;
-    constexpr int XT = SH * SW * CS, WT = KS * KS * COUT * CS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *sw = reinterpret_cast<bf16 *>(smem_raw);  // [KS*KS][COUT][CS]
-    bf16 *sxb = sw + WT;                             // 2 x [SH][SW][CS]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
-    const int per_img = tiles_x * tiles_y, ntiles = a.N * per_img;
-    for (int i = tid; i < KS * KS * COUT * C8; i += NTH) {
-        const int row = i / C8, c8 = i % C8;
-        cp_async16(sw + row * CS + c8 * 8, a.w + row * CIN + c8 * 8, true);
-    }
-    auto stage = [&](int t, bf16 *sx) {
-        const int n = t / per_img, r = t % per_img;
-        const int ty0 = (r / tiles_x) * TH, tx0 = (r % tiles_x) * TW;
-        for (int i = tid; i < SH * SW * C8; i += NTH) {
-            const int pix = i / C8, c8 = i % C8;
-            const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
-            const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const bf16 *src = in ? a.x + (((size_t)n * a.H + yy) * a.W + xx) * CIN + c8 * 8 : a.x;
-            cp_async16(sx + pix * CS + c8 * 8, src, in);
-        }
-    };
-    int t = blockIdx.x;
-    if (t < ntiles) stage(t, sxb);
-    cp_async_commit();
-    const int g = lane >> 2, q = lane & 3;
-    for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-        const bf16 *sx = sxb + (it & 1) * XT;
-        if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x, sxb + ((it + 1) & 1) * XT);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        float acc[2][NT][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-#pragma unroll
-        for (int ky = 0; ky < KS; ++ky)
-#pragma unroll
-            for (int kx = 0; kx < KS; ++kx) {
-                const int tap = ky * KS + kx;
-#pragma unroll
-                for (int kc = 0; kc < CIN / 16; ++kc) {
-                    uint32_t af[2][4];
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        const bf16 *r0 = sx + ((2 * warp + mt + ky) * SW + g + kx) * CS + kc * 16 + 2 * q;
-                        const bf16 *r8 = r0 + 8 * CS;
-                        af[mt][0] = ld32(r0);
-                        af[mt][1] = ld32(r8);
-                        af[mt][2] = ld32(r0 + 8);
-                        af[mt][3] = ld32(r8 + 8);
-                    }
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        const bf16 *wb = sw + (tap * COUT + nt * 8 + g) * CS + kc * 16 + 2 * q;
-                        const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
-                        mma_bf16(acc[0][nt], af[0], b0, b1);
-                        mma_bf16(acc[1][nt], af[1], b0, b1);
-                    }
-                }
-            }
-        // epilogue: lane holds pixels g and g + 8 of rows 2w, 2w + 1, channels 2q, 2q + 1 of
-        // each n8 fragment
-        const int n = t / per_img, r = t % per_img;
-        const int ty0 = (r / tiles_x) * TH, tx0 = (r % tiles_x) * TW;
-        const size_t img = (size_t)n * a.H * a.W;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int xx = tx0 + g + 8 * half;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int c = nt * 8 + 2 * q;
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int yy = ty0 + 2 * warp + mt;
-                    const bool in = yy < a.H && xx < a.W;
-                    const size_t pix = img + (size_t)yy * a.W + xx;
-                    float v0 = acc[mt][nt][2 * half] + (c < a.nbias ? a.bias[c] : 0.f);
-                    float v1 = acc[mt][nt][2 * half + 1] + (c + 1 < a.nbias ? a.bias[c + 1] : 0.f);
-                    if (MASK && in) {
-                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + c);
-                        if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                        if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
-                    }
-                    if (in) *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ystride + c) = __floats2bfloat162_rn(v0, v1);
-                }
-            }
-        }
-        __syncthreads();  // the next iteration stages into this buffer
-    }
-    cp_async_wait<0>();
-}
 
 // ---------------------------------------------------------------------------------------
 // The same convolution on the fifth-generation tensor cores (tcgen05): BF16 operands in shared
@@ -397,7 +275,7 @@ struct WsGeom {
 };
 constexpr int kWsThreads = 192;
 
-template <int CIN, int COUT, int KS, int ACT, int OUTM>
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK = false>
 __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_constant__ TcArgs args)
 {
     using G = WsGeom<CIN, COUT, KS>;
@@ -527,7 +405,7 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(const __grid_consta
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + acc)) : "memory");
             int n, ty0, tx0;
             origin(j, n, ty0, tx0);
-            tc_store<COUT, ACT, OUTM, false>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7));
+            tc_store<COUT, ACT, OUTM, MASK>(a, v, bias, n, ty0 + 4 * warp + (lane >> 3), tx0 + (lane & 7));
         }
     }
     __syncwarp();  // the single-lane roles rejoin their warps before the CTA barrier
@@ -1202,84 +1080,203 @@ __global__ void __launch_bounds__(kWsThreads) conv_s2_kernel(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------------------
-// Weight gradient of one convolution tap: dW[o][i][tap] += sum_p dz[p][o] x[p + off(tap)][i]
-// as a GEMM with M = COUT, N = CIN, K = pixels (128 per staged tile).  Grid (taps, chunks);
-// each CTA walks its chunk of pixel tiles with the accumulators in registers, then adds
-// them to the FP32 master-layout gradient [Cout][Cin][k][k] with atomics (pads skipped).
+// Weight gradient on the tensor cores (tcgen05): for every tap and channel pair
+//   dW[o][i][tap] = sum_p dz[p][o] x[p + off(tap)][i],
+// one GEMM D[(tap, i)][o] = sum_p A[(tap, i)][p] B[o][p] with the pixels as K: A is the
+// im2col of x (M = KS^2 * CIN rows, split into MT accumulators of 128 rows), B = dz^T
+// (N = COUT).  A CTA walks a contiguous range of 8 x 8 pixel tiles (K = 64 per tile) and keeps
+// its MT accumulators in tensor memory across the whole range:
+//   1. x (with a KS/2 halo, zero outside the image) and dz of the tile land in shared memory
+//      by cp.async as 16-byte pixel rows [chunk][row][col][8 channels], double-buffered;
+//   2. the four warps build the K-major operands from them with ldmatrix.trans: an 8 x 8
+//      block of (8 pixels of one tile row) x (8 channels) becomes one 128-byte core matrix
+//      (8 channels x 8 pixels); the tap's offset is applied in the ldmatrix row addresses;
+//   3. one thread issues MT x 4 MMAs (K = 16 each) and commits them to an mbarrier, which
+//      the warps wait on (bounded) before they overwrite the operands with the next tile.
+// Operand layouts (no swizzle): A tile mt at mt * 16 KB, core matrix (row group rg, pixel
+// row kg) at (16 kg + rg) * 128 (LBO 2048 between K groups, SBO 128 between row groups);
+// B core matrix (channel group og, kg) at (kg * COUT/8 + og) * 128 (LBO COUT * 16, SBO 128).
+// Rows of A past KS^2 * CIN are never written and their accumulator rows are discarded.
+// At the end each thread reads its accumulator row (one (tap, i)) and adds it to the FP32
+// master gradient [Cout][Cin][k][k] with atomics (padding channels skipped).
 struct WgradArgs {
     const bf16 *x, *dz;
     float *gw;  // master layout
     int N, H, W, cin_true, cout_true, tiles_per_cta;
+    int *status;
 };
 
 template <int CIN, int COUT, int KS>
-__global__ void __launch_bounds__(256) wgrad_kernel(const WgradArgs a)
+struct WgGeom {
+    static constexpr int P = KS / 2, SH = 8 + 2 * P, SW = 8 + 2 * P, C8 = CIN / 8, O8 = COUT / 8;
+    static constexpr int M = KS * KS * CIN, MT = (M + 127) / 128;
+    static constexpr int XP = (SH * SW * 16 + 127) / 128 * 128;  // one staged x chunk plane
+    static constexpr int STAGE = C8 * XP + O8 * 1024;            // x planes, then dz planes [8][8][8]
+    static constexpr int ABYTES = MT * 16384, BBYTES = O8 * 1024;
+    static constexpr int SMEM = 128 + 2 * STAGE + ABYTES + BBYTES + 16;
+    static constexpr int COLS = tmem_cols<MT * COUT>();
+    static constexpr int NU = KS * KS * C8 * 8;  // A core matrices per tile (tap, chunk, pixel row)
+    static_assert(MT * COUT <= 512, "accumulators exceed tensor memory");
+};
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
 {
-    constexpr int TP = 128, PS = TP + 8;  // pixels per tile, padded row stride
-    constexpr int MT = COUT / 16, NTL = CIN / 8, TILES = MT * NTL;
-    constexpr int PER = (TILES + 7) / 8;
-    __shared__ __align__(16) bf16 dzT[COUT * PS];
-    __shared__ __align__(16) bf16 xT[CIN * PS];
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+template <int CIN, int COUT, int KS>
+__global__ void __launch_bounds__(128) wgrad_tc_kernel(const WgradArgs a)
+{
+    using G = WgGeom<CIN, COUT, KS>;
+    constexpr int P = G::P, SW = G::SW, C8 = G::C8, O8 = G::O8, XP = G::XP, MT = G::MT;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0, "UMMA shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    unsigned char *stage0 = base;
+    unsigned char *opA = base + 2 * G::STAGE;
+    unsigned char *opB = opA + G::ABYTES;
+    uint64_t *done = reinterpret_cast<uint64_t *>(opB + G::BBYTES);
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tap = blockIdx.x, dy = tap / KS - KS / 2, dx = tap % KS - KS / 2;
-    const long long P = (long long)a.N * a.H * a.W;
-    const long long ntiles = (P + TP - 1) / TP;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[PER][4];
-#pragma unroll
-    for (int j = 0; j < PER; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-    for (long long tile = (long long)blockIdx.y * a.tiles_per_cta;
-         tile < ntiles && tile < (long long)(blockIdx.y + 1) * a.tiles_per_cta; ++tile) {
-        const long long p0 = tile * TP;
-        for (int i = tid; i < TP * COUT; i += 256) {
-            const int p = i / COUT, c = i % COUT;
-            dzT[c * PS + p] = (p0 + p < P) ? a.dz[(p0 + p) * COUT + c] : __float2bfloat16(0.f);
+    const int tiles_x = (a.W + 7) / 8, tiles_y = (a.H + 7) / 8;
+    const long long ntiles = (long long)a.N * tiles_x * tiles_y;
+    const long long t0 = (long long)blockIdx.x * a.tiles_per_cta;
+    const long long t1 = t0 + a.tiles_per_cta < ntiles ? t0 + a.tiles_per_cta : ntiles;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(G::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(done)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = s_tmem;
+
+    auto stage = [&](long long t, unsigned char *sb) {
+        const int n = (int)(t / ((long long)tiles_x * tiles_y));
+        const int r = (int)(t % ((long long)tiles_x * tiles_y));
+        const int ty0 = (r / tiles_x) * 8, tx0 = (r % tiles_x) * 8;
+        for (int e = tid; e < C8 * G::SH * SW; e += 128) {
+            const int c8 = e / (G::SH * SW), pix = e % (G::SH * SW);
+            const int yy = ty0 - P + pix / SW, xx = tx0 - P + pix % SW;
+            const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = in ? a.x + (((size_t)n * a.H + yy) * a.W + xx) * CIN + c8 * 8 : a.x;
+            cp_async16(sb + c8 * XP + pix * 16, src, in);
         }
-        for (int i = tid; i < TP * CIN; i += 256) {
-            const int p = i / CIN, c = i % CIN;
-            bf16 v = __float2bfloat16(0.f);
-            const long long q = p0 + p;
-            if (q < P) {
-                const long long hw = (long long)a.H * a.W;
-                const int n = (int)(q / hw), rem = (int)(q % hw), y = rem / a.W + dy, x = rem % a.W + dx;
-                if (y >= 0 && y < a.H && x >= 0 && x < a.W) v = a.x[((long long)n * hw + (long long)y * a.W + x) * CIN + c];
-            }
-            xT[c * PS + p] = v;
+        unsigned char *sd = sb + C8 * XP;
+        for (int e = tid; e < O8 * 64; e += 128) {
+            const int o8 = e / 64, pix = e % 64;
+            const int yy = ty0 + pix / 8, xx = tx0 + pix % 8;
+            const bool in = yy < a.H && xx < a.W;
+            const bf16 *src = in ? a.dz + (((size_t)n * a.H + yy) * a.W + xx) * COUT + o8 * 8 : a.dz;
+            cp_async16(sd + o8 * 1024 + pix * 16, src, in);
+        }
+    };
+
+    constexpr uint32_t idesc = umma_idesc(COUT);
+    int it = 0;
+    if (t0 < t1) stage(t0, stage0);
+    cp_async_commit();
+    for (long long t = t0; t < t1; ++t, ++it) {
+        unsigned char *sb = stage0 + (it & 1) * G::STAGE;
+        if (t + 1 < t1) stage(t + 1, stage0 + ((it + 1) & 1) * G::STAGE);
+        cp_async_commit();
+        cp_async_wait<1>();
+        // the MMAs of the previous tile must have read the operands before they are rebuilt
+        if (it > 0 && !mbar_wait_warp(smem_u32(done), (uint32_t)((it - 1) & 1))) {
+            if (lane == 0) s_fail = 1;
         }
         __syncthreads();
+        if (s_fail) break;
+        // A: unit q = (tap, chunk, pixel row ty); lanes 8j..8j+7 address unit q + j, row tx
+        const uint32_t xs = smem_u32(sb), as = smem_u32(opA);
+        for (int q = 4 * warp; q < G::NU; q += 16) {
+            const int u = q + (lane >> 3), tx = lane & 7;
+            const int ty = u % 8, c8 = (u / 8) % C8, tap = u / (8 * C8);
+            const int dy = tap / KS, dx = tap % KS;
+            uint32_t v[4];
+            ldsm_x4_trans(xs + c8 * XP + ((ty + dy) * SW + tx + dx) * 16, v[0], v[1], v[2], v[3]);
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int tl = warp + 8 * j;
-            if (tl < TILES) {
-                const int mt = tl / NTL, nt = tl % NTL;
+            for (int j = 0; j < 4; ++j) {
+                const int uj = q + j, tyj = uj % 8, m0 = (uj / (8 * C8)) * CIN + ((uj / 8) % C8) * 8;
+                const uint32_t dst = as + (m0 / 128) * 16384 + (tyj * 16 + (m0 % 128) / 8) * 128 + lane * 4;
+                asm volatile("st.shared.b32 [%0], %1;\n" ::"r"(dst), "r"(v[j]) : "memory");
+            }
+        }
+        // B: unit q = (channel group og, pixel row ty)
+        const uint32_t ds = xs + C8 * XP, bs = smem_u32(opB);
+        for (int q = 4 * warp; q < O8 * 8; q += 16) {
+            const int u = q + (lane >> 3), tx = lane & 7;
+            const int ty = u % 8, og = u / 8;
+            uint32_t v[4];
+            ldsm_x4_trans(ds + og * 1024 + (ty * 8 + tx) * 16, v[0], v[1], v[2], v[3]);
 #pragma unroll
-                for (int k = 0; k < TP / 16; ++k) {
-                    uint32_t af[4];
-                    const bf16 *r0 = dzT + (mt * 16 + g) * PS + k * 16 + 2 * t;
-                    af[0] = ld32(r0);
-                    af[1] = ld32(r0 + 8 * PS);
-                    af[2] = ld32(r0 + 8);
-                    af[3] = ld32(r0 + 8 * PS + 8);
-                    const bf16 *b = xT + (nt * 8 + g) * PS + k * 16 + 2 * t;
-                    mma_bf16(acc[j], af, ld32(b), ld32(b + 8));
+            for (int j = 0; j < 4; ++j) {
+                const int uj = q + j;
+                const uint32_t dst = bs + ((uj % 8) * O8 + uj / 8) * 128 + lane * 4;
+                asm volatile("st.shared.b32 [%0], %1;\n" ::"r"(dst), "r"(v[j]) : "memory");
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n");  // operands visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint64_t ad0 = umma_sdesc(as, 2048, 128), bd0 = umma_sdesc(bs, O8 * 128, 128);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint64_t bd = bd0 + (uint64_t)((2 * s * O8 * 128) >> 4);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const uint64_t ad = ad0 + (uint64_t)((mt * 16384 + 2 * s * 2048) >> 4);
+                    umma_bf16(tmem + (uint32_t)(mt * COUT), ad, bd, idesc, (it > 0 || s > 0) ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(done)));
+        }
+    }
+    cp_async_wait<0>();
+    bool ok = !s_fail;
+    if (ok && it > 0 && !mbar_wait_warp(smem_u32(done), (uint32_t)((it - 1) & 1))) {
+        ok = false;
+        if (lane == 0) s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0 && a.status) atomicExch(a.status, FLNR_STATUS_TIMEOUT);
+    } else if (it > 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const int r = 32 * warp + lane;
+#pragma unroll 1
+        for (int mt = 0; mt < MT; ++mt) {
+            const int m = mt * 128 + r, tap = m / CIN, i = m % CIN;
+#pragma unroll
+            for (int o0 = 0; o0 < COUT; o0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(mt * COUT + o0), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+                if (m < G::M && i < a.cin_true) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (o0 + j < a.cout_true)
+                            atomicAdd(a.gw + ((size_t)(o0 + j) * a.cin_true + i) * KS * KS + tap, v[j]);
                 }
             }
         }
-        __syncthreads();
     }
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int tl = warp + 8 * j;
-        if (tl >= TILES) continue;
-        const int mt = tl / NTL, nt = tl % NTL;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int o = mt * 16 + g + (e >= 2 ? 8 : 0), i = nt * 8 + 2 * t + (e & 1);
-            if (o < a.cout_true && i < a.cin_true)
-                atomicAdd(a.gw + ((size_t)o * a.cin_true + i) * KS * KS + tap, acc[j][e]);
-        }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::COLS));
     }
 }
 
@@ -1302,6 +1299,27 @@ __global__ void pack_input_kernel(const float *in, bf16 *x, int N, int H, int W)
         }
         *reinterpret_cast<uint4 *>(x + p * 16) = *reinterpret_cast<uint4 *>(v);
         *reinterpret_cast<uint4 *>(x + p * 16 + 8) = *reinterpret_cast<uint4 *>(v + 8);
+    }
+}
+
+// gradient with respect to the network's planar input [N][11][H][W] from the gradient dx
+// [N][H][W][16] with respect to the packed input x: the guides pass through; a radiance
+// channel was read as L = log(1 + max(Y, 0)), whose derivative is 1 / (1 + Y) = exp(-L) for
+// Y > 0 and 0 for Y < 0 (L is the stored bfloat16 value, so Y > 0 exactly when L > 0)
+__global__ void unpack_grad_kernel(const bf16 *dx, const bf16 *x, float *g, int N, int H, int W)
+{
+    const size_t hw = (size_t)H * W, total = (size_t)N * hw;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = p / hw, o = p % hw;
+#pragma unroll
+        for (int c = 0; c < 11; ++c) {
+            float d = __bfloat162float(dx[p * 16 + c]);
+            if (c >= 8) {
+                const float L = __bfloat162float(x[p * 16 + c]);
+                d = L > 0.f ? d * expf(-L) : 0.f;
+            }
+            g[(n * 11 + c) * hw + o] = d;
+        }
     }
 }
 
@@ -1470,30 +1488,6 @@ int egrid(size_t n) { return (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 81
 
 // ---------------------------------------------------------------------------------------
 // Launch helpers for the template instantiations the network uses.
-template <int CIN, int COUT, int KS, bool MASK, int WARPS = 8>
-cudaError_t conv_launch(const ConvArgs &a, cudaStream_t st)
-{
-    constexpr int P = KS / 2, TH = 2 * WARPS, TW = 16;
-    constexpr size_t smem = sizeof(bf16) * ((size_t)KS * KS * COUT * (CIN + 8) + 2 * (size_t)(TH + 2 * P) * (TW + 2 * P) * (CIN + 8));
-    static_assert(smem <= 227 * 1024, "conv tile does not fit in shared memory");
-    auto kern = conv_kernel<CIN, COUT, KS, MASK, WARPS>;
-    static int per_sm = 0, n_sm = 0;  // occupancy of this instantiation, computed once
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem)) != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
-    const long long ntiles = (long long)a.N * ((a.H + TH - 1) / TH) * ((a.W + TW - 1) / TW);
-    if (ntiles <= 0) return cudaSuccess;
-    const long long cap = (long long)per_sm * n_sm;
-    kern<<<(int)(ntiles < cap ? ntiles : cap), WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 {
@@ -1546,7 +1540,7 @@ cudaError_t make_tmap_parity(CUtensorMap *m, const void *base, int C, int W, int
 // kernel's registers, shared memory and threads, and capped at 512 / (TMEM columns per CTA);
 // where threads alone would allow more CTAs than TMEM can hold, the shared-memory request is
 // raised so that no more can be resident (an allocation never has to wait for another CTA).
-template <int CIN, int COUT, int KS, int ACT, int OUTM>
+template <int CIN, int COUT, int KS, int ACT, int OUTM, bool MASK = false>
 cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
 {
     using G = WsGeom<CIN, COUT, KS>;
@@ -1555,7 +1549,7 @@ cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
     constexpr int min_smem = tmem_cap < kThreadsPerSm / kWsThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
     constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
     static_assert(smem <= 227 * 1024, "warp-specialised conv tile does not fit in shared memory");
-    auto kern = conv_ws_kernel<CIN, COUT, KS, ACT, OUTM>;
+    auto kern = conv_ws_kernel<CIN, COUT, KS, ACT, OUTM, MASK>;
     static int per_sm = 0, n_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1588,6 +1582,19 @@ cudaError_t conv_ws_launch(const ConvArgs &a, cudaStream_t st)
     const long long cap = (long long)per_sm * n_sm;
     kern<<<(int)(ntiles < cap ? ntiles : cap), kWsThreads, smem, st>>>(ta);
     return cudaGetLastError();
+}
+
+// Input gradient of a layer on the tensor cores: the stride-1 convolution of dz with the
+// layer's weights rotated by 180 degrees and transposed ([tap][CinP][CoutP]), no bias, no
+// activation, times (mask > 0) when MASK (the ReLU of the layer input).  a: x = dz
+// [N][H][W][CIN], w, mask [N][H][W][COUT], y [N][H][W][ystride].
+template <int CIN, int COUT, int KS, bool MASK>
+cudaError_t dgrad_launch(ConvArgs a, int *status, cudaStream_t st)
+{
+    a.bias = nullptr;
+    a.nbias = 0;
+    a.status = status;
+    return conv_ws_launch<CIN, COUT, KS, 0, 0, MASK>(a, st);
 }
 
 // Launch of the fused KS x KS + 1x1 pair (c: first layer, c2: the 1x1 layer); residency
@@ -1731,16 +1738,48 @@ cudaError_t conv_s2_launch(const ConvArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Launch of the tensor-core weight gradient: one CTA per resident slot, each over a
+// contiguous range of 8 x 8 pixel tiles.  Residency as for conv_ws_launch: the shared-memory
+// request is raised where needed so that no more CTAs than tensor memory can hold share an SM.
 template <int CIN, int COUT, int KS>
 cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H, int W, int cin_true, int cout_true,
-                         int n_sm, cudaStream_t st)
+                         int *status, cudaStream_t st)
 {
-    WgradArgs a{x, dz, gw, N, H, W, cin_true, cout_true, 0};
-    const long long ntiles = ((long long)N * H * W + 127) / 128;
-    const int chunks = (int)(ntiles < 2LL * n_sm ? ntiles : 2LL * n_sm);
-    a.tiles_per_cta = (int)((ntiles + chunks - 1) / chunks);
-    dim3 grid(KS * KS, chunks);
-    wgrad_kernel<CIN, COUT, KS><<<grid, 256, 0, st>>>(a);
+    using G = WgGeom<CIN, COUT, KS>;
+    constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreads = 128, kThreadsPerSm = 2048;
+    constexpr int tmem_cap = 512 / G::COLS;
+    constexpr int min_smem = tmem_cap < kThreadsPerSm / kThreads ? kSmemPerSm / tmem_cap - kReservedPerCta - 256 : 0;
+    constexpr size_t smem = (size_t)(G::SMEM > min_smem ? G::SMEM : min_smem);
+    static_assert(smem <= 227 * 1024, "weight-gradient tile does not fit in shared memory");
+    auto kern = wgrad_tc_kernel<CIN, COUT, KS>;
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = (4 * (16384 / regs_per_warp)) / (kThreads / 32);
+        const int by_smem = kSmemPerSm / ((int)smem + (int)fa.sharedSizeBytes + kReservedPerCta);
+        int r = kThreadsPerSm / kThreads;
+        r = r < by_regs ? r : by_regs;
+        r = r < by_smem ? r : by_smem;
+        r = r < tmem_cap ? r : tmem_cap;
+        if (r < 1) return cudaErrorInvalidConfiguration;
+        per_sm = r;
+    }
+    const long long ntiles = (long long)N * ((H + 7) / 8) * ((W + 7) / 8);
+    if (ntiles <= 0) return cudaSuccess;
+    const long long slots = (long long)per_sm * n_sm;
+    const long long ctas = ntiles < slots ? ntiles : slots;
+    WgradArgs a{x, dz, gw, N, H, W, cin_true, cout_true, (int)((ntiles + ctas - 1) / ctas), status};
+    const long long grid = (ntiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
+    kern<<<(int)grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1944,14 +1983,13 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     return FLR_OK;
 }
 
-int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
+int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void *stream)
 {
     using namespace flnr;
     if (!n || !grad_out || n->N <= 0) return FLR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int N = n->N, H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const size_t P = (size_t)N * H * W;
-    const int ns = n->n_sm;
     auto gw = [&](int l) { return n->g + n->poff[l][0]; };
     auto gb = [&](int l) { return n->g + n->poff[l][1]; };
     auto bgrad = [&](const __nv_bfloat16 *dz, long long pix, int C, int ctrue, int l) {
@@ -1959,32 +1997,32 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
     };
     // output head: sigmoid, o1 (1x1, 16 -> 8 padded to 16), o0
     sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W);
-    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, 8, ns, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, 8, n->status, st)));
     bgrad(n->gA, (long long)P, 16, 8, 11);
-    FLNR_TRY((conv_launch<16, 16, 1, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
-    FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, ns, st)));
+    FLNR_TRY((dgrad_launch<16, 16, 1, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, n->status, st)));
     bgrad(n->gB, (long long)P, 16, 16, 10);
-    FLNR_TRY((conv_launch<16, 16, 3, true>({n->gB, n->wd[10], n->d0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((dgrad_launch<16, 16, 3, true>({n->gB, n->wd[10], n->d0, nullptr, n->gA, nullptr, N, H, W, 16}, n->status, st)));
     // decoder level 0
-    FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, ns, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, n->status, st)));
     bgrad(n->gA, (long long)P, 16, 16, 9);
-    FLNR_TRY((conv_launch<16, 16, 3, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((dgrad_launch<16, 16, 3, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
     upcat_kernel<<<egrid(P * 6), 256, 0, st>>>(n->d1, n->f0, n->c0, N, H, W, 32, 16);  // d0a's input
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, ns, st)));
+    FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, n->status, st)));
     bgrad(n->gB, (long long)P, 16, 16, 8);
-    FLNR_TRY((conv_launch<16, 48, 3, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, st)));
+    FLNR_TRY((dgrad_launch<16, 48, 3, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, n->status, st)));
     upcat_bwd_kernel<<<egrid(P * 48), 256, 0, st>>>(n->gC, n->d1, n->gLo, n->gskip0, N, H, W, 32, 16);  // gLo = dz(d1b)
     // decoder level 1 (H/2)
     const size_t P2 = P / 4;
-    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, ns, st)));
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, n->status, st)));
     bgrad(n->gLo, (long long)P2, 32, 32, 7);
-    FLNR_TRY((conv_launch<32, 32, 3, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, st)));
+    FLNR_TRY((dgrad_launch<32, 32, 3, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, n->status, st)));
     upcat_kernel<<<egrid(P2 * 12), 256, 0, st>>>(n->f2, n->f1, n->c1, N, H2, W2, 64, 32);  // d1a's input
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, ns, st)));
+    FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, n->status, st)));
     bgrad(n->gA, (long long)P2, 32, 32, 6);
-    FLNR_TRY((conv_launch<32, 96, 3, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, st)));
+    FLNR_TRY((dgrad_launch<32, 96, 3, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, n->status, st)));
     upcat_bwd_kernel<<<egrid(P2 * 96), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
     // encoder level 2: e2b (stride 2, H/2 -> H/4), then e2a (H/2).  A stride-2 layer's
     // gradients are those of the stride-1 kernels at its input's size on dz zero-upsampled
@@ -1993,27 +2031,31 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, void *stream)
     bgrad(n->gLo, (long long)P4, 64, 64, 5);
     join_bwd_kernel<2><<<egrid(P2 * 64), 256, 0, st>>>(nullptr, n->gLo, nullptr, n->gB, N, H4, W4, 64);
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gB, gw(5), N, H2, W2, 64, 64, ns, st)));
-    FLNR_TRY((conv_launch<64, 64, 3, true>({n->gB, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H2, W2, 64}, st)));
-    FLNR_TRY((wgrad_launch<32, 64, 3>(n->f1, n->gA, gw(4), N, H2, W2, 32, 64, ns, st)));
+    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gB, gw(5), N, H2, W2, 64, 64, n->status, st)));
+    FLNR_TRY((dgrad_launch<64, 64, 3, true>({n->gB, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H2, W2, 64}, n->status, st)));
+    FLNR_TRY((wgrad_launch<32, 64, 3>(n->f1, n->gA, gw(4), N, H2, W2, 32, 64, n->status, st)));
     bgrad(n->gA, (long long)P2, 64, 64, 4);
-    FLNR_TRY((conv_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 32}, st)));
+    FLNR_TRY((dgrad_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 32}, n->status, st)));
     // encoder level 1: e1b (stride 2, H -> H/2; f1 also feeds the d1a skip), then e1a (H)
     join_bwd_kernel<2><<<egrid(P * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gC, N, H2, W2, 32);
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gC, gw(3), N, H, W, 32, 32, ns, st)));
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gC, gw(3), N, H, W, 32, 32, n->status, st)));
     bgrad(n->gC, (long long)P, 32, 32, 3);
-    FLNR_TRY((conv_launch<32, 32, 3, true>({n->gC, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H, W, 32}, st)));
-    FLNR_TRY((wgrad_launch<16, 32, 3>(n->f0, n->gA, gw(2), N, H, W, 16, 32, ns, st)));
+    FLNR_TRY((dgrad_launch<32, 32, 3, true>({n->gC, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H, W, 32}, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 32, 3>(n->f0, n->gA, gw(2), N, H, W, 16, 32, n->status, st)));
     bgrad(n->gA, (long long)P, 32, 32, 2);
-    FLNR_TRY((conv_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, st)));
+    FLNR_TRY((dgrad_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
     join_bwd_kernel<1><<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
     // input projection (H)
-    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, ns, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, n->status, st)));
     bgrad(n->gLo, (long long)P, 16, 16, 1);
-    FLNR_TRY((conv_launch<16, 16, 1, true>({n->gLo, n->wd[1], n->a0, nullptr, n->gA, nullptr, N, H, W, 16}, st)));
-    FLNR_TRY((wgrad_launch<16, 16, 3>(n->x0, n->gA, gw(0), N, H, W, 11, 16, ns, st)));
+    FLNR_TRY((dgrad_launch<16, 16, 1, true>({n->gLo, n->wd[1], n->a0, nullptr, n->gA, nullptr, N, H, W, 16}, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->x0, n->gA, gw(0), N, H, W, 11, 16, n->status, st)));
     bgrad(n->gA, (long long)P, 16, 16, 0);
+    if (grad_in) {  // through in0 to the packed input, then through the input transform
+        FLNR_TRY((dgrad_launch<16, 16, 3, false>({n->gA, n->wd[0], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
+        unpack_grad_kernel<<<egrid(P), 256, 0, st>>>(n->gB, n->x0, grad_in, N, H, W);
+    }
     return cudaGetLastError() == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
 }
 
@@ -2075,11 +2117,11 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
     }
     if (op == FLNR_OP_DGRAD) {
         if (mask)
-            FLNR_TRY((conv_launch<CO, CI, KS, true>({dz, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+            FLNR_TRY((dgrad_launch<CO, CI, KS, true>({dz, n->wd[l], (const bf *)mask, nullptr, (bf *)out, nullptr, N, H, W, CI}, n->status, st)));
         else
-            FLNR_TRY((conv_launch<CO, CI, KS, false>({dz, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, st)));
+            FLNR_TRY((dgrad_launch<CO, CI, KS, false>({dz, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, n->status, st)));
     } else {
-        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->n_sm, st)));
+        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->status, st)));
         bias_grad_kernel<<<64, 256, 0, st>>>(dz, n->g + n->poff[l][1], P, CO, d.cout);
         FLNR_TRY(cudaGetLastError());
     }

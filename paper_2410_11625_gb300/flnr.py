@@ -32,7 +32,7 @@ def _lib():
         lib.flnr_get_weights.argtypes = [vp, vp, ctypes.c_size_t]
         lib.flnr_get_grads.argtypes = [vp, vp, ctypes.c_size_t]
         lib.flnr_guide_forward.argtypes = [vp, vp, vp, ip, ip, ip, vp]
-        lib.flnr_guide_backward.argtypes = [vp, vp, vp]
+        lib.flnr_guide_backward.argtypes = [vp, vp, vp, vp]
         lib.flnr_zero_grads.argtypes = [vp, vp]
         lib.flnr_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ip, vp]
         lib.flnr_l1_loss.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
@@ -131,10 +131,13 @@ class FLNR:
                     "flnr_guide_forward")
         return out
 
-    def backward(self, grad_out):
-        """Accumulate parameter gradients for dL/d(enhanced guides) = grad_out [N,8,H,W]."""
-        _flr._check(_lib().flnr_guide_backward(self._h, grad_out.contiguous().data_ptr(), _stream(grad_out)),
+    def backward(self, grad_out, grad_in=None):
+        """Accumulate parameter gradients for dL/d(enhanced guides) = grad_out [N,8,H,W];
+        grad_in (optional CUDA float32 [N,11,H,W]) receives dL/d(input)."""
+        gi = None if grad_in is None else ctypes.c_void_p(grad_in.data_ptr())
+        _flr._check(_lib().flnr_guide_backward(self._h, grad_out.contiguous().data_ptr(), gi, _stream(grad_out)),
                     "flnr_guide_backward")
+        return grad_in
 
     OP_FORWARD, OP_DGRAD, OP_WGRAD = 0, 1, 2
 

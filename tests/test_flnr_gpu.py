@@ -226,13 +226,23 @@ def network_case(N, H, W, seed):
 def test_network_matches_bf16_storage_oracle(N, H, W):
     p = params_with_bias(3)
     x, G = network_case(N, H, W, H)
+    x[:, 8:, ::7, ::5] = -0.3  # negative radiance: the input transform's zero-gradient branch
     ref, g_ref = flnr_ref.forward_backward(x, p, G, bf16_storage=True)
     ref64, _ = flnr_ref.forward_backward(x, p, G)
     net = flnr.FLNR(N * H * W, p)
     out = net.forward(to_dev(x))
     net.zero_grads(out)
-    net.backward(to_dev(G))
+    g_in = torch.full((N, 11, H, W), float("nan"), device="cuda")
+    net.backward(to_dev(G), grad_in=g_in)
     torch.cuda.synchronize()
+    # dL/d(input): guides directly, radiance through log(1 + max(Y, 0)); zero where Y < 0
+    gi, gi_ref = g_in.cpu().numpy().astype(np.float64), g_ref["input"]
+    assert np.all(np.isfinite(gi)) and np.all(gi[:, 8:][x[:, 8:] < 0] == 0)
+    for sl in (slice(0, 8), slice(8, 11)):
+        a, b = gi[:, sl], gi_ref[:, sl]
+        cos = np.sum(a * b) / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert cos >= 0.998 and rel <= 6e-2, ("input", sl, cos, rel)
     got = out.cpu().numpy()
     err = np.abs(got - ref)
     # outputs in (0, 1): a bfloat16 unit at 1 is 2^-8; rounding flips near boundaries cascade
