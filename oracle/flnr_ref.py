@@ -11,7 +11,10 @@ concatenated channel-wise, Sec. 3.3) to 8 enhanced guide channels through a 3-le
   encoder level 2    conv3x3 32->64, ReLU;  conv3x3 64->64 stride 2, ReLU           -> f2 (H/4)
   decoder level 1    nearest 2x up(f2) ++ f1;  conv3x3 96->32, ReLU;  conv3x3 32->32, ReLU -> d1
   decoder level 0    nearest 2x up(d1) ++ f0;  conv3x3 48->16, ReLU;  conv3x3 16->16, ReLU -> d0
-  output             conv3x3 16->16, ReLU;  conv1x1 16->8;  sigmoid                -> X'
+  output             conv3x3 16->16, ReLU;  conv1x1 16->Q';  sigmoid               -> X'
+Q' = 8 (one set of enhanced guides, used both to fit and to apply the regression), or the
+paper's two sets (Sec. 3.3): Q' = 2Q = 16 outputs, channels 0-7 the model guides X'_model
+and channels 8-15 the map guides X'_map.
 Sec. 3.3: each encoder block is two 3x3 convolutions, the second striding by 2 to
 downsample (no separate pooling).  Every 3x3 convolution has zero padding 1; a stride-2 one
 gives output (i, j) from inputs (2i + u - 1, 2j + v - 1).  H and W must be multiples of 4.
@@ -43,12 +46,15 @@ LAYERS = [
 ]
 
 
-def init_weights(seed=0):
+def init_weights(seed=0, outputs=8):
     """He-uniform weights and zero biases, float32 (the dtype the GPU master copy keeps);
-    the output projection o1 at a tenth of its He bound."""
+    the output projection o1 at a tenth of its He bound, with `outputs` (8, or 16 for the
+    model and map sets of Sec. 3.3) output channels."""
     rng = np.random.default_rng(seed)
     params = {}
     for name, _, cin, cout, k in LAYERS:
+        if name == "o1":
+            cout = outputs
         bound = np.sqrt(6.0 / (cin * k * k)) * (0.1 if name == "o1" else 1.0)
         params[name + ".w"] = rng.uniform(-bound, bound, size=(cout, cin, k, k)).astype(np.float32)
         params[name + ".b"] = np.zeros(cout, np.float32)

@@ -99,6 +99,24 @@ def test_gradients_match_finite_differences():
         assert abs(fd - grads["input"][idx]) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_two_output_sets_share_the_network():
+    """Sec. 3.3's 2Q outputs: the 16-channel head's first 8 channels equal the 8-channel
+    network whose o1 holds the first 8 rows of the 16-channel o1, and the other 8 follow the
+    same features with the remaining rows (the layers before o1 are shared)."""
+    rng = np.random.default_rng(12)
+    p16 = {k: v.astype(np.float64) for k, v in flnr_ref.init_weights(4, outputs=16).items()}
+    assert p16["o1.w"].shape == (16, 16, 1, 1) and p16["o1.b"].shape == (16,)
+    p16["o1.b"] = rng.normal(scale=0.1, size=16)
+    x = rng.uniform(size=(1, 11, 8, 12))
+    out16 = flnr_ref.forward(torch.tensor(x), {k: torch.tensor(v) for k, v in p16.items()}).numpy()
+    assert out16.shape == (1, 16, 8, 12)
+    for half in (slice(0, 8), slice(8, 16)):
+        p8 = dict(p16)
+        p8["o1.w"], p8["o1.b"] = p16["o1.w"][half], p16["o1.b"][half]
+        out8 = flnr_ref.forward(torch.tensor(x), {k: torch.tensor(v) for k, v in p8.items()}).numpy()
+        assert np.max(np.abs(out8 - out16[:, half])) < 1e-14
+
+
 def bf16_bits(a):
     """Round-to-nearest-even of float32 values to bfloat16, by integer arithmetic on the
     IEEE-754 bit patterns (finite inputs): keep the top 16 bits, adding 0x7FFF plus the
