@@ -374,9 +374,25 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
                  f"rooms, 8 noise realisations each, L1, Adam lr 2e-3 cosine to 1e-4) in {t_train:.1f} s; "
                  f"rendering {t_render:.1f} s on the host"),
     }
+    # the two guide sets of Sec. 3.3 (16 outputs: model guides, map guides), same recipe
+    tr2 = flnr_train.Trainer(flnr.init_weights(0, 16), batch=16, crop=128, lr=2e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr2.train(scenes, train_steps, seed=0, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train2 = time.perf_counter() - t0
+    _, p_2q = flnr_train.evaluate(tr2.net, tr2.flr, held_out)
+    rows["flnr_2q_psnr"] = {
+        "psnr_flnr_2q_db": round(float(np.mean(p_2q)), 3), "gain_db": round(float(np.mean(p_2q) - np.mean(p_flr)), 3),
+        "per_scene_gain_db": [round(a - b, 2) for a, b in zip(p_2q, p_flr)],
+        "rooms_improved": int(sum(a > b for a, b in zip(p_2q, p_flr))),
+        "what": f"as flnr_psnr with a 16-output head: channels 0-7 fit the models, 8-15 are FLR's map guide; "
+                f"trained {train_steps} steps in {t_train2:.1f} s"}
     xs, rs = flnr_train.sample_batch(np.random.default_rng(1), scenes, 16, 128)
+    t_step2 = timed(lambda i: tr2.step(xs, rs), 50)
+    tr2.net.close()
     t_step = timed(lambda i: tr.step(xs, rs), 50)
-    rows["flnr_train_step"] = {"ms_per_step": round(t_step, 4),
+    rows["flnr_train_step"] = {"ms_per_step": round(t_step, 4), "ms_per_step_2q": round(t_step2, 4),
                                "what": "batch 16 x 128x128: FLNR fwd, 16 x FLR, L1, 16 x FLR adjoint, FLNR bwd, Adam; "
                                        "includes the pinned H2D copy of the batch"}
     weights = tr.net.get_weights()

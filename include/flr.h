@@ -308,37 +308,41 @@ int flr_mbarrier_selftest(int ctas, unsigned long long timeout_ns, int *status);
 
 /*
  * FLNR (Sec. 3.3, "Fast Local Neural Regression"): a U-Net maps the guides and the noisy
- * radiance, concatenated channel-wise (11 channels: Q = 8 guides, then RGB), to 8 enhanced
- * guide channels that FLR then uses (Fig. 2).  Layers, in order (3x3 convolutions with zero
+ * radiance, concatenated channel-wise (11 channels: Q = 8 guides, then RGB), to enhanced
+ * guide channels that FLR then uses (Fig. 2): 8 (one set, used both to fit and to apply the
+ * models), or 16 = 2Q, the two sets of Sec. 3.3 (channels 0-7 the model guides X'_model,
+ * 8-15 the map guides X'_map, for FLR's map_guide).  Layers, in order (3x3 convolutions with zero
  * padding 1, stride 1 unless stated; ReLU unless stated):
  *   in0 3x3 11->16, in1 1x1 16->16 | e1a 3x3 16->32, e1b 3x3 32->32 stride 2 |
  *   e2a 3x3 32->64, e2b 3x3 64->64 stride 2 | up2 ++ e1b: d1a 3x3 96->32, d1b 3x3 32->32 |
- *   up2 ++ in1: d0a 3x3 48->16, d0b 3x3 16->16 | o0 3x3 16->16, o1 1x1 16->8 + sigmoid.
+ *   up2 ++ in1: d0a 3x3 48->16, d0b 3x3 16->16 | o0 3x3 16->16, o1 1x1 16->nout + sigmoid.
  * Each encoder block downsamples with its second convolution (stride 2, Sec. 3.3): output
  * (i, j) reads inputs (2i - 1 .. 2i + 1, 2j - 1 .. 2j + 1).
  * The network reads the radiance channels as log(1 + max(Y, 0)) (fireflies stay bounded).
- * BF16 convolutions on the tensor cores with FP32 accumulation (forward: tcgen05 UMMA with
- * accumulators in tensor memory; backward: warp-level MMA); FP32 master weights.
- * Parameters are one flat float array: per layer its weights [Cout][Cin][k][k] then its
- * biases [Cout], layers in the order above (flnr_param_count() floats).
+ * BF16 convolutions on the fifth-generation tensor cores (tcgen05 UMMA, FP32 accumulators in
+ * tensor memory) for the forward pass, the input gradients and the weight gradients; FP32
+ * master weights.  Parameters are one flat float array: per layer its weights
+ * [Cout][Cin][k][k] then its biases [Cout], layers in the order above
+ * (flnr_param_count(nout) floats).
  */
 typedef struct flnr_net flnr_net;
 
-/* Number of parameters (floats). */
-size_t flnr_param_count(void);
+/* Number of parameters (floats) of the network with nout = 8 or 16 outputs; 0 otherwise. */
+size_t flnr_param_count(int nout);
 
-/* Create a network whose activation buffers hold up to max_pixels = N*H*W input pixels. */
-int flnr_create(int max_pixels, flnr_net **out);
+/* Create a network with nout = 8 or 16 outputs whose activation buffers hold up to
+ * max_pixels = N*H*W input pixels.  Errors: FLR_ERR_ARG, FLR_ERR_NOMEM. */
+int flnr_create(int max_pixels, int nout, flnr_net **out);
 int flnr_destroy(flnr_net *net);
 
-/* Copy the master weights from / to host memory (count = flnr_param_count()); synchronous.
+/* Copy the master weights from / to host memory (count = flnr_param_count(nout)); synchronous.
  * flnr_set_weights also clears the Adam moments (a new model starts a new optimisation). */
 int flnr_set_weights(flnr_net *net, const float *host, size_t count);
 int flnr_get_weights(flnr_net *net, float *host, size_t count);
 
 /*
  * Forward pass on N images: in [N][11][H][W] planar float32 (device), guide_out
- * [N][8][H][W] planar float32 (device; NULL keeps the result only inside the network).
+ * [N][nout][H][W] planar float32 (device; NULL keeps the result only inside the network).
  * H and W multiples of 4.  Keeps the activations for flnr_guide_backward.
  * Errors: FLR_ERR_ARG, FLR_ERR_UNSUPPORTED (more than max_pixels), FLR_ERR_CUDA.
  */
@@ -355,7 +359,7 @@ int flnr_guide_forward(flnr_net *net, const float *in, float *guide_out, int N, 
  * written (as zero where the padded weights are zero).  The output size (Ho, Wo) is
  * (H, W), or (H/2, W/2) for the stride-2 layers 3 and 5 (which need H and W even).
  *   FLNR_OP_FORWARD  a = x [N][H][W][CinP]; out = y [N][Ho][Wo][CoutP] = bf16(ReLU(conv(x) + b)),
- *                    or, for layer 11, float32 planar [N][8][H][W] = sigmoid(conv(x) + b).
+ *                    or, for layer 11, float32 planar [N][nout][H][W] = sigmoid(conv(x) + b).
  *                    Layers 6 and 8 with b != NULL: a = the half-resolution decoder input
  *                    [N][H/2][W/2][64 or 32] and b = the skip [N][H][W][32 or 16]; the
  *                    result is the convolution of their concatenation (nearest 2x
@@ -388,7 +392,7 @@ int flnr_layer(flnr_net *net, int layer, int op, const void *a, const void *b, c
 
 /*
  * Backward pass of the last forward (Sec. 3.3's network trained end to end through FLR):
- * grad_out [N][8][H][W] = dL/d(enhanced guides), planar float32 (device).  ACCUMULATES the
+ * grad_out [N][nout][H][W] = dL/d(enhanced guides), planar float32 (device).  ACCUMULATES the
  * parameter gradients (flnr_zero_grads clears them).  grad_in (device, may be NULL)
  * receives dL/d(in), [N][11][H][W] planar float32, overwritten: the guide channels'
  * gradients, and for the radiance channels the gradient through log(1 + max(Y, 0)), i.e.

@@ -49,7 +49,8 @@ LAYERS = [
 def init_weights(seed=0, outputs=8):
     """He-uniform weights and zero biases, float32 (the dtype the GPU master copy keeps);
     the output projection o1 at a tenth of its He bound, with `outputs` (8, or 16 for the
-    model and map sets of Sec. 3.3) output channels."""
+    model and map sets of Sec. 3.3) output channels; with 16, the map rows of o1 start as a
+    copy of the model rows, so the network starts as the 8-output one."""
     rng = np.random.default_rng(seed)
     params = {}
     for name, _, cin, cout, k in LAYERS:
@@ -58,6 +59,8 @@ def init_weights(seed=0, outputs=8):
         bound = np.sqrt(6.0 / (cin * k * k)) * (0.1 if name == "o1" else 1.0)
         params[name + ".w"] = rng.uniform(-bound, bound, size=(cout, cin, k, k)).astype(np.float32)
         params[name + ".b"] = np.zeros(cout, np.float32)
+    if outputs == 16:  # the map set starts as a copy of the model set
+        params["o1.w"][8:] = params["o1.w"][:8]
     return params
 
 

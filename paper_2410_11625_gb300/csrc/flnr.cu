@@ -248,7 +248,8 @@ __device__ __forceinline__ void tc_store(const ConvArgs &a, float (&v)[COUT], co
     } else if (in) {
         const size_t hw = (size_t)a.H * a.W, off = (size_t)yy * a.W + xx;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) a.yf[((size_t)n * 8 + c) * hw + off] = 1.f / (1.f + expf(-v[c]));
+        for (int c = 0; c < COUT; ++c)  // a.nbias planes: the head's true outputs
+            if (c < a.nbias) a.yf[((size_t)n * a.nbias + c) * hw + off] = 1.f / (1.f + expf(-v[c]));
     }
 }
 
@@ -1347,8 +1348,9 @@ __global__ void upcat_kernel(const bf16 *lo, const bf16 *skip, bf16 *y, int N, i
     }
 }
 
-// gradient of the sigmoid output head: dz[p][c] = g * s (1 - s) for c < 8, 0 for the pads
-__global__ void sigmoid_bwd_kernel(const float *g, const float *s, bf16 *dz, int N, int H, int W)
+// gradient of the sigmoid output head (nout planar outputs): dz[p][c] = g * s (1 - s) for
+// c < nout, 0 for the pads of the 16 channels
+__global__ void sigmoid_bwd_kernel(const float *g, const float *s, bf16 *dz, int N, int H, int W, int nout)
 {
     const size_t hw = (size_t)H * W, total = (size_t)N * hw;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
@@ -1357,9 +1359,9 @@ __global__ void sigmoid_bwd_kernel(const float *g, const float *s, bf16 *dz, int
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             float d = 0.f;
-            if (c < 8) {
-                const float sv = s[(n * 8 + c) * hw + o];
-                d = g[(n * 8 + c) * hw + o] * sv * (1.f - sv);
+            if (c < nout) {
+                const float sv = s[(n * nout + c) * hw + o];
+                d = g[(n * nout + c) * hw + o] * sv * (1.f - sv);
             }
             v[c] = __float2bfloat16(d);
         }
@@ -1792,6 +1794,7 @@ cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H,
 struct flnr_net {
     int max_pix = 0;  // N * H * W the activation buffers hold
     int n_sm = 0;
+    int nout = 8;     // output channels of the head o1: 8, or 16 (model and map guide sets)
     size_t nparam = 0;
     size_t poff[flnr::kNL][2];  // offsets of each layer's weights and bias in the flat arrays
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // master fp32, grads, Adam moments
@@ -1819,10 +1822,18 @@ int nalloc(flnr_net *n, T **p, size_t count)
     return FLR_OK;
 }
 
+// layer l's true sizes in a network with `nout` head outputs
+flnr::LayerDef layer_def(int nout, int l)
+{
+    flnr::LayerDef d = flnr::kLayers[l];
+    if (l == flnr::kNL - 1) d.cout = nout;
+    return d;
+}
+
 cudaError_t refresh_weights(flnr_net *n, cudaStream_t st)
 {
     for (int l = 0; l < flnr::kNL; ++l) {
-        const auto &d = flnr::kLayers[l];
+        const auto d = layer_def(n->nout, l);
         const int cinp = flnr::pad16(d.cin), coutp = flnr::pad16(d.cout);
         const int total = d.k * d.k * cinp * coutp;
         flnr::weights_kernel<<<(total + 255) / 256, 256, 0, st>>>(n->w + n->poff[l][0], n->wf[l], n->wd[l], d.cin,
@@ -1836,29 +1847,31 @@ cudaError_t refresh_weights(flnr_net *n, cudaStream_t st)
 
 extern "C" {
 
-size_t flnr_param_count(void)
+size_t flnr_param_count(int outputs)
 {
+    if (outputs != 8 && outputs != 16) return 0;
     size_t s = 0;
     for (int l = 0; l < flnr::kNL; ++l) {
-        const auto &d = flnr::kLayers[l];
+        const auto d = layer_def(outputs, l);
         s += (size_t)d.cout * d.cin * d.k * d.k + d.cout;
     }
     return s;
 }
 
-int flnr_create(int max_pixels, flnr_net **out)
+int flnr_create(int max_pixels, int outputs, flnr_net **out)
 {
-    if (!out || max_pixels <= 0) return FLR_ERR_ARG;
+    if (!out || max_pixels <= 0 || (outputs != 8 && outputs != 16)) return FLR_ERR_ARG;
     *out = nullptr;
     flnr_net *n = new (std::nothrow) flnr_net();
     if (!n) return FLR_ERR_NOMEM;
     n->max_pix = max_pixels;
+    n->nout = outputs;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n->n_sm, cudaDevAttrMultiProcessorCount, dev);
     size_t off = 0;
     for (int l = 0; l < flnr::kNL; ++l) {
-        const auto &d = flnr::kLayers[l];
+        const auto d = layer_def(outputs, l);
         n->poff[l][0] = off;
         off += (size_t)d.cout * d.cin * d.k * d.k;
         n->poff[l][1] = off;
@@ -1879,7 +1892,7 @@ int flnr_create(int max_pixels, flnr_net **out)
     st |= nalloc(n, &n->a3, P2 * 32) | nalloc(n, &n->d1, P2 * 32) | nalloc(n, &n->c0, P * 48);
     st |= nalloc(n, &n->a4, P * 16) | nalloc(n, &n->d0, P * 16) | nalloc(n, &n->a5, P * 16);
     st |= nalloc(n, &n->gA, P * 48) | nalloc(n, &n->gB, P * 48) | nalloc(n, &n->gC, P * 48) | nalloc(n, &n->gLo, P * 16);
-    st |= nalloc(n, &n->gskip0, P * 16) | nalloc(n, &n->gskip1, P2 * 32) | nalloc(n, &n->out, P * 8);
+    st |= nalloc(n, &n->gskip0, P * 16) | nalloc(n, &n->gskip1, P2 * 32) | nalloc(n, &n->out, P * 16);
     st |= nalloc(n, &n->status, 1);
     if (st != FLR_OK) {
         flnr_destroy(n);
@@ -1954,7 +1967,7 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     auto conv = [&](const __nv_bfloat16 *x, int l, __nv_bfloat16 *y, int h, int w) {
         ConvArgs c = z;
         c.x = x; c.w = n->wf[l]; c.bias = bias(l); c.y = y; c.N = N; c.H = h; c.W = w;
-        c.ystride = pad16(kLayers[l].cout); c.nbias = kLayers[l].cout; c.status = n->status;
+        c.ystride = pad16(kLayers[l].cout); c.nbias = layer_def(n->nout, l).cout; c.status = n->status;
         return c;
     };
     ConvArgs c;
@@ -1979,7 +1992,7 @@ int flnr_guide_forward(flnr_net *n, const float *in, float *guide_out, int N, in
     // o0 and the head o1 (sigmoid into planar FP32) in one pass; a5 is still stored
     FLNR_TRY((conv_tail_launch<16, 16, 3, 16, 2, 1>(conv(n->d0, 10, n->a5, H, W), c, st)));
     if (guide_out)
-        FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        FLNR_TRY(cudaMemcpyAsync(n->out, guide_out, P * n->nout * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return FLR_OK;
 }
 
@@ -1996,9 +2009,9 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
         bias_grad_kernel<<<64, 256, 0, st>>>(dz, gb(l), pix, C, ctrue);
     };
     // output head: sigmoid, o1 (1x1, 16 -> 8 padded to 16), o0
-    sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W);
-    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, 8, n->status, st)));
-    bgrad(n->gA, (long long)P, 16, 8, 11);
+    sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W, n->nout);
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, n->nout, n->status, st)));
+    bgrad(n->gA, (long long)P, 16, n->nout, 11);
     FLNR_TRY((dgrad_launch<16, 16, 1, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
     FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, n->status, st)));
     bgrad(n->gB, (long long)P, 16, 16, 10);
@@ -2072,7 +2085,7 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
 {
     using namespace flnr;
     using bf = __nv_bfloat16;
-    const auto &d = kLayers[l];
+    const auto d = layer_def(n->nout, l);
     const long long P = (long long)N * H * W;
     if (op == FLNR_OP_FORWARD) {
         ConvArgs c{};

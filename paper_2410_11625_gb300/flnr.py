@@ -13,10 +13,15 @@ import numpy as np
 from . import flr as _flr
 
 # (name, cin, cout, kernel) in the library's order; the flat parameter array holds each
-# layer's weights [cout][cin][k][k] and then its biases [cout]
-LAYERS = [("in0", 11, 16, 3), ("in1", 16, 16, 1), ("e1a", 16, 32, 3), ("e1b", 32, 32, 3),
-          ("e2a", 32, 64, 3), ("e2b", 64, 64, 3), ("d1a", 96, 32, 3), ("d1b", 32, 32, 3),
-          ("d0a", 48, 16, 3), ("d0b", 16, 16, 3), ("o0", 16, 16, 3), ("o1", 16, 8, 1)]
+# layer's weights [cout][cin][k][k] and then its biases [cout].  The head o1 has 8 outputs,
+# or 16 for the two guide sets of Sec. 3.3 (layers(16)).
+def layers(outputs=8):
+    return [("in0", 11, 16, 3), ("in1", 16, 16, 1), ("e1a", 16, 32, 3), ("e1b", 32, 32, 3),
+            ("e2a", 32, 64, 3), ("e2b", 64, 64, 3), ("d1a", 96, 32, 3), ("d1b", 32, 32, 3),
+            ("d0a", 48, 16, 3), ("d0b", 16, 16, 3), ("o0", 16, 16, 3), ("o1", 16, outputs, 1)]
+
+
+LAYERS = layers(8)
 _bound = False
 
 
@@ -26,7 +31,8 @@ def _lib():
     if not _bound:
         vp, ip = ctypes.c_void_p, ctypes.c_int
         lib.flnr_param_count.restype = ctypes.c_size_t
-        lib.flnr_create.argtypes = [ip, ctypes.POINTER(ctypes.c_void_p)]
+        lib.flnr_param_count.argtypes = [ip]
+        lib.flnr_create.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_void_p)]
         lib.flnr_destroy.argtypes = [vp]
         lib.flnr_set_weights.argtypes = [vp, vp, ctypes.c_size_t]
         lib.flnr_get_weights.argtypes = [vp, vp, ctypes.c_size_t]
@@ -46,16 +52,19 @@ def _lib():
     return lib
 
 
-def init_weights(seed=0):
+def init_weights(seed=0, outputs=8):
     """Seeded initial parameters (dict name.w / name.b, float32): He-uniform weights, zero
-    biases, and the output projection o1 at a tenth of its He bound, so that the enhanced
-    guides start near 0.5 with small contrast and the sigmoid starts unsaturated."""
+    biases, and the output projection o1 (`outputs` channels) at a tenth of its He bound, so
+    that the enhanced guides start near 0.5 with small contrast and the sigmoid starts
+    unsaturated.  With 16 outputs the map rows of o1 start as a copy of the model rows."""
     rng = np.random.default_rng(seed)
     params = {}
-    for name, cin, cout, k in LAYERS:
+    for name, cin, cout, k in layers(outputs):
         bound = np.sqrt(6.0 / (cin * k * k)) * (0.1 if name == "o1" else 1.0)
         params[name + ".w"] = rng.uniform(-bound, bound, size=(cout, cin, k, k)).astype(np.float32)
         params[name + ".b"] = np.zeros(cout, np.float32)
+    if outputs == 16:  # the map set starts as a copy of the model set
+        params["o1.w"][8:] = params["o1.w"][:8]
     return params
 
 
@@ -66,9 +75,9 @@ def flatten(params):
                            for n, _, _, _ in LAYERS])
 
 
-def unflatten(flat):
+def unflatten(flat, outputs=8):
     out, o = {}, 0
-    for n, ci, co, k in LAYERS:
+    for n, ci, co, k in layers(outputs):
         out[n + ".w"] = flat[o:o + co * ci * k * k].reshape(co, ci, k, k)
         o += co * ci * k * k
         out[n + ".b"] = flat[o:o + co]
@@ -84,12 +93,17 @@ def _stream(t):
 class FLNR:
     """The guide network: forward, backward (accumulating), Adam, on CUDA tensors."""
 
-    def __init__(self, max_pixels, weights):
+    def __init__(self, max_pixels, weights, outputs=None):
+        """outputs: 8 (one guide set) or 16 (model and map sets, Sec. 3.3); by default the
+        size of the weights' output layer."""
         lib = _lib()
+        if outputs is None:
+            outputs = int(np.asarray(weights["o1.b"]).size) if isinstance(weights, dict) else 8
+        self.outputs = int(outputs)
         h = ctypes.c_void_p()
-        _flr._check(lib.flnr_create(int(max_pixels), ctypes.byref(h)), "flnr_create")
+        _flr._check(lib.flnr_create(int(max_pixels), self.outputs, ctypes.byref(h)), "flnr_create")
         self._h = h
-        self.count = int(lib.flnr_param_count())
+        self.count = int(lib.flnr_param_count(self.outputs))
         self.set_weights(weights)
 
     def close(self):
@@ -120,19 +134,19 @@ class FLNR:
         return flat
 
     def forward(self, x, out=None):
-        """x [N,11,H,W] CUDA float32 -> enhanced guides [N,8,H,W] float32."""
+        """x [N,11,H,W] CUDA float32 -> enhanced guides [N,outputs,H,W] float32."""
         import torch
         N, C, H, W = (int(v) for v in x.shape)
         if C != 11 or not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
             raise TypeError("x must be a contiguous CUDA float32 [N, 11, H, W] tensor")
         if out is None:
-            out = torch.empty((N, 8, H, W), dtype=torch.float32, device=x.device)
+            out = torch.empty((N, self.outputs, H, W), dtype=torch.float32, device=x.device)
         _flr._check(_lib().flnr_guide_forward(self._h, x.data_ptr(), out.data_ptr(), N, H, W, _stream(x)),
                     "flnr_guide_forward")
         return out
 
     def backward(self, grad_out, grad_in=None):
-        """Accumulate parameter gradients for dL/d(enhanced guides) = grad_out [N,8,H,W];
+        """Accumulate parameter gradients for dL/d(enhanced guides) = grad_out [N,outputs,H,W];
         grad_in (optional CUDA float32 [N,11,H,W]) receives dL/d(input)."""
         gi = None if grad_in is None else ctypes.c_void_p(grad_in.data_ptr())
         _flr._check(_lib().flnr_guide_backward(self._h, grad_out.contiguous().data_ptr(), gi, _stream(grad_out)),

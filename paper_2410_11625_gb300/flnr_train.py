@@ -3,7 +3,9 @@ through FLR, on crops of the project's own rendered scenes.
 
 One training step (batch B of c x c crops):
   X' = FLNR(X || Y)                      flnr_guide_forward
-  I_b = FLR(X'_b, Y_b), per crop         flr_denoise (X' is both model and map guide)
+  I_b = FLR(X'_b, Y_b), per crop         flr_denoise (8 outputs: X' is both model and map
+                                         guide; 16 outputs, Sec. 3.3's two sets: channels
+                                         0-7 fit the models, 8-15 are the map guide)
   L = mean |I - I_ref|, dL/dI             flnr_l1_loss
   dL/dX'_b = FLR adjoint, per crop       flr_backward
   parameter gradients                     flnr_guide_backward
@@ -80,9 +82,10 @@ class Trainer:
         self.r_host = torch.empty((batch, 3, crop, crop), dtype=torch.float32).pin_memory()
         self.x = torch.empty((batch, 11, crop, crop), **opt)
         self.ref = torch.empty((batch, 3, crop, crop), **opt)
-        self.guides = torch.empty((batch, 8, crop, crop), **opt)
+        self.outputs = self.net.outputs
+        self.guides = torch.empty((batch, self.outputs, crop, crop), **opt)
         self.out = torch.empty((batch, 3, crop, crop), **opt)
-        self.g_guides = torch.empty((batch, 8, crop, crop), **opt)
+        self.g_guides = torch.empty((batch, self.outputs, crop, crop), **opt)
         self.g_rad = torch.empty((batch, 3, crop, crop), **opt)
         self.steps = 0
         # After two eager warm-up steps the device part of a step (network forward, FLR per
@@ -111,10 +114,19 @@ class Trainer:
     def _device_step(self):
         """Forward, loss and gradients of the batch already on the device; returns the loss."""
         self.net.forward(self.x, out=self.guides)
-        self._per_crop(lambda b: self.flrs[b].denoise(self.guides[b], self.x[b, 8:11], out=self.out[b]))
+        if self.outputs == 16:  # model guides 0-7, map guides 8-15
+            self._per_crop(lambda b: self.flrs[b].denoise(self.guides[b, :8], self.x[b, 8:11],
+                                                         map_guide=self.guides[b, 8:], out=self.out[b]))
+        else:
+            self._per_crop(lambda b: self.flrs[b].denoise(self.guides[b], self.x[b, 8:11], out=self.out[b]))
         loss, g_out = _flnr.l1_loss(self.out, self.ref)
-        self._per_crop(lambda b: self.flrs[b].backward(self.guides[b], self.x[b, 8:11], g_out[b],
-                                                      grad_guide=self.g_guides[b], grad_radiance=self.g_rad[b]))
+        if self.outputs == 16:
+            self._per_crop(lambda b: self.flrs[b].backward(
+                self.guides[b, :8], self.x[b, 8:11], g_out[b], map_guide=self.guides[b, 8:],
+                grad_guide=self.g_guides[b, :8], grad_map_guide=self.g_guides[b, 8:], grad_radiance=self.g_rad[b]))
+        else:
+            self._per_crop(lambda b: self.flrs[b].backward(self.guides[b], self.x[b, 8:11], g_out[b],
+                                                          grad_guide=self.g_guides[b], grad_radiance=self.g_rad[b]))
         self.net.zero_grads(self.x)
         self.net.backward(self.g_guides)
         return loss
@@ -175,7 +187,10 @@ def evaluate(net, flr, scenes):
         y = xd[0, 8:11]
         plain = flr.denoise(xd[0, :8], y).cpu().numpy()
         guides = net.forward(xd)
-        learned = flr.denoise(guides[0], y).cpu().numpy()
+        if guides.shape[1] == 16:  # model and map guide sets
+            learned = flr.denoise(guides[0, :8], y, map_guide=guides[0, 8:]).cpu().numpy()
+        else:
+            learned = flr.denoise(guides[0], y).cpu().numpy()
         p_flr.append(psnr(plain * alb, ref * alb))
         p_flnr.append(psnr(learned * alb, ref * alb))
     return p_flr, p_flnr

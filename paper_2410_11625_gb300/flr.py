@@ -196,10 +196,10 @@ class FLR:
         return out
 
     def backward(self, guide, radiance, grad_out, map_guide=None, need_eps=False, stream=None,
-                 grad_guide=None, grad_radiance=None):
+                 grad_guide=None, grad_radiance=None, grad_map_guide=None):
         """Device FLR adjoint: gradients of <grad_out, I> for guide, radiance, map guide
         (when given) and eps.  Returns a dict of CUDA tensors (eps as a 1-element float64);
-        grad_guide / grad_radiance may be given as preallocated outputs."""
+        grad_guide / grad_radiance / grad_map_guide may be given as preallocated outputs."""
         import torch
         H, W = int(radiance.shape[-2]), int(radiance.shape[-1])
         dev = radiance.device
@@ -211,7 +211,10 @@ class FLR:
         gr = torch.empty((3, H, W), dtype=torch.float32, device=dev) if grad_radiance is None else grad_radiance
         _dev_ptr(gg, "grad_guide", (self.q, H, W))
         _dev_ptr(gr, "grad_radiance", (3, H, W))
-        gm = torch.empty((self.q, H, W), dtype=torch.float32, device=dev) if map_guide is not None else None
+        gm = None
+        if map_guide is not None:
+            gm = torch.empty((self.q, H, W), dtype=torch.float32, device=dev) if grad_map_guide is None else grad_map_guide
+            _dev_ptr(gm, "grad_map_guide", (self.q, H, W))
         ge = torch.zeros(1, dtype=torch.float64, device=dev) if need_eps else None
         if stream is None:
             stream = torch.cuda.current_stream(dev)

@@ -34,9 +34,9 @@ def pad16(c):
     return 16 * ((c + 15) // 16)
 
 
-def params_with_bias(seed):
+def params_with_bias(seed, outputs=8):
     rng = np.random.default_rng(seed + 100)
-    p = flnr_ref.init_weights(seed)
+    p = flnr_ref.init_weights(seed, outputs)
     for k in p:
         if k.endswith(".b"):
             p[k] = rng.normal(scale=0.1, size=p[k].shape).astype(np.float32)
@@ -222,10 +222,13 @@ def network_case(N, H, W, seed):
     return x, G
 
 
-@pytest.mark.parametrize("N,H,W", [(2, 32, 48), (1, 44, 52), (1, 4, 4)])
-def test_network_matches_bf16_storage_oracle(N, H, W):
-    p = params_with_bias(3)
+@pytest.mark.parametrize("N,H,W,outputs", [(2, 32, 48, 8), (1, 44, 52, 8), (1, 4, 4, 8), (2, 32, 48, 16)])
+def test_network_matches_bf16_storage_oracle(N, H, W, outputs):
+    """outputs = 16: the model and map guide sets of Sec. 3.3 from one 16-channel head."""
+    p = params_with_bias(3, outputs)
     x, G = network_case(N, H, W, H)
+    if outputs == 16:
+        G = np.concatenate([G, -0.5 * G[:, ::-1]], axis=1)
     x[:, 8:, ::7, ::5] = -0.3  # negative radiance: the input transform's zero-gradient branch
     ref, g_ref = flnr_ref.forward_backward(x, p, G, bf16_storage=True)
     ref64, _ = flnr_ref.forward_backward(x, p, G)
@@ -249,7 +252,8 @@ def test_network_matches_bf16_storage_oracle(N, H, W):
     # into a few such units at most, and rarely
     assert err.max() <= 8e-3 and np.sqrt(np.mean(err ** 2)) <= 1e-3, (err.max(), np.sqrt(np.mean(err ** 2)))
     assert np.sqrt(np.mean((got - ref64) ** 2)) <= 4e-3
-    g = flnr.unflatten(net.grads())
+    assert got.shape == (N, outputs, H, W)
+    g = flnr.unflatten(net.grads(), outputs)
     for name, *_ in flnr.LAYERS:
         for s in (".w", ".b"):
             a, b = g[name + s].astype(np.float64), g_ref[name + s]

@@ -15,15 +15,17 @@ def test_layer_table_matches_the_oracle_network():
         [(n, ci, co, k) for n, _, ci, co, k in flnr_ref.LAYERS]
 
 
-def test_parameter_count_and_flat_layout(tmp_path):
+@pytest.mark.parametrize("outputs", [8, 16])
+def test_parameter_count_and_flat_layout(tmp_path, outputs):
     import __graft_entry__
     __graft_entry__.build()
-    n = sum(co * ci * k * k + co for _, ci, co, k in flnr.LAYERS)
-    assert flnr._lib().flnr_param_count() == n
-    p = flnr.init_weights(3)
+    n = sum(co * ci * k * k + co for _, ci, co, k in flnr.layers(outputs))
+    assert flnr._lib().flnr_param_count(outputs) == n
+    assert flnr._lib().flnr_param_count(12) == 0  # 8 or 16 outputs only
+    p = flnr.init_weights(3, outputs)
     flat = flnr.flatten(p)
     assert flat.dtype == np.float32 and flat.size == n
-    q = flnr.unflatten(flat)
+    q = flnr.unflatten(flat, outputs)
     assert set(q) == set(p) and all(np.array_equal(q[k], p[k]) for k in p)
     # the first layer's weights lead, its biases follow, then the next layer
     ci, co, k = flnr.LAYERS[0][1:]
@@ -31,9 +33,11 @@ def test_parameter_count_and_flat_layout(tmp_path):
     assert np.array_equal(flat[co * ci * k * k:co * ci * k * k + co], p["in0.b"])
 
 
-def test_initialisation_matches_the_oracle():
-    a, b = flnr.init_weights(7), flnr_ref.init_weights(7)
+@pytest.mark.parametrize("outputs", [8, 16])
+def test_initialisation_matches_the_oracle(outputs):
+    a, b = flnr.init_weights(7, outputs), flnr_ref.init_weights(7, outputs)
     assert set(a) == set(b) and all(np.array_equal(a[k], b[k]) for k in a)
+    assert a["o1.w"].shape == (outputs, 16, 1, 1)
     bound = np.sqrt(6.0 / (16 * 1 * 1)) * 0.1  # o1 at a tenth of its He bound
     assert np.max(np.abs(a["o1.w"])) <= bound and np.all(a["o1.b"] == 0)
 

@@ -106,6 +106,8 @@ def test_two_output_sets_share_the_network():
     rng = np.random.default_rng(12)
     p16 = {k: v.astype(np.float64) for k, v in flnr_ref.init_weights(4, outputs=16).items()}
     assert p16["o1.w"].shape == (16, 16, 1, 1) and p16["o1.b"].shape == (16,)
+    assert np.array_equal(p16["o1.w"][8:], p16["o1.w"][:8])  # the map set starts as the model set
+    p16["o1.w"][8:] = rng.normal(scale=0.2, size=(8, 16, 1, 1))  # distinct halves for the check
     p16["o1.b"] = rng.normal(scale=0.1, size=16)
     x = rng.uniform(size=(1, 11, 8, 12))
     out16 = flnr_ref.forward(torch.tensor(x), {k: torch.tensor(v) for k, v in p16.items()}).numpy()
