@@ -350,7 +350,8 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
     if train_steps <= 0:  # timing only, with the initial weights
         return flnr_inference_row(flnr.init_weights(0), dev_frames, torch, dev, timed, rows)
     t0 = time.perf_counter()
-    scenes = flnr_train.render_scenes(range(1, 33), 192, 192, ref_spp=1024, noise=8)
+    n_train = 64
+    scenes = flnr_train.render_scenes(range(1, n_train + 1), 192, 192, ref_spp=1024, noise=8)
     n_eval = 16
     held_out = flnr_train.render_scenes(range(flnr_train.EVAL_SEED0, flnr_train.EVAL_SEED0 + n_eval), 256, 256,
                                         ref_spp=1024)
@@ -370,7 +371,7 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
         "rooms_improved": int(sum(a > b for a, b in zip(p_net, p_flr))),
         "what": (f"{n_eval} held-out rooms (seeds {flnr_train.EVAL_SEED0}..{flnr_train.EVAL_SEED0 + n_eval - 1}, "
                  f"256x256) vs 1024 spp references, albedo-modulated, "
-                 f"clamped to [0,1]; network trained here for {train_steps} steps (batch 16 x 128^2 crops of 32 "
+                 f"clamped to [0,1]; network trained here for {train_steps} steps (batch 16 x 128^2 crops of {n_train} "
                  f"rooms, 8 noise realisations each, L1, Adam lr 2e-3 cosine to 1e-4) in {t_train:.1f} s; "
                  f"rendering {t_render:.1f} s on the host"),
     }
@@ -630,7 +631,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", default="all",
                     help="comma list of extra rows to run: " + ",".join(ROW_NAMES) + " (or all, none)")
-    ap.add_argument("--flnr-steps", type=int, default=2000,
+    ap.add_argument("--flnr-steps", type=int, default=6000,
                     help="FLNR training steps before its PSNR and 1080p rows (0: 1080p timing only)")
     args = ap.parse_args()
     if args.warmup < 3:
