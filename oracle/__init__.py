@@ -59,6 +59,10 @@ def _load():
             ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_int,
             ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
         lib.flr_oracle_fast.restype = ctypes.c_int
+        lib.flr_oracle_fast_reg.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_int,
+            ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
+        lib.flr_oracle_fast_reg.restype = ctypes.c_int
         lib.flr_oracle_threads.argtypes = []
         lib.flr_oracle_threads.restype = ctypes.c_int
         lib.flr_oracle_set_threads.argtypes = [ctypes.c_int]
@@ -155,7 +159,7 @@ def flr_backward(guide, radiance, grad_out, radius, eps, coef_radius=0, map_guid
 
 
 def flr_fast(guide, radiance, factor=8, sigma_blocks=1.25, taps=3, eps=1e-3, map_guide=None,
-             scale=1, return_coef=False):
+             scale=1, return_coef=False, appendix=None):
     """Fast FLR in FP64 (Sec. 3.2, and Sec. 3.2.1 when ``scale`` > 1).
 
     guide [Q,Hi,Wi] and radiance [3,Hi,Wi] at the input resolution; map_guide [Q,Hi*scale,
@@ -163,6 +167,10 @@ def flr_fast(guide, radiance, factor=8, sigma_blocks=1.25, taps=3, eps=1e-3, map
     blurred by a Gaussian of ``sigma_blocks`` block units truncated at ``taps`` blocks,
     solved per block and bilinearly interpolated.  Returns out [3,Ho,Wo] (float64) and
     with ``return_coef`` the block models [(Q+1),3,Hb,Wb].
+
+    ``appendix`` = (eps_add, eps_mul) solves each block with the Appendix's regularised
+    normalised system (additive term eps_add used twice as printed, multiplicative term
+    eps_mul in [0, 1]) instead of the centred ridge with ``eps``.
     """
     g = _as_f32(guide)
     rad = _as_f32(radiance)
@@ -174,8 +182,13 @@ def flr_fast(guide, radiance, factor=8, sigma_blocks=1.25, taps=3, eps=1e-3, map
     Hb, Wb = -(-Hi // factor), -(-Wi // factor)
     out = np.empty((3, Ho, Wo), np.float64)
     coef = np.empty((q + 1, 3, Hb, Wb), np.float64) if return_coef else None
-    st = _load().flr_oracle_fast(q, Hi, Wi, _fptr(g), _fptr(rad), _fptr(mg), int(factor), int(scale),
-                                 float(sigma_blocks), int(taps), float(eps), _dptr(out), _dptr(coef))
+    if appendix is None:
+        st = _load().flr_oracle_fast(q, Hi, Wi, _fptr(g), _fptr(rad), _fptr(mg), int(factor), int(scale),
+                                     float(sigma_blocks), int(taps), float(eps), _dptr(out), _dptr(coef))
+    else:
+        st = _load().flr_oracle_fast_reg(q, Hi, Wi, _fptr(g), _fptr(rad), _fptr(mg), int(factor), int(scale),
+                                         float(sigma_blocks), int(taps), float(appendix[0]), 1, float(appendix[1]),
+                                         _dptr(out), _dptr(coef))
     if st != 0:
         raise OracleError(f"flr_oracle_fast failed with status {st}")
     return (out, coef) if return_coef else out

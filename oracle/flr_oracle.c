@@ -502,14 +502,24 @@ done:
  *   guide      [q][Hi][Wi]  model guides;  radiance [3][Hi][Wi]
  *   map_guide  [q][Ho][Wo] with Ho = Hi s, Wo = Wi s (NULL: the guide itself, s = 1 only)
  *   out        [3][Ho][Wo] double;  coef: NULL or [(q+1)*3][Hb][Wb] block models
+ *   appendix   0: the centred ridge of step 4 with eps;  1: the Appendix's regularised
+ *              normalised solve with additive term eps (the paper's epsilon) and
+ *              multiplicative term eps_mul (the paper's varepsilon), steps as printed:
+ *                W^ = S/n + eps_mul diag(mu^T mu) + eps I - (1 - eps_mul) mu^T mu,
+ *                sigma^ = sqrt(diag W^),  C^_ij = W^_ij / (sigma^_i sigma^_j),
+ *                B^_ic = (X^T Y_ic / n - mu_i muY_c) / sigma^_i,
+ *                A^ = (C^ + eps I)^-1 B^,  y = ((x - mu) / sigma^) A^ + muY,
+ *              stored as the same block model: a_ic = A^_ic / sigma^_i,
+ *              b_c = muY_c - sum_i a_ic mu_i.
  * Returns 0, -1 for bad arguments, -2 out of memory, -3 not positive definite.
  */
-int flr_oracle_fast(int q, int Hi, int Wi, const float *guide, const float *radiance,
-                    const float *map_guide, int F, int s, double sigma_b, int taps, double eps,
-                    double *out, double *coef)
+int flr_oracle_fast_reg(int q, int Hi, int Wi, const float *guide, const float *radiance,
+                        const float *map_guide, int F, int s, double sigma_b, int taps, double eps,
+                        int appendix, double eps_mul, double *out, double *coef)
 {
     if (q < 1 || q > ORACLE_MAX_Q || Hi <= 0 || Wi <= 0 || F < 1 || s < 1 || taps < 0 ||
-        !(sigma_b > 0.0) || !(eps >= 0.0) || !guide || !radiance || !out)
+        !(sigma_b > 0.0) || !(eps >= 0.0) || !guide || !radiance || !out || appendix < 0 || appendix > 1 ||
+        !(eps_mul >= 0.0 && eps_mul <= 1.0))
         return -1;
     if (!map_guide && s != 1) return -1;
     if (!map_guide) map_guide = guide;
@@ -560,13 +570,40 @@ int flr_oracle_fast(int q, int Hi, int Wi, const float *guide, const float *radi
                 }
                 blk[((size_t)by * Wb + bx) * nm + m] = acc;
             }
-    /* step 4: per-block centred ridge (Appendix), as in flr_oracle_forward */
+    /* step 4: per-block centred ridge (Appendix), as in flr_oracle_forward, or the
+       Appendix's regularised normalised solve */
     for (size_t k = 0; k < Pb && status == 0; ++k) {
         const double *b = blk + k * nm;
         const double n = b[tri_index(q1, 0, 0)];
         double mu[ORACLE_MAX_Q], mu_y[3], M[ORACLE_MAX_Q * ORACLE_MAX_Q], D[ORACLE_MAX_Q * 3], a[ORACLE_MAX_Q * 3];
         for (int i = 0; i < q; ++i) mu[i] = b[tri_index(q1, 0, i + 1)] / n;
         for (int c = 0; c < 3; ++c) mu_y[c] = b[nxx + c] / n;
+        if (appendix) {
+            double Wh[ORACLE_MAX_Q * ORACLE_MAX_Q], sg[ORACLE_MAX_Q], Bh[ORACLE_MAX_Q * 3], Ah[ORACLE_MAX_Q * 3];
+            for (int i = 0; i < q; ++i)
+                for (int j = 0; j < q; ++j) {
+                    int lo = i < j ? i : j, hi = i < j ? j : i;
+                    Wh[i * q + j] = b[tri_index(q1, lo + 1, hi + 1)] / n
+                                  + (i == j ? eps_mul * mu[i] * mu[i] + eps : 0.0)
+                                  - (1.0 - eps_mul) * mu[i] * mu[j];
+                }
+            for (int i = 0; i < q; ++i) sg[i] = sqrt(Wh[i * q + i]);
+            for (int i = 0; i < q; ++i)
+                for (int j = 0; j < q; ++j) M[i * q + j] = Wh[i * q + j] / (sg[i] * sg[j]) + (i == j ? eps : 0.0);
+            for (int i = 0; i < q; ++i)
+                for (int c = 0; c < 3; ++c) Bh[i * 3 + c] = (b[nxx + (i + 1) * 3 + c] / n - mu[i] * mu_y[c]) / sg[i];
+            if (cholesky_solve(q, M, Bh, 3, Ah) != 0) { status = -3; break; }
+            for (int c = 0; c < 3; ++c) {
+                double bb = mu_y[c];
+                for (int i = 0; i < q; ++i) {
+                    const double ai = Ah[i * 3 + c] / sg[i];
+                    bb -= ai * mu[i];
+                    cf[(size_t)((i + 1) * 3 + c) * Pb + k] = ai;
+                }
+                cf[(size_t)(0 * 3 + c) * Pb + k] = bb;
+            }
+            continue;
+        }
         for (int i = 0; i < q; ++i)
             for (int j = 0; j < q; ++j) {
                 int lo = i < j ? i : j, hi = i < j ? j : i;
@@ -615,4 +652,12 @@ done:
     free(cf);
     free(w);
     return status;
+}
+
+/* Fast FLR with the centred ridge of step 4 (flr_oracle_fast_reg with appendix = 0). */
+int flr_oracle_fast(int q, int Hi, int Wi, const float *guide, const float *radiance,
+                    const float *map_guide, int F, int s, double sigma_b, int taps, double eps,
+                    double *out, double *coef)
+{
+    return flr_oracle_fast_reg(q, Hi, Wi, guide, radiance, map_guide, F, s, sigma_b, taps, eps, 0, 0.0, out, coef);
 }

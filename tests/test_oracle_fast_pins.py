@@ -3,6 +3,9 @@
 * Per-block weighted least squares (the WLS equation of Sec. 3.2) solved by numpy's SVD
   lstsq on the explicit sqrt(w)-scaled window rows plus sqrt(n eps) ridge rows, where a
   pixel's weight is the product of the 1-D Gaussian weights of its block's offsets.
+* The Appendix's regularised normalised solve (additive and multiplicative terms) against
+  the same weighted least squares with the penalty its normalisation amounts to, solved
+  by lstsq on augmented rows; with both terms zero it is the plain weighted solve.
 * Exact affine recovery (also through 2x and 4x joint upsampling with a full-resolution
   map guide), constant radiance, and the eps -> infinity limit: block models reduce to
   Gaussian-weighted block means of Y, bilinearly interpolated (computed here with numpy).
@@ -48,6 +51,62 @@ def test_block_models_match_weighted_least_squares(H, W, F, sigma, taps):
     _, coef = oracle.flr_fast(g, y, factor=F, sigma_blocks=sigma, taps=taps, eps=1e-3, return_coef=True)
     ref = brute_block_models(g, y, F, sigma, taps, 1e-3)
     assert np.max(np.abs(coef - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+
+
+def brute_block_models_appendix(g, y, F, sigma, taps, e_add, e_mul):
+    """The Appendix's regularised normalised solve, derived independently of its printed
+    steps: with D_s = diag(sigma^), C^ + e_add I = D_s^-1 (W^ + e_add D_s^2) D_s^-1, so the
+    un-normalised model is a = (W^ + e_add diag(W^))^-1 D with
+    W^ = W + e_mul (mu mu^T + diag(mu^2)) + e_add I -- the weighted least squares with the
+    penalty n a^T R a, R = e_mul (mu mu^T + diag(mu^2)) + e_add I + e_add diag(W^), on the
+    guide coefficients only.  Solved here by lstsq on the sqrt(w)-scaled rows plus
+    sqrt(n) L^T rows (R = L L^T), with mu and W the weighted window statistics."""
+    q, H, W = g.shape
+    Hb, Wb = -(-H // F), -(-W // F)
+    w1 = gauss(sigma, taps)
+    A = np.zeros((q + 1, 3, Hb, Wb))
+    ys, xs = np.mgrid[0:H, 0:W]
+    for by in range(Hb):
+        for bx in range(Wb):
+            dy, dx = ys // F - by, xs // F - bx
+            m = (np.abs(dy) <= taps) & (np.abs(dx) <= taps)
+            wt = w1[dy[m] + taps] * w1[dx[m] + taps]
+            Xg = g[:, m].T.astype(np.float64)
+            n = wt.sum()
+            mu = (wt[:, None] * Xg).sum(0) / n
+            Wc = ((wt[:, None] * (Xg - mu)).T @ (Xg - mu)) / n
+            Wh = Wc + e_mul * (np.outer(mu, mu) + np.diag(mu ** 2)) + e_add * np.eye(q)
+            R = e_mul * (np.outer(mu, mu) + np.diag(mu ** 2)) + e_add * np.eye(q) + e_add * np.diag(np.diag(Wh))
+            L = np.linalg.cholesky(R)
+            X = np.concatenate([np.ones((wt.size, 1)), Xg], axis=1)
+            sw = np.sqrt(wt)[:, None]
+            reg = np.concatenate([np.zeros((q, 1)), np.sqrt(n) * L.T], axis=1)
+            Xa = np.concatenate([X * sw, reg])
+            Ya = np.concatenate([y[:, m].T.astype(np.float64) * sw, np.zeros((q, 3))])
+            A[:, :, by, bx] = np.linalg.lstsq(Xa, Ya, rcond=None)[0]
+    return A
+
+
+@pytest.mark.parametrize("e_add,e_mul", [(1e-3, 0.0), (1e-4, 1e-4), (3e-3, 0.2), (0.0, 0.05)])
+@pytest.mark.parametrize("H,W,F,sigma,taps", [(24, 40, 8, 1.25, 3), (21, 30, 4, 0.8, 2)])
+def test_appendix_solve_matches_augmented_least_squares(H, W, F, sigma, taps, e_add, e_mul):
+    """Appendix: W^ = S/n + e_mul diag(mu^T mu) + e_add I - (1 - e_mul) mu^T mu, normalised
+    by sigma^ = sqrt(diag W^), solved with (C^ + e_add I), un-normalised."""
+    g, y = synth.random_frame(H * W + 5, H, W, 4)
+    g = g + 0.7  # guides with nonzero means, so the multiplicative term acts
+    _, coef = oracle.flr_fast(g, y, factor=F, sigma_blocks=sigma, taps=taps, return_coef=True,
+                              appendix=(e_add, e_mul))
+    ref = brute_block_models_appendix(g, y, F, sigma, taps, e_add, e_mul)
+    assert np.max(np.abs(coef - ref)) <= 1e-8 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_appendix_without_regularisers_is_plain_weighted_least_squares():
+    """With both terms zero the normalisation cancels: the unregularised WLS models (the
+    ridge pin at eps = 0) come back, so the printed steps add no bias of their own."""
+    g, y = synth.random_frame(77, 24, 32, 4)
+    _, coef = oracle.flr_fast(g, y, factor=8, sigma_blocks=1.25, taps=3, return_coef=True, appendix=(0.0, 0.0))
+    ref = brute_block_models(g, y, 8, 1.25, 3, 0.0)
+    assert np.max(np.abs(coef - ref)) <= 1e-8 * max(1.0, np.max(np.abs(ref)))
 
 
 @pytest.mark.parametrize("scale", [1, 2, 4])
