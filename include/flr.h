@@ -223,10 +223,23 @@ typedef struct flr_fast_params {
     float sigma;       /* Gaussian standard deviation in blocks (the paper: sigma / 8, i.e.
                           1.25 for Fig. 3's sigma = 10 pixels) */
     int taps;          /* Gaussian half-width in blocks, 0..8 */
-    float eps;         /* ridge term, >= 0 */
+    float eps;         /* ridge term, >= 0; with FLR_FAST_APPENDIX the additive term */
     float pivot_ratio; /* FP64 re-solve threshold per block (as flr_params); <= 0: off */
-    unsigned flags;    /* must be 0 */
+    unsigned flags;    /* 0 or FLR_FAST_APPENDIX */
+    float eps_mul;     /* with FLR_FAST_APPENDIX the multiplicative term, in [0, 1]; else 0 */
 } flr_fast_params;
+
+/*
+ * flr_fast_params.flags: solve each block with the Appendix's regularised normalised
+ * system instead of the centred ridge.  With the window's guide means mu (absolute),
+ * centred covariance W = S/n - mu^T mu and D = X^T Y / n - mu^T mu_Y:
+ *   W^ = S/n + eps_mul diag(mu^T mu) + eps I - (1 - eps_mul) mu^T mu,
+ *   sigma^ = sqrt(diag W^), C^ = W^ / (sigma^ sigma^^T), B^ = D / sigma^,
+ *   A^ = (C^ + eps I)^-1 B^,  y = ((x - mu) / sigma^) A^ + mu_Y
+ * (eps used in both places, as printed).  The kernel solves the equivalent
+ * a = (W^ + eps diag(W^))^-1 D in one Cholesky, without the divisions by sigma^.
+ */
+#define FLR_FAST_APPENDIX 1u
 
 typedef struct flr_fast_handle flr_fast_handle;
 

@@ -70,6 +70,40 @@ __device__ __forceinline__ void chol_solve3(const float (&L)[Q * (Q + 1) / 2], c
     }
 }
 
+// In-place left-looking Cholesky M = L L^T of the packed lower triangle, keeping 1 / L_jj.
+// Returns whether a pivot fell to tau M_jj or below; pivots are floored at `floor` (every
+// exact pivot of M is at least that).  Inner loops run to Q with a predicate so that every
+// loop unrolls completely and L stays in registers.
+template <int Q>
+__device__ __forceinline__ bool chol_factor(float (&L)[Q * (Q + 1) / 2], float floor, float tau, float (&inv_d)[Q])
+{
+    bool low = false;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const float mjj = L[tri(j, j)];
+        float d = mjj;
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+            if (k < j) d = fmaf(-L[tri(j, k)], L[tri(j, k)], d);
+        low |= !(d > tau * mjj);
+        d = fmaxf(d, floor);
+        const float il = rsqrtf(d);
+        inv_d[j] = il;
+        L[tri(j, j)] = d * il;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (i > j) {
+                float t = L[tri(i, j)];
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+                    if (k < j) t = fmaf(-L[tri(i, k)], L[tri(j, k)], t);
+                L[tri(i, j)] = t * il;
+            }
+        }
+    }
+    return low;
+}
+
 // Centred ridge solve of one pixel from its window sums S(ch) = Sp[ch * VS].
 // Returns the model (a, b) in the CTA-shifted coordinates and whether a pivot fell low.
 template <int Q>
@@ -106,32 +140,7 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
 #pragma unroll
         for (int c = 0; c < 3; ++c) D[i][c] = fmaf(-mu[i], muy[c], Sp[C::xy(i, c) * VS] * inv_nx);
 
-    // left-looking Cholesky M = L L^T, keeping 1 / L_jj.  Inner loops run to Q with a
-    // predicate so that every loop unrolls completely and L stays in registers.
-    bool low = false;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        const float mjj = L[tri(j, j)];
-        float d = mjj;
-#pragma unroll
-        for (int k = 0; k < Q; ++k)
-            if (k < j) d = fmaf(-L[tri(j, k)], L[tri(j, k)], d);
-        low |= !(d > tau * mjj);
-        d = fmaxf(d, eps > 0.f ? eps : 1e-30f);  // every exact pivot is >= eps
-        const float il = rsqrtf(d);
-        inv_d[j] = il;
-        L[tri(j, j)] = d * il;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (i > j) {
-                float t = L[tri(i, j)];
-#pragma unroll
-                for (int k = 0; k < Q; ++k)
-                    if (k < j) t = fmaf(-L[tri(i, k)], L[tri(j, k)], t);
-                L[tri(i, j)] = t * il;
-            }
-        }
-    }
+    const bool low = chol_factor<Q>(L, eps > 0.f ? eps : 1e-30f, tau, inv_d);  // every exact pivot is >= eps
     // L z = D, then L^T a = z
 #pragma unroll
     for (int c = 0; c < 3; ++c) {

@@ -345,6 +345,8 @@ void frame_args(const flr_fast_handle *h, const flr_frame &fr, float *ws, flr::f
     a.taps = h->p.taps;
     a.eps = h->p.eps;
     a.tau = h->p.pivot_ratio;
+    a.appendix = (h->p.flags & FLR_FAST_APPENDIX) ? 1 : 0;
+    a.eps_mul = h->p.eps_mul;
     std::memcpy(a.w, h->w, sizeof(a.w));
 }
 
@@ -375,8 +377,9 @@ int flr_fast_create(const flr_fast_params *p, flr_fast_handle **out)
 {
     if (!out || !p) return FLR_ERR_ARG;
     *out = nullptr;
-    if (p->flags != 0u || !(p->eps >= 0.f) || !(p->sigma > 0.f) || p->taps < 0 || p->scale < 1 ||
-        p->pivot_ratio != p->pivot_ratio)
+    if ((p->flags & ~FLR_FAST_APPENDIX) != 0u || !(p->eps >= 0.f) || !(p->sigma > 0.f) || p->taps < 0 ||
+        p->scale < 1 || p->pivot_ratio != p->pivot_ratio || !(p->eps_mul >= 0.f && p->eps_mul <= 1.f) ||
+        (!(p->flags & FLR_FAST_APPENDIX) && p->eps_mul != 0.f))
         return FLR_ERR_ARG;
     if (p->q < 1 || p->q > FLR_MAX_Q || p->taps > flr::fast::kMaxTaps || p->scale > 8 ||
         (p->factor != 2 && p->factor != 4 && p->factor != 8))
@@ -450,6 +453,8 @@ int flr_fast_denoise(flr_fast_handle *h, const float *guide, const float *map_gu
     a.taps = h->p.taps;
     a.eps = h->p.eps;
     a.tau = h->p.pivot_ratio;
+    a.appendix = (h->p.flags & FLR_FAST_APPENDIX) ? 1 : 0;
+    a.eps_mul = h->p.eps_mul;
     a.status = h->status;
     std::memcpy(a.w, h->w, sizeof(a.w));
     cudaStream_t st = (cudaStream_t)stream;

@@ -39,6 +39,8 @@ struct FastArgs {
     unsigned long long *flag_count;
     int Hi, Wi, Ho, Wo, Hb, Wb, F, s, taps;
     float eps, tau;
+    int appendix;   // 1: the Appendix's regularised normalised solve (additive eps, multiplicative eps_mul)
+    float eps_mul;
     float w[2 * kMaxTaps + 1];             // Gaussian weights
     int *status = nullptr;                 // set to 1 if a bounded device wait ran out (may be NULL)
 };
@@ -204,6 +206,59 @@ __device__ __forceinline__ void stage_blur_h(const FastArgs &a, size_t k)
     a.tmp[C::NCH * bplane + k] = n;
 }
 
+// The Appendix's regularised normalised solve of one block (additive term eps, multiplicative
+// term eps_mul), in an equivalent un-normalised form.  With D_s = diag(sigma^),
+// C^ + eps I = D_s^-1 (W^ + eps D_s^2) D_s^-1 and B^ = D_s^-1 D, so the model
+// ((x - mu) / sigma^) A^ has guide coefficients a = A^ / sigma^ = (W^ + eps diag(W^))^-1 D:
+// one Cholesky solve of W^ with its diagonal scaled by (1 + eps), no divisions by sigma^.
+// W^ = W + eps_mul (mu mu^T + diag(mu^2)) + eps I takes the block's absolute guide means,
+// ref + (mean of the sums taken relative to ref); W and D are shift-invariant.  Returns the
+// model in the block-shifted coordinates, as solve_pixel, and whether a pivot fell low.
+template <int Q>
+__device__ __forceinline__ bool solve_appendix(const float *Sp, int VS, float n, float eps, float eps_mul,
+                                               float tau, const float *ref, float (&A)[Q][3], float (&bv)[3],
+                                               float (&mu)[Q], float (&muy)[3])
+{
+    using C = Chan<Q>;
+    // a one-pixel block: the guide moments drop out (a = 0, b = mu_y), as in solve_pixel
+    const float inv_n = 1.0f / n;
+    const float inv_nx = n > 1.5f ? inv_n : 0.f;
+    float ma[Q], L[Q * (Q + 1) / 2], inv_d[Q], D[Q][3];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        mu[i] = Sp[(C::X0 + i) * VS] * inv_nx;
+        ma[i] = ref[i] + mu[i];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) muy[c] = Sp[(C::Y0 + c) * VS] * inv_n;
+    const float grow = 1.f + eps;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            if (j <= i) {
+                float m = fmaf(-mu[i], mu[j], Sp[C::xx(j, i) * VS] * inv_nx);
+                m = fmaf(eps_mul * ma[i], ma[j], m);
+                if (i == j) m = (fmaf(eps_mul * ma[i], ma[i], m) + eps) * grow;
+                L[dev::tri(i, j)] = m;
+            }
+        }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) D[i][c] = fmaf(-mu[i], muy[c], Sp[C::xy(i, c) * VS] * inv_nx);
+    const bool low = dev::chol_factor<Q>(L, eps > 0.f ? eps : 1e-30f, tau, inv_d);  // every exact pivot is >= eps
+    dev::chol_solve3<Q>(L, inv_d, D, A);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float b = muy[c];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) b = fmaf(-A[i][c], mu[i], b);
+        bv[c] = b;
+    }
+    return low;
+}
+
 // 3. vertical Gaussian + per-block solve; S: this thread's column of a [NCH][stride] buffer
 template <int Q>
 __device__ __forceinline__ void stage_blur_v_solve(const FastArgs &a, size_t k, float *S, int stride)
@@ -236,8 +291,14 @@ __device__ __forceinline__ void stage_blur_v_solve(const FastArgs &a, size_t k, 
 #pragma unroll
         for (int c = 0; c < C::NCH; ++c) S[c * stride] = acc[c];
     }
-    float A[Q][3], bv[3], mu[Q], muy[3], L[Q * (Q + 1) / 2], inv_d[Q];
-    const bool low = dev::solve_pixel<Q>(S, stride, n, a.eps, a.tau, A, bv, mu, muy, L, inv_d);
+    float A[Q][3], bv[3], mu[Q], muy[3];
+    bool low;
+    if (a.appendix) {
+        low = solve_appendix<Q>(S, stride, n, a.eps, a.eps_mul, a.tau, rk, A, bv, mu, muy);
+    } else {
+        float L[Q * (Q + 1) / 2], inv_d[Q];
+        low = dev::solve_pixel<Q>(S, stride, n, a.eps, a.tau, A, bv, mu, muy, L, inv_d);
+    }
     if (low && a.tau > 0.f) {
         // FP64 re-solve of this block from the same (FP32) window sums
         atomicAdd(a.flag_count, 1ull);
@@ -251,8 +312,14 @@ __device__ __forceinline__ void stage_blur_v_solve(const FastArgs &a, size_t k, 
         for (int i = 0; i < Q; ++i) {
 #pragma unroll
             for (int j = 0; j < Q; ++j)
-                if (j <= i)
+                if (j <= i) {
                     M[i][j] = (double)S[C::xx(j, i) * stride] * inv_n - dmu[i] * dmu[j] + (i == j ? (double)a.eps : 0.0);
+                    if (a.appendix) {  // W^ with its diagonal scaled by (1 + eps), as solve_appendix
+                        const double mi = (double)rk[i] + dmu[i], mj = (double)rk[j] + dmu[j];
+                        M[i][j] += (double)a.eps_mul * mi * mj;
+                        if (i == j) M[i][j] = (M[i][j] + (double)a.eps_mul * mi * mi) * (1.0 + (double)a.eps);
+                    }
+                }
 #pragma unroll
             for (int c = 0; c < 3; ++c) D[i][c] = (double)S[C::xy(i, c) * stride] * inv_n - dmu[i] * dmuy[c];
         }

@@ -39,7 +39,10 @@ class FlrParams(ctypes.Structure):
 class FlrFastParams(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("factor", ctypes.c_int), ("scale", ctypes.c_int),
                 ("sigma", ctypes.c_float), ("taps", ctypes.c_int), ("eps", ctypes.c_float),
-                ("pivot_ratio", ctypes.c_float), ("flags", ctypes.c_uint)]
+                ("pivot_ratio", ctypes.c_float), ("flags", ctypes.c_uint), ("eps_mul", ctypes.c_float)]
+
+
+FLR_FAST_APPENDIX = 1
 
 
 class FlrFrame(ctypes.Structure):
@@ -275,11 +278,17 @@ class FLR:
 class FastFLR:
     """A fast-FLR handle (Sec. 3.2 block-downsampled moments; Sec. 3.2.1 with scale > 1)."""
 
-    def __init__(self, q=8, factor=8, scale=1, sigma=1.25, taps=3, eps=1e-3, pivot_ratio=1e-3):
+    def __init__(self, q=8, factor=8, scale=1, sigma=1.25, taps=3, eps=1e-3, pivot_ratio=1e-3, appendix=None):
+        """appendix = (eps_add, eps_mul): the Appendix's regularised normalised solve per block
+        (flags FLR_FAST_APPENDIX) instead of the centred ridge with eps."""
         lib = load_library()
         self.q, self.factor, self.scale = int(q), int(factor), int(scale)
-        p = FlrFastParams(self.q, self.factor, self.scale, float(sigma), int(taps), float(eps),
-                          float(pivot_ratio), 0)
+        if appendix is None:
+            p = FlrFastParams(self.q, self.factor, self.scale, float(sigma), int(taps), float(eps),
+                              float(pivot_ratio), 0, 0.0)
+        else:
+            p = FlrFastParams(self.q, self.factor, self.scale, float(sigma), int(taps), float(appendix[0]),
+                              float(pivot_ratio), FLR_FAST_APPENDIX, float(appendix[1]))
         h = ctypes.c_void_p()
         _check(lib.flr_fast_create(ctypes.byref(p), ctypes.byref(h)), "flr_fast_create")
         self._h = h

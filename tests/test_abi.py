@@ -56,6 +56,17 @@ def test_create_rejects_bad_params(lib, kw, status):
     assert not h.value
 
 
+@pytest.mark.parametrize("flags,eps_mul", [(0, 0.1), (flr.FLR_FAST_APPENDIX, 1.5), (flr.FLR_FAST_APPENDIX, -0.1),
+                                           (2, 0.0), (flr.FLR_FAST_APPENDIX, float("nan"))])
+def test_fast_create_rejects_bad_appendix_terms(lib, flags, eps_mul):
+    """The Appendix flag and its multiplicative term (in [0, 1], 0 without the flag) are
+    checked before any device work."""
+    p = flr.FlrFastParams(8, 8, 1, 1.25, 3, 1e-3, 1e-3, flags, eps_mul)
+    h = ctypes.c_void_p()
+    assert lib.flr_fast_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert not h.value
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.flr_create(None, None) == -1
     assert lib.flr_destroy(None) == 0
