@@ -192,3 +192,50 @@ def flr_fast(guide, radiance, factor=8, sigma_blocks=1.25, taps=3, eps=1e-3, map
     if st != 0:
         raise OracleError(f"flr_oracle_fast failed with status {st}")
     return (out, coef) if return_coef else out
+
+
+def flr_fast_param_grads(guide, radiance, grad_out, factor=8, sigma_blocks=1.25, taps=3, eps=1e-3, map_guide=None,
+                         scale=1, appendix=None, rel_step=1e-3):
+    """Derivatives of L = sum(grad_out * fast_FLR(...)) with respect to the Gaussian's
+    standard deviation (``sigma_blocks``) and the regularisation terms: Sec. 3.2 learns the
+    blur radius and the regularisers by backpropagation.  Keys: "sigma", "eps" (the ridge
+    term, or the Appendix's additive term when ``appendix`` = (eps_add, eps_mul) is given)
+    and, with ``appendix``, "eps_mul" (its multiplicative term).
+
+    The derivative is taken from its definition on the FP64 forward pass above: central
+    differences with step h = rel_step * theta and h / 2, combined by Richardson
+    extrapolation (4 D(h/2) - D(h)) / 3, which cancels the h^2 error term (the remaining
+    O(h^4) term and the rounding of the FP64 forward are far below 1e-8 relative for the
+    parameter ranges used).  Only positive parameters get a derivative (a zero term, e.g.
+    eps_mul = 0, sits at the edge of its domain and is left out of the result)."""
+    g_out = np.asarray(grad_out, np.float64)
+    base = dict(factor=factor, sigma_blocks=sigma_blocks, taps=taps, eps=eps, map_guide=map_guide, scale=scale)
+    params = {"sigma": float(sigma_blocks)}
+    if appendix is None:
+        params["eps"] = float(eps)
+    else:
+        params["eps"], params["eps_mul"] = float(appendix[0]), float(appendix[1])
+
+    def loss(name, value):
+        kw = dict(base)
+        app = None if appendix is None else [float(appendix[0]), float(appendix[1])]
+        if name == "sigma":
+            kw["sigma_blocks"] = value
+        elif name == "eps" and app is None:
+            kw["eps"] = value
+        elif name == "eps":
+            app[0] = value
+        else:
+            app[1] = value
+        return float(np.sum(g_out * flr_fast(guide, radiance, appendix=app, **kw)))
+
+    out = {}
+    for name, theta in params.items():
+        if not theta > 0.0:
+            continue
+        h = rel_step * theta
+
+        def diff(step):
+            return (loss(name, theta + step) - loss(name, theta - step)) / (2.0 * step)
+        out[name] = (4.0 * diff(h / 2.0) - diff(h)) / 3.0
+    return out

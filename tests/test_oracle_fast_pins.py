@@ -184,3 +184,85 @@ def test_huge_eps_is_blurred_block_mean_bilinearly_interpolated():
         means = blur(sums) / blur(ns)
         ref = bilinear(means, H, W, F, 1)
         assert np.max(np.abs(out[c] - ref)) <= 1e-9
+
+
+def brute_fast_forward(g, y, F, sigma, taps, eps):
+    """Fast FLR written with numpy: brute weighted least squares per block (above) and the
+    bilinear interpolation of the block models at every pixel (block centres at
+    ((i + 1/2) F - 1/2), clamped at the outermost centres), applied to (1, guides)."""
+    A = brute_block_models(g, y, F, sigma, taps, eps)
+    q, H, W = g.shape
+    Hb, Wb = A.shape[2:]
+
+    def axis(n, nb):
+        u = np.clip((np.arange(n) + 0.5) / F - 0.5, 0, nb - 1)
+        i0 = np.minimum(np.floor(u).astype(int), max(nb - 2, 0))
+        i1 = np.minimum(i0 + 1, nb - 1)
+        return i0, i1, u - i0
+    r0, r1, fy = axis(H, Hb)
+    c0, c1, fx = axis(W, Wb)
+    Ai = (A[:, :, r0][:, :, :, c0] * (1 - fy)[:, None] * (1 - fx)[None, :] +
+          A[:, :, r0][:, :, :, c1] * (1 - fy)[:, None] * fx[None, :] +
+          A[:, :, r1][:, :, :, c0] * fy[:, None] * (1 - fx)[None, :] +
+          A[:, :, r1][:, :, :, c1] * fy[:, None] * fx[None, :])
+    z = np.concatenate([np.ones((1, H, W)), g.astype(np.float64)])
+    return np.einsum("ichw,ihw->chw", Ai, z)
+
+
+def test_sigma_derivative_matches_the_numpy_forward():
+    """Sec. 3.2's learned blur radius: d/dsigma of <G, fast FLR> from the oracle equals the
+    same Richardson difference of the independent numpy forward."""
+    g, y = synth.random_frame(91, 24, 40, 4)
+    G = np.random.default_rng(2).normal(size=(3, 24, 40))
+    sig, eps = 1.1, 1e-3
+    got = oracle.flr_fast_param_grads(g, y, G, factor=8, sigma_blocks=sig, taps=3, eps=eps)
+    assert np.max(np.abs(oracle.flr_fast(g, y, factor=8, sigma_blocks=sig, taps=3, eps=eps)
+                         - brute_fast_forward(g, y, 8, sig, 3, eps))) < 1e-9
+
+    def f(s):
+        return np.sum(G * brute_fast_forward(g, y, 8, s, 3, eps))
+    h = 1e-3 * sig
+    d = lambda st: (f(sig + st) - f(sig - st)) / (2 * st)
+    ref = (4 * d(h / 2) - d(h)) / 3
+    assert abs(got["sigma"] - ref) <= 1e-7 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("appendix", [None, (1e-3, 0.0), (2e-3, 0.3)])
+def test_regulariser_derivatives_closed_form_on_one_block(appendix):
+    """A frame of one block has one model, applied at every pixel: out = b + a^T z with
+    a = M^-1 D.  Differentiating M a = D gives da = -M^-1 (dM) a and db = -mu^T da, with
+    dM / d eps = I for the ridge; for the Appendix's M = W^ + e_add diag(W^),
+    W^ = W + e_mul (mu mu^T + diag mu^2) + e_add I:
+    dM / d e_add = I + diag(W^) + e_add I and
+    dM / d e_mul = (mu mu^T + diag mu^2) + 2 e_add diag(mu^2)."""
+    F, q = 8, 4
+    g, y = synth.random_frame(17, F, F, q)
+    g = (g + 0.6).astype(np.float32)
+    G = np.random.default_rng(5).normal(size=(3, F, F))
+    X = g.reshape(q, -1).T.astype(np.float64)
+    Y = y.reshape(3, -1).T.astype(np.float64)
+    n = X.shape[0]
+    mu, muy = X.mean(0), Y.mean(0)
+    Wc = (X - mu).T @ (X - mu) / n
+    D = (X - mu).T @ (Y - muy) / n
+    if appendix is None:
+        e_add, e_mul = 1e-3, None
+        M = Wc + e_add * np.eye(q)
+        dMs = {"eps": np.eye(q)}
+    else:
+        e_add, e_mul = appendix
+        P = np.outer(mu, mu) + np.diag(mu ** 2)
+        Wh = Wc + e_mul * P + e_add * np.eye(q)
+        M = Wh + e_add * np.diag(np.diag(Wh))
+        dMs = {"eps": np.eye(q) + np.diag(np.diag(Wh)) + e_add * np.eye(q)}
+        if e_mul > 0:
+            dMs["eps_mul"] = P + 2 * e_add * np.diag(mu ** 2)
+    a = np.linalg.solve(M, D)
+    got = oracle.flr_fast_param_grads(g, y, G, factor=F, sigma_blocks=1.25, taps=3, eps=e_add, appendix=appendix)
+    assert set(got) == {"sigma"} | set(dMs)
+    for name, dM in dMs.items():
+        da = -np.linalg.solve(M, dM @ a)
+        db = -mu @ da
+        dout = db[:, None] + da.T @ X.T  # [3][pixels]
+        ref = float(np.sum(G.reshape(3, -1) * dout))
+        assert abs(got[name] - ref) <= 1e-7 * max(1.0, abs(ref)), (name, got[name], ref)
