@@ -266,6 +266,24 @@ int flr_fast_denoise(flr_fast_handle *h, const float *guide, const float *map_gu
  * fast path does not count non-finite outputs (nonfinite = 0). */
 int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out);
 
+/*
+ * Gradients of L = <grad_out, fast FLR output> with respect to the handle's parameters, for
+ * learning them by backpropagation (Sec. 3.2: the Gaussian's width and the regularisation
+ * terms are learned): grad (device, 3 doubles, overwritten) = dL/dsigma (sigma in block
+ * units, as flr_fast_params.sigma), dL/deps (the ridge term, or the Appendix's additive
+ * term with FLR_FAST_APPENDIX) and dL/deps_mul (the Appendix's multiplicative term; 0
+ * without the flag).  Inputs as flr_fast_denoise, grad_out [3][Ho][Wo] device float32.
+ * Forward-mode tangents: the blur of the block moments with dw/dsigma gives dS/dsigma; each
+ * block's model tangent solves M da = dD - dM a with the block's Cholesky factor
+ * (db = dmu_y - da^T mu - a^T dmu); each tangent model is applied like the model and reduced
+ * against grad_out in double, in a fixed order (deterministic).  Blocks whose pivot ratio is
+ * below pivot_ratio use the FP32 factor here.  Runs on `stream` without waiting.
+ * Errors: FLR_ERR_ARG, FLR_ERR_ALIGN (grad_out and images 16-byte, grad 8-byte aligned),
+ * FLR_ERR_NOMEM, FLR_ERR_CUDA.
+ */
+int flr_fast_param_grad(flr_fast_handle *h, const float *guide, const float *map_guide, const float *radiance,
+                        const float *grad_out, double *grad, int Hi, int Wi, void *stream);
+
 /* One frame of a batch: device pointers as in flr_denoise / flr_fast_denoise. */
 typedef struct flr_frame {
     const float *guide;     /* [q][H][W] (fast path: input resolution) */

@@ -62,6 +62,45 @@ __global__ void __launch_bounds__(256) fast_apply_kernel(const FastArgs a)
         fast::stage_apply<Q>(a, t);
 }
 
+// ---- parameter gradients (sigma and the regularisation terms) ---------------------------
+template <int Q>
+__global__ void __launch_bounds__(128) blur_v_tangent_kernel(const FastArgs a)
+{
+    extern __shared__ float sS[];  // [2][NCH][blockDim.x]: blurred sums, their sigma-derivative
+    fast::stage_blur_v_tangent<Q>(a, (size_t)blockIdx.x * blockDim.x + threadIdx.x, sS + threadIdx.x,
+                                  sS + Chan<Q>::NCH * blockDim.x + threadIdx.x, blockDim.x);
+}
+
+// Deterministic dot product: kDotBlocks partial sums in double (each thread strides through
+// the data in a fixed order, then a fixed tree per CTA), summed by one CTA in a fixed tree.
+constexpr int kDotBlocks = 256;
+__global__ void __launch_bounds__(256) dot_partial_kernel(const float *x, const float *y, size_t n, double *part)
+{
+    __shared__ double sp[256];
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc += (double)x[i] * (double)y[i];
+    sp[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sp[threadIdx.x] += sp[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sp[0];
+}
+
+__global__ void __launch_bounds__(256) dot_final_kernel(const double *part, double *out)
+{
+    __shared__ double sp[kDotBlocks];
+    sp[threadIdx.x] = part[threadIdx.x];
+    __syncthreads();
+    for (int o = kDotBlocks / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sp[threadIdx.x] += sp[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sp[0];
+}
+
 // ---- TMA version of the apply stage (rows 16-byte aligned) ------------------------------
 //
 // Persistent CTAs walk work items of kFW output columns; each item's map-guide rows arrive
@@ -253,6 +292,75 @@ cudaError_t launch_fast_q(const FastArgs &a, cudaStream_t st)
     return launch_apply_fast<Q>(a, st);
 }
 
+// Parameter gradients of one frame: the forward's moments and horizontal blur, the
+// horizontal blur with the weights' sigma-derivative, the tangent solve, then per parameter
+// the apply of its model tangents (frame reference without the radiance offset, tshift) and
+// the dot product with grad_out into grad[t].  dout: [3][Ho][Wo] scratch; part: kDotBlocks
+// doubles.
+template <int Q>
+cudaError_t launch_param_grad_q(const FastArgs &a, float *tshift, const float *grad_out, float *dout,
+                                double *part, double *grad, cudaStream_t st)
+{
+    cudaError_t e;
+    switch (a.F) {
+    case 2: e = launch_moments<Q, 2>(a, st); break;
+    case 4: e = launch_moments<Q, 4>(a, st); break;
+    case 8: e = launch_moments<Q, 8>(a, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    const size_t nb = (size_t)a.Hb * a.Wb;
+    const unsigned gb = (unsigned)((nb + 127) / 128);
+    blur_h_kernel<Q><<<gb, 128, 0, st>>>(a);
+    FastArgs ad = a;  // the horizontal blur with w' = dw/dsigma into tmp2
+    ad.tmp = a.tmp2;
+    std::memcpy(ad.w, a.wd, sizeof(ad.w));
+    blur_h_kernel<Q><<<gb, 128, 0, st>>>(ad);
+    const size_t smem = sizeof(float) * 2 * Chan<Q>::NCH * 128;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if ((e = cudaFuncSetAttribute(blur_v_tangent_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        attr_set = true;
+    }
+    blur_v_tangent_kernel<Q><<<gb, 128, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the frame reference the moments wrote, with the radiance offset zero: a tangent of the
+    // output carries no constant
+    if ((e = cudaMemcpyAsync(tshift, a.shift, sizeof(float) * Q, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(tshift + Q, 0, sizeof(float) * 3, st)) != cudaSuccess) return e;
+    const size_t runs = (size_t)a.Ho * (a.Wo / (a.F * a.s) + 2);
+    const size_t npx = 3 * (size_t)a.Ho * a.Wo;
+    for (int t = 0; t < 3; ++t) {
+        FastArgs at = a;
+        at.coef = a.dcoef + (size_t)t * 3 * (Q + 1) * nb;
+        at.shift = tshift;
+        at.out = dout;
+        fast_apply_kernel<Q><<<(unsigned)((runs + 255) / 256 < 16384 ? (runs + 255) / 256 : 16384), 256, 0, st>>>(at);
+        dot_partial_kernel<<<kDotBlocks, 256, 0, st>>>(dout, grad_out, npx, part);
+        dot_final_kernel<<<1, kDotBlocks, 0, st>>>(part, grad + t);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_param_grad(int q, const FastArgs &a, float *tshift, const float *grad_out, float *dout,
+                              double *part, double *grad, cudaStream_t st)
+{
+    switch (q) {
+    case 1: return launch_param_grad_q<1>(a, tshift, grad_out, dout, part, grad, st);
+    case 2: return launch_param_grad_q<2>(a, tshift, grad_out, dout, part, grad, st);
+    case 3: return launch_param_grad_q<3>(a, tshift, grad_out, dout, part, grad, st);
+    case 4: return launch_param_grad_q<4>(a, tshift, grad_out, dout, part, grad, st);
+    case 5: return launch_param_grad_q<5>(a, tshift, grad_out, dout, part, grad, st);
+    case 6: return launch_param_grad_q<6>(a, tshift, grad_out, dout, part, grad, st);
+    case 7: return launch_param_grad_q<7>(a, tshift, grad_out, dout, part, grad, st);
+    case 8: return launch_param_grad_q<8>(a, tshift, grad_out, dout, part, grad, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_fast(int q, const FastArgs &a, cudaStream_t st)
 {
     switch (q) {
@@ -308,6 +416,12 @@ struct flr_fast_handle {
     unsigned long long *count = nullptr;
     int *status = nullptr;  // set by a kernel whose bounded wait ran out
     cudaStream_t last_stream = nullptr;
+    // parameter gradients: sigma-derivative of the weights, workspace (second horizontal
+    // blur, model tangents, frame reference without radiance offset, output tangent), partials
+    float wd[2 * flr::fast::kMaxTaps + 1];
+    float *gws = nullptr;
+    size_t gws_floats = 0;
+    double *gpart = nullptr;
     // batch path: per-frame workspace, barrier words, status word
     float *bws = nullptr;
     size_t bws_floats = 0;
@@ -387,8 +501,11 @@ int flr_fast_create(const flr_fast_params *p, flr_fast_handle **out)
     flr_fast_handle *h = new (std::nothrow) flr_fast_handle();
     if (!h) return FLR_ERR_NOMEM;
     h->p = *p;
-    for (int d = -p->taps; d <= p->taps; ++d)
-        h->w[d + p->taps] = (float)std::exp(-(double)d * d / (2.0 * (double)p->sigma * p->sigma));
+    for (int d = -p->taps; d <= p->taps; ++d) {
+        const double sg = (double)p->sigma, wv = std::exp(-(double)d * d / (2.0 * sg * sg));
+        h->w[d + p->taps] = (float)wv;
+        h->wd[d + p->taps] = (float)(wv * (double)d * d / (sg * sg * sg));  // d w / d sigma
+    }
     if (cudaMalloc(&h->shift, sizeof(float) * (FLR_MAX_Q + 3)) != cudaSuccess ||
         cudaMalloc(&h->count, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&h->status, sizeof(int)) != cudaSuccess || cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
@@ -404,6 +521,8 @@ int flr_fast_destroy(flr_fast_handle *h)
     if (!h) return FLR_OK;
     cudaDeviceSynchronize();
     cudaFree(h->ws);
+    cudaFree(h->gws);
+    cudaFree(h->gpart);
     cudaFree(h->bws);
     cudaFree(h->bar);
     cudaFree(h->shift);
@@ -552,6 +671,79 @@ int flr_mbarrier_selftest(int ctas, unsigned long long timeout_ns, int *status)
     if (e == cudaSuccess) e = cudaMemcpy(status, d, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+int flr_fast_param_grad(flr_fast_handle *h, const float *guide, const float *map_guide, const float *radiance,
+                        const float *grad_out, double *grad, int Hi, int Wi, void *stream)
+{
+    if (!h || !guide || !radiance || !grad_out || !grad || Hi <= 0 || Wi <= 0) return FLR_ERR_ARG;
+    const int s = h->p.scale, F = h->p.factor, q = h->p.q;
+    if (s > 1 && !map_guide) return FLR_ERR_ARG;
+    if ((long long)Hi * s * Wi * s > 0x7fffffffLL) return FLR_ERR_ARG;
+    if (((uintptr_t)guide | (uintptr_t)radiance | (uintptr_t)grad_out | (uintptr_t)map_guide) & 15u ||
+        ((uintptr_t)grad & 7u))
+        return FLR_ERR_ALIGN;
+    const int Hb = (Hi + F - 1) / F, Wb = (Wi + F - 1) / F;
+    const size_t nb = (size_t)Hb * Wb, npx = (size_t)Hi * s * Wi * s;
+    const int nch = q + 3 + q * (q + 1) / 2 + 3 * q;
+    if (h->ws_blocks < nb || !h->ws) {
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_blocks = 0;
+        if (cudaMalloc(&h->ws, nb * sizeof(float) * (2 * (size_t)nch + (size_t)(q + 3) + 1 + 3 * (size_t)(q + 1))) != cudaSuccess)
+            return FLR_ERR_NOMEM;
+        h->ws_blocks = nb;
+    }
+    // gradient workspace: tmp2, dcoef, tshift (32 floats), dout
+    const size_t off_dc = (size_t)(nch + 1) * nb, off_ts = off_dc + 9 * (size_t)(q + 1) * nb;
+    const size_t off_out = (off_ts + 32 + 3) & ~(size_t)3, need = off_out + 3 * npx;
+    if (h->gws_floats < need || !h->gws) {
+        cudaFree(h->gws);
+        h->gws = nullptr;
+        h->gws_floats = 0;
+        if (cudaMalloc(&h->gws, need * sizeof(float)) != cudaSuccess) return FLR_ERR_NOMEM;
+        h->gws_floats = need;
+    }
+    if (!h->gpart && cudaMalloc(&h->gpart, sizeof(double) * flr::kDotBlocks) != cudaSuccess) return FLR_ERR_NOMEM;
+    flr::fast::FastArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.guide = guide;
+    a.rad = radiance;
+    a.map_guide = map_guide ? map_guide : guide;
+    a.out = nullptr;
+    a.blk = h->ws;
+    a.tmp = h->ws + nb * (nch + q + 3);
+    a.coef = a.tmp + nb * (nch + 1);
+    a.tmp2 = h->gws;
+    a.dcoef = h->gws + off_dc;
+    a.shift = h->shift;
+    a.flag_count = h->count;
+    a.Hi = Hi;
+    a.Wi = Wi;
+    a.Ho = Hi * s;
+    a.Wo = Wi * s;
+    a.Hb = Hb;
+    a.Wb = Wb;
+    a.F = F;
+    a.s = s;
+    a.taps = h->p.taps;
+    a.eps = h->p.eps;
+    a.tau = h->p.pivot_ratio;
+    a.appendix = (h->p.flags & FLR_FAST_APPENDIX) ? 1 : 0;
+    a.eps_mul = h->p.eps_mul;
+    a.status = h->status;
+    std::memcpy(a.w, h->w, sizeof(a.w));
+    std::memcpy(a.wd, h->wd, sizeof(a.wd));
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    cudaError_t e = cudaMemsetAsync(h->count, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+        e = flr::launch_param_grad(q, a, h->gws + off_ts, grad_out, h->gws + off_out, h->gpart, grad, st);
+    if (e != cudaSuccess) {
+        std::snprintf(flr::g_fast_err, sizeof(flr::g_fast_err), "%s", cudaGetErrorString(e));
+        return FLR_ERR_CUDA;
+    }
+    return FLR_OK;
 }
 
 int flr_fast_get_stats(flr_fast_handle *h, flr_stats *out)

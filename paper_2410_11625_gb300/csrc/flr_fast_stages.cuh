@@ -35,6 +35,8 @@ struct FastArgs {
     float *blk;   // [NCH + Q+3][Hb][Wb]: block sums relative to the block's reference, then that reference
     float *tmp;   // [NCH + 1][Hb][Wb]: horizontally blurred sums (same reference), weighted count
     float *coef;  // [(Q+1)*3][Hb][Wb]: block models relative to the frame reference
+    float *tmp2;  // parameter gradients: [NCH + 1][Hb][Wb] horizontal blur with the weights' sigma-derivative
+    float *dcoef; // parameter gradients: [3][(Q+1)*3][Hb][Wb] model tangents (sigma, eps, eps_mul)
     float *shift;                          // frame reference shift, Q + 3 floats
     unsigned long long *flag_count;
     int Hi, Wi, Ho, Wo, Hb, Wb, F, s, taps;
@@ -42,6 +44,7 @@ struct FastArgs {
     int appendix;   // 1: the Appendix's regularised normalised solve (additive eps, multiplicative eps_mul)
     float eps_mul;
     float w[2 * kMaxTaps + 1];             // Gaussian weights
+    float wd[2 * kMaxTaps + 1];            // their derivatives with respect to sigma (parameter gradients)
     int *status = nullptr;                 // set to 1 if a bounded device wait ran out (may be NULL)
 };
 
@@ -213,17 +216,19 @@ __device__ __forceinline__ void stage_blur_h(const FastArgs &a, size_t k)
 // one Cholesky solve of W^ with its diagonal scaled by (1 + eps), no divisions by sigma^.
 // W^ = W + eps_mul (mu mu^T + diag(mu^2)) + eps I takes the block's absolute guide means,
 // ref + (mean of the sums taken relative to ref); W and D are shift-invariant.  Returns the
-// model in the block-shifted coordinates, as solve_pixel, and whether a pivot fell low.
+// model in the block-shifted coordinates, as solve_pixel, with the factor of M, and whether
+// a pivot fell low.
 template <int Q>
 __device__ __forceinline__ bool solve_appendix(const float *Sp, int VS, float n, float eps, float eps_mul,
                                                float tau, const float *ref, float (&A)[Q][3], float (&bv)[3],
-                                               float (&mu)[Q], float (&muy)[3])
+                                               float (&mu)[Q], float (&muy)[3], float (&L)[Q * (Q + 1) / 2],
+                                               float (&inv_d)[Q])
 {
     using C = Chan<Q>;
     // a one-pixel block: the guide moments drop out (a = 0, b = mu_y), as in solve_pixel
     const float inv_n = 1.0f / n;
     const float inv_nx = n > 1.5f ? inv_n : 0.f;
-    float ma[Q], L[Q * (Q + 1) / 2], inv_d[Q], D[Q][3];
+    float ma[Q], D[Q][3];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         mu[i] = Sp[(C::X0 + i) * VS] * inv_nx;
@@ -293,11 +298,10 @@ __device__ __forceinline__ void stage_blur_v_solve(const FastArgs &a, size_t k, 
     }
     float A[Q][3], bv[3], mu[Q], muy[3];
     bool low;
-    if (a.appendix) {
-        low = solve_appendix<Q>(S, stride, n, a.eps, a.eps_mul, a.tau, rk, A, bv, mu, muy);
-    } else {
+    {
         float L[Q * (Q + 1) / 2], inv_d[Q];
-        low = dev::solve_pixel<Q>(S, stride, n, a.eps, a.tau, A, bv, mu, muy, L, inv_d);
+        low = a.appendix ? solve_appendix<Q>(S, stride, n, a.eps, a.eps_mul, a.tau, rk, A, bv, mu, muy, L, inv_d)
+                         : dev::solve_pixel<Q>(S, stride, n, a.eps, a.tau, A, bv, mu, muy, L, inv_d);
     }
     if (low && a.tau > 0.f) {
         // FP64 re-solve of this block from the same (FP32) window sums
@@ -384,6 +388,142 @@ __device__ __forceinline__ void stage_blur_v_solve(const FastArgs &a, size_t k, 
     for (int i = 0; i < Q; ++i)
 #pragma unroll
         for (int c = 0; c < 3; ++c) a.coef[(3 * (i + 1) + c) * bplane + k] = A[i][c];
+}
+
+// 3'. Tangents of the block models with respect to the Gaussian's sigma and the
+// regularisation terms, for their gradients (Sec. 3.2 learns them by backpropagation).  The
+// vertical blur gives the blurred sums S from tmp (the horizontal blur, weights w) and
+// dS/dsigma from tmp2 (the horizontal blur with w' = dw/dsigma) and tmp: with the separable
+// weights w(dy) w(dx), dS = V H' B + V' H B.  The model solves M a = D (b = mu_y - a^T mu), so
+// for each parameter theta
+//   da = M^-1 (dD - dM a),   db = dmu_y - da^T mu - a^T dmu,
+// using the block's Cholesky factor of M.  For sigma, dmu, dW and dD follow from dS and the
+// blurred count's tangent dn; eps (the ridge or the Appendix's additive term) and eps_mul (its
+// multiplicative term) enter M only:
+//   ridge:    M = W + eps I                          dM/deps = I
+//   Appendix: M = W^ + eps diag(W^),  W^ = W + eps_mul (m m^T + diag m^2) + eps I  (m: absolute
+//             guide means)   dM/deps = I + diag(W^) + eps I,
+//             dM/deps_mul = (m m^T + diag m^2) + 2 eps diag(m^2),
+//             and for sigma dW^ = dW + eps_mul (dm m^T + m dm^T + 2 diag(m dm)), dM = dW^ + eps diag(dW^).
+// Writes the three tangents of the block model in the coef layout, the bias re-expressed
+// relative to the frame reference (db - da^T (ref - frame reference)).  Blocks whose Cholesky
+// pivot fell low get tangents from the FP32 factor (no FP64 re-solve).  S, dS: this thread's
+// columns of two [NCH][stride] buffers.
+template <int Q>
+__device__ __forceinline__ void stage_blur_v_tangent(const FastArgs &a, size_t k, float *S, float *dS, int stride)
+{
+    using C = Chan<Q>;
+    constexpr int NS = Q + 3;
+    const size_t bplane = (size_t)a.Hb * a.Wb;
+    if (k >= bplane) return;
+    const int by = (int)(k / a.Wb), bx = (int)(k % a.Wb);
+    float rk[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) rk[q] = a.blk[(C::NCH + q) * bplane + k];
+    float n = 0.f, dn = 0.f;
+    for (int pass = 0; pass < 2; ++pass) {
+        float acc[C::NCH];
+#pragma unroll
+        for (int c = 0; c < C::NCH; ++c) acc[c] = 0.f;
+        for (int dd = -a.taps; dd <= a.taps; ++dd) {
+            const int yy = by + dd;
+            if (yy < 0 || yy >= a.Hb) continue;
+            const size_t kb = (size_t)yy * a.Wb + bx;
+            float d[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) d[q] = a.blk[(C::NCH + q) * bplane + kb] - rk[q];
+            const float nb = a.tmp[C::NCH * bplane + kb];
+            const float w = a.w[dd + a.taps];
+            if (pass == 0) {
+                accumulate_shifted<Q>(acc, a.tmp + kb, bplane, d, nb, w);
+                n = fmaf(w, nb, n);
+            } else {
+                const float nb2 = a.tmp2[C::NCH * bplane + kb], wd = a.wd[dd + a.taps];
+                accumulate_shifted<Q>(acc, a.tmp2 + kb, bplane, d, nb2, w);
+                accumulate_shifted<Q>(acc, a.tmp + kb, bplane, d, nb, wd);
+                dn = fmaf(w, nb2, fmaf(wd, nb, dn));
+            }
+        }
+        float *dst = pass == 0 ? S : dS;
+#pragma unroll
+        for (int c = 0; c < C::NCH; ++c) dst[c * stride] = acc[c];
+    }
+    float A[Q][3], bv[3], mu[Q], muy[3], L[Q * (Q + 1) / 2], inv_d[Q];
+    if (a.appendix)
+        solve_appendix<Q>(S, stride, n, a.eps, a.eps_mul, a.tau, rk, A, bv, mu, muy, L, inv_d);
+    else
+        dev::solve_pixel<Q>(S, stride, n, a.eps, a.tau, A, bv, mu, muy, L, inv_d);
+    const float inv_n = 1.0f / n;
+    const bool one_px = !(n > 1.5f);  // one-pixel block: a = 0, b = mu_y (see solve_pixel)
+    // the Appendix's absolute means and diag(W^)
+    float m[Q], whd[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        m[i] = rk[i] + mu[i];
+        whd[i] = fmaf(-mu[i], mu[i], S[C::xx(i, i) * stride] * inv_n) + 2.f * a.eps_mul * m[i] * m[i] + a.eps;
+    }
+    float dmu[Q], dmuy[3];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dmu[i] = one_px ? 0.f : (dS[(C::X0 + i) * stride] - mu[i] * dn) * inv_n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dmuy[c] = (dS[(C::Y0 + c) * stride] - muy[c] * dn) * inv_n;
+    for (int t = 0; t < 3; ++t) {
+        // dM (packed lower triangle) and dD of parameter t: 0 sigma, 1 eps, 2 eps_mul
+        float dM[Q * (Q + 1) / 2], R[Q][3], da[Q][3];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                if (j > i) continue;
+                float v = 0.f;
+                if (t == 0 && !one_px) {
+                    const float sxx = S[C::xx(j, i) * stride] * inv_n;
+                    v = (dS[C::xx(j, i) * stride] - sxx * dn) * inv_n - dmu[i] * mu[j] - mu[i] * dmu[j];
+                    if (a.appendix) v = fmaf(a.eps_mul, dmu[i] * m[j] + m[i] * dmu[j] + (i == j ? 2.f * m[i] * dmu[i] : 0.f), v);
+                } else if (t == 1) {
+                    v = i == j ? 1.f : 0.f;
+                } else if (t == 2 && a.appendix) {
+                    v = m[i] * m[j] + (i == j ? m[i] * m[i] : 0.f);
+                }
+                dM[dev::tri(i, j)] = v;
+            }
+        if (a.appendix) {  // M = W^ + eps diag(W^): add eps dW^_ii (and W^_ii for eps itself)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int ii = dev::tri(i, i);
+                dM[ii] = fmaf(a.eps, dM[ii], dM[ii]) + (t == 1 ? whd[i] : 0.f);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float r = 0.f;
+                if (t == 0 && !one_px) {
+                    const float sxy = S[C::xy(i, c) * stride] * inv_n;
+                    r = (dS[C::xy(i, c) * stride] - sxy * dn) * inv_n - dmu[i] * muy[c] - mu[i] * dmuy[c];
+                }
+#pragma unroll
+                for (int j = 0; j < Q; ++j) r = fmaf(-dM[j <= i ? dev::tri(i, j) : dev::tri(j, i)], A[j][c], r);
+                R[i][c] = r;
+            }
+        dev::chol_solve3<Q>(L, inv_d, R, da);
+        float *dc = a.dcoef + (size_t)t * 3 * (Q + 1) * bplane;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float db = t == 0 ? dmuy[c] : 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (one_px) da[i][c] = 0.f;
+                db = fmaf(-da[i][c], mu[i], db);
+                if (t == 0) db = fmaf(-A[i][c], dmu[i], db);
+                db = fmaf(-da[i][c], rk[i] - a.shift[i], db);  // re-expressed relative to the frame reference
+            }
+            dc[c * bplane + k] = db;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) dc[(3 * (i + 1) + c) * bplane + k] = da[i][c];
+        }
+    }
 }
 
 // 4. bilinear interpolation of the block models + apply.  Block centres are P = F s output

@@ -19,7 +19,7 @@ STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
            "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
            "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
-           "flr_fast_denoise", "flr_fast_get_stats", "flr_denoise_batch", "flr_fast_reserve_batch",
+           "flr_fast_denoise", "flr_fast_get_stats", "flr_fast_param_grad", "flr_denoise_batch", "flr_fast_reserve_batch",
            "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest",
            "flr_mbarrier_selftest", "flr_host_band_plan",
            "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
@@ -102,6 +102,8 @@ def load_library():
     lib.flr_fast_destroy.argtypes = [vp]
     lib.flr_fast_denoise.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
     lib.flr_fast_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
+    lib.flr_fast_param_grad.argtypes = [vp, fp, fp, fp, fp, vp, ip, ip, vp]
+    lib.flr_fast_param_grad.restype = ctypes.c_int
     for name in ("flr_fast_create", "flr_fast_destroy", "flr_fast_denoise", "flr_fast_get_stats"):
         getattr(lib, name).restype = ctypes.c_int
     lib.flr_denoise_batch.argtypes = [vp, ip, ctypes.POINTER(FlrFrame), vp]
@@ -319,6 +321,23 @@ class FastFLR:
             stream = torch.cuda.current_stream(radiance.device)
         _check(load_library().flr_fast_denoise(self._h, g, m, r, o, Hi, Wi,
                                                ctypes.c_void_p(stream.cuda_stream)), "flr_fast_denoise")
+        return out
+
+    def param_grad(self, guide, radiance, grad_out, map_guide=None, stream=None):
+        """dL/d(sigma, eps, eps_mul) for L = <grad_out, output> (flr_fast_param_grad): a CUDA
+        float64 tensor of 3 values (eps_mul's is 0 without the Appendix solve)."""
+        import torch
+        Hi, Wi = int(radiance.shape[-2]), int(radiance.shape[-1])
+        Ho, Wo = Hi * self.scale, Wi * self.scale
+        g = _dev_ptr(guide, "guide", (self.q, Hi, Wi))
+        r = _dev_ptr(radiance, "radiance", (3, Hi, Wi))
+        m = None if map_guide is None else _dev_ptr(map_guide, "map_guide", (self.q, Ho, Wo))
+        go = _dev_ptr(grad_out, "grad_out", (3, Ho, Wo))
+        out = torch.zeros(3, dtype=torch.float64, device=radiance.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(radiance.device)
+        _check(load_library().flr_fast_param_grad(self._h, g, m, r, go, ctypes.c_void_p(out.data_ptr()), Hi, Wi,
+                                                  ctypes.c_void_p(stream.cuda_stream)), "flr_fast_param_grad")
         return out
 
     def _frames(self, frames):
