@@ -333,6 +333,9 @@ def serving_batch_flnr(torch, np, dev, weights, n_iter=100):
 
 
 ROW_NAMES = ("backward", "fast", "joint", "serving", "flnr")
+# opt-in rows (not in "all"): flnr1080 renders 1920x1080 1024 spp references on the host
+# (about a minute per room) for the FLNR-vs-FLR PSNR comparison at full resolution
+EXTRA_ROWS = ("flnr1080",)
 
 # FLNR network (Sec. 3.3): multiply-accumulates per full-resolution pixel, layer by layer
 # (Cin x Cout x k^2 per output pixel, divided by 4 at half and 16 at quarter resolution; the
@@ -342,7 +345,7 @@ FLNR_MACS_PER_PIXEL = (11 * 16 * 9 + 16 * 16 + 16 * 32 * 9 + (32 * 32 * 9) / 4 +
                        + 16 * 16 * 9 + 16 * 8)
 
 
-def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
+def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps, full_hd_rooms=0):
     """FLNR rows: training on rendered crops, PSNR against 1024 spp references on held-out
     rooms, 1080p inference time (network + FLR on its guides), training-step time."""
     from paper_2410_11625_gb300 import flnr, flnr_train, flr
@@ -398,6 +401,24 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps):
                                        "includes the pinned H2D copy of the batch"}
     weights = tr.net.get_weights()
     tr.net.close()
+    if full_hd_rooms > 0:
+        # the same network (fully convolutional) on 1920x1080 held-out rooms
+        t0 = time.perf_counter()
+        seeds = range(flnr_train.EVAL_SEED0 + 100, flnr_train.EVAL_SEED0 + 100 + full_hd_rooms)
+        big = flnr_train.render_scenes(seeds, H, W, ref_spp=1024)
+        t_big = time.perf_counter() - t0
+        net_big = flnr.FLNR(H * W, weights)
+        f_big = flr.FLR(q=8, radius=8, eps=1e-3)
+        pf, pn = flnr_train.evaluate(net_big, f_big, big)
+        net_big.close()
+        f_big.close()
+        rows["flnr_psnr_1080p"] = {
+            "psnr_flr_db": round(float(np.mean(pf)), 3), "psnr_flnr_db": round(float(np.mean(pn)), 3),
+            "gain_db": round(float(np.mean(pn) - np.mean(pf)), 3),
+            "per_scene_gain_db": [round(a - b, 2) for a, b in zip(pn, pf)],
+            "what": (f"{full_hd_rooms} held-out rooms (seeds {seeds[0]}..{seeds[-1]}) at {W}x{H} vs 1024 spp "
+                     f"references (host path tracer, {t_big:.0f} s), FLR r=8 with rendered vs network guides; "
+                     f"network as flnr_psnr")}
     return flnr_inference_row(weights, dev_frames, torch, dev, timed, rows)
 
 
@@ -500,6 +521,8 @@ def run_ours(args):
 
     rows = {}
     want = set(ROW_NAMES) if args.rows == "all" else set(args.rows.split(",")) - {"none"}
+    if "flnr1080" in want:
+        want.add("flnr")
     if "backward" in want:
         fb = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
         gout = torch.randn((3, H, W), dtype=torch.float32, device=dev)
@@ -526,7 +549,8 @@ def run_ours(args):
         from paper_2410_11625_gb300 import flnr as _flnr
         rows["batch_serving_flnr"] = serving_batch_flnr(torch, np, dev, _flnr.init_weights(0))
     if rank == 0 and "flnr" in want:
-        rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps))
+        rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps,
+                              full_hd_rooms=4 if "flnr1080" in want else 0))
 
     # parity of the timed configuration: the last timed frame against the oracle on blocks
     f2 = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
@@ -630,7 +654,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", default="all",
-                    help="comma list of extra rows to run: " + ",".join(ROW_NAMES) + " (or all, none)")
+                    help="comma list of extra rows to run: " + ",".join(ROW_NAMES + EXTRA_ROWS) + " (or all, none; "
+                         "all leaves out " + ",".join(EXTRA_ROWS) + ")")
     ap.add_argument("--flnr-steps", type=int, default=6000,
                     help="FLNR training steps before its PSNR and 1080p rows (0: 1080p timing only)")
     args = ap.parse_args()
