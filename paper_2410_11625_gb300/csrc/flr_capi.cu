@@ -483,8 +483,9 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     h->last_stream = s;
     const int r = h->p.radius, rc = h->p.coef_radius;
 
-    // 1. models A_k (forward kernel, coefficient output forced), FP64 re-solve of flagged pixels
+    // 1. the frame reference shift (the fields need it before the adjoint kernel runs)
     FLR_CUDA(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(unsigned long long), s), "reset counters");
+    FLR_CUDA(flr::launch_frame_shift(q, guide, radiance, H, W, 0, h->d_shift, s), "backward: frame shift launch");
     flr::FwdArgs fa;
     fa.guide = guide;
     fa.map_guide = map_guide;
@@ -508,9 +509,9 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     fa.geps = nullptr;
     fa.status = h->d_status;
     dim3 grid((W + flr::kTW - 1) / flr::kTW, (H + fa.TH - 1) / fa.TH);
-    FLR_CUDA(flr::launch_fwd(q, fa, grid, h->fwd_smem, s), "backward: model kernel launch");
-    if (h->p.pivot_ratio > 0.f) {
-        flr::Fp64Args da;
+    flr::Fp64Args da;
+    const bool fp64_fix = h->p.pivot_ratio > 0.f;
+    if (fp64_fix) {
         da.guide = guide;
         da.map_guide = map_guide;
         da.rad = radiance;
@@ -526,7 +527,6 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
         da.flag_list = h->d_flags;
         da.flag_cap = h->flag_cap;
         da.force_coef = 1;
-        FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "backward: fp64 re-solve launch");
     }
     // 2. adjoint of the apply and of the average: G(A_k)
     const float *z = map_guide ? map_guide : guide;
@@ -547,7 +547,11 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
     fa.geps = geps;
     fa.status = h->d_status;
     fa.force_coef = 0;
+    // the adjoint kernel also writes each pixel's model A_k (coefficients relative to the frame
+    // reference) and lists the pixels whose pivot fell low, whose models the FP64 re-solve
+    // then replaces (these feed only the averaged models of the applied guide)
     FLR_CUDA(flr::launch_adj(q, fa, grid, h->adj_smem, s), "backward: adjoint kernel launch");
+    if (fp64_fix) FLR_CUDA(flr::launch_fp64(q, da, h->n_sm, s), "backward: fp64 re-solve launch");
     // 4. adjoint of the window sums, the averaged models for the applied guide, contraction
     FLR_CUDA(flr::launch_box_sum(GS, BS, nch, H, W, r, s, h->d_status), "backward: window-sum adjoint launch");
     const float *BA = Acoef;

@@ -501,6 +501,19 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
                 if constexpr (ADJ) {
                     geps_acc += adjoint_pixel<Q>(A, mu, muy, L, inv_d, ny * nx, a.gA, a.gS, plane, off,
                                                  s_cta, s_ref);
+                    if (a.coef) {  // the model itself (for the backward's averaged models)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float bb = bv[c] + (s_cta[Q + c] - s_ref[Q + c]);
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) bb = fmaf(-A[i][c], s_cta[i] - s_ref[i], bb);
+                            a.coef[c * plane + off] = bb;
+                        }
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.coef[(3 * (i + 1) + c) * plane + off] = A[i][c];
+                    }
                 } else {
                     // re-express the bias relative to the frame reference shift
 #pragma unroll
@@ -536,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
                             for (int c = 0; c < 3; ++c) a.coef[(3 * (i + 1) + c) * plane + off] = A[i][c];
                     }
                 }
-                if (!ADJ && low && tau > 0.f) {
+                if ((!ADJ || a.coef) && low && tau > 0.f) {
                     const unsigned long long slot = atomicAdd(a.flag_count, 1ull);
                     if (slot < (unsigned long long)a.flag_cap) a.flag_list[slot] = (int)off;
                 }
@@ -551,6 +564,17 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
         for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
         if (lane == 0 && g != 0.0) atomicAdd(a.geps, g);
     }
+}
+
+// The frame reference shift alone (the forward kernel's s_ref: the same sample of rows
+// [0, ref_rows)), for a pass that needs it before any forward-kernel launch.
+template <int Q>
+__global__ void frame_shift_kernel(const float *guide, const float *rad, int H, int W, int ref_rows, float *shift_out)
+{
+    __shared__ float s[Q + 3];
+    sample_mean<Q>(s, guide, rad, H, W, 0, ref_rows > 0 ? min(ref_rows, H) : H, 0, W, threadIdx.x & 31);
+    __syncwarp();
+    if (threadIdx.x < Q + 3) shift_out[threadIdx.x] = s[threadIdx.x];
 }
 
 // Radii with a compile-time specialisation (the radii of the 256x256 and 1080p workloads);
@@ -647,6 +671,14 @@ cudaError_t launch_fwd(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStre
 cudaError_t launch_adj(int q, const FwdArgs &a, dim3 grid, size_t smem, cudaStream_t st)
 {
     FLR_Q_DISPATCH(q, return launch_fwd_q<QQ, true>(a, grid, smem, st));
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_frame_shift(int q, const float *guide, const float *rad, int H, int W, int ref_rows, float *shift_out,
+                               cudaStream_t st)
+{
+    FLR_Q_DISPATCH(q, frame_shift_kernel<QQ><<<1, 32, 0, st>>>(guide, rad, H, W, ref_rows, shift_out);
+                   return cudaGetLastError());
     return cudaErrorInvalidValue;
 }
 

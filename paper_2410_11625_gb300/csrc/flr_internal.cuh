@@ -202,6 +202,9 @@ cudaError_t launch_bwd_fields(int q, const float *g, const float *z, const float
 cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int W, int rad, cudaStream_t st,
                            int *status = nullptr);
 cudaError_t launch_bwd_contract(int q, const BwdArgs &a, cudaStream_t st);
+// the frame reference shift of the forward kernel (Q + 3 floats), by itself
+cudaError_t launch_frame_shift(int q, const float *guide, const float *rad, int H, int W, int ref_rows, float *shift_out,
+                               cudaStream_t st);
 namespace fast { struct FastArgs; }
 bool batch_supported(int q, int F);
 cudaError_t launch_batch(int q, int F, const void *args, cudaStream_t st);
