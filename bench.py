@@ -333,9 +333,6 @@ def serving_batch_flnr(torch, np, dev, weights, n_iter=100):
 
 
 ROW_NAMES = ("backward", "fast", "joint", "serving", "flnr")
-# opt-in rows (not in "all"): flnr1080 renders 1920x1080 1024 spp references on the host
-# (about a minute per room) for the FLNR-vs-FLR PSNR comparison at full resolution
-EXTRA_ROWS = ("flnr1080",)
 
 # FLNR network (Sec. 3.3): multiply-accumulates per full-resolution pixel, layer by layer
 # (Cin x Cout x k^2 per output pixel, divided by 4 at half and 16 at quarter resolution; the
@@ -354,10 +351,10 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps, full_hd_ro
         return flnr_inference_row(flnr.init_weights(0), dev_frames, torch, dev, timed, rows)
     t0 = time.perf_counter()
     n_train = 64
-    scenes = flnr_train.render_scenes(range(1, n_train + 1), 192, 192, ref_spp=1024, noise=8)
+    scenes = flnr_train.render_scenes(range(1, n_train + 1), 192, 192, ref_spp=1024, noise=8, gpu_ref=True)
     n_eval = 16
     held_out = flnr_train.render_scenes(range(flnr_train.EVAL_SEED0, flnr_train.EVAL_SEED0 + n_eval), 256, 256,
-                                        ref_spp=1024)
+                                        ref_spp=1024, gpu_ref=True)
     t_render = time.perf_counter() - t0
     tr = flnr_train.Trainer(flnr.init_weights(0), batch=16, crop=128, lr=2e-3)
     torch.cuda.synchronize()
@@ -376,7 +373,7 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps, full_hd_ro
                  f"256x256) vs 1024 spp references, albedo-modulated, "
                  f"clamped to [0,1]; network trained here for {train_steps} steps (batch 16 x 128^2 crops of {n_train} "
                  f"rooms, 8 noise realisations each, L1, Adam lr 2e-3 cosine to 1e-4) in {t_train:.1f} s; "
-                 f"rendering {t_render:.1f} s on the host"),
+                 f"rendering {t_render:.1f} s (guides and 1 spp on the host, references on the GPU)"),
     }
     # the two guide sets of Sec. 3.3 (16 outputs: model guides, map guides), same recipe
     tr2 = flnr_train.Trainer(flnr.init_weights(0, 16), batch=16, crop=128, lr=2e-3)
@@ -405,7 +402,7 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps, full_hd_ro
         # the same network (fully convolutional) on 1920x1080 held-out rooms
         t0 = time.perf_counter()
         seeds = range(flnr_train.EVAL_SEED0 + 100, flnr_train.EVAL_SEED0 + 100 + full_hd_rooms)
-        big = flnr_train.render_scenes(seeds, H, W, ref_spp=1024)
+        big = flnr_train.render_scenes(seeds, H, W, ref_spp=1024, gpu_ref=True)
         t_big = time.perf_counter() - t0
         net_big = flnr.FLNR(H * W, weights)
         f_big = flr.FLR(q=8, radius=8, eps=1e-3)
@@ -417,8 +414,8 @@ def flnr_rows(frames, dev_frames, torch, np, dev, timed, train_steps, full_hd_ro
             "gain_db": round(float(np.mean(pn) - np.mean(pf)), 3),
             "per_scene_gain_db": [round(a - b, 2) for a, b in zip(pn, pf)],
             "what": (f"{full_hd_rooms} held-out rooms (seeds {seeds[0]}..{seeds[-1]}) at {W}x{H} vs 1024 spp "
-                     f"references (host path tracer, {t_big:.0f} s), FLR r=8 with rendered vs network guides; "
-                     f"network as flnr_psnr")}
+                     f"references (GPU path tracer; guides and 1 spp on the host: {t_big:.0f} s), FLR r=8 with "
+                     f"rendered vs network guides; network as flnr_psnr")}
     return flnr_inference_row(weights, dev_frames, torch, dev, timed, rows)
 
 
@@ -521,8 +518,6 @@ def run_ours(args):
 
     rows = {}
     want = set(ROW_NAMES) if args.rows == "all" else set(args.rows.split(",")) - {"none"}
-    if "flnr1080" in want:
-        want.add("flnr")
     if "backward" in want:
         fb = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
         gout = torch.randn((3, H, W), dtype=torch.float32, device=dev)
@@ -549,8 +544,7 @@ def run_ours(args):
         from paper_2410_11625_gb300 import flnr as _flnr
         rows["batch_serving_flnr"] = serving_batch_flnr(torch, np, dev, _flnr.init_weights(0))
     if rank == 0 and "flnr" in want:
-        rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps,
-                              full_hd_rooms=4 if "flnr1080" in want else 0))
+        rows.update(flnr_rows(frames, dev_frames, torch, np, dev, timed, args.flnr_steps, full_hd_rooms=8))
 
     # parity of the timed configuration: the last timed frame against the oracle on blocks
     f2 = flr.FLR(q=Q, radius=R, coef_radius=RC, eps=EPS, pivot_ratio=TAU)
@@ -654,8 +648,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", default="all",
-                    help="comma list of extra rows to run: " + ",".join(ROW_NAMES + EXTRA_ROWS) + " (or all, none; "
-                         "all leaves out " + ",".join(EXTRA_ROWS) + ")")
+                    help="comma list of extra rows to run: " + ",".join(ROW_NAMES) + " (or all, none)")
     ap.add_argument("--flnr-steps", type=int, default=6000,
                     help="FLNR training steps before its PSNR and 1080p rows (0: 1080p timing only)")
     args = ap.parse_args()

@@ -26,14 +26,20 @@ from . import flr as _flr
 EVAL_SEED0 = 1_000_000
 
 
-def render_scenes(seeds, H, W, ref_spp=1024, noise=1):
+def render_scenes(seeds, H, W, ref_spp=1024, noise=1, gpu_ref=False):
     """Per seed: (x [11,H,W], ref [3,H,W], albedo [3,H,W], extra [noise-1,3,H,W]) float32,
     x = guides ++ 1 spp radiance; `extra` holds further independent 1 spp renders of the
-    same scene (cheap next to the reference), which training draws from as well."""
+    same scene (cheap next to the reference), which training draws from as well.  With
+    gpu_ref the reference is traced by the input generator's GPU renderer (the same room,
+    estimator and random numbers as the host's)."""
     import synth
     out = []
     for s in seeds:
-        g, y, ref = synth.render(int(s), H, W, ref_spp=ref_spp)
+        if gpu_ref:
+            g, y = synth.render(int(s), H, W)
+            ref = synth.render_reference_gpu(int(s), H, W, ref_spp).cpu().numpy()
+        else:
+            g, y, ref = synth.render(int(s), H, W, ref_spp=ref_spp)
         extra = synth.render_noise(int(s), H, W, noise - 1) if noise > 1 else np.empty((0, 3, H, W), np.float32)
         out.append((np.ascontiguousarray(np.concatenate([g, y])), ref, g[:3].copy(), extra))
     return out

@@ -21,7 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIBPATH = os.path.join(_LIBDIR, "libsynth.so")
-_SOURCES = ["pathtracer.c"]
+_SOURCES = ["pathtracer.c", "scene.h"]
+_GPU_LIBPATH = os.path.join(_LIBDIR, "libsynth_gpu.so")
+_GPU_SOURCES = ["pathtracer_gpu.cu", "scene.h"]
 
 GUIDE_CHANNELS = ("albedo_r", "albedo_g", "albedo_b", "normal_x", "normal_y", "normal_z",
                   "depth", "ao")
@@ -38,7 +40,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIBDIR, exist_ok=True)
     tmp = _LIBPATH + f".tmp{os.getpid()}"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp]
-                   + srcs + ["-lm"], check=True)
+                   + [s for s in srcs if s.endswith(".c")] + ["-lm"], check=True)
     os.replace(tmp, _LIBPATH)
     return _LIBPATH
 
@@ -55,8 +57,60 @@ def _load():
         lib.synth_render_noise.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                            ctypes.c_int, fp]
         lib.synth_render_noise.restype = ctypes.c_int
+        lib.synth_build_scene.argtypes = [ctypes.c_uint64, ctypes.c_void_p]
+        lib.synth_build_scene.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+_gpu_lib = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile ``libsynth_gpu.so`` (the reference renderer on the GPU) with nvcc for sm_103a,
+    without fused multiply-adds so that its ray arithmetic rounds as the host's does."""
+    srcs = [os.path.join(_HERE, s) for s in _GPU_SOURCES]
+    if not force and os.path.exists(_GPU_LIBPATH):
+        if os.path.getmtime(_GPU_LIBPATH) >= max(os.path.getmtime(s) for s in srcs):
+            return _GPU_LIBPATH
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _GPU_LIBPATH + f".tmp{os.getpid()}"
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false", "-std=c++17",
+                    "-Xcompiler", "-fPIC", "-shared", "-o", tmp, srcs[0]], check=True)
+    os.replace(tmp, _GPU_LIBPATH)
+    return _GPU_LIBPATH
+
+
+def scene_record(seed: int) -> bytes:
+    """The room of ``seed`` as the host builds it (a scene_t record)."""
+    lib = _load()
+    n = lib.synth_build_scene(ctypes.c_uint64(seed), None)
+    buf = ctypes.create_string_buffer(n)
+    lib.synth_build_scene(ctypes.c_uint64(seed), buf)
+    return buf.raw
+
+
+def render_reference_gpu(seed: int, H: int, W: int, spp: int, device="cuda"):
+    """The ``spp``-sample reference [3, H, W] of ``render(seed, H, W, ref_spp=spp)`` traced on
+    the GPU (same room, estimator and random numbers; a CUDA float32 tensor)."""
+    import torch
+    global _gpu_lib
+    if _gpu_lib is None:
+        build_gpu()
+        lib = ctypes.CDLL(_GPU_LIBPATH)
+        lib.synth_reference_gpu.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        lib.synth_reference_gpu.restype = ctypes.c_int
+        _gpu_lib = lib
+    rec = scene_record(seed)
+    out = torch.empty((3, H, W), dtype=torch.float32, device=device)
+    st = _gpu_lib.synth_reference_gpu(rec, len(rec), ctypes.c_uint64(seed), int(H), int(W), int(spp),
+                                      ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(torch.cuda.current_stream(out.device).cuda_stream))
+    if st != 0:
+        raise RuntimeError(f"synth_reference_gpu failed with status {st}")
+    return out
 
 
 def render(seed: int, H: int, W: int, ref_spp: int = 0):

@@ -34,15 +34,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ROOM_X 8.0f
-#define ROOM_Y 4.0f
-#define ROOM_Z 8.0f
-#define N_BOXES 8
-#define N_SPHERES 2
-#define AO_RAYS 64
-#define AO_DIST 2.0f
-#define RAY_EPS 1e-4f
-#define PI_F 3.14159265358979323846f
+#include "scene.h"
 
 /* ---- counter-based random numbers ------------------------------------------------ */
 
@@ -67,8 +59,6 @@ static float urand(uint64_t seed, uint64_t pixel, uint64_t sample, uint64_t dim)
 
 /* ---- scene --------------------------------------------------------------------------- */
 
-typedef struct { float x, y, z; } vec3;
-
 static vec3 v3(float x, float y, float z) { vec3 v = {x, y, z}; return v; }
 static vec3 vadd(vec3 a, vec3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
 static vec3 vsub(vec3 a, vec3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -79,27 +69,6 @@ static vec3 vcross(vec3 a, vec3 b)
     return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 static vec3 vnorm(vec3 a) { return vmul(a, 1.0f / sqrtf(vdot(a, a))); }
-
-typedef struct {
-    vec3 lo, hi;
-    float albedo[3];
-} box_t;
-
-typedef struct {
-    vec3 c;
-    float r;
-    float albedo[3];
-} sphere_t;
-
-typedef struct {
-    float wall_albedo[6][3]; /* -x, +x, -y (floor), +y (ceiling), -z, +z */
-    box_t box[N_BOXES];
-    sphere_t sph[N_SPHERES];
-    float lx0, lx1, lz0, lz1, ly; /* light rectangle, facing down */
-    float le[3];                  /* emitted radiance */
-    vec3 cam_pos, cam_fwd, cam_right, cam_up;
-    float tan_half_fov;
-} scene_t;
 
 typedef struct {
     float t;
@@ -178,6 +147,12 @@ static void build_scene(uint64_t seed, scene_t *s)
     s->cam_right = vnorm(vcross(s->cam_fwd, v3(0.0f, 1.0f, 0.0f)));
     s->cam_up = vcross(s->cam_right, s->cam_fwd);
     s->tan_half_fov = tanf(0.5f * 60.0f * PI_F / 180.0f);
+}
+
+int synth_build_scene(uint64_t seed, scene_t *s)
+{
+    if (s) build_scene(seed, s);
+    return (int)sizeof(scene_t);
 }
 
 /* ---- ray casting --------------------------------------------------------------------- */
