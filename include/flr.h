@@ -297,7 +297,8 @@ typedef struct flr_frame {
 #define FLR_BATCH_TIMEOUT 1 /* device status word value after a barrier wait ran out */
 
 /*
- * The per-pixel FLR pass (flr_denoise) over n frames of any sizes, in order, on one stream.
+ * The per-pixel FLR pass (flr_denoise, Sec. 3.1-3.2) over n frames of any sizes, in order, on
+ * one stream: the serving form of a frame sequence (the paper's real-time setting, Sec. 4).
  * Errors as flr_denoise, for the first frame that fails.
  */
 int flr_denoise_batch(flr_handle *h, int n, const flr_frame *frames, void *stream);
