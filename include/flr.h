@@ -446,6 +446,15 @@ int flnr_adam_step(flnr_net *net, float lr, float beta1, float beta2, float eps,
 int flnr_l1_loss(const float *pred, const float *ref, float *grad, float *loss, size_t count, void *stream);
 
 /*
+ * SMAPE of pred against ref, the loss Sec. 3.3 trains FLNR on (count floats, device):
+ * *loss (device float) receives mean |p - r| / (|p| + |r| + eps) and grad (device) its
+ * gradient (sign(p - r) / D - |p - r| sign(p) / D^2) / count, D = |p| + |r| + eps (sign(0) = 0).
+ * Errors: FLR_ERR_ARG (eps <= 0), FLR_ERR_CUDA.
+ */
+int flnr_smape_loss(const float *pred, const float *ref, float *grad, float *loss, size_t count, float eps,
+                    void *stream);
+
+/*
  * Measured FP32 FMA throughput of the current device, for the roofline of the per-pixel FLR
  * path, which is bound by the FP32 ALUs (not a paper operation).  Runs `iters` x 16 rounds of
  * 8 independent FMA chains in 4 x 256 threads per SM, four times, and reports the fastest of

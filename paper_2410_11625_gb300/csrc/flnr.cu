@@ -1468,6 +1468,28 @@ __global__ void adam_kernel(float *w, const float *g, float *m, float *v, size_t
 
 // L1 loss between prediction and reference (planar fp32, n values): writes d/dpred = sign / n
 // and accumulates the mean absolute error into *loss
+// SMAPE of pred against ref (Sec. 3.3 trains FLNR on it): loss += mean |p - r| / D with
+// D = |p| + |r| + eps, and d/dp = (sign(p - r) / D - |p - r| sign(p) / D^2) / n
+__global__ void smape_kernel(const float *pred, const float *ref, float *grad, float *loss, size_t n, float eps)
+{
+    __shared__ float part[256];
+    float s = 0.f;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const float p = pred[e], d = p - ref[e], a = fabsf(d);
+        const float inv = 1.f / (fabsf(p) + fabsf(ref[e]) + eps);
+        const float sd = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f), sp = p > 0.f ? 1.f : (p < 0.f ? -1.f : 0.f);
+        grad[e] = (sd - a * sp * inv) * inv / (float)n;
+        s += a * inv;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, part[0] / (float)n);
+}
+
 __global__ void l1_kernel(const float *pred, const float *ref, float *grad, float *loss, size_t n)
 {
     __shared__ float part[256];
@@ -2198,6 +2220,16 @@ int flnr_l1_loss(const float *pred, const float *ref, float *grad, float *loss, 
     cudaStream_t st = (cudaStream_t)stream;
     FLNR_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
     flnr::l1_kernel<<<flnr::egrid(count) < 1024 ? flnr::egrid(count) : 1024, 256, 0, st>>>(pred, ref, grad, loss, count);
+    return cudaGetLastError() == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+int flnr_smape_loss(const float *pred, const float *ref, float *grad, float *loss, size_t count, float eps, void *stream)
+{
+    if (!pred || !ref || !grad || !loss || count == 0 || !(eps > 0.f)) return FLR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    FLNR_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    flnr::smape_kernel<<<flnr::egrid(count) < 1024 ? flnr::egrid(count) : 1024, 256, 0, st>>>(pred, ref, grad, loss, count,
+                                                                                                 eps);
     return cudaGetLastError() == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
 }
 

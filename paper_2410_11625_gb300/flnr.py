@@ -42,11 +42,12 @@ def _lib():
         lib.flnr_zero_grads.argtypes = [vp, vp]
         lib.flnr_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ip, vp]
         lib.flnr_l1_loss.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.flnr_smape_loss.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, ctypes.c_float, vp]
         lib.flnr_layer.argtypes = [vp, ip, ip, vp, vp, vp, vp, ip, ip, ip, vp]
         lib.flnr_status.argtypes = [vp]
         for name in ("flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights", "flnr_get_grads",
                      "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_adam_step",
-                     "flnr_l1_loss", "flnr_layer", "flnr_status"):
+                     "flnr_l1_loss", "flnr_smape_loss", "flnr_layer", "flnr_status"):
             getattr(lib, name).restype = ctypes.c_int
         _bound = True
     return lib
@@ -187,4 +188,15 @@ def l1_loss(pred, ref):
     loss = torch.empty(1, dtype=torch.float32, device=pred.device)
     _flr._check(_lib().flnr_l1_loss(pred.data_ptr(), ref.data_ptr(), grad.data_ptr(), loss.data_ptr(),
                                     pred.numel(), _stream(pred)), "flnr_l1_loss")
+    return loss, grad
+
+
+def smape_loss(pred, ref, eps=1e-2):
+    """SMAPE mean |p - r| / (|p| + |r| + eps) and its gradient (Sec. 3.3's training loss),
+    computed by the library's kernel."""
+    import torch
+    grad = torch.empty_like(pred)
+    loss = torch.empty(1, dtype=torch.float32, device=pred.device)
+    _flr._check(_lib().flnr_smape_loss(pred.data_ptr(), ref.data_ptr(), grad.data_ptr(), loss.data_ptr(),
+                                       pred.numel(), float(eps), _stream(pred)), "flnr_smape_loss")
     return loss, grad

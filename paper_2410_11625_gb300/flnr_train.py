@@ -6,7 +6,9 @@ One training step (batch B of c x c crops):
   I_b = FLR(X'_b, Y_b), per crop         flr_denoise (8 outputs: X' is both model and map
                                          guide; 16 outputs, Sec. 3.3's two sets: channels
                                          0-7 fit the models, 8-15 are the map guide)
-  L = mean |I - I_ref|, dL/dI             flnr_l1_loss
+  L = mean |I - I_ref|, dL/dI             flnr_l1_loss (config 4), or Sec. 3.3's SMAPE
+                                         mean |I - I_ref| / (|I| + |I_ref| + 0.01)
+                                         (flnr_smape_loss, loss="smape")
   dL/dX'_b = FLR adjoint, per crop       flr_backward
   parameter gradients                     flnr_guide_backward
   Adam on the FP32 master weights         flnr_adam_step (BF16 copies refreshed)
@@ -70,9 +72,13 @@ def sample_batch(rng, scenes, batch, crop):
 class Trainer:
     """Holds the network, the FLR handle and the device buffers of one batch shape."""
 
-    def __init__(self, weights, batch=16, crop=128, radius=8, eps=1e-3, lr=1e-3, device="cuda", graph=True):
+    def __init__(self, weights, batch=16, crop=128, radius=8, eps=1e-3, lr=1e-3, device="cuda", graph=True,
+                 loss="l1"):
         import torch
+        if loss not in ("l1", "smape"):
+            raise ValueError("loss must be 'l1' or 'smape'")
         self.B, self.c, self.lr = batch, crop, lr
+        self.loss_fn = _flnr.l1_loss if loss == "l1" else _flnr.smape_loss
         self.net = _flnr.FLNR(batch * crop * crop, weights)
         # one FLR handle and stream per crop: the crops' FLR passes and adjoints (small
         # grids each) run concurrently, and no two of them share a handle's workspace.
@@ -125,7 +131,7 @@ class Trainer:
                                                          map_guide=self.guides[b, 8:], out=self.out[b]))
         else:
             self._per_crop(lambda b: self.flrs[b].denoise(self.guides[b], self.x[b, 8:11], out=self.out[b]))
-        loss, g_out = _flnr.l1_loss(self.out, self.ref)
+        loss, g_out = self.loss_fn(self.out, self.ref)
         if self.outputs == 16:
             self._per_crop(lambda b: self.flrs[b].backward(
                 self.guides[b, :8], self.x[b, 8:11], g_out[b], map_guide=self.guides[b, 8:],

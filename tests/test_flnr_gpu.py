@@ -330,3 +330,26 @@ def test_adam_and_l1_match_their_formulas():
     d = pred.astype(np.float64) - ref
     assert abs(float(loss.item()) - np.abs(d).mean()) <= 1e-5
     assert np.array_equal(grad.cpu().numpy(), (np.sign(d) / d.size).astype(np.float32))
+
+
+def test_smape_matches_its_formula():
+    """Sec. 3.3's SMAPE loss mean |p - r| / (|p| + |r| + eps) and its gradient, against numpy;
+    the gradient formula itself against central differences of the loss."""
+    rng = np.random.default_rng(21)
+    pred = rng.normal(size=(2, 3, 17, 19)).astype(np.float32)
+    ref = rng.normal(size=(2, 3, 17, 19)).astype(np.float32)
+    pred.ravel()[:5] = ref.ravel()[:5]  # zero differences
+    pred.ravel()[5:9] = 0.0             # zero predictions
+    eps = 1e-2
+    loss, grad = flnr.smape_loss(to_dev(pred), to_dev(ref), eps=eps)
+    p, r = pred.astype(np.float64), ref.astype(np.float64)
+    D = np.abs(p) + np.abs(r) + eps
+    L = np.mean(np.abs(p - r) / D)
+    G = (np.sign(p - r) / D - np.abs(p - r) * np.sign(p) / D ** 2) / p.size
+    assert abs(float(loss.item()) - L) <= 1e-5 * L
+    assert np.max(np.abs(grad.cpu().numpy() - G)) <= 1e-6 * np.max(np.abs(G))
+    f = lambda q: np.mean(np.abs(q - r) / (np.abs(q) + np.abs(r) + eps))
+    for idx in [(0, 1, 3, 4), (1, 2, 16, 0), (0, 0, 8, 8)]:
+        e = np.zeros_like(p)
+        e[idx] = 1e-6
+        assert abs((f(p + e) - f(p - e)) / 2e-6 - G[idx]) <= 1e-6 * max(1.0, abs(G[idx]) * p.size) / p.size
