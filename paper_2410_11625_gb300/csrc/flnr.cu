@@ -1098,14 +1098,33 @@ __global__ void __launch_bounds__(kWsThreads) conv_s2_kernel(const __grid_consta
 // row kg) at (16 kg + rg) * 128 (LBO 2048 between K groups, SBO 128 between row groups);
 // B core matrix (channel group og, kg) at (kg * COUT/8 + og) * 128 (LBO COUT * 16, SBO 128).
 // Rows of A past KS^2 * CIN are never written and their accumulator rows are discarded.
-// At the end each thread reads its accumulator row (one (tap, i)) and adds it to the FP32
-// master gradient [Cout][Cin][k][k] with atomics (padding channels skipped).
+// At the end each thread writes its accumulator row (one (tap, i)) to the CTA's slot of a
+// partials buffer; wgrad_reduce_kernel then adds the CTAs' partials in CTA order to the FP32
+// master gradient [Cout][Cin][k][k] (padding channels skipped), so the result does not depend
+// on the order in which CTAs finish.
 struct WgradArgs {
     const bf16 *x, *dz;
-    float *gw;  // master layout
+    float *gw;    // master layout
+    float *part;  // per-CTA partial products [grid][KS^2 CIN][COUT]
     int N, H, W, cin_true, cout_true, tiles_per_cta;
     int *status;
 };
+
+// gw[o][i][tap] += sum over the CTAs, in CTA order, of their partial (tap CIN + i, o): the
+// weight gradient without atomics, the same every run
+template <int CIN, int COUT, int KS>
+__global__ void wgrad_reduce_kernel(const float *part, int nctas, float *gw, int cin_true, int cout_true)
+{
+    constexpr int M = KS * KS * CIN;
+    const int total = cout_true * cin_true * KS * KS;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int tap = e % (KS * KS), i = (e / (KS * KS)) % cin_true, o = e / (KS * KS * cin_true);
+        const float *p = part + (size_t)(tap * CIN + i) * COUT + o;
+        float s = 0.f;
+        for (int b = 0; b < nctas; ++b) s += p[(size_t)b * M * COUT];
+        gw[e] += s;
+    }
+}
 
 template <int CIN, int COUT, int KS>
 struct WgGeom {
@@ -1258,17 +1277,16 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const WgradArgs a)
         const int r = 32 * warp + lane;
 #pragma unroll 1
         for (int mt = 0; mt < MT; ++mt) {
-            const int m = mt * 128 + r, tap = m / CIN, i = m % CIN;
+            const int m = mt * 128 + r;
 #pragma unroll
             for (int o0 = 0; o0 < COUT; o0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(mt * COUT + o0), v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-                if (m < G::M && i < a.cin_true) {
+                if (m < G::M) {  // this CTA's partial row, summed in a fixed order by wgrad_reduce_kernel
+                    float4 *dst = reinterpret_cast<float4 *>(a.part + ((size_t)blockIdx.x * G::M + m) * COUT + o0);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (o0 + j < a.cout_true)
-                            atomicAdd(a.gw + ((size_t)(o0 + j) * a.cin_true + i) * KS * KS + tap, v[j]);
+                    for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
             }
         }
@@ -1420,23 +1438,21 @@ __global__ void join_bwd_kernel(const float *g_skip, const bf16 *g_path, const b
     }
 }
 
-// bias gradient: gb[c] += sum_p dz[p][c], c < ctrue (one CTA per channel block)
-__global__ void bias_grad_kernel(const bf16 *dz, float *gb, long long P, int C, int ctrue)
+// bias gradient: gb[c] += sum_p dz[p][c], one CTA per channel c < ctrue (grid = ctrue), each
+// thread summing a fixed stride of pixels, then a fixed tree: the same result every run
+__global__ void bias_grad_kernel(const bf16 *dz, float *gb, long long P, int C)
 {
     __shared__ float part[256];
-    for (int c = 0; c < ctrue; ++c) {
-        float s = 0.f;
-        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
-            s += __bfloat162float(dz[p * C + c]);
-        part[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) atomicAdd(gb + c, part[0]);
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dz[p * C + c]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
+    if (threadIdx.x == 0) gb[c] += part[0];
 }
 
 // master fp32 [Cout][Cin][k][k] -> forward bf16 [tap][CoutP][CinP] and dgrad bf16
@@ -1767,7 +1783,7 @@ cudaError_t conv_s2_launch(const ConvArgs &a, cudaStream_t st)
 // request is raised where needed so that no more CTAs than tensor memory can hold share an SM.
 template <int CIN, int COUT, int KS>
 cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H, int W, int cin_true, int cout_true,
-                         int *status, cudaStream_t st)
+                         float *part, size_t part_floats, int *status, cudaStream_t st)
 {
     using G = WgGeom<CIN, COUT, KS>;
     constexpr int kSmemPerSm = 228 * 1024, kReservedPerCta = 1024, kThreads = 128, kThreadsPerSm = 2048;
@@ -1799,11 +1815,18 @@ cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H,
     }
     const long long ntiles = (long long)N * ((H + 7) / 8) * ((W + 7) / 8);
     if (ntiles <= 0) return cudaSuccess;
-    const long long slots = (long long)per_sm * n_sm;
+    long long slots = (long long)per_sm * n_sm;
+    const long long fit = (long long)(part_floats / ((size_t)G::M * COUT));  // partial slots the buffer holds
+    if (slots > fit) slots = fit;
+    if (slots < 1) return cudaErrorInvalidValue;
     const long long ctas = ntiles < slots ? ntiles : slots;
-    WgradArgs a{x, dz, gw, N, H, W, cin_true, cout_true, (int)((ntiles + ctas - 1) / ctas), status};
+    WgradArgs a{x, dz, gw, part, N, H, W, cin_true, cout_true, (int)((ntiles + ctas - 1) / ctas), status};
     const long long grid = (ntiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
     kern<<<(int)grid, kThreads, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int total = cout_true * cin_true * KS * KS;
+    wgrad_reduce_kernel<CIN, COUT, KS><<<(total + 255) / 256, 256, 0, st>>>(part, (int)grid, gw, cin_true, cout_true);
     return cudaGetLastError();
 }
 
@@ -1826,6 +1849,8 @@ struct flnr_net {
     __nv_bfloat16 *x0, *a0, *f0, *a1, *f1, *a2, *f2, *c1, *a3, *d1, *c0, *a4, *d0, *a5;
     __nv_bfloat16 *gA, *gB, *gC, *gLo;  // gradient scratch (largest: 48 channels at full res)
     float *gskip0, *gskip1;             // skip gradients (fp32)
+    float *wpart = nullptr;             // per-CTA partial weight gradients (fixed-order reduction)
+    size_t wpart_floats = 0;
     float *out = nullptr;               // last forward output, planar fp32 [N][8][H][W]
     int *status = nullptr;              // device status word of the tensor-core kernels
     int N = 0, H = 0, W = 0;            // shape of the last forward
@@ -1916,6 +1941,9 @@ int flnr_create(int max_pixels, int outputs, flnr_net **out)
     st |= nalloc(n, &n->gA, P * 48) | nalloc(n, &n->gB, P * 48) | nalloc(n, &n->gC, P * 48) | nalloc(n, &n->gLo, P * 16);
     st |= nalloc(n, &n->gskip0, P * 16) | nalloc(n, &n->gskip1, P2 * 32) | nalloc(n, &n->out, P * 16);
     st |= nalloc(n, &n->status, 1);
+    // partial weight gradients: two CTAs per SM of the largest layer (e2b, 9 * 64 x 64)
+    n->wpart_floats = 2 * (size_t)n->n_sm * 9 * 64 * 64;
+    st |= nalloc(n, &n->wpart, n->wpart_floats);
     if (st != FLR_OK) {
         flnr_destroy(n);
         return FLR_ERR_NOMEM;
@@ -2028,34 +2056,34 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     auto gw = [&](int l) { return n->g + n->poff[l][0]; };
     auto gb = [&](int l) { return n->g + n->poff[l][1]; };
     auto bgrad = [&](const __nv_bfloat16 *dz, long long pix, int C, int ctrue, int l) {
-        bias_grad_kernel<<<64, 256, 0, st>>>(dz, gb(l), pix, C, ctrue);
+        bias_grad_kernel<<<ctrue, 256, 0, st>>>(dz, gb(l), pix, C);
     };
     // output head: sigmoid, o1 (1x1, 16 -> 8 padded to 16), o0
     sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W, n->nout);
-    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, n->nout, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a5, n->gA, gw(11), N, H, W, 16, n->nout, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P, 16, n->nout, 11);
     FLNR_TRY((dgrad_launch<16, 16, 1, true>({n->gA, n->wd[11], n->a5, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
-    FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->d0, n->gB, gw(10), N, H, W, 16, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gB, (long long)P, 16, 16, 10);
     FLNR_TRY((dgrad_launch<16, 16, 3, true>({n->gB, n->wd[10], n->d0, nullptr, n->gA, nullptr, N, H, W, 16}, n->status, st)));
     // decoder level 0
-    FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->a4, n->gA, gw(9), N, H, W, 16, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P, 16, 16, 9);
     FLNR_TRY((dgrad_launch<16, 16, 3, true>({n->gA, n->wd[9], n->a4, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
     upcat_kernel<<<egrid(P * 6), 256, 0, st>>>(n->d1, n->f0, n->c0, N, H, W, 32, 16);  // d0a's input
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, n->status, st)));
+    FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gB, (long long)P, 16, 16, 8);
     FLNR_TRY((dgrad_launch<16, 48, 3, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, n->status, st)));
     upcat_bwd_kernel<<<egrid(P * 48), 256, 0, st>>>(n->gC, n->d1, n->gLo, n->gskip0, N, H, W, 32, 16);  // gLo = dz(d1b)
     // decoder level 1 (H/2)
     const size_t P2 = P / 4;
-    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, n->status, st)));
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gLo, (long long)P2, 32, 32, 7);
     FLNR_TRY((dgrad_launch<32, 32, 3, true>({n->gLo, n->wd[7], n->a3, nullptr, n->gA, nullptr, N, H2, W2, 32}, n->status, st)));
     upcat_kernel<<<egrid(P2 * 12), 256, 0, st>>>(n->f2, n->f1, n->c1, N, H2, W2, 64, 32);  // d1a's input
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, n->status, st)));
+    FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P2, 32, 32, 6);
     FLNR_TRY((dgrad_launch<32, 96, 3, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, n->status, st)));
     upcat_bwd_kernel<<<egrid(P2 * 96), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
@@ -2066,26 +2094,26 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     bgrad(n->gLo, (long long)P4, 64, 64, 5);
     join_bwd_kernel<2><<<egrid(P2 * 64), 256, 0, st>>>(nullptr, n->gLo, nullptr, n->gB, N, H4, W4, 64);
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gB, gw(5), N, H2, W2, 64, 64, n->status, st)));
+    FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gB, gw(5), N, H2, W2, 64, 64, n->wpart, n->wpart_floats, n->status, st)));
     FLNR_TRY((dgrad_launch<64, 64, 3, true>({n->gB, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H2, W2, 64}, n->status, st)));
-    FLNR_TRY((wgrad_launch<32, 64, 3>(n->f1, n->gA, gw(4), N, H2, W2, 32, 64, n->status, st)));
+    FLNR_TRY((wgrad_launch<32, 64, 3>(n->f1, n->gA, gw(4), N, H2, W2, 32, 64, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P2, 64, 64, 4);
     FLNR_TRY((dgrad_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 32}, n->status, st)));
     // encoder level 1: e1b (stride 2, H -> H/2; f1 also feeds the d1a skip), then e1a (H)
     join_bwd_kernel<2><<<egrid(P * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gC, N, H2, W2, 32);
     FLNR_TRY(cudaGetLastError());
-    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gC, gw(3), N, H, W, 32, 32, n->status, st)));
+    FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gC, gw(3), N, H, W, 32, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gC, (long long)P, 32, 32, 3);
     FLNR_TRY((dgrad_launch<32, 32, 3, true>({n->gC, n->wd[3], n->a1, nullptr, n->gA, nullptr, N, H, W, 32}, n->status, st)));
-    FLNR_TRY((wgrad_launch<16, 32, 3>(n->f0, n->gA, gw(2), N, H, W, 16, 32, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 32, 3>(n->f0, n->gA, gw(2), N, H, W, 16, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P, 32, 32, 2);
     FLNR_TRY((dgrad_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
     join_bwd_kernel<1><<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
     // input projection (H)
-    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gLo, (long long)P, 16, 16, 1);
     FLNR_TRY((dgrad_launch<16, 16, 1, true>({n->gLo, n->wd[1], n->a0, nullptr, n->gA, nullptr, N, H, W, 16}, n->status, st)));
-    FLNR_TRY((wgrad_launch<16, 16, 3>(n->x0, n->gA, gw(0), N, H, W, 11, 16, n->status, st)));
+    FLNR_TRY((wgrad_launch<16, 16, 3>(n->x0, n->gA, gw(0), N, H, W, 11, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P, 16, 16, 0);
     if (grad_in) {  // through in0 to the packed input, then through the input transform
         FLNR_TRY((dgrad_launch<16, 16, 3, false>({n->gA, n->wd[0], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
@@ -2156,8 +2184,8 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
         else
             FLNR_TRY((dgrad_launch<CO, CI, KS, false>({dz, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, n->status, st)));
     } else {
-        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->status, st)));
-        bias_grad_kernel<<<64, 256, 0, st>>>(dz, n->g + n->poff[l][1], P, CO, d.cout);
+        FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->wpart, n->wpart_floats, n->status, st)));
+        bias_grad_kernel<<<d.cout, 256, 0, st>>>(dz, n->g + n->poff[l][1], P, CO);
         FLNR_TRY(cudaGetLastError());
     }
     return FLR_OK;

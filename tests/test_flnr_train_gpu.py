@@ -46,3 +46,17 @@ def test_trained_flnr_beats_flr_on_held_out_scenes(data, outputs):
         w0 = flnr.init_weights(0, 16)["o1.w"]
         assert np.linalg.norm(w[8:] - w0[8:]) > 0.1 * np.linalg.norm(w0[8:])
     tr.net.close()
+
+
+def test_training_is_deterministic(data):
+    """Weight gradients add their per-CTA partials in a fixed order and bias gradients use a
+    fixed tree (no floating-point atomics), so two runs of the same recipe give the same
+    weights bit for bit."""
+    scenes, _ = data
+    ws = []
+    for _ in range(2):
+        tr = flnr_train.Trainer(flnr.init_weights(0), batch=16, crop=128, lr=2e-3)
+        tr.train(scenes, 40, seed=3)
+        ws.append(tr.net.get_weights())
+        tr.net.close()
+    assert np.array_equal(ws[0], ws[1])
