@@ -146,6 +146,33 @@ int flr_backward(flr_handle *h, const float *guide, const float *map_guide, cons
 int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
                      const float *radiance, float *out, int H, int W, void *stream);
 
+/*
+ * The same pass on HOST images of a stream of frames (a renderer's frame sequence),
+ * without waiting: enqueues the copy of guide, map_guide (if not NULL) and radiance to a
+ * handle-owned device staging slot on a handle-owned copy-in stream, flr_denoise's kernels
+ * on `stream`, and the copy of the result to `out` on a handle-owned copy-out stream, then
+ * returns.  Consecutive calls on one handle alternate between two staging slots, so frame
+ * i + 1 is copied in while frame i's kernels run and frame i's result is copied out while
+ * frame i + 1's kernels run; the result equals flr_denoise's bit for bit.  The kernels also
+ * follow the work already queued on `stream`; the input copies do not wait for it.
+ * Ownership: the host buffers stay the caller's, must not be written (inputs) or read
+ * (out) until flr_host_wait(h) returns, and should be page-locked (cudaHostAlloc or
+ * cudaHostRegister): with pageable memory the copies are correct but do not overlap.  A
+ * frame larger than its slot first waits for the frames in flight, then grows the slot
+ * ((2 Q + 6) floats per pixel per slot).  Errors as flr_denoise; after an error, call
+ * flr_host_wait before queueing further frames.
+ */
+int flr_denoise_host_async(flr_handle *h, const float *guide, const float *map_guide,
+                           const float *radiance, float *out, int H, int W, void *stream);
+
+/*
+ * Blocks until every frame queued by flr_denoise_host_async on this handle is in host
+ * memory (returns at once when none is queued).  flr_denoise_host calls it first.  A
+ * kernel's expired bounded wait is reported by flr_get_stats, as for flr_denoise.
+ * Errors: FLR_ERR_ARG, FLR_ERR_CUDA.
+ */
+int flr_host_wait(flr_handle *h);
+
 /* Most row bands flr_denoise_host cuts a frame into. */
 #define FLR_HOST_MAX_BANDS 8
 

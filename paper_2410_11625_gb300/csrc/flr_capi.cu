@@ -137,6 +137,14 @@ struct flr_handle {
     float *d_fshift = nullptr;
     int fcta = 0;
     bool last_fused = false;  // the last forward call took the fused path
+    // asynchronous host path (flr_denoise_host_async): two device staging slots (guide, map
+    // guide, radiance, out), per slot the events "inputs copied in", "kernels done" and
+    // "result copied out", and the slot the next frame takes
+    float *aslot[2] = {nullptr, nullptr};
+    size_t aslot_px[2] = {0, 0};
+    cudaEvent_t a_in[2] = {}, a_comp[2] = {}, a_out[2] = {};
+    int a_next = 0;
+    bool a_pending = false;
 };
 
 namespace {
@@ -271,6 +279,30 @@ int band_plan(int H, int r, int rc, int *c, int *in_end, int *o)
     return K;
 }
 
+// Device staging of the host paths: guide (q planes), map guide (q), radiance (3) and output
+// (3) of a px-pixel frame, each region starting 16-byte aligned (planes px floats apart).
+size_t staging_floats(size_t px, int q)
+{
+    const size_t pxa = (px + 3) & ~(size_t)3;
+    return pxa * (2 * (size_t)q + 6);
+}
+void staging_regions(float *base, size_t px, int q, float **dg, float **dm, float **dr, float **dout)
+{
+    auto up = [](size_t n) { return (n + 3) & ~(size_t)3; };
+    *dg = base;
+    *dm = *dg + up((size_t)q * px);
+    *dr = *dm + up((size_t)q * px);
+    *dout = *dr + up(3 * px);
+}
+
+// The handle's copy-in and copy-out streams (created on first use).
+int copy_streams(flr_handle *h)
+{
+    if (!h->s_in) FLR_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "copy stream");
+    if (!h->s_out) FLR_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "copy stream");
+    return FLR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -343,6 +375,11 @@ int flr_destroy(flr_handle *h)
     cudaFree(h->d_fcount);
     cudaFree(h->d_fshift);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(h->aslot[k]);
+        for (cudaEvent_t ev : {h->a_in[k], h->a_comp[k], h->a_out[k]})
+            if (ev) cudaEventDestroy(ev);
+    }
     delete h;
     return FLR_OK;
 }
@@ -596,19 +633,18 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
     if ((long long)H * W > 0x7fffffffLL) return FLR_ERR_ARG;
     const int q = h->p.q, r = h->p.radius, rc = h->p.coef_radius;
     const size_t px = (size_t)H * W;
+    if (int st = flr_host_wait(h)) return st;  // frames queued by flr_denoise_host_async
     if (h->stage_px < px || !h->stage) {
         cudaFree(h->stage);
         h->stage = nullptr;
         h->stage_px = 0;
-        if (cudaMalloc(&h->stage, px * (2 * (size_t)FLR_MAX_Q + 6) * sizeof(float)) != cudaSuccess)
+        if (cudaMalloc(&h->stage, staging_floats(px, FLR_MAX_Q) * sizeof(float)) != cudaSuccess)
             return FLR_ERR_NOMEM;
         h->stage_px = px;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    float *dg = h->stage;
-    float *dm = dg + (size_t)q * px;
-    float *dr = dm + (size_t)q * px;
-    float *dout = dr + 3 * px;
+    float *dg, *dm, *dr, *dout;
+    staging_regions(h->stage, px, q, &dg, &dm, &dr, &dout);
     // Row bands: the copy of band k + 1 overlaps the kernels of band k, whose output copy
     // overlaps the kernels of band k + 1 (separate copy-in and copy-out streams).  Band k's
     // kernels compute the models of rows [c_k, c_k+1) from input rows up to c_k+1 + r and
@@ -631,9 +667,8 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
         int st = grow(h, H, W);
         if (st != FLR_OK) return st;
     }
-    if (!h->s_in) {
-        FLR_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "copy stream");
-        FLR_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "copy stream");
+    if (!h->d_fstart) {
+        if (int st = copy_streams(h)) return st;
         FLR_CUDA(cudaMalloc(&h->d_fstart, sizeof(unsigned long long)), "re-solve index");
         h->band_ev.resize(2 * FLR_HOST_MAX_BANDS + 1);
         for (auto &e : h->band_ev) FLR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "band event");
@@ -758,6 +793,66 @@ int flr_denoise_host(flr_handle *h, const float *guide, const float *map_guide,
     }
     FLR_CUDA(cudaStreamSynchronize(h->s_out), "host-path synchronise");
     FLR_CUDA(cudaStreamSynchronize(s), "host-path synchronise");
+    return FLR_OK;
+}
+
+int flr_denoise_host_async(flr_handle *h, const float *guide, const float *map_guide,
+                           const float *radiance, float *out, int H, int W, void *stream)
+{
+    if (!h || !guide || !radiance || !out || H <= 0 || W <= 0) return FLR_ERR_ARG;
+    if ((long long)H * W > 0x7fffffffLL) return FLR_ERR_ARG;
+    const int q = h->p.q;
+    const size_t px = (size_t)H * W;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int st = copy_streams(h)) return st;
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t *ev : {&h->a_in[k], &h->a_comp[k], &h->a_out[k]})
+            if (!*ev) FLR_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "host-path event");
+    const int k = h->a_next;
+    if (h->aslot_px[k] < px) {
+        // a larger frame: the frames in flight may still use the slot, so they finish first
+        if (int st = flr_host_wait(h)) return st;
+        cudaFree(h->aslot[k]);
+        h->aslot[k] = nullptr;
+        h->aslot_px[k] = 0;
+        if (cudaMalloc(&h->aslot[k], staging_floats(px, q) * sizeof(float)) != cudaSuccess) return FLR_ERR_NOMEM;
+        h->aslot_px[k] = px;
+    }
+    float *dg, *dm, *dr, *dout;
+    staging_regions(h->aslot[k], px, q, &dg, &dm, &dr, &dout);
+    h->a_pending = true;
+    // inputs: into the slot once the frame that used it last has been computed
+    FLR_CUDA(cudaStreamWaitEvent(h->s_in, h->a_comp[k], 0), "host-path wait");
+    FLR_CUDA(cudaMemcpyAsync(dg, guide, sizeof(float) * q * px, cudaMemcpyHostToDevice, h->s_in), "h2d guide");
+    if (map_guide)
+        FLR_CUDA(cudaMemcpyAsync(dm, map_guide, sizeof(float) * q * px, cudaMemcpyHostToDevice, h->s_in),
+                 "h2d map guide");
+    FLR_CUDA(cudaMemcpyAsync(dr, radiance, sizeof(float) * 3 * px, cudaMemcpyHostToDevice, h->s_in), "h2d radiance");
+    FLR_CUDA(cudaEventRecord(h->a_in[k], h->s_in), "host-path event");
+    // kernels: after the inputs, and after the slot's previous result has been copied out
+    FLR_CUDA(cudaStreamWaitEvent(s, h->a_in[k], 0), "host-path wait");
+    FLR_CUDA(cudaStreamWaitEvent(s, h->a_out[k], 0), "host-path wait");
+    int st = flr_denoise(h, dg, map_guide ? dm : nullptr, dr, dout, H, W, stream);
+    if (st != FLR_OK) return st;
+    FLR_CUDA(cudaEventRecord(h->a_comp[k], s), "host-path event");
+    // result: copied out while the next frame's kernels run
+    FLR_CUDA(cudaStreamWaitEvent(h->s_out, h->a_comp[k], 0), "host-path wait");
+    FLR_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * 3 * px, cudaMemcpyDeviceToHost, h->s_out), "d2h out");
+    FLR_CUDA(cudaEventRecord(h->a_out[k], h->s_out), "host-path event");
+    h->a_next = k ^ 1;
+    return FLR_OK;
+}
+
+int flr_host_wait(flr_handle *h)
+{
+    if (!h) return FLR_ERR_ARG;
+    if (!h->a_pending) return FLR_OK;
+    h->a_pending = false;
+    // every result copy follows its frame's kernels, which follow its input copies; the
+    // events of both slots cover a frame whose call returned early with an error
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t ev : {h->a_in[k], h->a_comp[k], h->a_out[k]})
+            if (ev) FLR_CUDA(cudaEventSynchronize(ev), "host-path wait");
     return FLR_OK;
 }
 

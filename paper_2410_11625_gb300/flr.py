@@ -17,6 +17,7 @@ STATUS = {0: "FLR_OK", -1: "FLR_ERR_ARG", -2: "FLR_ERR_ALIGN", -3: "FLR_ERR_CUDA
 
 # every symbol include/flr.h declares
 EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
+           "flr_denoise_host_async", "flr_host_wait",
            "flr_get_stats", "flr_get_kernel_times", "flr_status_string", "flr_last_cuda_error",
            "flr_denoise_noalloc", "flr_backward", "flr_fast_create", "flr_fast_destroy",
            "flr_fast_denoise", "flr_fast_get_stats", "flr_fast_param_grad", "flr_denoise_batch", "flr_fast_reserve_batch",
@@ -93,6 +94,8 @@ def load_library():
     lib.flr_reserve.argtypes = [vp, ip, ip]
     lib.flr_denoise.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
     lib.flr_denoise_host.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_denoise_host_async.argtypes = [vp, fp, fp, fp, fp, ip, ip, vp]
+    lib.flr_host_wait.argtypes = [vp]
     lib.flr_host_band_plan.argtypes = [ip, ip, ip, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.flr_get_stats.argtypes = [vp, ctypes.POINTER(FlrStats)]
     lib.flr_get_kernel_times.argtypes = [vp, ctypes.POINTER(FlrKernelTimes), ip]
@@ -124,7 +127,7 @@ def load_library():
     lib.flr_last_cuda_error.argtypes = []
     lib.flr_last_cuda_error.restype = ctypes.c_char_p
     for name in ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoise_host",
-                 "flr_get_stats", "flr_get_kernel_times"):
+                 "flr_denoise_host_async", "flr_host_wait", "flr_get_stats", "flr_get_kernel_times"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -248,6 +251,22 @@ class FLR:
         st = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
         _check(load_library().flr_denoise_host(self._h, g, m, r, o, H, W, st), "flr_denoise_host")
         return out
+
+    def denoise_host_async(self, guide, radiance, out, map_guide=None, stream=None):
+        """Queue one frame of a host frame stream (numpy float32, page-locked for overlap);
+        `out` and the inputs belong to the library until host_wait() returns."""
+        H, W = radiance.shape[-2], radiance.shape[-1]
+        g = _host_ptr(guide, "guide", (self.q, H, W))
+        r = _host_ptr(radiance, "radiance", (3, H, W))
+        m = None if map_guide is None else _host_ptr(map_guide, "map_guide", (self.q, H, W))
+        o = _host_ptr(out, "out", (3, H, W))
+        st = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
+        _check(load_library().flr_denoise_host_async(self._h, g, m, r, o, H, W, st), "flr_denoise_host_async")
+        return out
+
+    def host_wait(self):
+        """Wait until every frame queued by denoise_host_async is in host memory."""
+        _check(load_library().flr_host_wait(self._h), "flr_host_wait")
 
     def denoise_batch(self, frames, stream=None):
         """Per-pixel FLR over frames in order: list of (guide, radiance, map_guide, out)."""

@@ -72,6 +72,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.flr_destroy(None) == 0
     assert lib.flr_denoise(None, None, None, None, None, 8, 8, None) == -1
     assert lib.flr_denoise_host(None, None, None, None, None, 8, 8, None) == -1
+    assert lib.flr_denoise_host_async(None, None, None, None, None, 8, 8, None) == -1
+    assert lib.flr_host_wait(None) == -1
     assert lib.flr_reserve(None, 8, 8) == -1
     assert lib.flr_get_stats(None, None) == -1
     assert lib.flr_get_kernel_times(None, None, 0) == -1

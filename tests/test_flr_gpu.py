@@ -170,9 +170,12 @@ def test_rendered_full_hd_sampled_blocks(flr):
     assert worst <= TOL, f"max rel err {worst:.3e}"
 
 
-def test_deterministic_and_host_path_matches(flr):
+@pytest.mark.parametrize("H,W", [(150, 260), (97, 131)])
+def test_deterministic_and_host_path_matches(flr, H, W):
+    """97 x 131 has an odd pixel count: the host path's staging regions must still start
+    16-byte aligned."""
     import torch
-    g, y = synth.render(2, 150, 260)
+    g, y = synth.render(2, H, W)
     f = flr.FLR(q=8, radius=8, coef_radius=8, eps=1e-3)
     a = f.denoise(to_dev(g), to_dev(y)).cpu().numpy()
     b = f.denoise(to_dev(g), to_dev(y)).cpu().numpy()
