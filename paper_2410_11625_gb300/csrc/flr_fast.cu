@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kFW, 3) apply_tma_kernel(const __grid_constant
     auto issue = [&](int item, int st) {
         const int ci = item / ncx, cx = item % ncx;
         tma::mbar_expect_tx(bar + st, (unsigned)(Q * P * kFW * 4));
-        tma::load_3d(base + st * STAGE, &k.t0, cx * kFW, P * ci - P / 2, 0, bar + st);
+        tma::load_3d_hint(base + st * STAGE, &k.t0, cx * kFW, P * ci - P / 2, 0, bar + st, fast::l2_policy_stream());
     };
     if (tid == 0 && (int)blockIdx.x < nitems) issue(blockIdx.x, 0);
     float sh[Q + 3];
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kFW, 3) apply_tma_kernel(const __grid_constant
                         const int kk = 3 * (i + 1) + c;
                         o = fmaf(fmaf(fy, dtb[kk], top[kk]), z[i], o);
                     }
-                    a.out[c * oplane + off] = o + sh[Q + c];
+                    __stcs(a.out + c * oplane + off, o + sh[Q + c]);  // streamed: not kept in L2
                 }
             }
         }

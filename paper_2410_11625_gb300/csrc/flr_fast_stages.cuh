@@ -29,6 +29,32 @@ __device__ __forceinline__ void moments_all(float (&acc)[Chan<Q>::NCH], const fl
     (moment_one<Q, I>(acc[I], v), ...);
 }
 
+// L2 eviction priorities for the full-resolution planes.  The moment stage reads the guide
+// planes with evict_last so that they are still in L2 when the apply stage reads them again
+// as the map guide (66 MB at 1080p, half of L2); the radiance, read once, and the apply's own
+// reads take evict_first, so they do not push the guides out.
+__device__ __forceinline__ uint64_t l2_policy_keep()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_stream()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+// 8-byte read-only load with an L2 eviction policy
+__device__ __forceinline__ float2 ld_f2_hint(const float *p, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;\n"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
 struct FastArgs {
     const float *guide, *rad, *map_guide;  // model inputs [q|3][Hi][Wi], map guide [q][Ho][Wo]
     float *out;                            // [3][Ho][Wo]
@@ -88,6 +114,7 @@ __device__ __forceinline__ void stage_moments(const FastArgs &a, int by, int cx)
         // 16-byte aligned)
         const bool vec = (a.Wi & 1) == 0;
         const bool two = x + 1 < a.Wi;
+        const uint64_t pol_keep = l2_policy_keep(), pol_stream = l2_policy_stream();
 #pragma unroll
         for (int yy = 0; yy < F; ++yy) {
             const int y = y0 + yy;
@@ -97,13 +124,13 @@ __device__ __forceinline__ void stage_moments(const FastArgs &a, int by, int cx)
             if (vec) {
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
-                    const float2 g = __ldg(reinterpret_cast<const float2 *>(a.guide + k * plane + off));
+                    const float2 g = ld_f2_hint(a.guide + k * plane + off, pol_keep);
                     v0[k] = g.x - ref[k];
                     v1[k] = g.y - ref[k];
                 }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 g = __ldg(reinterpret_cast<const float2 *>(a.rad + c * plane + off));
+                    const float2 g = ld_f2_hint(a.rad + c * plane + off, pol_stream);
                     v0[Q + c] = g.x - ref[Q + c];
                     v1[Q + c] = g.y - ref[Q + c];
                 }

@@ -72,6 +72,17 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *tm, int x,
         : "memory");
 }
 
+// The same load with an L2 eviction policy (from createpolicy)
+__device__ __forceinline__ void load_3d_hint(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar,
+                                             uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
 // Bounded wait for the phase of `bar` with the given parity, polled by lane 0 of each warp
 // (try_wait suspends up to 20 us per call).  Returns false if timeout_ns ran out.
 __device__ __forceinline__ bool wait_warp(uint64_t *bar, uint32_t parity, unsigned long long timeout_ns)
