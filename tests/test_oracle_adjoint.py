@@ -107,3 +107,32 @@ def test_guide_gradient_sums_to_zero_per_channel(rc):
     bw = oracle.flr_backward(g, y, G, r, 1e-3, coef_radius=rc)
     scale = np.max(np.abs(bw["guide"]))
     assert np.max(np.abs(bw["guide"].sum(axis=(1, 2)))) <= 1e-9 * scale * H * W
+
+
+def test_gradient_is_local_to_the_block_and_its_halo():
+    """With grad_out nonzero only in a block, the gradient lives in the block plus its
+    radius-(r + rc) halo and depends only on the inputs there (each output reads the models
+    of its rc-window, each model the inputs of its r-window, clipped alike at the frame
+    edge).  So the adjoint of the frame equals the sum of the adjoints of disjoint crops,
+    exactly: the premise of the GPU test that checks a 1080p frame block by block."""
+    H, W, r, rc, B = 120, 160, 4, 3, 12
+    R = r + rc
+    g, y = synth.render(2, H, W)
+    blocks = [(0, 0), (H - B, W - B), (50, 70)]
+    G = np.zeros((3, H, W), np.float32)
+    rng = np.random.default_rng(0)
+    for by, bx in blocks:
+        G[:, by:by + B, bx:bx + B] = rng.normal(size=(3, B, B))
+    full = oracle.flr_backward(g, y, G, r, 1e-3, coef_radius=rc)
+    acc = {k: np.zeros_like(full[k]) for k in ("guide", "radiance")}
+    e = 0.0
+    for by, bx in blocks:
+        y0, y1, x0, x1 = max(0, by - R), min(H, by + B + R), max(0, bx - R), min(W, bx + B + R)
+        part = oracle.flr_backward(g[:, y0:y1, x0:x1], y[:, y0:y1, x0:x1], G[:, y0:y1, x0:x1], r, 1e-3,
+                                   coef_radius=rc)
+        for k in acc:
+            acc[k][:, y0:y1, x0:x1] += part[k]
+        e += part["eps"]
+    for k in acc:
+        assert np.max(np.abs(acc[k] - full[k])) <= 1e-12 * np.sqrt(np.mean(full[k] ** 2)), k
+    assert abs(e - full["eps"]) <= 1e-12 * abs(full["eps"])
