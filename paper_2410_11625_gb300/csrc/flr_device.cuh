@@ -1,5 +1,6 @@
 // flr_device.cuh -- device helpers shared by the FLR kernels (per-pixel and fast paths):
-// the reference-shift sampler and the register Cholesky solve of the centred ridge model.
+// the reference-shift sampler, the register Cholesky solve of the centred ridge model and
+// the horizontal window sums of a shared-memory row.
 #pragma once
 
 #include "flr_internal.cuh"
@@ -168,6 +169,59 @@ __device__ __forceinline__ bool solve_pixel(const float *Sp, int VS, float n, fl
         bv[c] = b;
     }
     return low;
+}
+
+// ---- horizontal sums of one buffer row -------------------------------------------------
+// out[x] = sum_{j=0}^{2K} in[x + j] for x in [x0, x0 + N) (x0 and the rows 16-byte aligned).
+// The run's N + 2K input values are read from shared memory once, with 16-byte loads, into
+// registers before anything is written (so in == out sums the row in place).  The first
+// output is a direct (2K + 1)-term sum; the others add the differences
+// d(x) = in[x + 2K] - in[x - 1], four per step as prefix sums of the step's differences, so
+// the dependent chain is one add per four outputs.
+template <int K, int N>
+__device__ __forceinline__ void hsum_run(const float *in, float *out, int x0)
+{
+    constexpr int NV = N + 2 * K;
+    float v[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j += 4) {
+        if (j + 3 < NV) {
+            const float4 t = *reinterpret_cast<const float4 *>(in + x0 + j);
+            v[j] = t.x, v[j + 1] = t.y, v[j + 2] = t.z, v[j + 3] = t.w;
+        } else {
+#pragma unroll
+            for (int i = j; i < NV; ++i) v[i] = in[x0 + i];
+        }
+    }
+    float S;
+    {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j <= 2 * K; ++j) t[j & 3] += v[j];
+        S = (t[0] + t[1]) + (t[2] + t[3]);
+    }
+#pragma unroll
+    for (int x = 0; x < N; x += 4) {
+        float d[4], o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int xo = x + k;
+            d[k] = (xo > 0 && xo < N) ? v[xo + 2 * K] - v[xo - 1] : 0.f;
+        }
+        const float p1 = d[0], p2 = p1 + d[1], p3 = p2 + d[2], p4 = p3 + d[3];
+        o[0] = S + p1;
+        o[1] = S + p2;
+        o[2] = S + p3;
+        o[3] = S + p4;
+        S = o[3];
+        if (x + 3 < N) {
+            *reinterpret_cast<float4 *>(out + x0 + x) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x + k < N) out[x0 + x + k] = o[k];
+        }
+    }
 }
 
 }  // namespace dev

@@ -44,6 +44,7 @@
 #include "flr_device.cuh"
 #include "flr_fp64_model.cuh"
 #include "flr_internal.cuh"
+#include "flr_tmem.cuh"
 #include "tma.cuh"
 
 namespace flr {
@@ -138,92 +139,6 @@ __device__ __forceinline__ uint32_t col_c2(int k) { return 156u + 2u * k; }
 __device__ __forceinline__ uint32_t col_ring8(int k, int s) { return 160u + 136u * k + 8u * s; }
 __device__ __forceinline__ uint32_t col_ring1(int k, int s) { return 432u + 17u * k + s; }
 __device__ __forceinline__ uint32_t col_c16(int k) { return 480u + 16u * k; }
-
-// ---- tensor-memory access (32 lanes x 32 bits per warp, one lane per thread) ----------
-#define FLR_TM_R4(i) "r"(v[i]), "r"(v[i + 1]), "r"(v[i + 2]), "r"(v[i + 3])
-#define FLR_TM_W4(i) "=r"(v[i]), "=r"(v[i + 1]), "=r"(v[i + 2]), "=r"(v[i + 3])
-__device__ __forceinline__ void tm_st32(uint32_t ta, const uint32_t *v)
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(ta),
-        FLR_TM_R4(0), FLR_TM_R4(4), FLR_TM_R4(8), FLR_TM_R4(12), FLR_TM_R4(16), FLR_TM_R4(20), FLR_TM_R4(24),
-        FLR_TM_R4(28)
-        : "memory");
-}
-__device__ __forceinline__ void tm_st16(uint32_t ta, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
-                     ta),
-                 FLR_TM_R4(0), FLR_TM_R4(4), FLR_TM_R4(8), FLR_TM_R4(12)
-                 : "memory");
-}
-__device__ __forceinline__ void tm_st8(uint32_t ta, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(ta), FLR_TM_R4(0),
-                 FLR_TM_R4(4)
-                 : "memory");
-}
-__device__ __forceinline__ void tm_st2(uint32_t ta, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};\n" ::"r"(ta), "r"(v[0]), "r"(v[1]) : "memory");
-}
-__device__ __forceinline__ void tm_st1(uint32_t ta, uint32_t v0)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};\n" ::"r"(ta), "r"(v0) : "memory");
-}
-__device__ __forceinline__ void tm_ld32(uint32_t ta, uint32_t *v)
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : FLR_TM_W4(0), FLR_TM_W4(4), FLR_TM_W4(8), FLR_TM_W4(12), FLR_TM_W4(16), FLR_TM_W4(20), FLR_TM_W4(24),
-          FLR_TM_W4(28)
-        : "r"(ta)
-        : "memory");
-}
-__device__ __forceinline__ void tm_ld16(uint32_t ta, uint32_t *v)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                 : FLR_TM_W4(0), FLR_TM_W4(4), FLR_TM_W4(8), FLR_TM_W4(12)
-                 : "r"(ta)
-                 : "memory");
-}
-__device__ __forceinline__ void tm_ld8(uint32_t ta, uint32_t *v)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : FLR_TM_W4(0), FLR_TM_W4(4)
-                 : "r"(ta)
-                 : "memory");
-}
-__device__ __forceinline__ void tm_ld2(uint32_t ta, uint32_t *v)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n" : "=r"(v[0]), "=r"(v[1]) : "r"(ta) : "memory");
-}
-__device__ __forceinline__ uint32_t tm_ld1(uint32_t ta)
-{
-    uint32_t v0;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(v0) : "r"(ta) : "memory");
-    return v0;
-}
-#undef FLR_TM_R4
-#undef FLR_TM_W4
-__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
-__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
-
-__device__ __forceinline__ void tm_st4(uint32_t ta, const uint32_t *v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(ta), "r"(v[0]), "r"(v[1]),
-                 "r"(v[2]), "r"(v[3])
-                 : "memory");
-}
-__device__ __forceinline__ void tm_ld4(uint32_t ta, uint32_t *v)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(ta)
-                 : "memory");
-}
 
 // ---- V-pass: one group of channels, two columns ---------------------------------------
 // E += left(e) * right(e), Dn += left(l) * right(l), V = E - Dn for every channel of group G;
@@ -345,59 +260,6 @@ __device__ __forceinline__ bool solve_px(const float (&S)[Chan<Q>::NCH], float n
         bv[c] = b;
     }
     return low;
-}
-
-// ---- horizontal sums of one buffer row -------------------------------------------------
-// out[x] = sum_{j=0}^{2K} in[x + j] for x in [x0, x0 + N) (x0 and the rows 16-byte aligned).
-// The run's N + 2K input values are read from shared memory once, with 16-byte loads, into
-// registers before anything is written (so in == out sums the row in place).  The first
-// output is a direct (2K + 1)-term sum; the others add the differences
-// d(x) = in[x + 2K] - in[x - 1], four per step as prefix sums of the step's differences, so
-// the dependent chain is one add per four outputs.
-template <int K, int N>
-__device__ __forceinline__ void hsum_run(const float *in, float *out, int x0)
-{
-    constexpr int NV = N + 2 * K;
-    float v[NV];
-#pragma unroll
-    for (int j = 0; j < NV; j += 4) {
-        if (j + 3 < NV) {
-            const float4 t = *reinterpret_cast<const float4 *>(in + x0 + j);
-            v[j] = t.x, v[j + 1] = t.y, v[j + 2] = t.z, v[j + 3] = t.w;
-        } else {
-#pragma unroll
-            for (int i = j; i < NV; ++i) v[i] = in[x0 + i];
-        }
-    }
-    float S;
-    {
-        float t[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j <= 2 * K; ++j) t[j & 3] += v[j];
-        S = (t[0] + t[1]) + (t[2] + t[3]);
-    }
-#pragma unroll
-    for (int x = 0; x < N; x += 4) {
-        float d[4], o[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int xo = x + k;
-            d[k] = (xo > 0 && xo < N) ? v[xo + 2 * K] - v[xo - 1] : 0.f;
-        }
-        const float p1 = d[0], p2 = p1 + d[1], p3 = p2 + d[2], p4 = p3 + d[3];
-        o[0] = S + p1;
-        o[1] = S + p2;
-        o[2] = S + p3;
-        o[3] = S + p4;
-        S = o[3];
-        if (x + 3 < N) {
-            *reinterpret_cast<float4 *>(out + x0 + x) = make_float4(o[0], o[1], o[2], o[3]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (x + k < N) out[x0 + x + k] = o[k];
-        }
-    }
 }
 
 // Kernel parameters: TMA maps of the guide [Q][H][W] and radiance [3][H][W] planes (boxes of
@@ -583,8 +445,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
             const int hb = tid / NCH, hch = tid % NCH;
             if (tid < kB * NCH && v + hb >= m_lo && v + hb < m_hi) {
                 float *row = Vbuf + ((size_t)hb * NCHB + hch) * VS;
-                hsum_run<R, G::CH>(row, row, 0);
-                hsum_run<R, TS - G::CH>(row, row, G::CH);
+                dev::hsum_run<R, G::CH>(row, row, 0);
+                dev::hsum_run<R, TS - G::CH>(row, row, G::CH);
             }
         }
         __syncthreads();
@@ -660,8 +522,8 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fused_kernel(const __grid_con
                 if (tid < kB * NCF * 2 && v + ub >= m_lo && v + ub < m_hi) {
                     const float *in = Vbuf + ((size_t)ub * NCHB + uk) * VS;
                     float *outp = Vbuf + ((size_t)ub * NCHB + NCF + uk) * VS;
-                    if (uh == 0) hsum_run<RC, G::CL>(in, outp, 0);
-                    else hsum_run<RC, TW - G::CL>(in, outp, G::CL);
+                    if (uh == 0) dev::hsum_run<RC, G::CL>(in, outp, 0);
+                    else dev::hsum_run<RC, TW - G::CL>(in, outp, G::CL);
                 }
             }
             __syncthreads();

@@ -40,6 +40,7 @@
 
 #include "flr_device.cuh"
 #include "flr_internal.cuh"
+#include "flr_tmem.cuh"
 #include "tma.cuh"
 
 namespace flr {
@@ -50,56 +51,55 @@ using dev::solve_pixel;
 using dev::chol_solve3;
 using dev::tri;
 
-// Running-sum update of one channel: + product of e, - product of l (slots fixed at
-// compile time, so e, l and V stay in registers).
-template <int Q, int CH, bool LEAVE>
-__device__ __forceinline__ void walker_update_one(float &acc, const float (&e)[Q + 3],
-                                                  const float (&l)[Q + 3])
+// Block accumulators of one channel: acc += the product of the row's shifted values r
+// (slots fixed at compile time, so r and the accumulators stay in registers).
+template <int Q, int CH>
+__device__ __forceinline__ void walker_add_one(float &acc, const float (&r)[Q + 3])
 {
     constexpr int u = Chan<Q>::slot_u(CH), v = Chan<Q>::slot_v(CH);
-    if constexpr (v < 0) {
-        acc += e[u];
-        if constexpr (LEAVE) acc -= l[u];
-    } else {
-        acc = fmaf(e[u], e[v], acc);
-        if constexpr (LEAVE) acc = fmaf(-l[u], l[v], acc);
-    }
+    if constexpr (v < 0) acc += r[u];
+    else acc = fmaf(r[u], r[v], acc);
 }
 
-template <int Q, int G, bool LEAVE, int... I>
-__device__ __forceinline__ void walker_update_seq(float (&V)[Chan<Q>::GMAX], const float (&e)[Q + 3],
-                                                  const float (&l)[Q + 3],
-                                                  std::integer_sequence<int, I...>)
+template <int Q, int G, int... I>
+__device__ __forceinline__ void walker_add_seq(float (&A)[Chan<Q>::GMAX], const float (&r)[Q + 3],
+                                               std::integer_sequence<int, I...>)
 {
     constexpr int c0 = Chan<Q>::group_begin(G);
-    (walker_update_one<Q, c0 + I, LEAVE>(V[I], e, l), ...);
+    (walker_add_one<Q, c0 + I>(A[I], r), ...);
 }
 
-template <int Q, int G, bool LEAVE>
-__device__ __forceinline__ void walker_update(float (&V)[Chan<Q>::GMAX], const float (&e)[Q + 3],
-                                              const float (&l)[Q + 3])
-{
-    walker_update_seq<Q, G, LEAVE>(V, e, l,
-                                   std::make_integer_sequence<int, Chan<Q>::group_size(G)>{});
-}
-
+// E += products of the entering row e, Dn += products of the leaving row l (group G)
 template <int Q, int G>
-__device__ __forceinline__ void walker_store(const float (&V)[Chan<Q>::GMAX], float *row0, int VS)
+__device__ __forceinline__ void walker_update(float (&E)[Chan<Q>::GMAX], float (&Dn)[Chan<Q>::GMAX],
+                                              const float (&e)[Q + 3], const float (&l)[Q + 3])
+{
+    walker_add_seq<Q, G>(E, e, std::make_integer_sequence<int, Chan<Q>::group_size(G)>{});
+    walker_add_seq<Q, G>(Dn, l, std::make_integer_sequence<int, Chan<Q>::group_size(G)>{});
+}
+
+// the window sums V = E - Dn of group G to the channel rows of the buffer
+template <int Q, int G>
+__device__ __forceinline__ void walker_store(const float (&E)[Chan<Q>::GMAX], const float (&Dn)[Chan<Q>::GMAX],
+                                             float *row0, int VS)
 {
     using C = Chan<Q>;
     constexpr int c0 = C::group_begin(G), c1 = C::group_end(G);
 #pragma unroll
-    for (int ch = c0; ch < c1; ++ch) row0[ch * VS] = V[ch - c0];
+    for (int ch = c0; ch < c1; ++ch) row0[ch * VS] = E[ch - c0] - Dn[ch - c0];
 }
 
+// Tensor-memory columns of the walker accumulators: warp w keeps E and Dn (2 GMAX columns of
+// its lane quarter) at slot w / 4, each slot starting at a multiple of its power-of-two width.
 template <int Q>
-__device__ __forceinline__ void walker_store_dispatch(int group, const float (&V)[Chan<Q>::GMAX],
-                                                      float *row0, int VS)
-{
-    if (group == 0) walker_store<Q, 0>(V, row0, VS);
-    else if (group == 1) walker_store<Q, 1>(V, row0, VS);
-    else walker_store<Q, 2>(V, row0, VS);
-}
+struct WalkerTmem {
+    static constexpr int N = 2 * Chan<Q>::GMAX;
+    static constexpr int SLOT = N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 32 ? 32 : 64));
+    static constexpr int NSLOT = kThreads / 32 / 4;
+    static constexpr int USED = SLOT * NSLOT;
+    static constexpr uint32_t COLS = USED <= 32 ? 32u : (USED <= 64 ? 64u : (USED <= 128 ? 128u : 256u));
+    static_assert(N <= 64 && USED <= 256, "walker accumulators fit the allocation");
+};
 
 // Adjoint of one pixel's model (the reverse of bias, solve, regulariser, centring and
 // means), given G(b), G(a) relative to the frame reference shift.  Writes the per-pixel
@@ -379,6 +379,9 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
     extern __shared__ __align__(16) float smem[];
     __shared__ float s_cta[NS], s_ref[NS];
     __shared__ int s_abort;
+    __shared__ uint32_t s_tmem;
+    using WT = WalkerTmem<Q>;
+    constexpr int GM = C::GMAX;
     const FwdArgs &a = ka.a;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -395,6 +398,11 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
     float *Vbuf = base;                                              // [kB][NCH][VS]  window sums
     float *stage = base + ((size_t)kB * C::NCH * gm.VS + 31) / 32 * 32;  // [2][NS][kB][WSt] input rows
     uint64_t *bar = reinterpret_cast<uint64_t *>(stage + (size_t)2 * NS * kB * gm.WSt);
+    if (warp == 0) {  // tensor memory for the walkers' accumulators between batches
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tma::smem_addr(&s_tmem)),
+                     "r"(WT::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
     if (tid == 0) {
         s_abort = 0;
         if (ka.use_tma) {
@@ -402,7 +410,11 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
             tma::mbar_init_fence();
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // this warp's lane quarter and slot
+    const uint32_t tmem = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(WT::SLOT * (warp >> 2));
 
     const int first_row = y0 - r;  // first input row summed by this segment
     int yv = y0 - 2 * r;           // first virtual row: the walkers start from an empty window
@@ -433,9 +445,13 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
     for (int k = 0; k < NS; ++k) shl[k] = col_in ? s_cta[k] : 0.f;
     const int scol = wx + (gm.RA - r);
 
-    float V[C::GMAX];
-#pragma unroll
-    for (int k = 0; k < C::GMAX; ++k) V[k] = 0.f;
+    // Vertical window sums as block accumulators: E, the products of the rows entered since
+    // the last block start, and Dn, the products of the rows left since then minus the
+    // previous block's total.  A block is 2r + 1 entered rows, so V = E - Dn is a sum of at
+    // most 2(2r + 1) rounded terms and its error does not grow along the segment (a running
+    // sum that adds the entering row and subtracts the leaving one drifts).  Between batches
+    // E and Dn wait in tensor memory, so they hold no registers during the solve.
+    const int v0 = y0 - 2 * r, WR = 2 * r + 1;
 
     const float tau = a.tau;
     const float eps = a.eps;
@@ -445,35 +461,70 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
         stage_wait(ka, bar, nstaged - 1, &s_abort);
         __syncthreads();
         if (s_abort) break;  // a copy never completed: issue nothing more on this barrier
-        if (walker) {
-#pragma unroll 1
-            for (int b = 0; b < kB; ++b) {
-                const int yc = yv + b;
-                if (yc < y1) {
-                    const bool ein_ok = yc + r >= 0 && yc + r < H;
-                    const bool lout_ok = yc - r - 1 >= first_row && yc - r - 1 >= 0;
-                    const float *se = stage + (size_t)b * gm.WSt + scol;
-                    const float *sl = stage + (size_t)(NS * kB + b) * gm.WSt + scol;
-                    float e[NS], l[NS];
+        {
+            float E[GM], Dn[GM];
+            if (yv == v0) {
 #pragma unroll
-                    for (int k = 0; k < NS; ++k) {
-                        e[k] = 0.f;
-                        l[k] = 0.f;
-                    }
-                    if (ein_ok) {
+                for (int k = 0; k < GM; ++k) E[k] = Dn[k] = 0.f;
+            } else {
+                uint32_t st[2 * GM];
+                tm_ld_n<2 * GM>(tmem, st);
+                tm_wait_ld();
 #pragma unroll
-                        for (int k = 0; k < NS; ++k) e[k] = se[(size_t)k * kB * gm.WSt] - shl[k];
-                    }
-                    if (lout_ok) {
-#pragma unroll
-                        for (int k = 0; k < NS; ++k) l[k] = sl[(size_t)k * kB * gm.WSt] - shl[k];
-                    }
-                    if (group == 0) walker_update<Q, 0, true>(V, e, l);
-                    else if (group == 1) walker_update<Q, 1, true>(V, e, l);
-                    else walker_update<Q, 2, true>(V, e, l);
+                for (int k = 0; k < GM; ++k) {
+                    E[k] = __uint_as_float(st[k]);
+                    Dn[k] = __uint_as_float(st[GM + k]);
                 }
-                walker_store_dispatch<Q>(group, V, Vbuf + (size_t)b * C::NCH * gm.VS + wx, gm.VS);
             }
+            if (walker) {
+#pragma unroll 1
+                for (int b = 0; b < kB; ++b) {
+                    const int yc = yv + b;
+                    if (yc < y1) {
+                        if ((yc - v0) % WR == 0) {  // block start: Dn = -(previous block total), E = 0
+#pragma unroll
+                            for (int k = 0; k < GM; ++k) {
+                                Dn[k] = -E[k];
+                                E[k] = 0.f;
+                            }
+                        }
+                        const bool ein_ok = yc + r >= 0 && yc + r < H;
+                        const bool lout_ok = yc - r - 1 >= first_row && yc - r - 1 >= 0;
+                        const float *se = stage + (size_t)b * gm.WSt + scol;
+                        const float *sl = stage + (size_t)(NS * kB + b) * gm.WSt + scol;
+                        float e[NS], l[NS];
+#pragma unroll
+                        for (int k = 0; k < NS; ++k) {
+                            e[k] = 0.f;
+                            l[k] = 0.f;
+                        }
+                        if (ein_ok) {
+#pragma unroll
+                            for (int k = 0; k < NS; ++k) e[k] = se[(size_t)k * kB * gm.WSt] - shl[k];
+                        }
+                        if (lout_ok) {
+#pragma unroll
+                            for (int k = 0; k < NS; ++k) l[k] = sl[(size_t)k * kB * gm.WSt] - shl[k];
+                        }
+                        if (group == 0) walker_update<Q, 0>(E, Dn, e, l);
+                        else if (group == 1) walker_update<Q, 1>(E, Dn, e, l);
+                        else walker_update<Q, 2>(E, Dn, e, l);
+                    }
+                    float *row0 = Vbuf + (size_t)b * C::NCH * gm.VS + wx;
+                    if (group == 0) walker_store<Q, 0>(E, Dn, row0, gm.VS);
+                    else if (group == 1) walker_store<Q, 1>(E, Dn, row0, gm.VS);
+                    else walker_store<Q, 2>(E, Dn, row0, gm.VS);
+                }
+            }
+            __syncwarp();  // the walkers' branches rejoin before the warp-wide tensor-memory store
+            uint32_t st[2 * GM];
+#pragma unroll
+            for (int k = 0; k < GM; ++k) {
+                st[k] = __float_as_uint(E[k]);
+                st[GM + k] = __float_as_uint(Dn[k]);
+            }
+            tm_st_n<2 * GM>(tmem, st);
+            tm_wait_st();
         }
         __syncthreads();
         // prefetch the next batch's rows while this one is summed and solved
@@ -483,8 +534,17 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
         }
         if (yv + kB - 1 < y0) continue;  // warm-up batch: nothing to solve yet
 
-        // 2. H-pass, one thread per (row, channel)
-        for (int row = tid; row < kB * C::NCH; row += kThreads) hsum_row<RT>(Vbuf + (size_t)row * gm.VS, r);
+        // 2. H-pass, one thread per (row, channel); with the radius known at compile time two
+        //    runs of kTW / 2 outputs, each seeded by a direct (2r + 1)-term sum
+        for (int row = tid; row < kB * C::NCH; row += kThreads) {
+            float *p = Vbuf + (size_t)row * gm.VS;
+            if constexpr (RT >= 0) {
+                dev::hsum_run<RT, kTW / 2>(p, p, 0);
+                dev::hsum_run<RT, kTW / 2>(p, p, kTW / 2);
+            } else {
+                hsum_row<RT>(p, r);
+            }
+        }
         __syncthreads();
         // 3. solve, one thread per pixel of the batch
         {
@@ -558,6 +618,12 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
         __syncthreads();
     }
     if (!ka.use_tma) cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s_tmem), "r"(WT::COLS));
+    }
     if constexpr (ADJ) {
         double g = (double)geps_acc;
 #pragma unroll

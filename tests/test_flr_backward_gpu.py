@@ -1,13 +1,16 @@
 """Parity of the CUDA FLR backward pass (flr_backward, through the C ABI) with the FP64
 oracle's analytic gradient (itself pinned to finite differences in test_oracle_adjoint).
 
-Gradient bar, per gradient array: max |err| <= 1e-3 * RMS(ref) and RMS(err) <= 1e-4 * RMS(ref);
+Gradient bar, per gradient array: max |err| <= 7e-4 * RMS(ref) and RMS(err) <= 2e-5 * RMS(ref);
 d/d eps within 1e-4 relative.  Derivation: in a window where a model guide is flat, the
 guide gradient is the difference of two box sums of 1/eps-scaled adjoint terms
 (2 sum_k GS_k x_j and 2 sum_k GS_k mu_k), which cancel in exact arithmetic; their FP32
-error (u_eff ~ 1e-6 after the running sums) times the 1/eps gain (~1e3 at eps = 1e-3)
-leaves ~1e-3 of the gradient's scale at isolated pixels.  The image metric of the forward
-tests (relative to the value, floored at 1% of RMS) is reported but not used as the bar.
+error (a few units of rounding of the window sums, which the block accumulators of the
+forward's vertical pass keep from growing along a segment) times the 1/eps gain (~1e3 at
+eps = 1e-3) leaves a few 1e-4 of the gradient's scale at isolated pixels.  Measured: max
+4.6e-4 (rendered 1080p blocks and 128x128 frames), RMS at most 1e-5.  The image metric of
+the forward tests (relative to the value, floored at 1% of RMS) is printed but not used as
+the bar.
 """
 import numpy as np
 import pytest
@@ -18,7 +21,7 @@ from helpers import rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
-MAX_TOL, RMS_TOL, EPS_TOL = 1e-3, 1e-4, 1e-4
+MAX_TOL, RMS_TOL, EPS_TOL = 7e-4, 2e-5, 1e-4
 
 
 @pytest.fixture(scope="module")
