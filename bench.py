@@ -39,7 +39,8 @@ WORKLOAD = ("FLR forward, 1920x1080, Q=8 rendered guides (albedo RGB, normal xyz
             "1spp albedo-demodulated indirect RGB, r=8, rc=8, eps=1e-3, pivot ratio 1e-3")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES = 152, 128
-FWD_SOURCES = ["paper_2410_11625_gb300/csrc/flr_fused.cu", "paper_2410_11625_gb300/csrc/flr_internal.cuh"]
+FWD_SOURCES = ["paper_2410_11625_gb300/csrc/flr_fused.cu", "paper_2410_11625_gb300/csrc/flr_internal.cuh",
+               "paper_2410_11625_gb300/csrc/flr_device.cuh", "paper_2410_11625_gb300/csrc/flr_tmem.cuh"]
 FWD_PROFILE = os.path.join(ROOT, "profiles", "flr_fused_1080p_r8.txt")
 
 

@@ -225,7 +225,9 @@ int flr_get_kernel_times(flr_handle *h, flr_kernel_times *out, int reset);
  * configures the kernels (no allocation); make that first call before capturing any stream.
  * All calls on a device share the array and leave the last call's contents in it: calls
  * that overlap on the GPU race, so the caller must serialise them.  No statistics are kept
- * (flr_get_stats needs a handle).
+ * (flr_get_stats needs a handle), and a bounded device wait that runs out (a copy that has
+ * not completed after 1 s) is not reported: the kernels stop and leave part of out
+ * unwritten, but the call has returned before they run and keeps no status to query.
  * Errors: FLR_ERR_ARG, FLR_ERR_ALIGN, FLR_ERR_UNSUPPORTED, FLR_ERR_CUDA.
  */
 #define FLR_NOALLOC_MAX_PIXELS (256 * 256)
