@@ -401,6 +401,16 @@ int flnr_destroy(flnr_net *net);
 int flnr_set_weights(flnr_net *net, const float *host, size_t count);
 int flnr_get_weights(flnr_net *net, float *host, size_t count);
 
+/* The optimiser state, for checkpoints: the master weights, then Adam's first and second
+ * moments, each flnr_param_count(nout) floats (count = 3 * flnr_param_count(nout), host
+ * memory); synchronous.  flnr_set_state restores all three exactly and refreshes the
+ * bfloat16 weight copies, so training resumed from a saved state continues as it would have
+ * without the interruption (given the same step count, learning rate and data).  The paper
+ * has no counterpart: checkpointing is part of training the network it describes (Sec. 3.3).
+ * Errors: FLR_ERR_ARG (count), FLR_ERR_CUDA. */
+int flnr_get_state(flnr_net *net, float *host, size_t count);
+int flnr_set_state(flnr_net *net, const float *host, size_t count);
+
 /*
  * Forward pass on N images: in [N][11][H][W] planar float32 (device), guide_out
  * [N][nout][H][W] planar float32 (device; NULL keeps the result only inside the network).

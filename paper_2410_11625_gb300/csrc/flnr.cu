@@ -1981,6 +1981,29 @@ int flnr_get_weights(flnr_net *n, float *host, size_t count)
     return cudaMemcpy(host, n->w, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
 }
 
+int flnr_get_state(flnr_net *n, float *host, size_t count)
+{
+    if (!n || !host || count != 3 * n->nparam) return FLR_ERR_ARG;
+    const size_t b = n->nparam * sizeof(float);
+    if (cudaMemcpy(host, n->w, b, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host + n->nparam, n->m, b, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host + 2 * n->nparam, n->v, b, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FLR_ERR_CUDA;
+    return FLR_OK;
+}
+
+int flnr_set_state(flnr_net *n, const float *host, size_t count)
+{
+    if (!n || !host || count != 3 * n->nparam) return FLR_ERR_ARG;
+    const size_t b = n->nparam * sizeof(float);
+    if (cudaMemcpy(n->w, host, b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(n->m, host + n->nparam, b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(n->v, host + 2 * n->nparam, b, cudaMemcpyHostToDevice) != cudaSuccess)
+        return FLR_ERR_CUDA;
+    if (refresh_weights(n, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FLR_ERR_CUDA;
+    return FLR_OK;
+}
+
 int flnr_get_grads(flnr_net *n, float *host, size_t count)
 {
     if (!n || !host || count != n->nparam) return FLR_ERR_ARG;

@@ -9,18 +9,23 @@ namespace flr {
 namespace dev {
 
 // Mean of the inputs over a kShiftSamples^2 grid of pixel centres of [ya,yb) x [xa,xb),
-// computed by one warp in a fixed order (identical in every CTA for the same region).
+// computed by one warp in a fixed order (identical in every CTA for the same region): lane l
+// adds samples l, l + 32, ... in turn, then a shuffle tree.  The sample loop has a fixed
+// trip count and is unrolled, so all of a lane's loads can be in flight at once.
 template <int Q>
 __device__ void sample_mean(float *dst, const float *__restrict__ guide,
                             const float *__restrict__ rad, int H, int W, int ya, int yb, int xa,
                             int xb, int lane)
 {
     constexpr int NS = kShiftSamples;
+    static_assert(NS * NS % 32 == 0, "every lane takes the same number of samples");
     const size_t plane = (size_t)H * W;
     float acc[Q + 3];
 #pragma unroll
     for (int k = 0; k < Q + 3; ++k) acc[k] = 0.f;
-    for (int s = lane; s < NS * NS; s += 32) {
+#pragma unroll
+    for (int it = 0; it < NS * NS / 32; ++it) {
+        const int s = lane + 32 * it;
         const int iy = s / NS, ix = s % NS;
         const int y = ya + (int)(((long long)(2 * iy + 1) * (yb - ya)) / (2 * NS));
         const int x = xa + (int)(((long long)(2 * ix + 1) * (xb - xa)) / (2 * NS));

@@ -37,6 +37,8 @@ def _lib():
         lib.flnr_set_weights.argtypes = [vp, vp, ctypes.c_size_t]
         lib.flnr_get_weights.argtypes = [vp, vp, ctypes.c_size_t]
         lib.flnr_get_grads.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.flnr_get_state.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.flnr_set_state.argtypes = [vp, vp, ctypes.c_size_t]
         lib.flnr_guide_forward.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         lib.flnr_guide_backward.argtypes = [vp, vp, vp, vp]
         lib.flnr_zero_grads.argtypes = [vp, vp]
@@ -46,7 +48,8 @@ def _lib():
         lib.flnr_layer.argtypes = [vp, ip, ip, vp, vp, vp, vp, ip, ip, ip, vp]
         lib.flnr_status.argtypes = [vp]
         for name in ("flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights", "flnr_get_grads",
-                     "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_adam_step",
+                     "flnr_get_state", "flnr_set_state", "flnr_guide_forward", "flnr_guide_backward",
+                     "flnr_zero_grads", "flnr_adam_step",
                      "flnr_l1_loss", "flnr_smape_loss", "flnr_layer", "flnr_status"):
             getattr(lib, name).restype = ctypes.c_int
         _bound = True
@@ -128,6 +131,19 @@ class FLNR:
         flat = np.empty(self.count, np.float32)
         _flr._check(_lib().flnr_get_weights(self._h, flat.ctypes.data, flat.size), "flnr_get_weights")
         return flat
+
+    def get_state(self):
+        """Master weights, Adam first and second moments: float32 [3 * count] (host)."""
+        flat = np.empty(3 * self.count, np.float32)
+        _flr._check(_lib().flnr_get_state(self._h, flat.ctypes.data, flat.size), "flnr_get_state")
+        return flat
+
+    def set_state(self, state):
+        """Restores what get_state returned (weights and Adam moments, exactly)."""
+        flat = np.ascontiguousarray(state, np.float32)
+        if flat.size != 3 * self.count:
+            raise ValueError(f"expected {3 * self.count} floats, got {flat.size}")
+        _flr._check(_lib().flnr_set_state(self._h, flat.ctypes.data, flat.size), "flnr_set_state")
 
     def grads(self):
         flat = np.empty(self.count, np.float32)

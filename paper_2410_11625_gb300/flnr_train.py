@@ -13,12 +13,16 @@ One training step (batch B of c x c crops):
   parameter gradients                     flnr_guide_backward
   Adam on the FP32 master weights         flnr_adam_step (BF16 copies refreshed)
 Every step runs in the library's kernels; this module samples crops on the host and
-moves them to the device.  Data: `synth.render` scenes with 1 spp inputs and high-spp
+moves them to the device, and writes and reads training checkpoints (save_checkpoint,
+load_checkpoint: weights, Adam moments, step count, learning rate, sampler state).  Data: `synth.render` scenes with 1 spp inputs and high-spp
 references; held-out evaluation scenes use seeds >= 1,000,000.
 """
 from __future__ import annotations
 
+import json
 import math
+import struct
+import zlib
 
 import numpy as np
 
@@ -168,18 +172,92 @@ class Trainer:
         self.net.adam_step(self.steps, lr=self.lr, stream_of=self.x)
         return loss
 
-    def train(self, scenes, steps, seed=0, lr_final=None, log_every=0):
-        """`steps` Adam steps on random crops of `scenes`; cosine decay to lr_final."""
-        rng = np.random.default_rng(seed)
+    def train(self, scenes, steps, seed=0, lr_final=None, log_every=0, rng=None, t0=0, total=None):
+        """`steps` Adam steps on random crops of `scenes`, with the learning rate on a cosine
+        from self.lr down to lr_final over `total` steps (default: `steps`), starting at step
+        t0 of that schedule.  Crops are drawn from `rng` (a numpy Generator; default: a new
+        one seeded with `seed`).  A run resumed from a checkpoint passes the generator that
+        load_checkpoint returns and t0 = the steps already taken, so that it draws and
+        schedules exactly what the uninterrupted run would have."""
+        rng = np.random.default_rng(seed) if rng is None else rng
+        total = steps if total is None else total
         lr0, lr1 = self.lr, (self.lr if lr_final is None else lr_final)
         losses = []
         for t in range(steps):
-            self.lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * t / max(steps, 1)))
+            self.lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * (t0 + t) / max(total, 1)))
             loss = self.step(*sample_batch(rng, scenes, self.B, self.c))
             if log_every and (t % log_every == 0 or t == steps - 1):
-                losses.append((t, float(loss.item())))
+                losses.append((t0 + t, float(loss.item())))
         self.lr = lr0
         return losses
+
+
+# ---- checkpoints ---------------------------------------------------------------------
+# A file holds everything a training run needs to continue where it stopped: the network's
+# FP32 master weights and Adam moments (flnr_get_state), the Adam step count, the base
+# learning rate and the state of the crop sampler's random generator.  Layout: the 8-byte
+# magic, a little-endian u32 header length, the header (UTF-8 JSON), the state as
+# little-endian float32, and a u32 CRC-32 of everything before it.
+CKPT_MAGIC = b"FLNRCKP1"
+CKPT_VERSION = 1
+
+
+def pack_checkpoint(state, meta):
+    """Bytes of a checkpoint: state (float32 array) and meta (JSON-serialisable dict)."""
+    state = np.ascontiguousarray(state, dtype="<f4")
+    head = dict(meta, version=CKPT_VERSION, floats=int(state.size))
+    hj = json.dumps(head, sort_keys=True).encode("utf-8")
+    body = CKPT_MAGIC + struct.pack("<I", len(hj)) + hj + state.tobytes()
+    return body + struct.pack("<I", zlib.crc32(body) & 0xFFFFFFFF)
+
+
+def unpack_checkpoint(blob):
+    """(state float32 array, meta dict) from pack_checkpoint's bytes; raises ValueError on a
+    wrong magic, version, length or CRC."""
+    if len(blob) < len(CKPT_MAGIC) + 8 or blob[:len(CKPT_MAGIC)] != CKPT_MAGIC:
+        raise ValueError("not an FLNR checkpoint")
+    body, (crc,) = blob[:-4], struct.unpack("<I", blob[-4:])
+    if zlib.crc32(body) & 0xFFFFFFFF != crc:
+        raise ValueError("checkpoint CRC mismatch (file damaged)")
+    (hl,) = struct.unpack("<I", body[len(CKPT_MAGIC):len(CKPT_MAGIC) + 4])
+    p = len(CKPT_MAGIC) + 4
+    meta = json.loads(body[p:p + hl].decode("utf-8"))
+    if meta.get("version") != CKPT_VERSION:
+        raise ValueError(f"checkpoint version {meta.get('version')} (expected {CKPT_VERSION})")
+    data = body[p + hl:]
+    if len(data) != 4 * meta["floats"]:
+        raise ValueError("checkpoint length does not match its header")
+    return np.frombuffer(data, dtype="<f4").astype(np.float32), meta
+
+
+def save_checkpoint(path, trainer, rng=None):
+    """Writes trainer's optimiser state, step count and base learning rate, and the state of
+    rng (the crop sampler's numpy Generator), to path (replaced atomically)."""
+    import os
+    meta = {"outputs": trainer.outputs, "params": trainer.net.count, "steps": trainer.steps, "lr": trainer.lr,
+            "rng": None if rng is None else rng.bit_generator.state}
+    blob = pack_checkpoint(trainer.net.get_state(), meta)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        f.write(blob)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path, trainer):
+    """Restores what save_checkpoint wrote into trainer (same network size); returns the
+    crop sampler's generator in its saved state (None if none was saved)."""
+    with open(path, "rb") as f:
+        state, meta = unpack_checkpoint(f.read())
+    if meta["outputs"] != trainer.outputs or meta["params"] != trainer.net.count:
+        raise ValueError("checkpoint is for a network of another size")
+    trainer.net.set_state(state)
+    trainer.steps = int(meta["steps"])
+    trainer.lr = float(meta["lr"])
+    if meta.get("rng") is None:
+        return None
+    rng = np.random.Generator(getattr(np.random, meta["rng"]["bit_generator"])())
+    rng.bit_generator.state = meta["rng"]
+    return rng
 
 
 def psnr(img, ref):

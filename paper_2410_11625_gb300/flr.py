@@ -24,6 +24,7 @@ EXPORTS = ("flr_create", "flr_destroy", "flr_reserve", "flr_denoise", "flr_denoi
            "flr_fast_denoise_batch", "flr_fast_batch_status", "flr_barrier_selftest",
            "flr_mbarrier_selftest", "flr_host_band_plan",
            "flnr_param_count", "flnr_create", "flnr_destroy", "flnr_set_weights", "flnr_get_weights",
+           "flnr_get_state", "flnr_set_state",
            "flnr_guide_forward", "flnr_guide_backward", "flnr_zero_grads", "flnr_get_grads",
            "flnr_adam_step", "flnr_l1_loss", "flnr_smape_loss", "flnr_layer", "flnr_status", "flr_fp32_fma_peak")
 BATCH_TIMEOUT = 1

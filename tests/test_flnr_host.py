@@ -1,7 +1,8 @@
 """Host-side parts of FLNR on the CPU: the layer table agrees with the oracle's network
 and the library's parameter count, the flat parameter layout round-trips, the seeded
 initialisation matches the oracle's, training crops are windows of the rendered scenes,
-PSNR and the bench's multiply-accumulate count follow their definitions."""
+PSNR and the bench's multiply-accumulate count follow their definitions, and the training
+checkpoint format round-trips and detects damage."""
 import numpy as np
 import pytest
 
@@ -86,3 +87,26 @@ def test_bench_multiply_accumulates_per_pixel():
              "d0a": 1, "d0b": 1, "o0": 1, "o1": 1}
     macs = sum(ci * co * k * k / scale[n] for n, ci, co, k in flnr.LAYERS)
     assert bench.FLNR_MACS_PER_PIXEL == pytest.approx(macs) == pytest.approx(36528.0)
+
+
+def test_checkpoint_file_round_trip_and_damage_detection():
+    """The checkpoint format (magic, JSON header, float32 state, CRC-32) round-trips the state,
+    the metadata and a numpy generator's state exactly, and rejects damaged files."""
+    from paper_2410_11625_gb300 import flnr_train as ft
+    state = np.random.default_rng(0).standard_normal(3 * 1000).astype(np.float32)
+    rng = np.random.default_rng(5)
+    rng.integers(10, size=7)
+    blob = ft.pack_checkpoint(state, {"steps": 3, "lr": 2e-3, "rng": rng.bit_generator.state})
+    got, meta = ft.unpack_checkpoint(blob)
+    assert np.array_equal(got, state) and meta["steps"] == 3 and meta["lr"] == 2e-3
+    again = np.random.Generator(getattr(np.random, meta["rng"]["bit_generator"])())
+    again.bit_generator.state = meta["rng"]
+    assert np.array_equal(again.integers(1 << 30, size=8), rng.integers(1 << 30, size=8))
+    damaged = bytearray(blob)
+    damaged[len(blob) // 2] ^= 0x10
+    with pytest.raises(ValueError, match="CRC"):
+        ft.unpack_checkpoint(bytes(damaged))
+    with pytest.raises(ValueError, match="not an FLNR checkpoint"):
+        ft.unpack_checkpoint(b"XXXXXXXX" + blob[8:])
+    with pytest.raises(ValueError):
+        ft.unpack_checkpoint(blob[:-9] + blob[-4:])  # truncated payload, CRC no longer matches

@@ -60,3 +60,33 @@ def test_training_is_deterministic(data):
         ws.append(tr.net.get_weights())
         tr.net.close()
     assert np.array_equal(ws[0], ws[1])
+
+
+@pytest.mark.parametrize("outputs", [8, 16])
+def test_resumed_training_equals_uninterrupted(data, tmp_path, outputs):
+    """Checkpoint and resume: 3 steps, save (weights, Adam moments, step count, learning
+    rate, crop sampler state), a new trainer loads it and takes 3 more steps; its weights
+    and Adam moments equal, bit for bit, those of 6 uninterrupted steps of the same recipe
+    (the steps are deterministic, and the resumed run draws the same crops and learning
+    rates)."""
+    scenes, _ = data
+    kw = dict(batch=4, crop=64, lr=2e-3)
+    ref = flnr_train.Trainer(flnr.init_weights(0, outputs), **kw)
+    ref.train(scenes, 6, lr_final=1e-4, rng=np.random.default_rng(7))
+    want = ref.net.get_state()
+    ref.net.close()
+
+    first = flnr_train.Trainer(flnr.init_weights(0, outputs), **kw)
+    rng = np.random.default_rng(7)
+    first.train(scenes, 3, lr_final=1e-4, rng=rng, total=6)
+    path = tmp_path / "flnr.ckpt"
+    flnr_train.save_checkpoint(path, first, rng)
+    first.net.close()
+
+    resumed = flnr_train.Trainer(flnr.init_weights(1, outputs), **kw)  # other weights: all must come from the file
+    rng2 = flnr_train.load_checkpoint(path, resumed)
+    assert resumed.steps == 3
+    resumed.train(scenes, 3, lr_final=1e-4, rng=rng2, t0=3, total=6)
+    got = resumed.net.get_state()
+    resumed.net.close()
+    assert np.array_equal(got, want)
