@@ -290,6 +290,86 @@ __global__ void __launch_bounds__(256) bwd_contract_kernel(const BwdArgs a)
     }
 }
 
+// The same contraction for four consecutive pixels of a row per thread (W a multiple of 4,
+// every plane 16-byte aligned): one 16-byte load per plane and four pixels instead of four
+// 4-byte loads, and each output channel's gradient formed from its own planes in turn, so
+// that a thread holds four pixels' inputs and one channel's operands at a time.  Every
+// pixel's arithmetic (operands, order of the fused multiply-adds) is that of
+// bwd_contract_kernel, so the results are the same bit for bit.
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c)
+{
+    return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z), fmaf(a.w, b.w, c.w));
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) bwd_contract4_kernel(const BwdArgs a)
+{
+    using C = Chan<Q>;
+    const int H = a.H, W = a.W;
+    const size_t plane = (size_t)H * W;
+    const size_t nq = plane / 4;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = 4 * q;
+        const int y = (int)(p / W), x0 = (int)(p % W);
+        float4 xs[Q], ys[3], gc[3];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float4 v = ld4(a.guide + i * plane + p);
+            const float s = a.shift[i];
+            xs[i] = make_float4(v.x - s, v.y - s, v.z - s, v.w - s);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 v = ld4(a.rad + c * plane + p);
+            const float s = a.shift[Q + c];
+            ys[c] = make_float4(v.x - s, v.y - s, v.z - s, v.w - s);
+            gc[c] = ld4(a.g + c * plane + p);
+        }
+        float inv_m[4] = {1.f, 1.f, 1.f, 1.f};
+        if (a.rc > 0) {
+            const float ny = (float)(min(y + a.rc, H - 1) - max(y - a.rc, 0) + 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = x0 + k;
+                const float nx = (float)(min(x + a.rc, W - 1) - max(x - a.rc, 0) + 1);
+                inv_m[k] = 1.0f / (ny * nx);
+            }
+        }
+        const float *BS = a.BS;
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {  // one guide channel's 15 planes in flight at a time
+            float4 d = ld4(BS + (C::X0 + i) * plane + p);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const int t = (i <= j ? C::xx(i, j) : C::xx(j, i));
+                const float4 b = ld4(BS + t * plane + p);
+                d = fma4(make_float4(2.f * b.x, 2.f * b.y, 2.f * b.z, 2.f * b.w), xs[j], d);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d = fma4(ld4(BS + C::xy(i, c) * plane + p), ys[c], d);
+            float4 dz = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dz = fma4(ld4(a.BA + (3 * (i + 1) + c) * plane + p), gc[c], dz);
+            dz = make_float4(dz.x * inv_m[0], dz.y * inv_m[1], dz.z * inv_m[2], dz.w * inv_m[3]);
+            if (a.separate_map) {
+                st4(a.grad_guide + i * plane + p, d);
+                if (a.grad_map) st4(a.grad_map + i * plane + p, dz);
+            } else {
+                st4(a.grad_guide + i * plane + p, make_float4(d.x + dz.x, d.y + dz.y, d.z + dz.z, d.w + dz.w));
+            }
+        }
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            float4 d = ld4(BS + (C::Y0 + c) * plane + p);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) d = fma4(ld4(BS + C::xy(i, c) * plane + p), xs[i], d);
+            st4(a.grad_rad + c * plane + p, d);
+        }
+    }
+}
+
 int elem_grid(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
 
 }  // namespace
@@ -354,6 +434,23 @@ cudaError_t launch_box_sum(const float *in, float *out, int nplanes, int H, int 
 
 cudaError_t launch_bwd_contract(int q, const BwdArgs &a, cudaStream_t st)
 {
+    auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if ((a.W & 3) == 0 && al(a.guide) && al(a.rad) && al(a.g) && al(a.BS) && al(a.BA) && al(a.grad_guide) &&
+        al(a.grad_map) && al(a.grad_rad)) {
+        const int grid4 = (int)(((size_t)a.H * a.W / 4 + 255) / 256);  // one thread per four pixels
+        switch (q) {
+        case 1: bwd_contract4_kernel<1><<<grid4, 256, 0, st>>>(a); break;
+        case 2: bwd_contract4_kernel<2><<<grid4, 256, 0, st>>>(a); break;
+        case 3: bwd_contract4_kernel<3><<<grid4, 256, 0, st>>>(a); break;
+        case 4: bwd_contract4_kernel<4><<<grid4, 256, 0, st>>>(a); break;
+        case 5: bwd_contract4_kernel<5><<<grid4, 256, 0, st>>>(a); break;
+        case 6: bwd_contract4_kernel<6><<<grid4, 256, 0, st>>>(a); break;
+        case 7: bwd_contract4_kernel<7><<<grid4, 256, 0, st>>>(a); break;
+        case 8: bwd_contract4_kernel<8><<<grid4, 256, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int grid = (int)(((size_t)a.H * a.W + 255) / 256);  // one thread per pixel
     switch (q) {
     case 1: bwd_contract_kernel<1><<<grid, 256, 0, st>>>(a); break;
