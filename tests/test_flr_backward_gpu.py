@@ -114,20 +114,22 @@ def test_autograd_function_matches_backward(flr):
     f.close()
 
 
-def test_backward_full_hd_sampled_blocks(flr):
-    """1920x1080, r = rc = 8 (the benchmark's frame size and radii), so the adjoint runs with
-    the launch geometry of a full frame: several row segments per strip, the 71-plane box
+@pytest.mark.parametrize("H,W", [(1080, 1920), (2160, 3840)])
+def test_backward_full_hd_sampled_blocks(flr, H, W):
+    """1920x1080 (the benchmark's frame size) and 3840x2160, r = rc = 8, so the adjoint runs
+    with the launch geometry of a full frame: several row segments per strip, the 71-plane box
     sums over many tiles.  grad_out is nonzero only in 12 blocks of 32 x 32 (corners, edges,
     interior).  The gradient of <grad_out, I> then lives in each block plus its radius-(r + rc)
     halo, and depends only on inputs there, so the oracle's adjoint of that crop gives it
     exactly; the crops are kept disjoint and the gradients are compared on them, and must be
     zero (up to rounding residue of the sliding sums) everywhere else."""
     import torch
-    H, W, r, rc, B = 1080, 1920, 8, 8, 32
+    r, rc, B = 8, 8, 32
     R = r + rc
     g, y = synth.render(2, H, W)
-    blocks = [(0, 0), (0, W - B), (H - B, 0), (H - B, W - B), (0, 960), (H - B, 480), (512, 0),
-              (700, W - B), (200, 300), (300, 1200), (600, 800), (850, 1500)]
+    k = H // 1080  # the 1080p positions, scaled to the frame
+    blocks = [(0, 0), (0, W - B), (H - B, 0), (H - B, W - B), (0, 960 * k), (H - B, 480 * k), (512 * k, 0),
+              (700 * k, W - B), (200 * k, 300 * k), (300 * k, 1200 * k), (600 * k, 800 * k), (850 * k, 1500 * k)]
     crops = [(max(0, by - R), min(H, by + B + R), max(0, bx - R), min(W, bx + B + R)) for by, bx in blocks]
     for i, a in enumerate(crops):  # disjoint crops: the blocks' gradients do not add up anywhere
         for b in crops[i + 1:]:

@@ -141,12 +141,13 @@ def test_small_eps_reports_and_reduces_error(flr):
     assert rms(got1) < rms(got0)
 
 
-def test_rendered_full_hd_sampled_blocks(flr):
-    """1920x1080, r = rc = 8 (the benchmark's launch): 16 blocks, including corners and
-    edges, checked against the oracle run on the block plus its radius-(r + rc) halo,
-    which contains every input the block's outputs depend on."""
+@pytest.mark.parametrize("H,W", [(1080, 1920), (2160, 3840)])
+def test_rendered_full_hd_sampled_blocks(flr, H, W):
+    """1920x1080 (the benchmark's launch) and 3840x2160, r = rc = 8: 16 blocks, including
+    corners and edges, checked against the oracle run on the block plus its radius-(r + rc)
+    halo, which contains every input the block's outputs depend on."""
     import torch
-    H, W, r, rc = 1080, 1920, 8, 8
+    r, rc = 8, 8
     g, y = synth.render(1, H, W)
     f = flr.FLR(q=8, radius=r, coef_radius=rc, eps=1e-3)
     out = f.denoise(to_dev(g), to_dev(y))
