@@ -1111,18 +1111,30 @@ struct WgradArgs {
 };
 
 // gw[o][i][tap] += sum over the CTAs, in CTA order, of their partial (tap CIN + i, o): the
-// weight gradient without atomics, the same every run
+// weight gradient without atomics, the same every run.  Thread f takes element f of the
+// partials' own layout ((tap CIN + i) COUT + o), so that the threads of a warp read
+// consecutive addresses of each CTA's partial; the loads of several CTAs are in flight at once
+// while the additions keep CTA order.
 template <int CIN, int COUT, int KS>
 __global__ void wgrad_reduce_kernel(const float *part, int nctas, float *gw, int cin_true, int cout_true)
 {
     constexpr int M = KS * KS * CIN;
-    const int total = cout_true * cin_true * KS * KS;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        const int tap = e % (KS * KS), i = (e / (KS * KS)) % cin_true, o = e / (KS * KS * cin_true);
-        const float *p = part + (size_t)(tap * CIN + i) * COUT + o;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M * COUT; f += gridDim.x * blockDim.x) {
+        const int o = f % COUT, row = f / COUT, i = row % CIN, tap = row / CIN;
+        if (i >= cin_true || o >= cout_true) continue;
+        const float *p = part + f;
+        // the partials in CTA order, 32 loads in flight ahead of their additions
         float s = 0.f;
-        for (int b = 0; b < nctas; ++b) s += p[(size_t)b * M * COUT];
-        gw[e] += s;
+        int b = 0;
+        for (; b + 32 <= nctas; b += 32) {
+            float v[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) v[u] = p[(size_t)(b + u) * M * COUT];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) s += v[u];
+        }
+        for (; b < nctas; ++b) s += p[(size_t)b * M * COUT];
+        gw[((size_t)o * cin_true + i) * (KS * KS) + tap] += s;
     }
 }
 
@@ -1440,19 +1452,42 @@ __global__ void join_bwd_kernel(const float *g_skip, const bf16 *g_path, const b
 
 // bias gradient: gb[c] += sum_p dz[p][c], one CTA per channel c < ctrue (grid = ctrue), each
 // thread summing a fixed stride of pixels, then a fixed tree: the same result every run
-__global__ void bias_grad_kernel(const bf16 *dz, float *gb, long long P, int C)
+// Bias gradients gb[c] += sum over the pixels of dz[p][c], without atomics and in a fixed
+// order, in two passes: thread (t, c) of bias_part_kernel sums dz[p][c] over the pixels
+// p = t, t + 256, t + 512, ... in turn (consecutive threads take consecutive channels, so a
+// warp reads consecutive values), and bias_tree_kernel, one CTA per channel, adds the 256
+// partial sums by halving.  These are the partial sums and the tree of one 256-thread CTA per
+// channel walking the pixels, only spread so that the loads are coalesced.
+__global__ void __launch_bounds__(256) bias_part_kernel(const bf16 *dz, float *part, long long P, int C)
 {
-    __shared__ float part[256];
-    const int c = blockIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 256 * C) return;
+    const int t = g / C, c = g % C;
+    // the pixels in turn, their loads issued 64 ahead of the additions
     float s = 0.f;
-    for (long long p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dz[p * C + c]);
-    part[threadIdx.x] = s;
+    long long p = t;
+    for (; p + 63 * 256 < P; p += 64 * 256) {
+        float v[64];
+#pragma unroll
+        for (int u = 0; u < 64; ++u) v[u] = __bfloat162float(dz[(p + (long long)u * 256) * C + c]);
+#pragma unroll
+        for (int u = 0; u < 64; ++u) s += v[u];
+    }
+    for (; p < P; p += 256) s += __bfloat162float(dz[p * C + c]);
+    part[(size_t)t * C + c] = s;
+}
+
+__global__ void __launch_bounds__(256) bias_tree_kernel(const float *part, float *gb, int C)
+{
+    __shared__ float red[256];
+    const int c = blockIdx.x, t = threadIdx.x;
+    red[t] = part[(size_t)t * C + c];
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) red[t] += red[t + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gb[c] += part[0];
+    if (t == 0) gb[c] += red[0];
 }
 
 // master fp32 [Cout][Cin][k][k] -> forward bf16 [tap][CoutP][CinP] and dgrad bf16
@@ -1825,8 +1860,8 @@ cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H,
     kern<<<(int)grid, kThreads, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int total = cout_true * cin_true * KS * KS;
-    wgrad_reduce_kernel<CIN, COUT, KS><<<(total + 255) / 256, 256, 0, st>>>(part, (int)grid, gw, cin_true, cout_true);
+    wgrad_reduce_kernel<CIN, COUT, KS><<<(KS * KS * CIN * COUT + 255) / 256, 256, 0, st>>>(part, (int)grid, gw, cin_true,
+                                                                                         cout_true);
     return cudaGetLastError();
 }
 
@@ -2079,7 +2114,8 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     auto gw = [&](int l) { return n->g + n->poff[l][0]; };
     auto gb = [&](int l) { return n->g + n->poff[l][1]; };
     auto bgrad = [&](const __nv_bfloat16 *dz, long long pix, int C, int ctrue, int l) {
-        bias_grad_kernel<<<ctrue, 256, 0, st>>>(dz, gb(l), pix, C);
+        bias_part_kernel<<<C, 256, 0, st>>>(dz, n->wpart, pix, C);  // 256 C threads; wpart is free between layers
+        bias_tree_kernel<<<ctrue, 256, 0, st>>>(n->wpart, gb(l), C);
     };
     // output head: sigmoid, o1 (1x1, 16 -> 8 padded to 16), o0
     sigmoid_bwd_kernel<<<egrid(P), 256, 0, st>>>(grad_out, n->out, n->gA, N, H, W, n->nout);
@@ -2208,7 +2244,8 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
             FLNR_TRY((dgrad_launch<CO, CI, KS, false>({dz, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, n->status, st)));
     } else {
         FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->wpart, n->wpart_floats, n->status, st)));
-        bias_grad_kernel<<<d.cout, 256, 0, st>>>(dz, n->g + n->poff[l][1], P, CO);
+        bias_part_kernel<<<CO, 256, 0, st>>>(dz, n->wpart, P, CO);
+        bias_tree_kernel<<<d.cout, 256, 0, st>>>(n->wpart, n->g + n->poff[l][1], CO);
         FLNR_TRY(cudaGetLastError());
     }
     return FLR_OK;
