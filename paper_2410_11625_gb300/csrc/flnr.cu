@@ -1455,23 +1455,33 @@ __global__ void join_bwd_kernel(const float *g_skip, const bf16 *g_path, const b
 // Bias gradients gb[c] += sum over the pixels of dz[p][c], without atomics and in a fixed
 // order, in two passes: thread (t, c) of bias_part_kernel sums dz[p][c] over the pixels
 // p = t, t + 256, t + 512, ... in turn (consecutive threads take consecutive channels, so a
-// warp reads consecutive values), and bias_tree_kernel, one CTA per channel, adds the 256
-// partial sums by halving.  These are the partial sums and the tree of one 256-thread CTA per
-// channel walking the pixels, only spread so that the loads are coalesced.
-__global__ void __launch_bounds__(256) bias_part_kernel(const bf16 *dz, float *part, long long P, int C)
+// warp reads consecutive values; one warp per CTA, so the 256 C threads spread over 8 C SMs),
+// and bias_tree_kernel, one CTA per channel, adds the 256 partial sums by halving.  These are
+// the partial sums and the tree of one 256-thread CTA per channel walking the pixels, only
+// spread so that the loads are coalesced and many are in flight.
+__device__ __forceinline__ unsigned short ld_b16(const bf16 *p)
 {
+    unsigned short v;
+    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
+__global__ void __launch_bounds__(32) bias_part_kernel(const bf16 *dz, float *part, long long P, int C)
+{
+    constexpr int NB = 128;  // loads issued ahead of their additions
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= 256 * C) return;
     const int t = g / C, c = g % C;
-    // the pixels in turn, their loads issued 64 ahead of the additions
+    // the pixels in turn; each batch's loads are issued (in order, as volatile loads) before
+    // any of its additions, so a thread has NB of them in flight
     float s = 0.f;
     long long p = t;
-    for (; p + 63 * 256 < P; p += 64 * 256) {
-        float v[64];
+    for (; p + (NB - 1) * 256LL < P; p += NB * 256LL) {
+        unsigned short v[NB];
 #pragma unroll
-        for (int u = 0; u < 64; ++u) v[u] = __bfloat162float(dz[(p + (long long)u * 256) * C + c]);
+        for (int u = 0; u < NB; ++u) v[u] = ld_b16(dz + (p + (long long)u * 256) * C + c);
 #pragma unroll
-        for (int u = 0; u < 64; ++u) s += v[u];
+        for (int u = 0; u < NB; ++u) s += __bfloat162float(__ushort_as_bfloat16(v[u]));
     }
     for (; p < P; p += 256) s += __bfloat162float(dz[p * C + c]);
     part[(size_t)t * C + c] = s;
@@ -2114,7 +2124,7 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     auto gw = [&](int l) { return n->g + n->poff[l][0]; };
     auto gb = [&](int l) { return n->g + n->poff[l][1]; };
     auto bgrad = [&](const __nv_bfloat16 *dz, long long pix, int C, int ctrue, int l) {
-        bias_part_kernel<<<C, 256, 0, st>>>(dz, n->wpart, pix, C);  // 256 C threads; wpart is free between layers
+        bias_part_kernel<<<8 * C, 32, 0, st>>>(dz, n->wpart, pix, C);  // 256 C threads; wpart is free between layers
         bias_tree_kernel<<<ctrue, 256, 0, st>>>(n->wpart, gb(l), C);
     };
     // output head: sigmoid, o1 (1x1, 16 -> 8 padded to 16), o0
@@ -2244,7 +2254,7 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
             FLNR_TRY((dgrad_launch<CO, CI, KS, false>({dz, n->wd[l], nullptr, nullptr, (bf *)out, nullptr, N, H, W, CI}, n->status, st)));
     } else {
         FLNR_TRY((wgrad_launch<CI, CO, KS>((const bf *)a, dz, n->g + n->poff[l][0], N, H, W, d.cin, d.cout, n->wpart, n->wpart_floats, n->status, st)));
-        bias_part_kernel<<<CO, 256, 0, st>>>(dz, n->wpart, P, CO);
+        bias_part_kernel<<<8 * CO, 32, 0, st>>>(dz, n->wpart, P, CO);
         bias_tree_kernel<<<d.cout, 256, 0, st>>>(n->wpart, n->g + n->poff[l][1], CO);
         FLNR_TRY(cudaGetLastError());
     }
