@@ -1116,22 +1116,25 @@ struct WgradArgs {
 // consecutive addresses of each CTA's partial; the loads of several CTAs are in flight at once
 // while the additions keep CTA order.
 template <int CIN, int COUT, int KS>
-__global__ void wgrad_reduce_kernel(const float *part, int nctas, float *gw, int cin_true, int cout_true)
+__global__ void __launch_bounds__(32) wgrad_reduce_kernel(const float *part, int nctas, float *gw, int cin_true,
+                                                          int cout_true)
 {
-    constexpr int M = KS * KS * CIN;
+    constexpr int M = KS * KS * CIN, NB = 64;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M * COUT; f += gridDim.x * blockDim.x) {
         const int o = f % COUT, row = f / COUT, i = row % CIN, tap = row / CIN;
         if (i >= cin_true || o >= cout_true) continue;
         const float *p = part + f;
-        // the partials in CTA order, 32 loads in flight ahead of their additions
+        // the partials in CTA order; each batch's loads are issued (in order, as volatile loads)
+        // before any of its additions, so a thread has NB of them in flight
         float s = 0.f;
         int b = 0;
-        for (; b + 32 <= nctas; b += 32) {
-            float v[32];
+        for (; b + NB <= nctas; b += NB) {
+            float v[NB];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) v[u] = p[(size_t)(b + u) * M * COUT];
+            for (int u = 0; u < NB; ++u)
+                asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v[u]) : "l"(p + (size_t)(b + u) * M * COUT));
 #pragma unroll
-            for (int u = 0; u < 32; ++u) s += v[u];
+            for (int u = 0; u < NB; ++u) s += v[u];
         }
         for (; b < nctas; ++b) s += p[(size_t)b * M * COUT];
         gw[((size_t)o * cin_true + i) * (KS * KS) + tap] += s;
@@ -1870,8 +1873,9 @@ cudaError_t wgrad_launch(const bf16 *x, const bf16 *dz, float *gw, int N, int H,
     kern<<<(int)grid, kThreads, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    wgrad_reduce_kernel<CIN, COUT, KS><<<(KS * KS * CIN * COUT + 255) / 256, 256, 0, st>>>(part, (int)grid, gw, cin_true,
-                                                                                         cout_true);
+    // one warp per CTA: the M COUT chains of additions spread over as many SMs as they fill
+    wgrad_reduce_kernel<CIN, COUT, KS><<<(KS * KS * CIN * COUT + 31) / 32, 32, 0, st>>>(part, (int)grid, gw, cin_true,
+                                                                                       cout_true);
     return cudaGetLastError();
 }
 
