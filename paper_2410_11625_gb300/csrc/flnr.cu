@@ -1408,21 +1408,45 @@ __global__ void sigmoid_bwd_kernel(const float *g, const float *s, bf16 *dz, int
 __global__ void upcat_bwd_kernel(const bf16 *gy, const bf16 *lo, bf16 *g_lo, float *g_skip, int N, int H, int W,
                                  int Ca, int Cb)
 {
+    // eight channels of one pixel per thread (Ca and Cb are multiples of 8): 16-byte loads and
+    // stores, the index arithmetic once per eight values
     const int C = Ca + Cb, Hl = H / 2, Wl = W / 2;
-    const size_t tl = (size_t)N * Hl * Wl * Ca, ts = (size_t)N * H * W * Cb;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tl + ts; e += (size_t)gridDim.x * blockDim.x) {
-        if (e < tl) {
+    const size_t tl = (size_t)N * Hl * Wl * Ca / 8, ts = (size_t)N * H * W * Cb / 8;
+    for (size_t e8 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e8 < tl + ts; e8 += (size_t)gridDim.x * blockDim.x) {
+        if (e8 < tl) {
+            const size_t e = 8 * e8;
             const int c = (int)(e % Ca);
             const size_t q = e / Ca;
             const int xl = (int)(q % Wl), yl = (int)((q / Wl) % Hl), n = (int)(q / ((size_t)Wl * Hl));
             const size_t b = (((size_t)n * H + 2 * yl) * W + 2 * xl) * C + c;
-            const float s = __bfloat162float(gy[b]) + __bfloat162float(gy[b + C]) + __bfloat162float(gy[b + (size_t)W * C]) +
-                            __bfloat162float(gy[b + (size_t)W * C + C]);
-            g_lo[e] = __float2bfloat16(__bfloat162float(lo[e]) > 0.f ? s : 0.f);
+            const uint4 r0 = *reinterpret_cast<const uint4 *>(gy + b), r1 = *reinterpret_cast<const uint4 *>(gy + b + C);
+            const uint4 r2 = *reinterpret_cast<const uint4 *>(gy + b + (size_t)W * C);
+            const uint4 r3 = *reinterpret_cast<const uint4 *>(gy + b + (size_t)W * C + C);
+            const uint4 l = *reinterpret_cast<const uint4 *>(lo + e);
+            const bf16 *g0 = reinterpret_cast<const bf16 *>(&r0), *g1 = reinterpret_cast<const bf16 *>(&r1);
+            const bf16 *g2 = reinterpret_cast<const bf16 *>(&r2), *g3 = reinterpret_cast<const bf16 *>(&r3);
+            const bf16 *lv = reinterpret_cast<const bf16 *>(&l);
+            uint4 o;
+            bf16 *ov = reinterpret_cast<bf16 *>(&o);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float sum = __bfloat162float(g0[i]) + __bfloat162float(g1[i]) + __bfloat162float(g2[i]) +
+                                  __bfloat162float(g3[i]);
+                ov[i] = __float2bfloat16(__bfloat162float(lv[i]) > 0.f ? sum : 0.f);
+            }
+            *reinterpret_cast<uint4 *>(g_lo + e) = o;
         } else {
-            const size_t f = e - tl;
+            const size_t f = 8 * (e8 - tl);
             const int c = (int)(f % Cb);
-            g_skip[f] = __bfloat162float(gy[(f / Cb) * C + Ca + c]);
+            const uint4 r = *reinterpret_cast<const uint4 *>(gy + (f / Cb) * C + Ca + c);
+            const bf16 *rv = reinterpret_cast<const bf16 *>(&r);
+            float4 v0, v1;
+            v0.x = __bfloat162float(rv[0]); v0.y = __bfloat162float(rv[1]);
+            v0.z = __bfloat162float(rv[2]); v0.w = __bfloat162float(rv[3]);
+            v1.x = __bfloat162float(rv[4]); v1.y = __bfloat162float(rv[5]);
+            v1.z = __bfloat162float(rv[6]); v1.w = __bfloat162float(rv[7]);
+            *reinterpret_cast<float4 *>(g_skip + f) = v0;
+            *reinterpret_cast<float4 *>(g_skip + f + 4) = v1;
         }
     }
 }
@@ -1437,24 +1461,41 @@ template <int S>
 __global__ void join_bwd_kernel(const float *g_skip, const bf16 *g_path, const bf16 *f, bf16 *dz, int N, int Ho, int Wo,
                                 int C)
 {
+    // eight channels of one pixel per thread (C a multiple of 8): 16-byte loads and stores
     const int H = S * Ho, W = S * Wo;
-    const size_t total = (size_t)N * H * W * C;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t total8 = (size_t)N * H * W * C / 8;
+    for (size_t e8 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e8 < total8; e8 += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = 8 * e8;
         const int c = (int)(e % C);
         const size_t p = e / C;
         const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((size_t)W * H));
-        float v = 0.f;
+        uint4 o = make_uint4(0u, 0u, 0u, 0u);  // bfloat16 +0
         if (S == 1 || ((x | y) & 1) == 0) {
             const size_t q = (((size_t)n * Ho + y / S) * Wo + x / S) * C + c;
-            v = __bfloat162float(g_path[q]) + (g_skip ? g_skip[q] : 0.f);
-            if (f && !(__bfloat162float(f[q]) > 0.f)) v = 0.f;
+            const uint4 gp = *reinterpret_cast<const uint4 *>(g_path + q);
+            const bf16 *gv = reinterpret_cast<const bf16 *>(&gp);
+            float sk[8];
+            if (g_skip) {
+                const float4 s0 = *reinterpret_cast<const float4 *>(g_skip + q);
+                const float4 s1 = *reinterpret_cast<const float4 *>(g_skip + q + 4);
+                sk[0] = s0.x; sk[1] = s0.y; sk[2] = s0.z; sk[3] = s0.w;
+                sk[4] = s1.x; sk[5] = s1.y; sk[6] = s1.z; sk[7] = s1.w;
+            }
+            uint4 fm = make_uint4(0u, 0u, 0u, 0u);
+            if (f) fm = *reinterpret_cast<const uint4 *>(f + q);
+            const bf16 *fv = reinterpret_cast<const bf16 *>(&fm);
+            bf16 *ov = reinterpret_cast<bf16 *>(&o);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float v = __bfloat162float(gv[i]) + (g_skip ? sk[i] : 0.f);
+                if (f && !(__bfloat162float(fv[i]) > 0.f)) v = 0.f;
+                ov[i] = __float2bfloat16(v);
+            }
         }
-        dz[e] = __float2bfloat16(v);
+        *reinterpret_cast<uint4 *>(dz + e) = o;
     }
 }
 
-// bias gradient: gb[c] += sum_p dz[p][c], one CTA per channel c < ctrue (grid = ctrue), each
-// thread summing a fixed stride of pixels, then a fixed tree: the same result every run
 // Bias gradients gb[c] += sum over the pixels of dz[p][c], without atomics and in a fixed
 // order, in two passes: thread (t, c) of bias_part_kernel sums dz[p][c] over the pixels
 // p = t, t + 256, t + 512, ... in turn (consecutive threads take consecutive channels, so a
@@ -2148,7 +2189,7 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     FLNR_TRY((wgrad_launch<48, 16, 3>(n->c0, n->gB, gw(8), N, H, W, 48, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gB, (long long)P, 16, 16, 8);
     FLNR_TRY((dgrad_launch<16, 48, 3, false>({n->gB, n->wd[8], nullptr, nullptr, n->gC, nullptr, N, H, W, 48}, n->status, st)));
-    upcat_bwd_kernel<<<egrid(P * 48), 256, 0, st>>>(n->gC, n->d1, n->gLo, n->gskip0, N, H, W, 32, 16);  // gLo = dz(d1b)
+    upcat_bwd_kernel<<<egrid(P * 48 / 8), 256, 0, st>>>(n->gC, n->d1, n->gLo, n->gskip0, N, H, W, 32, 16);  // gLo = dz(d1b)
     // decoder level 1 (H/2)
     const size_t P2 = P / 4;
     FLNR_TRY((wgrad_launch<32, 32, 3>(n->a3, n->gLo, gw(7), N, H2, W2, 32, 32, n->wpart, n->wpart_floats, n->status, st)));
@@ -2159,13 +2200,13 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     FLNR_TRY((wgrad_launch<96, 32, 3>(n->c1, n->gA, gw(6), N, H2, W2, 96, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P2, 32, 32, 6);
     FLNR_TRY((dgrad_launch<32, 96, 3, false>({n->gA, n->wd[6], nullptr, nullptr, n->gC, nullptr, N, H2, W2, 96}, n->status, st)));
-    upcat_bwd_kernel<<<egrid(P2 * 96), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
+    upcat_bwd_kernel<<<egrid(P2 * 96 / 8), 256, 0, st>>>(n->gC, n->f2, n->gLo, n->gskip1, N, H2, W2, 64, 32);  // gLo = dz(e2b)
     // encoder level 2: e2b (stride 2, H/2 -> H/4), then e2a (H/2).  A stride-2 layer's
     // gradients are those of the stride-1 kernels at its input's size on dz zero-upsampled
     // onto that grid.
     const size_t P4 = P / 16;
     bgrad(n->gLo, (long long)P4, 64, 64, 5);
-    join_bwd_kernel<2><<<egrid(P2 * 64), 256, 0, st>>>(nullptr, n->gLo, nullptr, n->gB, N, H4, W4, 64);
+    join_bwd_kernel<2><<<egrid(P2 * 64 / 8), 256, 0, st>>>(nullptr, n->gLo, nullptr, n->gB, N, H4, W4, 64);
     FLNR_TRY(cudaGetLastError());
     FLNR_TRY((wgrad_launch<64, 64, 3>(n->a2, n->gB, gw(5), N, H2, W2, 64, 64, n->wpart, n->wpart_floats, n->status, st)));
     FLNR_TRY((dgrad_launch<64, 64, 3, true>({n->gB, n->wd[5], n->a2, nullptr, n->gA, nullptr, N, H2, W2, 64}, n->status, st)));
@@ -2173,7 +2214,7 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     bgrad(n->gA, (long long)P2, 64, 64, 4);
     FLNR_TRY((dgrad_launch<64, 32, 3, false>({n->gA, n->wd[4], nullptr, nullptr, n->gB, nullptr, N, H2, W2, 32}, n->status, st)));
     // encoder level 1: e1b (stride 2, H -> H/2; f1 also feeds the d1a skip), then e1a (H)
-    join_bwd_kernel<2><<<egrid(P * 32), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gC, N, H2, W2, 32);
+    join_bwd_kernel<2><<<egrid(P * 32 / 8), 256, 0, st>>>(n->gskip1, n->gB, n->f1, n->gC, N, H2, W2, 32);
     FLNR_TRY(cudaGetLastError());
     FLNR_TRY((wgrad_launch<32, 32, 3>(n->a1, n->gC, gw(3), N, H, W, 32, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gC, (long long)P, 32, 32, 3);
@@ -2181,7 +2222,7 @@ int flnr_guide_backward(flnr_net *n, const float *grad_out, float *grad_in, void
     FLNR_TRY((wgrad_launch<16, 32, 3>(n->f0, n->gA, gw(2), N, H, W, 16, 32, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gA, (long long)P, 32, 32, 2);
     FLNR_TRY((dgrad_launch<32, 16, 3, false>({n->gA, n->wd[2], nullptr, nullptr, n->gB, nullptr, N, H, W, 16}, n->status, st)));
-    join_bwd_kernel<1><<<egrid(P * 16), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
+    join_bwd_kernel<1><<<egrid(P * 16 / 8), 256, 0, st>>>(n->gskip0, n->gB, n->f0, n->gLo, N, H, W, 16);  // dz(in1)
     // input projection (H)
     FLNR_TRY((wgrad_launch<16, 16, 1>(n->a0, n->gLo, gw(1), N, H, W, 16, 16, n->wpart, n->wpart_floats, n->status, st)));
     bgrad(n->gLo, (long long)P, 16, 16, 1);
@@ -2247,7 +2288,7 @@ int layer_ops(flnr_net *n, int l, int op, const void *a, const void *b, const vo
     if constexpr (S2) {  // dz [N][H/2][W/2][CO], zero-upsampled onto the input grid in scratch
         if ((H | W) & 1) return FLR_ERR_ARG;
         if (P * CO > (long long)n->max_pix * 48) return FLR_ERR_UNSUPPORTED;
-        join_bwd_kernel<2><<<egrid((size_t)P * CO), 256, 0, st>>>(nullptr, dz, nullptr, n->gC, N, H / 2, W / 2, CO);
+        join_bwd_kernel<2><<<egrid((size_t)P * CO / 8), 256, 0, st>>>(nullptr, dz, nullptr, n->gC, N, H / 2, W / 2, CO);
         FLNR_TRY(cudaGetLastError());
         dz = n->gC;
     }
