@@ -299,21 +299,14 @@ __device__ __forceinline__ void stage_wait(const FwdKArgs &k, uint64_t *bar, int
     }
 }
 
-// Horizontal radius-r sums of one shared-memory row, in place: slot xo <- sum of
-// p[xo .. xo + 2r] for xo in [0, kTW).  Chunks of 8 outputs load every operand before
-// writing, so no slot is overwritten while still needed.  RT >= 0: radius known at
-// compile time and 16/8-byte vector accesses; RT < 0: runtime radius, scalar accesses.
-template <int RT>
+// Horizontal radius-r sums of one shared-memory row, in place, for a radius known only at
+// run time: slot xo <- sum of p[xo .. xo + 2r] for xo in [0, kTW).  Chunks of 8 outputs load
+// every operand before writing, so no slot is overwritten while still needed.  (Radii known
+// at compile time use dev::hsum_run: two runs, each seeded by a direct sum.)
 __device__ __forceinline__ void hsum_row(float *p, int r)
 {
     float s;
-    if constexpr (RT >= 0) {
-        constexpr int N = 2 * RT + 1;
-        float t[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < N; ++k) t[k & 3] += p[k];
-        s = (t[0] + t[1]) + (t[2] + t[3]);
-    } else {
+    {
         float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
         int k = 0;
         for (; k + 4 <= 2 * r + 1; k += 4) {
@@ -329,30 +322,10 @@ __device__ __forceinline__ void hsum_row(float *p, int r)
 #pragma unroll 2
     for (int xo = 0; xo < kTW; xo += 8) {
         float add[8], old[8];
-        if constexpr (RT >= 0) {
-            const float4 o0 = *reinterpret_cast<const float4 *>(p + xo);
-            const float4 o1 = *reinterpret_cast<const float4 *>(p + xo + 4);
-            old[0] = o0.x; old[1] = o0.y; old[2] = o0.z; old[3] = o0.w;
-            old[4] = o1.x; old[5] = o1.y; old[6] = o1.z; old[7] = o1.w;
-            if constexpr ((2 * RT) % 4 == 0) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(p + xo + 2 * RT);
-                const float4 a1 = *reinterpret_cast<const float4 *>(p + xo + 2 * RT + 4);
-                add[0] = a0.x; add[1] = a0.y; add[2] = a0.z; add[3] = a0.w;
-                add[4] = a1.x; add[5] = a1.y; add[6] = a1.z; add[7] = a1.w;
-            } else {
 #pragma unroll
-                for (int t = 0; t < 8; t += 2) {
-                    const float2 v = *reinterpret_cast<const float2 *>(p + xo + 2 * RT + t);
-                    add[t] = v.x;
-                    add[t + 1] = v.y;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                add[t] = p[xo + t + 2 * r];
-                old[t] = p[xo + t];
-            }
+        for (int t = 0; t < 8; ++t) {
+            add[t] = p[xo + t + 2 * r];
+            old[t] = p[xo + t];
         }
         float out[8];
 #pragma unroll
@@ -361,13 +334,8 @@ __device__ __forceinline__ void hsum_row(float *p, int r)
             vprev = old[t];
             out[t] = s;
         }
-        if constexpr (RT >= 0) {
-            *reinterpret_cast<float4 *>(p + xo) = make_float4(out[0], out[1], out[2], out[3]);
-            *reinterpret_cast<float4 *>(p + xo + 4) = make_float4(out[4], out[5], out[6], out[7]);
-        } else {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) p[xo + t] = out[t];
-        }
+        for (int t = 0; t < 8; ++t) p[xo + t] = out[t];
     }
 }
 
@@ -542,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) flr_fwd_kernel(const __grid_const
                 dev::hsum_run<RT, kTW / 2>(p, p, 0);
                 dev::hsum_run<RT, kTW / 2>(p, p, kTW / 2);
             } else {
-                hsum_row<RT>(p, r);
+                hsum_row(p, r);
             }
         }
         __syncthreads();
