@@ -1,0 +1,60 @@
+"""A second, independent formulation of FLR pins the C oracle at sizes brute force cannot
+reach: PyTorch CPU float64, in the shape of the paper's Fig. 3 (outer products of the guide
+vector with itself and with the radiance, a window filter over each product plane, one
+batched linear solve per pixel, the model applied to the guides), with the clipped box
+window of the oracle instead of the figure's Gaussian, and the regulariser of reading c2.
+
+The bias is a guide column of ones, so each pixel solves the augmented (Q + 1) x (Q + 1)
+system of window means
+    [ E[x x^T] + eps I   E[x] ] [ a ]   [ E[x y^T] ]
+    [ E[x]^T             1    ] [ b ] = [ E[y]^T   ]
+(eps on the guide rows only, bias unpenalised; Sec. 3.1's closed form with the Appendix's
+centring eliminated: its Schur complement is the oracle's centred system).  Window means
+are box sums of the zero-padded planes divided by the box sum of the ones plane (clipped
+windows); torch.linalg.solve is an LU solve, the oracle a Cholesky of the centred system.
+Coefficient averaging (rc > 0) averages a and b over the clipped radius-rc window."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+
+
+def box_sum(planes, r):
+    """Sum of each [C, H, W] plane over the clipped (2r + 1)^2 window (zero padding)."""
+    c = planes.shape[0]
+    k = torch.ones((c, 1, 2 * r + 1, 2 * r + 1), dtype=planes.dtype)
+    return torch.nn.functional.conv2d(planes[None], k, padding=r, groups=c)[0]
+
+
+def flr_torch(g, y, r, eps, rc):
+    x = torch.from_numpy(np.asarray(g, np.float64))
+    yy = torch.from_numpy(np.asarray(y, np.float64))
+    q, H, W = x.shape
+    xa = torch.cat([x, torch.ones((1, H, W), dtype=torch.float64)])  # guides and the bias column
+    n = box_sum(torch.ones((1, H, W), dtype=torch.float64), r)[0]
+    xx = box_sum(torch.einsum("ihw,jhw->ijhw", xa, xa).reshape(-1, H, W), r).reshape(q + 1, q + 1, H, W) / n
+    xy = box_sum(torch.einsum("ihw,jhw->ijhw", xa, yy).reshape(-1, H, W), r).reshape(q + 1, 3, H, W) / n
+    reg = torch.zeros((q + 1, q + 1), dtype=torch.float64)
+    reg[:q, :q] = eps * torch.eye(q, dtype=torch.float64)
+    A = torch.linalg.solve(xx.permute(2, 3, 0, 1) + reg, xy.permute(2, 3, 0, 1))  # [H, W, q+1, 3]
+    if rc > 0:
+        m = box_sum(torch.ones((1, H, W), dtype=torch.float64), rc)[0]
+        A = (box_sum(A.permute(2, 3, 0, 1).reshape(-1, H, W), rc) / m).reshape(q + 1, 3, H, W).permute(2, 3, 0, 1)
+    return torch.einsum("ihw,hwic->chw", xa, A).numpy()
+
+
+@pytest.mark.parametrize("kind,H,W,r,rc", [
+    ("random", 40, 52, 3, 2), ("random", 33, 47, 5, 0), ("rendered", 64, 64, 5, 5), ("rendered", 48, 80, 8, 0),
+])
+def test_oracle_matches_an_independent_torch_formulation(kind, H, W, r, rc):
+    if kind == "random":
+        g, y = synth.random_frame(17 + H, H, W, 8)
+    else:
+        g, y = synth.render(4, H, W)
+    ref = oracle.flr_forward(g, y, r, 1e-3, coef_radius=rc)
+    got = flr_torch(g, y, r, 1e-3, rc)
+    scale = np.sqrt(np.mean(ref ** 2))
+    assert np.max(np.abs(got - ref)) <= 1e-9 * scale
