@@ -58,3 +58,41 @@ def test_oracle_matches_an_independent_torch_formulation(kind, H, W, r, rc):
     got = flr_torch(g, y, r, 1e-3, rc)
     scale = np.sqrt(np.mean(ref ** 2))
     assert np.max(np.abs(got - ref)) <= 1e-9 * scale
+
+
+def flr_torch_t(x, yy, r, eps, rc):
+    """flr_torch on tensors (differentiable in x, yy and eps)."""
+    q, H, W = x.shape
+    xa = torch.cat([x, torch.ones((1, H, W), dtype=torch.float64)])
+    n = box_sum(torch.ones((1, H, W), dtype=torch.float64), r)[0]
+    xx = box_sum(torch.einsum("ihw,jhw->ijhw", xa, xa).reshape(-1, H, W), r).reshape(q + 1, q + 1, H, W) / n
+    xy = box_sum(torch.einsum("ihw,jhw->ijhw", xa, yy).reshape(-1, H, W), r).reshape(q + 1, 3, H, W) / n
+    mask = torch.zeros((q + 1, q + 1), dtype=torch.float64)
+    mask[:q, :q] = torch.eye(q, dtype=torch.float64)
+    A = torch.linalg.solve(xx.permute(2, 3, 0, 1) + eps * mask, xy.permute(2, 3, 0, 1))
+    if rc > 0:
+        m = box_sum(torch.ones((1, H, W), dtype=torch.float64), rc)[0]
+        A = (box_sum(A.permute(2, 3, 0, 1).reshape(-1, H, W), rc) / m).reshape(q + 1, 3, H, W).permute(2, 3, 0, 1)
+    return torch.einsum("ihw,hwic->chw", xa, A)
+
+
+@pytest.mark.parametrize("kind,H,W,r,rc", [("random", 24, 30, 3, 2), ("rendered", 32, 40, 4, 4)])
+def test_oracle_adjoint_matches_autograd_of_the_torch_formulation(kind, H, W, r, rc):
+    """The oracle's analytic adjoint (reverse mode through centring, Cholesky, bias and the
+    average) against reverse-mode automatic differentiation of the independent formulation:
+    gradients of <G, I> with respect to the guides (model and map guide alike), the radiance
+    and eps."""
+    if kind == "random":
+        g, y = synth.random_frame(40 + H, H, W, 8)
+    else:
+        g, y = synth.render(6, H, W)
+    G = np.random.default_rng(H).normal(size=(3, H, W))
+    x = torch.tensor(np.asarray(g, np.float64), requires_grad=True)
+    yy = torch.tensor(np.asarray(y, np.float64), requires_grad=True)
+    e = torch.tensor(1e-3, dtype=torch.float64, requires_grad=True)
+    (flr_torch_t(x, yy, r, e, rc) * torch.from_numpy(G)).sum().backward()
+    ref = oracle.flr_backward(g, y, G, r, 1e-3, coef_radius=rc)
+    for name, got in (("guide", x.grad.numpy()), ("radiance", yy.grad.numpy())):
+        scale = np.sqrt(np.mean(ref[name] ** 2))
+        assert np.max(np.abs(got - ref[name])) <= 1e-11 * scale, name
+    assert abs(float(e.grad) - ref["eps"]) <= 1e-11 * abs(ref["eps"])
