@@ -2,7 +2,8 @@
 reach: PyTorch CPU float64, in the shape of the paper's Fig. 3 (outer products of the guide
 vector with itself and with the radiance, a window filter over each product plane, one
 batched linear solve per pixel, the model applied to the guides), with the clipped box
-window of the oracle instead of the figure's Gaussian, and the regulariser of reading c2.
+window of the oracle instead of the figure's Gaussian, and the oracle's regulariser (eps on
+the centred guide covariance of window means, the bias unpenalised).
 
 The bias is a guide column of ones, so each pixel solves the augmented (Q + 1) x (Q + 1)
 system of window means
@@ -12,7 +13,8 @@ system of window means
 centring eliminated: its Schur complement is the oracle's centred system).  Window means
 are box sums of the zero-padded planes divided by the box sum of the ones plane (clipped
 windows); torch.linalg.solve is an LU solve, the oracle a Cholesky of the centred system.
-Coefficient averaging (rc > 0) averages a and b over the clipped radius-rc window."""
+Coefficient averaging (rc > 0) averages a and b over the clipped radius-rc window.  The
+formulation's reverse-mode automatic derivative pins the oracle's analytic adjoint too."""
 import numpy as np
 import pytest
 
