@@ -1,7 +1,7 @@
 """Shared test helpers: the parity metric and GPU plumbing."""
 import numpy as np
 
-# Bar for FP32 GPU results against the FP64 oracle (max relative error, see c7 metric).
+# Bar for FP32 GPU results against the FP64 oracle (max relative error, rel_err below).
 TOL = 1e-4
 
 

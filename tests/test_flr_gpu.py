@@ -241,7 +241,7 @@ def test_rendered_unaveraged_with_tighter_pivot(flr):
 
 @pytest.mark.parametrize("H,W,rc", [(64, 96, 0), (64, 96, 2), (600, 64, 3)])
 def test_nonfinite_outputs_are_counted(flr, H, W, rc):
-    """Non-finite inputs are not sanitised (reading c11): they reach every output whose
+    """Non-finite inputs are not sanitised: they reach every output whose
     windows hold them, and flr_get_stats reports how many output values are NaN or
     infinite -- exactly the number in the returned frame, through the device entry point
     and (600 rows: two bands) the host one.  A clean frame reports none."""
