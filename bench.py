@@ -227,9 +227,10 @@ def cpu_baseline(frame):
 
 
 def sampled_parity(got, frame, blocks=12, B=32, seed=0):
-    """max relative error (|got - ref| / max(|ref|, 1% of RMS(ref))) of the timed frame's result against the oracle on
-    sampled B x B blocks (corners, edges, random interior), each computed by the oracle on
-    the block plus its radius-(r + rc) halo, which holds every input its outputs depend on."""
+    """max relative error, |got - ref| / max(|ref|, 1% of RMS(ref)), of the timed frame's
+    result against the oracle on sampled B x B blocks (corners, edges, random interior), each
+    computed by the oracle on the block plus its radius-(r + rc) halo, which holds every input
+    its outputs depend on."""
     import numpy as np
 
     import oracle
