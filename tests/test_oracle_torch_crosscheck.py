@@ -14,7 +14,8 @@ centring eliminated: its Schur complement is the oracle's centred system).  Wind
 are box sums of the zero-padded planes divided by the box sum of the ones plane (clipped
 windows); torch.linalg.solve is an LU solve, the oracle a Cholesky of the centred system.
 Coefficient averaging (rc > 0) averages a and b over the clipped radius-rc window.  The
-formulation's reverse-mode automatic derivative pins the oracle's analytic adjoint too."""
+formulation's reverse-mode automatic derivative pins the oracle's analytic adjoint too, and
+the paper's fast FLR (Sec. 3.2, 3.2.1) written the same way pins the fast-FLR oracle."""
 import numpy as np
 import pytest
 
@@ -98,3 +99,68 @@ def test_oracle_adjoint_matches_autograd_of_the_torch_formulation(kind, H, W, r,
         scale = np.sqrt(np.mean(ref[name] ** 2))
         assert np.max(np.abs(got - ref[name])) <= 1e-11 * scale, name
     assert abs(float(e.grad) - ref["eps"]) <= 1e-11 * abs(ref["eps"])
+
+
+def fast_torch(g, y, F, sigma, taps, eps, z=None, s=1):
+    """The paper's fast FLR (Sec. 3.2, 3.2.1) as array operations: block sums of the outer
+    products of (1, x) with itself and with y over F x F blocks, a separable Gaussian over the
+    block grid (weights exp(-d^2 / 2 sigma^2), |d| <= taps, clipped at the grid edge), the
+    augmented ridge system of each block's weighted sums solved by LU, and the block models
+    interpolated bilinearly between block centres ((i + 1/2) F s - 1/2 in output pixels,
+    clamped to the outermost centres) and applied to the map guide."""
+    x = torch.from_numpy(np.asarray(g, np.float64))
+    yy = torch.from_numpy(np.asarray(y, np.float64))
+    q, Hi, Wi = x.shape
+    Hb, Wb = -(-Hi // F), -(-Wi // F)
+    xa = torch.cat([torch.ones((1, Hi, Wi), dtype=torch.float64), x])
+
+    def blocks(p):  # [C, Hi, Wi] -> block sums [C, Hb, Wb] (zero padding to whole blocks)
+        pp = torch.nn.functional.pad(p, (0, Wb * F - Wi, 0, Hb * F - Hi))
+        return pp.reshape(p.shape[0], Hb, F, Wb, F).sum(dim=(2, 4))
+
+    S = blocks(torch.einsum("ihw,jhw->ijhw", xa, xa).reshape(-1, Hi, Wi)).reshape(q + 1, q + 1, Hb, Wb)
+    T = blocks(torch.einsum("ihw,jhw->ijhw", xa, yy).reshape(-1, Hi, Wi)).reshape(q + 1, 3, Hb, Wb)
+    d = torch.arange(-taps, taps + 1, dtype=torch.float64)
+    w = torch.exp(-d * d / (2.0 * sigma * sigma))
+
+    def blur(p):  # [C, Hb, Wb], separable, clipped (zero padding)
+        c = p.shape[0]
+        kx = w.reshape(1, 1, 1, -1).repeat(c, 1, 1, 1)
+        ky = w.reshape(1, 1, -1, 1).repeat(c, 1, 1, 1)
+        p = torch.nn.functional.conv2d(p[None], kx, padding=(0, taps), groups=c)
+        return torch.nn.functional.conv2d(p, ky, padding=(taps, 0), groups=c)[0]
+
+    S = blur(S.reshape(-1, Hb, Wb)).reshape(q + 1, q + 1, Hb, Wb)
+    T = blur(T.reshape(-1, Hb, Wb)).reshape(q + 1, 3, Hb, Wb)
+    n = S[0, 0]
+    reg = torch.zeros((q + 1, q + 1), dtype=torch.float64)
+    reg[1:, 1:] = eps * torch.eye(q, dtype=torch.float64)
+    A = torch.linalg.solve((S / n).permute(2, 3, 0, 1) + reg, (T / n).permute(2, 3, 0, 1))  # [Hb, Wb, q+1, 3]
+    zz = x if z is None else torch.from_numpy(np.asarray(z, np.float64))
+    Ho, Wo = zz.shape[1:]
+    P = F * s
+
+    def axis(nout, nb):  # lower block index and weight per output coordinate
+        u = ((torch.arange(nout, dtype=torch.float64) + 0.5) / P - 0.5).clamp(0, nb - 1)
+        i0 = torch.floor(u).long().clamp(max=max(nb - 2, 0))
+        i1 = (i0 + 1).clamp(max=nb - 1)
+        return i0, i1, u - i0
+    i0, i1, fy = axis(Ho, Hb)
+    j0, j1, fx = axis(Wo, Wb)
+    fy, fx = fy[:, None, None, None], fx[None, :, None, None]
+    Ai = (1 - fy) * ((1 - fx) * A[i0][:, j0] + fx * A[i0][:, j1]) + fy * ((1 - fx) * A[i1][:, j0] + fx * A[i1][:, j1])
+    za = torch.cat([torch.ones((1, Ho, Wo), dtype=torch.float64), zz])
+    return torch.einsum("ihw,hwic->chw", za, Ai).numpy()
+
+
+@pytest.mark.parametrize("H,W,F,s,taps", [(64, 80, 8, 1, 3), (50, 70, 4, 1, 2), (40, 56, 4, 2, 3)])
+def test_fast_oracle_matches_an_independent_torch_formulation(H, W, F, s, taps):
+    g, y = synth.render(8, H, W)
+    if s == 1:
+        z = None
+        ref = oracle.flr_fast(g, y, factor=F, sigma_blocks=1.25, taps=taps, eps=1e-3)
+    else:  # joint upsampling: model guides and radiance at H x W, the map guide s times finer
+        z = synth.render(8, H * s, W * s)[0]
+        ref = oracle.flr_fast(g, y, factor=F, sigma_blocks=1.25, taps=taps, eps=1e-3, map_guide=z, scale=s)
+    got = fast_torch(g, y, F, 1.25, taps, 1e-3, z=z, s=s)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.sqrt(np.mean(ref ** 2))
