@@ -63,8 +63,8 @@ def test_oracle_matches_an_independent_torch_formulation(kind, H, W, r, rc):
     assert np.max(np.abs(got - ref)) <= 1e-9 * scale
 
 
-def flr_torch_t(x, yy, r, eps, rc):
-    """flr_torch on tensors (differentiable in x, yy and eps)."""
+def flr_torch_t(x, yy, r, eps, rc, z=None):
+    """flr_torch on tensors (differentiable in x, yy, eps and the map guide z, default x)."""
     q, H, W = x.shape
     xa = torch.cat([x, torch.ones((1, H, W), dtype=torch.float64)])
     n = box_sum(torch.ones((1, H, W), dtype=torch.float64), r)[0]
@@ -76,7 +76,26 @@ def flr_torch_t(x, yy, r, eps, rc):
     if rc > 0:
         m = box_sum(torch.ones((1, H, W), dtype=torch.float64), rc)[0]
         A = (box_sum(A.permute(2, 3, 0, 1).reshape(-1, H, W), rc) / m).reshape(q + 1, 3, H, W).permute(2, 3, 0, 1)
-    return torch.einsum("ihw,hwic->chw", xa, A)
+    za = xa if z is None else torch.cat([z, torch.ones((1, H, W), dtype=torch.float64)])
+    return torch.einsum("ihw,hwic->chw", za, A)
+
+
+@pytest.mark.parametrize("rc", [0, 3])
+def test_oracle_map_guide_adjoint_matches_autograd(rc):
+    """With a separate map guide z (Sec. 3.3's second guide set) the oracle returns the
+    gradients of the model guides and of the map guide apart; both against autograd."""
+    H, W, r = 26, 34, 3
+    g, y = synth.random_frame(71, H, W, 8)
+    z, _ = synth.random_frame(72, H, W, 8)
+    G = np.random.default_rng(5).normal(size=(3, H, W))
+    x = torch.tensor(np.asarray(g, np.float64), requires_grad=True)
+    yy = torch.tensor(np.asarray(y, np.float64), requires_grad=True)
+    zt = torch.tensor(np.asarray(z, np.float64), requires_grad=True)
+    (flr_torch_t(x, yy, r, 1e-3, rc, z=zt) * torch.from_numpy(G)).sum().backward()
+    ref = oracle.flr_backward(g, y, G, r, 1e-3, coef_radius=rc, map_guide=z)
+    for name, got in (("guide", x.grad.numpy()), ("radiance", yy.grad.numpy()), ("map_guide", zt.grad.numpy())):
+        scale = np.sqrt(np.mean(ref[name] ** 2))
+        assert np.max(np.abs(got - ref[name])) <= 1e-11 * scale, name
 
 
 @pytest.mark.parametrize("kind,H,W,r,rc", [("random", 24, 30, 3, 2), ("rendered", 32, 40, 4, 4)])
