@@ -140,7 +140,7 @@ def fast_torch(g, y, F, sigma, taps, eps, z=None, s=1):
     S = blocks(torch.einsum("ihw,jhw->ijhw", xa, xa).reshape(-1, Hi, Wi)).reshape(q + 1, q + 1, Hb, Wb)
     T = blocks(torch.einsum("ihw,jhw->ijhw", xa, yy).reshape(-1, Hi, Wi)).reshape(q + 1, 3, Hb, Wb)
     d = torch.arange(-taps, taps + 1, dtype=torch.float64)
-    w = torch.exp(-d * d / (2.0 * sigma * sigma))
+    w = torch.exp(-d * d / (2.0 * sigma * sigma))  # sigma may be a tensor (autograd)
 
     def blur(p):  # [C, Hb, Wb], separable, clipped (zero padding)
         c = p.shape[0]
@@ -152,9 +152,9 @@ def fast_torch(g, y, F, sigma, taps, eps, z=None, s=1):
     S = blur(S.reshape(-1, Hb, Wb)).reshape(q + 1, q + 1, Hb, Wb)
     T = blur(T.reshape(-1, Hb, Wb)).reshape(q + 1, 3, Hb, Wb)
     n = S[0, 0]
-    reg = torch.zeros((q + 1, q + 1), dtype=torch.float64)
-    reg[1:, 1:] = eps * torch.eye(q, dtype=torch.float64)
-    A = torch.linalg.solve((S / n).permute(2, 3, 0, 1) + reg, (T / n).permute(2, 3, 0, 1))  # [Hb, Wb, q+1, 3]
+    mask = torch.zeros((q + 1, q + 1), dtype=torch.float64)
+    mask[1:, 1:] = torch.eye(q, dtype=torch.float64)
+    A = torch.linalg.solve((S / n).permute(2, 3, 0, 1) + eps * mask, (T / n).permute(2, 3, 0, 1))  # [Hb, Wb, q+1, 3]
     zz = x if z is None else torch.from_numpy(np.asarray(z, np.float64))
     Ho, Wo = zz.shape[1:]
     P = F * s
@@ -169,7 +169,8 @@ def fast_torch(g, y, F, sigma, taps, eps, z=None, s=1):
     fy, fx = fy[:, None, None, None], fx[None, :, None, None]
     Ai = (1 - fy) * ((1 - fx) * A[i0][:, j0] + fx * A[i0][:, j1]) + fy * ((1 - fx) * A[i1][:, j0] + fx * A[i1][:, j1])
     za = torch.cat([torch.ones((1, Ho, Wo), dtype=torch.float64), zz])
-    return torch.einsum("ihw,hwic->chw", za, Ai).numpy()
+    out = torch.einsum("ihw,hwic->chw", za, Ai)
+    return out if torch.is_tensor(sigma) or torch.is_tensor(eps) else out.numpy()
 
 
 @pytest.mark.parametrize("H,W,F,s,taps", [(64, 80, 8, 1, 3), (50, 70, 4, 1, 2), (40, 56, 4, 2, 3)])
@@ -183,3 +184,19 @@ def test_fast_oracle_matches_an_independent_torch_formulation(H, W, F, s, taps):
         ref = oracle.flr_fast(g, y, factor=F, sigma_blocks=1.25, taps=taps, eps=1e-3, map_guide=z, scale=s)
     got = fast_torch(g, y, F, 1.25, taps, 1e-3, z=z, s=s)
     assert np.max(np.abs(got - ref)) <= 1e-10 * np.sqrt(np.mean(ref ** 2))
+
+
+def test_fast_parameter_gradients_match_autograd():
+    """Sec. 3.2 learns the blur's sigma and the regulariser by backpropagation; the oracle
+    takes those derivatives by Richardson-extrapolated central differences of its FP64
+    forward pass.  Reverse-mode automatic differentiation of the independent formulation
+    gives them exactly."""
+    H, W = 48, 64
+    g, y = synth.render(9, H, W)
+    G = np.random.default_rng(9).normal(size=(3, H, W))
+    sig = torch.tensor(1.25, dtype=torch.float64, requires_grad=True)
+    e = torch.tensor(1e-3, dtype=torch.float64, requires_grad=True)
+    (fast_torch(g, y, 4, sig, 2, e) * torch.from_numpy(G)).sum().backward()
+    ref = oracle.flr_fast_param_grads(g, y, G, factor=4, sigma_blocks=1.25, taps=2, eps=1e-3)
+    assert abs(float(sig.grad) - ref["sigma"]) <= 1e-9 * abs(ref["sigma"])
+    assert abs(float(e.grad) - ref["eps"]) <= 1e-9 * abs(ref["eps"])
