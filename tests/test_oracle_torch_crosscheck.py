@@ -200,3 +200,62 @@ def test_fast_parameter_gradients_match_autograd():
     ref = oracle.flr_fast_param_grads(g, y, G, factor=4, sigma_blocks=1.25, taps=2, eps=1e-3)
     assert abs(float(sig.grad) - ref["sigma"]) <= 1e-9 * abs(ref["sigma"])
     assert abs(float(e.grad) - ref["eps"]) <= 1e-9 * abs(ref["eps"])
+
+
+def fast_appendix_torch(g, y, F, sigma, taps, eps_add, eps_mul):
+    """Fast FLR with the Appendix's regularised normalised solve, through the un-normalised
+    form it reduces to: per block a = (Wh + eps_add diag(Wh))^-1 D with
+    Wh = W + eps_mul (m m^T + diag(m^2)) + eps_add I (W the centred guide covariance of the
+    blurred window means, m the absolute guide means, D the centred guide-radiance
+    covariance), b = mean(y) - a^T m; the oracle follows the printed steps (normalise by the
+    standard deviations, solve with eps_add added, un-normalise)."""
+    x = torch.from_numpy(np.asarray(g, np.float64))
+    yy = torch.from_numpy(np.asarray(y, np.float64))
+    q, Hi, Wi = x.shape
+    Hb, Wb = -(-Hi // F), -(-Wi // F)
+    xa = torch.cat([torch.ones((1, Hi, Wi), dtype=torch.float64), x])
+
+    def blocks(p):
+        pp = torch.nn.functional.pad(p, (0, Wb * F - Wi, 0, Hb * F - Hi))
+        return pp.reshape(p.shape[0], Hb, F, Wb, F).sum(dim=(2, 4))
+
+    d = torch.arange(-taps, taps + 1, dtype=torch.float64)
+    w = torch.exp(-d * d / (2.0 * sigma * sigma))
+
+    def blur(p):
+        c = p.shape[0]
+        p = torch.nn.functional.conv2d(p[None], w.reshape(1, 1, 1, -1).repeat(c, 1, 1, 1), padding=(0, taps), groups=c)
+        return torch.nn.functional.conv2d(p, w.reshape(1, 1, -1, 1).repeat(c, 1, 1, 1), padding=(taps, 0), groups=c)[0]
+
+    S = blur(blocks(torch.einsum("ihw,jhw->ijhw", xa, xa).reshape(-1, Hi, Wi))).reshape(q + 1, q + 1, Hb, Wb)
+    T = blur(blocks(torch.einsum("ihw,jhw->ijhw", xa, yy).reshape(-1, Hi, Wi))).reshape(q + 1, 3, Hb, Wb)
+    n = S[0, 0]
+    m = (S[0, 1:] / n).permute(1, 2, 0)                     # [Hb, Wb, q] absolute guide means
+    my = (T[0] / n).permute(1, 2, 0)                        # [Hb, Wb, 3]
+    Wc = (S[1:, 1:] / n).permute(2, 3, 0, 1) - m[..., :, None] * m[..., None, :]
+    D = (T[1:] / n).permute(2, 3, 0, 1) - m[..., :, None] * my[..., None, :]
+    eye = torch.eye(q, dtype=torch.float64)
+    Wh = Wc + eps_mul * (m[..., :, None] * m[..., None, :] + torch.diag_embed(m * m)) + eps_add * eye
+    M = Wh + eps_add * torch.diag_embed(torch.diagonal(Wh, dim1=-2, dim2=-1))
+    a = torch.linalg.solve(M, D)                            # [Hb, Wb, q, 3]
+    b = my - torch.einsum("hwic,hwi->hwc", a, m)
+    A = torch.cat([b[..., None, :], a], dim=-2)             # [Hb, Wb, q + 1, 3], bias first
+    P = F
+
+    def axis(nout, nb):
+        u = ((torch.arange(nout, dtype=torch.float64) + 0.5) / P - 0.5).clamp(0, nb - 1)
+        j0 = torch.floor(u).long().clamp(max=max(nb - 2, 0))
+        return j0, (j0 + 1).clamp(max=nb - 1), u - j0
+    i0, i1, fy = axis(Hi, Hb)
+    j0, j1, fx = axis(Wi, Wb)
+    fy, fx = fy[:, None, None, None], fx[None, :, None, None]
+    Ai = (1 - fy) * ((1 - fx) * A[i0][:, j0] + fx * A[i0][:, j1]) + fy * ((1 - fx) * A[i1][:, j0] + fx * A[i1][:, j1])
+    return torch.einsum("ihw,hwic->chw", xa, Ai).numpy()
+
+
+@pytest.mark.parametrize("eps_add,eps_mul", [(1e-4, 0.0), (1e-5, 0.2), (1e-3, 1.0)])
+def test_fast_appendix_oracle_matches_its_unnormalised_form(eps_add, eps_mul):
+    g, y = synth.render(10, 48, 64)
+    ref = oracle.flr_fast(g, y, factor=4, sigma_blocks=1.25, taps=2, appendix=(eps_add, eps_mul))
+    got = fast_appendix_torch(g, y, 4, 1.25, 2, eps_add, eps_mul)
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.sqrt(np.mean(ref ** 2))
