@@ -463,6 +463,22 @@ def flnr_inference_row(weights, dev_frames, torch, dev, timed, rows):
                                   "measured dense bf16 peak"}
     f.close()
     net.close()
+    # the network's backward pass alone at the training batch shape (16 x 128^2 crops): its
+    # activation gradients, input- and weight-gradient convolutions and their reductions
+    tb = flnr.FLNR(16 * 128 * 128, weights)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    xb = torch.rand((16, 11, 128, 128), device=dev, generator=gen)
+    gb = torch.randn((16, tb.outputs, 128, 128), device=dev, generator=gen) * 1e-3
+    tb.forward(xb)
+
+    def bwd(i):
+        tb.zero_grads(xb)
+        tb.backward(gb)
+    rows["flnr_backward_16x128"] = {"ms": round(timed(bwd, 20), 4),
+                                    "what": "FLNR backward pass (tcgen05 input- and weight-gradient convolutions, "
+                                            "fixed-order reductions) on a 16 x 128x128 batch, without FLR"}
+    tb.close()
     return rows
 
 
